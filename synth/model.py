@@ -1,0 +1,164 @@
+"""Seeded REANN parameter sets in the flat FP32 layout read by both sides.
+
+The paper trains its networks on DFT data (Sec. 4.1); those weights are not
+available, so seeded draws stand in for them.  The parameter set covers what
+Eqs. 1-2 and the output network (Sec. 2.1) need:
+
+* ``c0[e][m]`` -- per-element initial orbital coefficients (layer 0), N(0, 1);
+* ``W[t][l][m][k]`` -- per-layer contraction of the ``N_phi`` primitive
+  Gaussians of angular momentum ``l`` into ``N_orb`` orbitals, Xavier-normal;
+* per layer ``t`` and element ``e`` an atomic network
+  ``F -> H1 -> H2 -> out`` (SiLU between layers, zero biases, Xavier-normal
+  weights), ``out = N_phi`` for the coefficient networks ``t < T-1`` (Eq. 2) and
+  ``out = 1`` for the energy network ``t = T-1``.
+
+Flat order (all float32, row-major, ``x @ W`` convention so ``W1`` is
+``[F][H1]``)::
+
+    c0        [n_elem][n_phi]
+    W         [T][L+1][n_phi][n_orb]
+    for t in 0..T-1, for e in 0..n_elem-1:
+        W1 [F][H1], b1 [H1], W2 [H1][H2], b2 [H2], W3 [H2][out_t], b3 [out_t]
+
+with ``F = (L+1) * n_orb`` features ordered ``f = l * n_orb + k``.
+
+Two fixed scale factors are folded into the draws (trained models absorb
+them; random ones need them so that values stay O(1)):
+
+* every ``W1`` row of angular momentum ``l`` of layer ``t`` and element ``e``
+  is multiplied by ``FEATURE_SCALE[t][e][l]`` so that the network inputs are
+  O(1) in every layer (Eq. 1 squares the coefficients, so without it the
+  features grow or decay geometrically with ``t``);
+* every energy-network ``W3`` is multiplied by ``ENERGY_SCALE`` so that forces
+  are O(1) eV/A.
+
+No REANN arithmetic happens here: the module only draws and lays out numbers.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# Input scale folded into the W1 rows of angular momentum l, per layer t and
+# element e: FEATURE_SCALE[t][e][l].  Chosen once so that every layer's
+# network inputs are O(1) on the 64-molecule water box (H, O) and the 4,000-atom
+# fcc Cu box (Cu) with the default seed (reciprocal RMS of each feature block,
+# two significant digits; the Cu l=1 block, suppressed by the fcc symmetry, takes
+# the l=0 value instead of being amplified).  Layers beyond the table reuse its
+# last row.
+FEATURE_SCALE = (
+    ((0.36, 1.3, 0.014), (0.32, 2.7, 0.014), (0.8, 0.8, 0.026)),
+    ((7.8, 13.0, 1.3), (5.7, 11.0, 1.6), (4.4, 4.4, 0.11)),
+    ((3.9, 1.9, 0.34), (3.4, 3.0, 0.4), (14.0, 14.0, 0.58)),
+    ((1.4, 1.4, 0.14), (1.5, 2.4, 0.2), (3.0, 3.0, 0.42)),
+    ((1.0, 1.2, 0.18), (1.1, 1.4, 0.21), (2.2, 2.2, 0.14)),
+)
+# Multiplier on the energy network's output weights (eV): gives force RMS of
+# about 1 eV/A on the water box and 0.1 eV/A on the Cu box at T = 3.
+ENERGY_SCALE = 0.2
+
+
+@dataclasses.dataclass
+class ModelSpec:
+    n_elem: int
+    T: int
+    n_phi: int
+    l_max: int
+    n_orb: int
+    h1: int
+    h2: int
+    r_c: float
+    alpha: float
+    params: np.ndarray  # float32 flat
+
+    @property
+    def n_feat(self) -> int:
+        return (self.l_max + 1) * self.n_orb
+
+    def out_dim(self, t: int) -> int:
+        return 1 if t == self.T - 1 else self.n_phi
+
+
+def param_layout(n_elem: int, T: int, n_phi: int, l_max: int, n_orb: int, h1: int, h2: int) -> dict:
+    """Offsets (in floats) of every block of the flat parameter vector."""
+    f = (l_max + 1) * n_orb
+    off = 0
+    lay: dict = {"c0": (off, (n_elem, n_phi))}
+    off += n_elem * n_phi
+    lay["W"] = (off, (T, l_max + 1, n_phi, n_orb))
+    off += T * (l_max + 1) * n_phi * n_orb
+    for t in range(T):
+        out = 1 if t == T - 1 else n_phi
+        for e in range(n_elem):
+            for name, shape in (
+                ("W1", (f, h1)),
+                ("b1", (h1,)),
+                ("W2", (h1, h2)),
+                ("b2", (h2,)),
+                ("W3", (h2, out)),
+                ("b3", (out,)),
+            ):
+                lay[(t, e, name)] = (off, shape)
+                off += int(np.prod(shape))
+    lay["total"] = off
+    return lay
+
+
+def _xavier(rng: np.random.Generator, fan_in: int, fan_out: int, gain: float = 1.0) -> np.ndarray:
+    std = gain * math.sqrt(2.0 / (fan_in + fan_out))
+    return rng.normal(0.0, std, size=(fan_in, fan_out))
+
+
+def make_model(
+    T: int = 3,
+    seed: int = 1234,
+    n_elem: int = 3,
+    n_phi: int = 8,
+    l_max: int = 2,
+    n_orb: int = 16,
+    h1: int = 64,
+    h2: int = 64,
+    r_c: float = 5.0,
+    alpha: float = 0.5,
+    feature_scale: tuple | None = None,
+    energy_scale: float | None = None,
+) -> ModelSpec:
+    """Draw a seeded parameter set (see module docstring for the layout)."""
+    if T < 1:
+        raise ValueError("T must be >= 1")
+    fs = FEATURE_SCALE if feature_scale is None else feature_scale
+    if any(len(row) < l_max + 1 for per_t in fs for row in per_t):
+        raise ValueError("feature_scale needs one entry per l")
+    es = ENERGY_SCALE if energy_scale is None else energy_scale
+    lay = param_layout(n_elem, T, n_phi, l_max, n_orb, h1, h2)
+
+    def stream(*key):
+        # an independent substream per block, so layer t's draws do not depend on T
+        return np.random.Generator(np.random.PCG64([seed, *key]))
+
+    p = np.zeros(lay["total"], dtype=np.float64)
+
+    def put(key, arr):
+        o, shape = lay[key]
+        p[o : o + int(np.prod(shape))] = np.asarray(arr, dtype=np.float64).reshape(-1)
+
+    put("c0", stream(0).normal(0.0, 1.0, size=(n_elem, n_phi)))
+    put("W", np.stack([np.stack([_xavier(stream(1, t, l), n_phi, n_orb) for l in range(l_max + 1)]) for t in range(T)]))
+    f = (l_max + 1) * n_orb
+    for t in range(T):
+        out = 1 if t == T - 1 else n_phi
+        for e in range(n_elem):
+            row = np.asarray(fs[min(t, len(fs) - 1)][min(e, len(fs[0]) - 1)][: l_max + 1], dtype=np.float64)
+            put((t, e, "W1"), _xavier(stream(2, t, e), f, h1) * np.repeat(row, n_orb)[:, None])
+            put((t, e, "b1"), np.zeros(h1))
+            put((t, e, "W2"), _xavier(stream(3, t, e), h1, h2))
+            put((t, e, "b2"), np.zeros(h2))
+            w3 = _xavier(stream(4 if t < T - 1 else 5, t, e), h2, out)
+            if t == T - 1:
+                w3 = w3 * es
+            put((t, e, "W3"), w3)
+            put((t, e, "b3"), np.zeros(out))
+    return ModelSpec(n_elem, T, n_phi, l_max, n_orb, h1, h2, float(r_c), float(alpha), p.astype(np.float32))
