@@ -1,0 +1,185 @@
+/*
+ * reann.h -- C ABI of the GB300 (sm_103a) REANN energy/force library.
+ *
+ * What is computed (arXiv 2505.06711, "Efficient Parallelization of Message
+ * Passing Neural Networks"):
+ *   * Sec. 2.1, Eq. 1: per message-passing layer t, the embedded-atom density
+ *     of every atom i, rho^t_{i,l,k} = sum_{lx+ly+lz=l} l!/(lx! ly! lz!)
+ *     [ sum_{j != i, d_ij < r_c} sum_m c^t_{j,m} phi_m(d_ij) x^lx y^ly z^lz W^t_{l,m,k} ]^2
+ *     with phi_m(d) = exp(-alpha (d - mu_m)^2) f_c(d), mu_m = m r_c/(N_phi - 1),
+ *     f_c(d) = (cos(pi d / r_c)/2 + 1/2)^2 and (x, y, z) = r_j - r_i in A;
+ *   * Sec. 2.1, Eq. 2: c^{t+1}_i = M^t_{Z_i}(rho^t_i) for t < T-1 (per-element
+ *     networks F -> 64 -> 64 -> N_phi, SiLU), and after T layers the atomic
+ *     energies eps_i = M^{T-1}_{Z_i}(rho^{T-1}_i), E = sum_i eps_i;
+ *   * Sec. 2.2, Eqs. 3-5: forces F = -dE/dr by one reverse pass through all
+ *     layers (vector-Jacobian products, never a full Jacobian);
+ *   * Sec. 2.2: ONE neighbour list of radius r_c (+ skin) serves every layer,
+ *     so the cost is linear in T, and ghost (periodic-image) atoms receive
+ *     their owners' coefficients by an index gather once per layer instead of
+ *     being recomputed (the paper's per-layer ghost-atom message refresh, Fig. 4a).
+ *
+ * Model shape fixed by this build: N_phi = 8 Gaussians, L = 2 (10 Cartesian
+ * terms), N_orb = 16 orbitals (F = 48 features), hidden widths 64 and 64,
+ * up to 8 elements, alpha r_c^2 <= 80.  Other shapes are rejected with REANN_E_ARG.
+ *
+ * Units: A, eV, amu, fs.  Cells are 3x3 row-major, rows = lattice vectors.
+ *
+ * Conventions for every entry point:
+ *   * Pointers marked "dev" are CUDA device pointers (e.g. torch tensors'
+ *     data_ptr()); "host" pointers are ordinary host memory.  The caller owns
+ *     every pointer it passes; the library never frees caller memory and keeps
+ *     no pointer to it after the call returns (it copies what it keeps).
+ *   * Handles (reann_model, reann_ctx, reann_nlist) are owned by the library
+ *     and released with the matching *_free.
+ *   * Work is enqueued on the context's CUDA stream and is asynchronous unless
+ *     stated otherwise; results in "dev" outputs are valid once that stream
+ *     has reached the call's end.
+ *   * Return value 0 (REANN_OK) or a negative REANN_E_* code; the message of
+ *     the last failure on a context is returned by reann_last_error().
+ *   * Atom order in and out is the caller's; any internal reordering is
+ *     invisible.
+ */
+#ifndef REANN_H
+#define REANN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define REANN_OK 0
+#define REANN_E_ARG (-1)      /* invalid argument or unsupported model shape  */
+#define REANN_E_MISMATCH (-2) /* r_c or T differs from the model's            */
+#define REANN_E_NOMEM (-3)    /* device or host allocation failed             */
+#define REANN_E_GEOM (-4)     /* non-finite position, coincident atoms, singular cell */
+#define REANN_E_CUDA (-5)     /* a CUDA runtime call failed                   */
+#define REANN_E_TIMEOUT (-6)  /* a bounded device wait ran out                */
+#define REANN_E_CAPACITY (-7) /* a neighbour/ghost capacity was exceeded (rebuild) */
+
+#define REANN_MLP_FP32 0 /* atomic networks in FP32 SIMT arithmetic                    */
+#define REANN_MLP_BF16 1 /* atomic networks on tcgen05 tensor cores, BF16 in, FP32 acc */
+
+typedef struct reann_model reann_model;
+typedef struct reann_ctx reann_ctx;
+typedef struct reann_nlist reann_nlist;
+
+/* ---------------------------------------------------------------- model --- */
+
+/*
+ * Create a model from hyper-parameters and a flat FP32 parameter vector
+ * (host).  Layout (row-major, "x @ W" convention, F = (l_max+1) n_orb,
+ * features ordered f = l n_orb + k):
+ *   c0 [n_elem][n_phi]                      initial coefficients c^0 (Sec. 2.1)
+ *   W  [T][l_max+1][n_phi][n_orb]           per-layer orbital contraction (Eq. 1)
+ *   for t in 0..T-1, for e in 0..n_elem-1:  atomic network M^t_e (Eq. 2)
+ *     W1 [F][h1], b1 [h1], W2 [h1][h2], b2 [h2], W3 [h2][o_t], b3 [o_t]
+ *     with o_t = n_phi for t < T-1 and o_t = 1 (energy) for t = T-1.
+ * n_params must equal the length implied by the shape.  Host only (no CUDA
+ * call); the parameters are copied.  Errors: REANN_E_ARG.
+ */
+int reann_model_create(int n_elem, int T, int n_phi, int l_max, int n_orb, int h1, int h2, double r_c, double alpha,
+                       const float* params, int64_t n_params, reann_model** out);
+void reann_model_free(reann_model* model);
+
+/* -------------------------------------------------------------- context --- */
+
+/*
+ * Create an execution context on the current CUDA device: uploads the model
+ * (FP32 and BF16 copies) and binds `cuda_stream` (a cudaStream_t; NULL = the
+ * legacy default stream).  The model may be freed after this call.
+ * Errors: REANN_E_ARG, REANN_E_NOMEM, REANN_E_CUDA.
+ */
+int reann_ctx_create(const reann_model* model, void* cuda_stream, reann_ctx** out);
+void reann_ctx_free(reann_ctx* ctx);
+
+/* Precision of the atomic networks (REANN_MLP_FP32 default, REANN_MLP_BF16). */
+int reann_ctx_set_mlp_precision(reann_ctx* ctx, int precision);
+
+/* Message of the last failure on `ctx` (static storage of the context). */
+const char* reann_last_error(const reann_ctx* ctx);
+
+/*
+ * Wait for the context's stream and report device-side error flags raised
+ * since the last check (coincident atoms in an evaluation -> REANN_E_GEOM,
+ * neighbour/ghost capacity exceeded during a device-side rebuild ->
+ * REANN_E_CAPACITY).  Synchronous.
+ */
+int reann_ctx_check(reann_ctx* ctx);
+
+/* ------------------------------------------------------- neighbour list --- */
+
+/*
+ * Build the periodic neighbour list of radius r_c + skin (Sec. 2.2: the single
+ * r_c list re-used by every layer; the skin lets it survive atom motion of up
+ * to skin/2, Sec. 1) and the ghost map (every periodic image within r_c + skin
+ * of the cell becomes a ghost slot that points at its owner atom).
+ *   n_atoms  number of atoms N >= 1
+ *   pos      dev, N x 3 FP64 Cartesian positions (A), any image
+ *   species  dev, N int32 element indices in [0, n_elem)
+ *   cell     host, 9 FP64, rows = lattice vectors (A); must be non-singular
+ *   r_c      must equal the model's cutoff (else REANN_E_MISMATCH)
+ *   skin     >= 0 (A)
+ * A pair (i, j, n) is listed iff |(x_j - x_i) + n.H| < r_c + skin in FP64
+ * after wrapping positions into the cell, excluding only the zero-shift self
+ * term (periodic self-images are neighbours).  The returned handle also holds
+ * the structure's per-layer device buffers, so it stays resident for repeated
+ * evaluations.  Synchronous (waits for the stream).
+ * Errors: REANN_E_ARG (N < 1, species out of range), REANN_E_MISMATCH,
+ * REANN_E_GEOM (non-finite position, coincident atoms, singular cell),
+ * REANN_E_NOMEM, REANN_E_CUDA.
+ */
+int reann_build_nlist(reann_ctx* ctx, int64_t n_atoms, const double* pos, const int32_t* species, const double* cell,
+                      double r_c, double skin, reann_nlist** out);
+void reann_nlist_free(reann_nlist* nl);
+
+/* Sizes: atoms, ghost slots and listed (i, j, n) entries (host outputs, nullable). */
+int reann_nlist_info(const reann_nlist* nl, int64_t* n_atoms, int64_t* n_ghosts, int64_t* n_pairs);
+
+/*
+ * Copy the list to host arrays as (i, j, n) triples in the caller's atom
+ * order with n relative to the caller's (unwrapped) positions at build time:
+ * r_ij = x_j + n.H - x_i.  Writes min(cap, count) entries; *count = total.
+ * Synchronous.  Errors: REANN_E_ARG.
+ */
+int reann_nlist_export(reann_ctx* ctx, const reann_nlist* nl, int64_t cap, int32_t* i, int32_t* j, int32_t* n,
+                       int64_t* count);
+
+/* ------------------------------------------------------------ evaluation --- */
+
+/*
+ * Energy and forces of the structure of `nl` at positions `pos` (Eqs. 1-5).
+ *   pos          dev, N x 3 FP64 (A); atoms must have moved less than skin/2
+ *                since the list was built (the caller decides when to rebuild)
+ *   T            number of message-passing layers; must equal the model's
+ *   energy       dev, 1 FP64: E = sum_i eps_i (eV), summed in FP64
+ *   forces       dev, N x 3 FP32: F = -dE/dr (eV/A)
+ *   atom_energy  dev, N FP32 per-atom energies eps_i, or NULL
+ * Asynchronous.  Coincident atoms are reported by reann_ctx_check().
+ * Errors: REANN_E_ARG, REANN_E_MISMATCH, REANN_E_CUDA.
+ */
+int reann_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy, float* forces,
+                        float* atom_energy);
+
+/*
+ * Same as reann_energy_forces with HOST buffers: copies pos (host, N x 3
+ * FP64) to the device, rebuilds the neighbour list when any atom moved more
+ * than skin/2 since the last build, evaluates, and copies energy (host, 1
+ * FP64) and forces (host, N x 3 FP32) back.  Synchronous.  Pinned host memory
+ * makes the copies asynchronous DMA; pageable memory works but is slower.
+ */
+int reann_energy_forces_host(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy,
+                             float* forces);
+
+/*
+ * Per-layer intermediates of the last evaluation of `nl`, in caller order
+ * (inspection and testing): rho (dev, N x F FP32) and c (dev, N x N_phi FP32)
+ * of layer `layer` in [0, T).  Either output may be NULL.  Asynchronous.
+ */
+int reann_get_layer(reann_ctx* ctx, const reann_nlist* nl, int layer, float* rho, float* coef);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REANN_H */

@@ -1,0 +1,111 @@
+"""GB300-native REANN energy/force evaluation (arXiv 2505.06711).
+
+The computation lives in the CUDA library ``libreann.so`` (``csrc/``, C ABI in
+``include/reann.h``).  This package holds its ctypes binding
+(:mod:`.binding`, same names as the C entry points) and a small convenience
+layer that keeps device buffers in torch tensors.  PyTorch provides device
+memory and streams only.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from . import binding
+from .binding import ReannError  # noqa: F401
+
+__all__ = ["Potential", "System", "binding", "ReannError"]
+
+
+class Potential:
+    """A model uploaded to one CUDA device with its own execution context."""
+
+    def __init__(self, spec, stream=None, precision: int = binding.REANN_MLP_FP32):
+        import torch
+
+        self.spec = spec
+        self.T = spec.T
+        self.r_c = float(spec.r_c)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._model = binding.reann_model_create(spec)
+        try:
+            self.ctx = binding.reann_ctx_create(self._model, stream)
+        finally:
+            binding.reann_model_free(self._model)
+            self._model = None
+        if precision != binding.REANN_MLP_FP32:
+            binding.reann_ctx_set_mlp_precision(self.ctx, precision)
+
+    def set_precision(self, precision: int) -> None:
+        binding.reann_ctx_set_mlp_precision(self.ctx, precision)
+
+    def system(self, pos, species, cell, skin: float = 1.0) -> "System":
+        return System(self, pos, species, cell, skin)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None) is not None:
+            binding.reann_ctx_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):  # pragma: no cover - best effort
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class System:
+    """One periodic structure with its resident neighbour list and buffers."""
+
+    def __init__(self, pot: Potential, pos, species, cell, skin: float = 1.0):
+        import torch
+
+        self.pot = pot
+        self.cell = np.ascontiguousarray(cell, dtype=np.float64).reshape(3, 3)
+        self.skin = float(skin)
+        self.pos = torch.as_tensor(np.asarray(pos, dtype=np.float64), device=pot.device).contiguous()
+        self.species = torch.as_tensor(np.asarray(species, dtype=np.int32), device=pot.device).contiguous()
+        self.n = int(self.pos.shape[0])
+        self.nl = binding.reann_build_nlist(pot.ctx, self.pos, self.species, self.cell, pot.r_c, self.skin)
+        self.energy = torch.zeros(1, dtype=torch.float64, device=pot.device)
+        self.forces = torch.zeros((self.n, 3), dtype=torch.float32, device=pot.device)
+        self.atom_energy = torch.zeros(self.n, dtype=torch.float32, device=pot.device)
+
+    def rebuild(self) -> None:
+        binding.reann_nlist_free(self.nl)
+        self.nl = binding.reann_build_nlist(self.pot.ctx, self.pos, self.species, self.cell, self.pot.r_c, self.skin)
+
+    def evaluate(self, pos=None, atom_energy: bool = True) -> None:
+        """Enqueue one energy + force evaluation (results in .energy/.forces/.atom_energy)."""
+        p = self.pos if pos is None else pos
+        binding.reann_energy_forces(
+            self.pot.ctx, self.nl, p, self.pot.T, self.energy, self.forces, self.atom_energy if atom_energy else None
+        )
+
+    def layer(self, t: int):
+        import torch
+
+        rho = torch.zeros((self.n, 48), dtype=torch.float32, device=self.pot.device)
+        coef = torch.zeros((self.n, 8), dtype=torch.float32, device=self.pot.device)
+        binding.reann_get_layer(self.pot.ctx, self.nl, t, rho, coef)
+        return rho, coef
+
+    def neighbors(self):
+        return binding.reann_nlist_export(self.pot.ctx, self.nl)
+
+    def info(self):
+        return binding.reann_nlist_info(self.nl)
+
+    def check(self) -> None:
+        binding.reann_ctx_check(self.pot.ctx)
+
+    def close(self) -> None:
+        if getattr(self, "nl", None) is not None:
+            binding.reann_nlist_free(self.nl)
+            self.nl = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

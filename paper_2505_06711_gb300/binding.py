@@ -1,0 +1,215 @@
+"""Thin ctypes binding of the C ABI in ``include/reann.h``.
+
+Functions carry the C names and only marshal arguments (torch CUDA tensors ->
+device pointers, numpy arrays -> host pointers); every step of the
+computation runs in ``libreann.so``.  There is no CPU fallback: if the library
+is missing, :func:`lib` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+REANN_OK = 0
+REANN_E_ARG = -1
+REANN_E_MISMATCH = -2
+REANN_E_NOMEM = -3
+REANN_E_GEOM = -4
+REANN_E_CUDA = -5
+REANN_E_TIMEOUT = -6
+REANN_E_CAPACITY = -7
+REANN_MLP_FP32 = 0
+REANN_MLP_BF16 = 1
+
+_NAMES = {
+    REANN_E_ARG: "REANN_E_ARG",
+    REANN_E_MISMATCH: "REANN_E_MISMATCH",
+    REANN_E_NOMEM: "REANN_E_NOMEM",
+    REANN_E_GEOM: "REANN_E_GEOM",
+    REANN_E_CUDA: "REANN_E_CUDA",
+    REANN_E_TIMEOUT: "REANN_E_TIMEOUT",
+    REANN_E_CAPACITY: "REANN_E_CAPACITY",
+}
+
+
+class ReannError(RuntimeError):
+    def __init__(self, code: int, msg: str = ""):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_vp, _i64, _i32, _int, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int, ctypes.c_double
+
+_SIGS = {
+    "reann_model_create": ([_int] * 7 + [_dbl, _dbl, _vp, _i64, ctypes.POINTER(_vp)], _int),
+    "reann_model_free": ([_vp], None),
+    "reann_ctx_create": ([_vp, _vp, ctypes.POINTER(_vp)], _int),
+    "reann_ctx_free": ([_vp], None),
+    "reann_ctx_set_mlp_precision": ([_vp, _int], _int),
+    "reann_last_error": ([_vp], ctypes.c_char_p),
+    "reann_ctx_check": ([_vp], _int),
+    "reann_build_nlist": ([_vp, _i64, _vp, _vp, _vp, _dbl, _dbl, ctypes.POINTER(_vp)], _int),
+    "reann_nlist_free": ([_vp], None),
+    "reann_nlist_info": ([_vp, _vp, _vp, _vp], _int),
+    "reann_nlist_export": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], _int),
+    "reann_energy_forces": ([_vp, _vp, _vp, _int, _vp, _vp, _vp], _int),
+    "reann_energy_forces_host": ([_vp, _vp, _vp, _int, _vp, _vp], _int),
+    "reann_get_layer": ([_vp, _vp, _int, _vp, _vp], _int),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load ``libreann.so``; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built ({path}); run __graft_entry__.build()")
+        handle = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(handle, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = handle
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev(t, dtype, shape=None, name="tensor"):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+def _check(rc, ctx=None):
+    if rc != REANN_OK:
+        msg = lib().reann_last_error(ctx).decode() if ctx else ""
+        raise ReannError(rc, msg)
+
+
+# ------------------------------------------------------------------ model --
+def reann_model_create(spec) -> ctypes.c_void_p:
+    """``spec`` is a :class:`synth.model.ModelSpec` (or any object with its fields)."""
+    params = np.ascontiguousarray(spec.params, dtype=np.float32)
+    out = _vp()
+    rc = lib().reann_model_create(
+        spec.n_elem, spec.T, spec.n_phi, spec.l_max, spec.n_orb, spec.h1, spec.h2,
+        float(spec.r_c), float(spec.alpha), _ptr(params), params.size, ctypes.byref(out),
+    )
+    _check(rc)
+    return out
+
+
+def reann_model_free(model) -> None:
+    lib().reann_model_free(model)
+
+
+# ---------------------------------------------------------------- context --
+def reann_ctx_create(model, stream=None) -> ctypes.c_void_p:
+    """``stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None (current torch stream)."""
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    out = _vp()
+    _check(lib().reann_ctx_create(model, _vp(handle), ctypes.byref(out)))
+    return out
+
+
+def reann_ctx_free(ctx) -> None:
+    lib().reann_ctx_free(ctx)
+
+
+def reann_ctx_set_mlp_precision(ctx, precision: int) -> None:
+    _check(lib().reann_ctx_set_mlp_precision(ctx, int(precision)), ctx)
+
+
+def reann_last_error(ctx) -> str:
+    return lib().reann_last_error(ctx).decode()
+
+
+def reann_ctx_check(ctx) -> None:
+    _check(lib().reann_ctx_check(ctx), ctx)
+
+
+# ---------------------------------------------------------- neighbour list --
+def reann_build_nlist(ctx, pos, species, cell, r_c: float, skin: float):
+    import torch
+
+    n = pos.shape[0]
+    _dev(pos, torch.float64, (n, 3), "pos")
+    _dev(species, torch.int32, (n,), "species")
+    c = np.ascontiguousarray(cell, dtype=np.float64).reshape(9)
+    out = _vp()
+    _check(lib().reann_build_nlist(ctx, n, _ptr(pos), _ptr(species), _ptr(c), float(r_c), float(skin), ctypes.byref(out)), ctx)
+    return out
+
+
+def reann_nlist_free(nl) -> None:
+    lib().reann_nlist_free(nl)
+
+
+def reann_nlist_info(nl) -> tuple[int, int, int]:
+    a, g, p = (np.zeros(1, np.int64) for _ in range(3))
+    _check(lib().reann_nlist_info(nl, _ptr(a), _ptr(g), _ptr(p)))
+    return int(a[0]), int(g[0]), int(p[0])
+
+
+def reann_nlist_export(ctx, nl):
+    """(i, j, shift) of every listed pair, caller order, caller-relative shifts (host arrays)."""
+    cnt = np.zeros(1, np.int64)
+    _check(lib().reann_nlist_export(ctx, nl, 0, None, None, None, _ptr(cnt)), ctx)
+    k = int(cnt[0])
+    i = np.empty(max(k, 1), np.int32)
+    j = np.empty(max(k, 1), np.int32)
+    s = np.empty((max(k, 1), 3), np.int32)
+    _check(lib().reann_nlist_export(ctx, nl, k, _ptr(i), _ptr(j), _ptr(s), _ptr(cnt)), ctx)
+    return i[:k], j[:k], s[:k]
+
+
+# -------------------------------------------------------------- evaluation --
+def reann_energy_forces(ctx, nl, pos, T: int, energy, forces, atom_energy=None) -> None:
+    import torch
+
+    n = pos.shape[0]
+    _dev(pos, torch.float64, (n, 3), "pos")
+    _dev(energy, torch.float64, (1,), "energy")
+    _dev(forces, torch.float32, (n, 3), "forces")
+    if atom_energy is not None:
+        _dev(atom_energy, torch.float32, (n,), "atom_energy")
+    _check(lib().reann_energy_forces(ctx, nl, _ptr(pos), int(T), _ptr(energy), _ptr(forces), _ptr(atom_energy)), ctx)
+
+
+def reann_energy_forces_host(ctx, nl, pos: np.ndarray, T: int, energy: np.ndarray, forces: np.ndarray) -> None:
+    for a, dt in ((pos, np.float64), (energy, np.float64), (forces, np.float32)):
+        if not isinstance(a, np.ndarray) or a.dtype != dt or not a.flags.c_contiguous:
+            raise TypeError("host buffers must be contiguous numpy arrays (pos f64, energy f64, forces f32)")
+    _check(lib().reann_energy_forces_host(ctx, nl, _ptr(pos), int(T), _ptr(energy), _ptr(forces)), ctx)
+
+
+def reann_get_layer(ctx, nl, layer: int, rho=None, coef=None) -> None:
+    _check(lib().reann_get_layer(ctx, nl, int(layer), _ptr(rho), _ptr(coef)), ctx)

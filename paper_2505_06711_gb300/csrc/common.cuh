@@ -1,0 +1,186 @@
+// Internal declarations shared by the library's translation units.
+// Fixed model shape (Sec. 2.1): N_phi = 8 primitive Gaussians, L = 2
+// (10 Cartesian terms x^lx y^ly z^lz), N_orb = 16 orbitals, F = 48 features,
+// atomic networks 48 -> 64 -> 64 -> {8 | 1}.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/reann.h"
+
+namespace reann {
+
+constexpr int NPHI = 8;
+constexpr int NANG = 10;  // angular terms for L = 2
+constexpr int LMAX = 2;
+constexpr int NORB = 16;
+constexpr int NFEAT = (LMAX + 1) * NORB;  // 48
+constexpr int NB = NANG * NPHI;           // 80 per-atom density partials b_{a,m}
+constexpr int H1 = 64;
+constexpr int H2 = 64;
+constexpr int MAX_ELEM = 8;
+constexpr int MLP_TILE = 64;  // rows per FP32 network tile
+
+// Internal angular order: 1, x, y, z, xx, yy, zz, xy, xz, yz.
+// l(a), multinomial weight l!/(lx! ly! lz!) and parity (-1)^l.
+
+// Device-side error flags (ctx->d_flags)
+enum Flag { FLAG_GEOM = 0, FLAG_NBR_OVERFLOW = 1, FLAG_GHOST_OVERFLOW = 2, FLAG_MAXNBR = 3, FLAG_SPECIES = 4, NFLAGS = 8 };
+
+// Constants of the radial basis, passed by value to kernels.  Constants that
+// enter every edge identically are split into a float pair (hi + lo) so that
+// their FP32 rounding does not bias all atoms the same way (in a crystal every
+// atom sees the same neighbour shells, so a rounded constant would shift every
+// atomic energy by the same amount).
+struct Radial {
+    float rc, rc2;
+    float alpha_hi, alpha_lo;  // alpha
+    float tad_hi, tad_lo;      // 2 alpha Delta, Delta = r_c / (N_phi - 1)
+    float mu_hi[NPHI], mu_lo[NPHI];      // Gaussian centres m Delta
+    float kap_hi[NPHI], kap_lo[NPHI];    // exp(-alpha Delta^2 (2m+1)) for the Gaussian recurrence
+};
+
+// Cell geometry for the neighbour build (FP64) and ghost refresh.
+struct CellGeom {
+    double h[9];     // rows = lattice vectors
+    double hinv[9];  // frac = x . hinv
+    double reach[3]; // r_cut / width_k + margin (fractional units)
+    int nmax[3];     // largest |image shift| per axis
+    int nb[3];       // owned bins per axis
+    int pad[3];      // extra bins per side for ghosts
+    int nbx[3];      // nb + 2 pad
+    int sw[3];       // stencil half-width in bins per axis
+    double rcut2;    // (r_c + skin)^2
+    float rcut2_f;
+    float margin;    // FP32 pre-test band around rcut2 (A^2) decided in FP64
+};
+
+struct Model {
+    int n_elem, T;
+    double r_c, alpha;
+    std::vector<float> params;  // host copy, flat layout of reann.h
+};
+
+// Per-layer/element network weights on the device.
+struct NetDev {
+    const float* W1;  // [48][64]
+    const float* b1;  // [64]
+    const float* W2;  // [64][64]
+    const float* b2;  // [64]
+    const float* W3;  // [64][out]
+    const float* b3;  // [out]
+    const float* W1t; // [64][48]
+    const float* W2t; // [64][64]
+    const float* W3t; // [out][64]
+};
+
+struct NetTable {
+    NetDev net[8][MAX_ELEM];  // [t][e]
+};
+
+struct Tile {
+    int elem, row0, nrows, pad;
+};
+
+}  // namespace reann
+
+struct reann_model {
+    reann::Model m;
+};
+
+struct reann_nlist {
+    int64_t n = 0, g = 0, g_cap = 0;  // atoms, ghosts, ghost capacity
+    int stride = 0;                   // neighbour row capacity
+    int n_elem = 0, T = 0;
+    double r_c = 0, skin = 0;
+    reann::CellGeom geom{};
+    int elem_start[reann::MAX_ELEM + 1] = {0};
+    std::vector<reann::Tile> tiles_h;
+    // device arrays
+    int32_t* perm = nullptr;       // internal -> caller
+    int32_t* species = nullptr;    // internal order
+    int32_t* wrapm = nullptr;      // N x 3 wrap shifts m (x_w = x - m.H), internal order
+    int32_t* g_owner = nullptr;    // g_cap
+    int32_t* g_shift = nullptr;    // g_cap, packed (n0+128) | (n1+128)<<8 | (n2+128)<<16
+    int32_t* nbr = nullptr;        // N x stride ext slots
+    int32_t* nbr_cnt = nullptr;    // N
+    int32_t* live = nullptr;       // N x stride, live (d < r_c) entries first
+    int32_t* live_cnt = nullptr;   // N
+    reann::Tile* tiles = nullptr;  // MLP tiles
+    double* pos_ref = nullptr;     // N x 3 FP64 caller positions at build (caller order)
+    // per-evaluation state (resident)
+    float4* pos_hi = nullptr;      // N + g_cap
+    float4* pos_lo = nullptr;      // N + g_cap
+    float* coef = nullptr;         // T x (N + g_cap) x 8
+    float* rho = nullptr;          // T x N x 48
+    float* bck = nullptr;          // T x N x 80
+    float* eps = nullptr;          // N
+    float* rhobar = nullptr;       // N x 48
+    float* bbar = nullptr;         // (N + g_cap) x 80
+    float* cbar = nullptr;         // N x 8
+    float* grad = nullptr;         // N x 3
+    double* partial = nullptr;     // energy partial sums
+    int n_partial = 0;
+    std::vector<void*> allocs;
+};
+
+struct reann_ctx {
+    reann::Model model;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int precision = REANN_MLP_FP32;
+    reann::Radial radial{};
+    float* d_params = nullptr;     // model parameters (FP32, flat + transposed copies)
+    reann::NetTable nets{};
+    const float* d_c0 = nullptr;   // [n_elem][8]
+    const float* d_W = nullptr;    // [T][3][8][16]
+    void* d_bf16 = nullptr;        // BF16 weight images for the tensor-core networks
+    int* d_flags = nullptr;        // reann::NFLAGS ints
+    int* h_flags = nullptr;        // pinned mirror
+    std::string err;
+    int num_sms = 0;
+};
+
+namespace reann {
+
+int set_error(reann_ctx* ctx, int code, const std::string& msg);
+
+#define REANN_CUDA_TRY(ctx, expr)                                                                   \
+    do {                                                                                            \
+        cudaError_t _e = (expr);                                                                    \
+        if (_e != cudaSuccess)                                                                      \
+            return ::reann::set_error((ctx), REANN_E_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+// ---- launchers (defined in the .cu files) ----
+// neighbour list (nlist.cu)
+int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const int32_t* species);
+cudaError_t launch_refresh_positions(cudaStream_t s, const reann_nlist* nl, const double* pos);
+cudaError_t launch_live_edges(cudaStream_t s, const reann_nlist* nl, float rc2, int* flags);
+int export_nlist(reann_ctx* ctx, const reann_nlist* nl, int64_t cap, int32_t* i, int32_t* j, int32_t* n, int64_t* count);
+
+// density (density.cu)
+cudaError_t launch_init_coef(cudaStream_t s, const reann_nlist* nl, const float* c0);
+cudaError_t launch_gather_ghost_rows(cudaStream_t s, const reann_nlist* nl, float* base, int width);
+cudaError_t launch_density_fwd(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* W, const float* coef,
+                               float* rho, float* bck);
+cudaError_t launch_bbar(cudaStream_t s, const reann_nlist* nl, const float* W, const float* bck, const float* rhobar,
+                        float* bbar);
+cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* coef,
+                               const float* bbar, float* cbar, float* grad, bool want_cbar, int* flags);
+cudaError_t launch_energy_sum(cudaStream_t s, const reann_nlist* nl, double* energy);
+cudaError_t launch_scatter_outputs(cudaStream_t s, const reann_nlist* nl, float* forces, float* atom_energy);
+cudaError_t launch_unpermute_rows(cudaStream_t s, const reann_nlist* nl, const float* src, int src_stride, float* dst,
+                                  int width);
+
+// atomic networks, FP32 SIMT (mlp_fp32.cu)
+cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
+                               const float* rho, float* out, int out_stride);
+cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
+                               const float* rho, const float* ybar, float* rhobar);
+
+}  // namespace reann

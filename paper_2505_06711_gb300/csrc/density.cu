@@ -1,0 +1,529 @@
+// Edge kernels of the REANN message-passing layer and its adjoint.
+//
+// Forward (Sec. 2.1, Eq. 1), per owned atom i and layer t:
+//   b_{i,a,m} = sum_{j live} c^t_{j,m} phi_m(d_ij) A_a(r_ij)
+//   g_{i,a,k} = sum_m b_{i,a,m} W^t_{l(a),m,k}
+//   rho_{i,l,k} = sum_{a in l} w_a g_{i,a,k}^2
+// Reverse (Sec. 2.2, Eqs. 3-5), per layer, given rhobar:
+//   gbar = 2 w_a g rhobar,  bbar_{a,m} = sum_k gbar_{a,k} W_{l(a),m,k}
+//   and, gathering over atom k's own (symmetric, full) list with r = r_j - r_k:
+//     dE/dr_k = -sum_j sum_{a,m} [bbar_{k,a,m} c_{j,m} + (-1)^l bbar_{j,a,m} c_{k,m}] grad_r(phi_m A_a)(r)
+//     cbar_{k,m} = sum_j phi_m(d) sum_a (-1)^l bbar_{j,a,m} A_a(r)
+//   (the second term of each line is the reverse edge j -> k, written with
+//   A_a(-r) = (-1)^l A_a(r); ghost slots j carry their owner's bbar, which is
+//   the paper's ghost-gradient exchange as a vector-Jacobian product, Sec. 2.2).
+// No atomics: every output row is written by the one quad that owns it.
+//
+// Layout: a quad of 4 lanes per centre atom (8 atoms per warp).  Each lane
+// walks every 4th live neighbour, gathers the neighbour's hi/lo FP32 position
+// (32 B) and coefficients (32 B) and accumulates the 80 products in
+// registers; a butterfly reduce-scatter leaves 20 of the 80 b values in each
+// lane, which then contracts its 4 orbitals from shared memory.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace reann {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kWarps = 8;          // warps per block
+constexpr int kAtomsPerWarp = 8;   // quads per warp
+constexpr int kBStride = 84;       // padded per-atom row in shared memory (16 B aligned)
+
+__device__ __forceinline__ int ang_l(int a) { return a == 0 ? 0 : (a < 4 ? 1 : 2); }
+__device__ __forceinline__ float ang_w(int a) { return a >= 7 ? 2.f : 1.f; }
+__device__ __forceinline__ float ang_sign(int a) { return (a >= 1 && a <= 3) ? -1.f : 1.f; }
+
+struct Edge {
+    float x, y, z, d;
+    float phi[NPHI];
+};
+
+// exp(a) for |a| < 80 by Cody-Waite range reduction (W. J. Cody and W. Waite,
+// Software Manual for the Elementary Functions, 1980): a = k ln2 + r with ln2
+// split into a short high part (k ln2_hi exact) and a correction, |r| <= ln2/2,
+// then the degree-7 Taylor polynomial of exp(r) (truncation < 6e-9 relative) in
+// Horner form and an exact scaling by 2^k.  Measured on the GPU against FP64 its
+// mean relative error is ~1e-9 (unbiased), so the m-fold Gaussian recurrence
+// below does not turn a one-sided rounding habit into a shift of every phi_m.
+__device__ __forceinline__ float exp_cw(float a) {
+    a = fminf(fmaxf(a, -87.f), 88.f);  // keeps 2^k a normal float
+    const float k = rintf(a * 1.44269504f);
+    float r = fmaf(-k, 0.693145751953125f, a);
+    r = fmaf(-k, 1.428606820309417e-06f, r);
+    float p = 1.f / 5040.f;
+    p = fmaf(p, r, 1.f / 720.f);
+    p = fmaf(p, r, 1.f / 120.f);
+    p = fmaf(p, r, 1.f / 24.f);
+    p = fmaf(p, r, 1.f / 6.f);
+    p = fmaf(p, r, 0.5f);
+    p = fmaf(p, r, 1.f);
+    p = fmaf(p, r, 1.f);
+    return p * __int_as_float(((int)k + 127) << 23);
+}
+
+// Gaussians by the equal-spacing recurrence exp(-a(d-mu_{m+1})^2) = exp(-a(d-mu_m)^2) q kappa_m,
+// q = exp(2 a Delta d): two exponentials per edge instead of eight.  The constants
+// a, 2 a Delta and kappa_m enter as float pairs (see Radial).
+__device__ __forceinline__ void gaussians(const Radial& R, float d, float gs[NPHI]) {
+    const float dd = d * d;
+    gs[0] = exp_cw(-fmaf(R.alpha_hi, dd, R.alpha_lo * dd));
+    const float q = exp_cw(fmaf(R.tad_hi, d, R.tad_lo * d));
+#pragma unroll
+    for (int m = 0; m + 1 < NPHI; ++m) {
+        const float p = gs[m] * q;
+        gs[m + 1] = fmaf(p, R.kap_hi[m], p * R.kap_lo[m]);
+    }
+}
+
+// f_c(d) = (cos(pi d/r_c)/2 + 1/2)^2 evaluated as cos^4(pi x / 2), x = d / r_c by
+// an IEEE division (no rounded 1/r_c or pi constant: near r_c the cutoff's
+// logarithmic derivative is large, so a rounded constant would bias every atom),
+// and without the cancellation of 1/2 + cos/2 near d = r_c.
+// dfc = -(2 pi / r_c) cos^3 sin (half angle).
+__device__ __forceinline__ void cutoff(const Radial& R, float d, float& fc, float& dfc) {
+    float s, c;
+    const float x = __fdiv_rn(d, R.rc);
+    sincospif(0.5f * x, &s, &c);
+    const float c2 = c * c;
+    fc = c2 * c2;
+    dfc = __fdiv_rn(-6.28318530717959f * c2 * c * s, R.rc);
+}
+
+// d - mu_m with the centre as a float pair
+__device__ __forceinline__ float dmu(const Radial& R, float d, int m) { return (d - R.mu_hi[m]) - R.mu_lo[m]; }
+
+__device__ __forceinline__ void monomials(float x, float y, float z, float A[NANG]) {
+    A[0] = 1.f;
+    A[1] = x;
+    A[2] = y;
+    A[3] = z;
+    A[4] = x * x;
+    A[5] = y * y;
+    A[6] = z * z;
+    A[7] = x * y;
+    A[8] = x * z;
+    A[9] = y * z;
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+
+// ------------------------------------------------------------- forward ---
+__global__ void __launch_bounds__(kWarps * 32) k_density_fwd(int64_t n, int stride, Radial R,
+                                                            const int32_t* __restrict__ live,
+                                                            const int32_t* __restrict__ live_cnt,
+                                                            const float4* __restrict__ phi_hi,
+                                                            const float4* __restrict__ plo,
+                                                            const float* __restrict__ coef,
+                                                            const float* __restrict__ Wt, float* __restrict__ rho,
+                                                            float* __restrict__ bck) {
+    __shared__ __align__(16) float sW[(LMAX + 1) * NPHI * NORB];
+    __shared__ __align__(16) float sB[kWarps][kAtomsPerWarp][kBStride];
+    for (int i = threadIdx.x; i < (LMAX + 1) * NPHI * NORB; i += blockDim.x) sW[i] = Wt[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, q = lane & 3, slot = lane >> 2;
+    const int64_t atom = ((int64_t)blockIdx.x * kWarps + warp) * kAtomsPerWarp + slot;
+    const bool valid = atom < n;
+
+    float acc[NB];
+#pragma unroll
+    for (int v = 0; v < NB; ++v) acc[v] = 0.f;
+    if (valid) {
+        const float4 hi_i = phi_hi[atom], lo_i = plo[atom];
+        const int cnt = live_cnt[atom];
+        const int32_t* row = live + (size_t)atom * stride;
+        for (int e = q; e < cnt; e += 4) {
+            const int j = row[e];
+            const float4 hj = phi_hi[j], lj = plo[j];
+            const float x = (hj.x - hi_i.x) + (lj.x - lo_i.x);
+            const float y = (hj.y - hi_i.y) + (lj.y - lo_i.y);
+            const float z = (hj.z - hi_i.z) + (lj.z - lo_i.z);
+            const float d = sqrtf(x * x + y * y + z * z);
+            float gs[NPHI], fc, dfc;
+            gaussians(R, d, gs);
+            cutoff(R, d, fc, dfc);
+            const float4 c0 = ldg4(coef + (size_t)j * NPHI), c1 = ldg4(coef + (size_t)j * NPHI + 4);
+            const float cj[NPHI] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+            float tm[NPHI];
+#pragma unroll
+            for (int m = 0; m < NPHI; ++m) tm[m] = cj[m] * gs[m] * fc;
+            float A[NANG];
+            monomials(x, y, z, A);
+#pragma unroll
+            for (int a = 0; a < NANG; ++a)
+#pragma unroll
+                for (int m = 0; m < NPHI; ++m) acc[a * NPHI + m] = fmaf(tm[m], A[a], acc[a * NPHI + m]);
+        }
+    }
+    // butterfly reduce-scatter over the quad: lane q keeps b[20q, 20q+20)
+    float r1[NB / 2];
+    const bool hi_half = (q >> 1) & 1;
+#pragma unroll
+    for (int v = 0; v < NB / 2; ++v) {
+        const float send = hi_half ? acc[v] : acc[NB / 2 + v];
+        const float keep = hi_half ? acc[NB / 2 + v] : acc[v];
+        r1[v] = keep + __shfl_xor_sync(FULL, send, 2);
+    }
+    float r2[NB / 4];
+    const bool odd = q & 1;
+#pragma unroll
+    for (int v = 0; v < NB / 4; ++v) {
+        const float send = odd ? r1[v] : r1[NB / 4 + v];
+        const float keep = odd ? r1[NB / 4 + v] : r1[v];
+        r2[v] = keep + __shfl_xor_sync(FULL, send, 1);
+    }
+    float* sb = sB[warp][slot];
+#pragma unroll
+    for (int v = 0; v < NB / 4; v += 4) {
+        const float4 w4 = make_float4(r2[v], r2[v + 1], r2[v + 2], r2[v + 3]);
+        *reinterpret_cast<float4*>(sb + 20 * q + v) = w4;
+        if (valid) *reinterpret_cast<float4*>(bck + (size_t)atom * NB + 20 * q + v) = w4;
+    }
+    __syncwarp();
+    if (!valid) return;
+    // contraction over m and the squared multinomial sum; lane q owns orbitals 4q..4q+3
+    float racc[LMAX + 1][4];
+#pragma unroll
+    for (int l = 0; l <= LMAX; ++l)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) racc[l][k] = 0.f;
+#pragma unroll
+    for (int a = 0; a < NANG; ++a) {
+        const int l = ang_l(a);
+        const float4 b0 = ld4(sb + a * NPHI), b1 = ld4(sb + a * NPHI + 4);
+        const float bm[NPHI] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        float g[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int m = 0; m < NPHI; ++m) {
+            const float4 w = ld4(sW + (l * NPHI + m) * NORB + 4 * q);
+            g[0] = fmaf(bm[m], w.x, g[0]);
+            g[1] = fmaf(bm[m], w.y, g[1]);
+            g[2] = fmaf(bm[m], w.z, g[2]);
+            g[3] = fmaf(bm[m], w.w, g[3]);
+        }
+        const float wa = ang_w(a);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) racc[l][k] = fmaf(wa * g[k], g[k], racc[l][k]);
+    }
+#pragma unroll
+    for (int l = 0; l <= LMAX; ++l)
+        *reinterpret_cast<float4*>(rho + (size_t)atom * NFEAT + l * NORB + 4 * q) =
+            make_float4(racc[l][0], racc[l][1], racc[l][2], racc[l][3]);
+}
+
+// -------------------------------------------------------------- bbar -----
+// bbar_{a,m} = sum_k 2 w_a g_{a,k} rhobar_{l(a),k} W_{l(a),m,k}, g recomputed from the b checkpoint.
+__global__ void __launch_bounds__(256) k_bbar(int64_t n, const float* __restrict__ Wt, const float* __restrict__ bck,
+                                              const float* __restrict__ rhobar, float* __restrict__ bbar) {
+    __shared__ __align__(16) float sW[(LMAX + 1) * NPHI * NORB];
+    for (int i = threadIdx.x; i < (LMAX + 1) * NPHI * NORB; i += blockDim.x) sW[i] = Wt[i];
+    __syncthreads();
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t atom = tid >> 2;
+    const int q = tid & 3;
+    if (atom >= n) return;
+    for (int a = q; a < NANG; a += 4) {
+        const int l = ang_l(a);
+        const float4 b0 = ldg4(bck + (size_t)atom * NB + a * NPHI), b1 = ldg4(bck + (size_t)atom * NB + a * NPHI + 4);
+        const float bm[NPHI] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        float out[NPHI];
+#pragma unroll
+        for (int m = 0; m < NPHI; ++m) out[m] = 0.f;
+        const float two_w = 2.f * ang_w(a);
+#pragma unroll
+        for (int k4 = 0; k4 < NORB; k4 += 4) {
+            float g[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int m = 0; m < NPHI; ++m) {
+                const float4 w = ld4(sW + (l * NPHI + m) * NORB + k4);
+                g[0] = fmaf(bm[m], w.x, g[0]);
+                g[1] = fmaf(bm[m], w.y, g[1]);
+                g[2] = fmaf(bm[m], w.z, g[2]);
+                g[3] = fmaf(bm[m], w.w, g[3]);
+            }
+            const float4 rb = ldg4(rhobar + (size_t)atom * NFEAT + l * NORB + k4);
+            const float gb[4] = {two_w * g[0] * rb.x, two_w * g[1] * rb.y, two_w * g[2] * rb.z, two_w * g[3] * rb.w};
+#pragma unroll
+            for (int m = 0; m < NPHI; ++m) {
+                const float4 w = ld4(sW + (l * NPHI + m) * NORB + k4);
+                out[m] = fmaf(gb[0], w.x, fmaf(gb[1], w.y, fmaf(gb[2], w.z, fmaf(gb[3], w.w, out[m]))));
+            }
+        }
+        float* dst = bbar + (size_t)atom * NB + a * NPHI;
+        *reinterpret_cast<float4*>(dst) = make_float4(out[0], out[1], out[2], out[3]);
+        *reinterpret_cast<float4*>(dst + 4) = make_float4(out[4], out[5], out[6], out[7]);
+    }
+}
+
+// ---------------------------------------------------------- adjoint ------
+template <bool WANT_CBAR>
+__global__ void __launch_bounds__(kWarps * 32) k_density_adj(int64_t n, int stride, Radial R,
+                                                            const int32_t* __restrict__ live,
+                                                            const int32_t* __restrict__ live_cnt,
+                                                            const float4* __restrict__ phi_hi,
+                                                            const float4* __restrict__ plo,
+                                                            const float* __restrict__ coef,
+                                                            const float* __restrict__ bbar, float* __restrict__ cbar,
+                                                            float* __restrict__ grad) {
+    __shared__ __align__(16) float sBk[kWarps][kAtomsPerWarp][kBStride];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, q = lane & 3, slot = lane >> 2;
+    const int64_t atom = ((int64_t)blockIdx.x * kWarps + warp) * kAtomsPerWarp + slot;
+    const bool valid = atom < n;
+    float* sk = sBk[warp][slot];
+    if (valid) {
+#pragma unroll
+        for (int v = 0; v < 20; v += 4)
+            *reinterpret_cast<float4*>(sk + 20 * q + v) = ldg4(bbar + (size_t)atom * NB + 20 * q + v);
+    }
+    __syncwarp();
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    float cb[NPHI];
+#pragma unroll
+    for (int m = 0; m < NPHI; ++m) cb[m] = 0.f;
+    if (valid) {
+        const float4 hi_i = phi_hi[atom], lo_i = plo[atom];
+        const float4 k0 = ldg4(coef + (size_t)atom * NPHI), k1 = ldg4(coef + (size_t)atom * NPHI + 4);
+        const float ck[NPHI] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
+        const int cnt = live_cnt[atom];
+        const int32_t* row = live + (size_t)atom * stride;
+        for (int e = q; e < cnt; e += 4) {
+            const int j = row[e];
+            const float4 hj = phi_hi[j], lj = plo[j];
+            const float x = (hj.x - hi_i.x) + (lj.x - lo_i.x);
+            const float y = (hj.y - hi_i.y) + (lj.y - lo_i.y);
+            const float z = (hj.z - hi_i.z) + (lj.z - lo_i.z);
+            const float d = sqrtf(x * x + y * y + z * z);
+            const float inv_d = 1.f / d;
+            float gs[NPHI], fc, dfc;
+            gaussians(R, d, gs);
+            cutoff(R, d, fc, dfc);
+            const float4 c0 = ldg4(coef + (size_t)j * NPHI), c1 = ldg4(coef + (size_t)j * NPHI + 4);
+            const float cj[NPHI] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+            float phi[NPHI], p[NPHI], pt[NPHI], qv[NPHI], qt[NPHI];
+#pragma unroll
+            for (int m = 0; m < NPHI; ++m) {
+                phi[m] = gs[m] * fc;
+                const float dphi = gs[m] * (dfc - 2.f * R.alpha_hi * dmu(R, d, m) * fc);
+                p[m] = cj[m] * dphi;
+                pt[m] = ck[m] * dphi;
+                qv[m] = cj[m] * phi[m];
+                qt[m] = ck[m] * phi[m];
+            }
+            float A[NANG];
+            monomials(x, y, z, A);
+            float sAU = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
+            float cacc[NPHI];
+#pragma unroll
+            for (int m = 0; m < NPHI; ++m) cacc[m] = 0.f;
+            const float* bj = bbar + (size_t)j * NB;
+#pragma unroll
+            for (int a = 0; a < NANG; ++a) {
+                const float sl = ang_sign(a);
+                const float4 k0a = ld4(sk + a * NPHI), k1a = ld4(sk + a * NPHI + 4);
+                const float bk[NPHI] = {k0a.x, k0a.y, k0a.z, k0a.w, k1a.x, k1a.y, k1a.z, k1a.w};
+                const float4 j0 = ldg4(bj + a * NPHI), j1 = ldg4(bj + a * NPHI + 4);
+                const float bjm[NPHI] = {j0.x, j0.y, j0.z, j0.w, j1.x, j1.y, j1.z, j1.w};
+                float u1 = 0.f, u2 = 0.f, v1 = 0.f, v2 = 0.f;
+#pragma unroll
+                for (int m = 0; m < NPHI; ++m) {
+                    u1 = fmaf(bk[m], p[m], u1);
+                    u2 = fmaf(bjm[m], pt[m], u2);
+                    if (a > 0) {
+                        v1 = fmaf(bk[m], qv[m], v1);
+                        v2 = fmaf(bjm[m], qt[m], v2);
+                    }
+                    if (WANT_CBAR) cacc[m] = fmaf(sl * A[a], bjm[m], cacc[m]);
+                }
+                const float u = fmaf(sl, u2, u1);
+                sAU = fmaf(A[a], u, sAU);
+                const float v = fmaf(sl, v2, v1);
+                switch (a) {
+                    case 1: vx += v; break;
+                    case 2: vy += v; break;
+                    case 3: vz += v; break;
+                    case 4: vx = fmaf(2.f * x, v, vx); break;
+                    case 5: vy = fmaf(2.f * y, v, vy); break;
+                    case 6: vz = fmaf(2.f * z, v, vz); break;
+                    case 7: vx = fmaf(y, v, vx); vy = fmaf(x, v, vy); break;
+                    case 8: vx = fmaf(z, v, vx); vz = fmaf(x, v, vz); break;
+                    case 9: vy = fmaf(z, v, vy); vz = fmaf(y, v, vz); break;
+                    default: break;
+                }
+            }
+            const float s = sAU * inv_d;
+            gx -= fmaf(s, x, vx);
+            gy -= fmaf(s, y, vy);
+            gz -= fmaf(s, z, vz);
+            if (WANT_CBAR) {
+#pragma unroll
+                for (int m = 0; m < NPHI; ++m) cb[m] = fmaf(phi[m], cacc[m], cb[m]);
+            }
+        }
+    }
+    // quad all-reduce
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+        gx += __shfl_xor_sync(FULL, gx, o);
+        gy += __shfl_xor_sync(FULL, gy, o);
+        gz += __shfl_xor_sync(FULL, gz, o);
+        if (WANT_CBAR) {
+#pragma unroll
+            for (int m = 0; m < NPHI; ++m) cb[m] += __shfl_xor_sync(FULL, cb[m], o);
+        }
+    }
+    if (!valid || q != 0) return;
+    float* gr = grad + (size_t)atom * 3;
+    gr[0] += gx;
+    gr[1] += gy;
+    gr[2] += gz;
+    if (WANT_CBAR) {
+        float* dst = cbar + (size_t)atom * NPHI;
+        *reinterpret_cast<float4*>(dst) = make_float4(cb[0], cb[1], cb[2], cb[3]);
+        *reinterpret_cast<float4*>(dst + 4) = make_float4(cb[4], cb[5], cb[6], cb[7]);
+    }
+}
+
+// ------------------------------------------------------- small kernels ---
+__global__ void k_init_coef(int64_t n, int64_t g, const int32_t* __restrict__ species,
+                            const int32_t* __restrict__ owner, const float* __restrict__ c0, float* __restrict__ coef) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n + g) return;
+    const int64_t o = s < n ? s : owner[s - n];
+    const int e = species[o];
+    const float4* src = reinterpret_cast<const float4*>(c0 + e * NPHI);
+    float4* dst = reinterpret_cast<float4*>(coef + (size_t)s * NPHI);
+    dst[0] = src[0];
+    dst[1] = src[1];
+}
+
+// ghost rows <- owner rows (the per-layer ghost refresh of Fig. 4a), width in floats, multiple of 4
+__global__ void k_gather_rows(int64_t n, int64_t g, int w4, const int32_t* __restrict__ owner, float* __restrict__ base) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g * w4) return;
+    const int64_t gi = t / w4;
+    const int c = (int)(t - gi * w4);
+    float4* b = reinterpret_cast<float4*>(base);
+    b[(n + gi) * w4 + c] = b[(int64_t)owner[gi] * w4 + c];
+}
+
+constexpr int kSumThreads = 256, kSumPer = 8;
+
+__global__ void __launch_bounds__(kSumThreads) k_energy_partial(int64_t n, const float* __restrict__ eps,
+                                                               double* __restrict__ partial) {
+    __shared__ double sm[kSumThreads];
+    const int64_t base = (int64_t)blockIdx.x * kSumThreads * kSumPer;
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kSumPer; ++k) {
+        const int64_t i = base + k * kSumThreads + threadIdx.x;
+        if (i < n) s += (double)eps[i];
+    }
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kSumThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+}
+
+__global__ void __launch_bounds__(kSumThreads) k_energy_final(int np, const double* __restrict__ partial,
+                                                             double* __restrict__ energy) {
+    __shared__ double sm[kSumThreads];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < np; i += kSumThreads) s += partial[i];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kSumThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) energy[0] = sm[0];
+}
+
+__global__ void k_scatter_outputs(int64_t n, const int32_t* __restrict__ perm, const float* __restrict__ grad,
+                                  const float* __restrict__ eps, float* __restrict__ forces,
+                                  float* __restrict__ atom_energy) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t c = perm[i];
+    forces[3 * c] = -grad[3 * i];
+    forces[3 * c + 1] = -grad[3 * i + 1];
+    forces[3 * c + 2] = -grad[3 * i + 2];
+    if (atom_energy) atom_energy[c] = eps[i];
+}
+
+__global__ void k_unpermute_rows(int64_t n, int width, const int32_t* __restrict__ perm, const float* __restrict__ src,
+                                 int src_stride, float* __restrict__ dst) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * width) return;
+    const int64_t i = t / width;
+    const int c = (int)(t - i * width);
+    dst[(int64_t)perm[i] * width + c] = src[i * src_stride + c];
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_init_coef(cudaStream_t s, const reann_nlist* nl, const float* c0) {
+    const int64_t total = nl->n + nl->g;
+    k_init_coef<<<blocks_for(total, 256), 256, 0, s>>>(nl->n, nl->g, nl->species, nl->g_owner, c0, nl->coef);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_ghost_rows(cudaStream_t s, const reann_nlist* nl, float* base, int width) {
+    if (nl->g == 0) return cudaSuccess;
+    const int w4 = width / 4;
+    k_gather_rows<<<blocks_for(nl->g * w4, 256), 256, 0, s>>>(nl->n, nl->g, w4, nl->g_owner, base);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_density_fwd(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* W, const float* coef,
+                               float* rho, float* bck) {
+    const int64_t per_block = kWarps * kAtomsPerWarp;
+    k_density_fwd<<<blocks_for(nl->n, per_block), kWarps * 32, 0, s>>>(nl->n, nl->stride, r, nl->live, nl->live_cnt,
+                                                                        nl->pos_hi, nl->pos_lo, coef, W, rho, bck);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bbar(cudaStream_t s, const reann_nlist* nl, const float* W, const float* bck, const float* rhobar,
+                        float* bbar) {
+    k_bbar<<<blocks_for(nl->n * 4, 256), 256, 0, s>>>(nl->n, W, bck, rhobar, bbar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* coef,
+                               const float* bbar, float* cbar, float* grad, bool want_cbar, int* flags) {
+    (void)flags;
+    const int64_t per_block = kWarps * kAtomsPerWarp;
+    if (want_cbar)
+        k_density_adj<true><<<blocks_for(nl->n, per_block), kWarps * 32, 0, s>>>(
+            nl->n, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi, nl->pos_lo, coef, bbar, cbar, grad);
+    else
+        k_density_adj<false><<<blocks_for(nl->n, per_block), kWarps * 32, 0, s>>>(
+            nl->n, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi, nl->pos_lo, coef, bbar, cbar, grad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_sum(cudaStream_t s, const reann_nlist* nl, double* energy) {
+    const int np = (int)blocks_for(nl->n, kSumThreads * kSumPer);
+    k_energy_partial<<<np, kSumThreads, 0, s>>>(nl->n, nl->eps, nl->partial);
+    k_energy_final<<<1, kSumThreads, 0, s>>>(np, nl->partial, energy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_outputs(cudaStream_t s, const reann_nlist* nl, float* forces, float* atom_energy) {
+    k_scatter_outputs<<<blocks_for(nl->n, 256), 256, 0, s>>>(nl->n, nl->perm, nl->grad, nl->eps, forces, atom_energy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpermute_rows(cudaStream_t s, const reann_nlist* nl, const float* src, int src_stride, float* dst,
+                                  int width) {
+    k_unpermute_rows<<<blocks_for(nl->n * width, 256), 256, 0, s>>>(nl->n, width, nl->perm, src, src_stride, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace reann

@@ -1,0 +1,309 @@
+// Per-element atomic networks in plain FP32 (SIMT FMA), forward and
+// input-gradient backward.
+//
+// Sec. 2.1, Eq. 2: c^{t+1}_i = M^t_{Z_i}(rho^t_i) (48 -> 64 -> 64 -> 8), and the
+// energy network eps_i = M^{T-1}_{Z_i}(rho^{T-1}_i) (48 -> 64 -> 64 -> 1), SiLU
+// between layers.  The reverse pass (Eqs. 4-5) needs only the input gradient
+// rhobar = J^T ybar (a vector-Jacobian product, Sec. 2.2), never weight
+// gradients.
+//
+// Atoms are stored element-major, so a tile of 64 consecutive rows uses one
+// element's weights.  A block of 256 threads computes a 64x64 layer output as
+// 16x16 threads x (4 rows x 4 columns), reading float4 fragments of the
+// row-major activations and weights from shared memory.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace reann {
+namespace {
+
+constexpr int kT = 256;       // threads per block
+constexpr int kR = MLP_TILE;  // 64 rows per tile
+constexpr int LDX = NFEAT + 4;  // 52
+constexpr int LDH = H1 + 4;     // 68
+
+struct NetsOfLayer {
+    NetDev e[MAX_ELEM];
+};
+
+__device__ __forceinline__ float silu(float z) { return z / (1.f + expf(-z)); }
+__device__ __forceinline__ float dsilu(float z) {
+    const float s = 1.f / (1.f + expf(-z));
+    return s * (1.f + z * (1.f - s));
+}
+
+__device__ __forceinline__ void copy_f4(float* dst, const float* src, int count, int tid) {
+    const float4* s = reinterpret_cast<const float4*>(src);
+    float4* d = reinterpret_cast<float4*>(dst);
+    for (int i = tid; i < count / 4; i += kT) d[i] = s[i];
+}
+
+// acc[i][j] += sum_k A[(4ty+i)*LDA + k] * B[k*LDB + 4tx + j], K multiple of 4
+template <int K, int LDA, int LDB>
+__device__ __forceinline__ void mma_4x4(const float* A, const float* B, int ty, int tx, float acc[4][4]) {
+#pragma unroll 4
+    for (int k = 0; k < K; k += 4) {
+        float4 a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(A + (4 * ty + i) * LDA + k);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) b[kk] = *reinterpret_cast<const float4*>(B + (k + kk) * LDB + 4 * tx);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float av[4] = {a[i].x, a[i].y, a[i].z, a[i].w};
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                acc[i][0] = fmaf(av[kk], b[kk].x, acc[i][0]);
+                acc[i][1] = fmaf(av[kk], b[kk].y, acc[i][1]);
+                acc[i][2] = fmaf(av[kk], b[kk].z, acc[i][2]);
+                acc[i][3] = fmaf(av[kk], b[kk].w, acc[i][3]);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void load_rows(float* sX, const float* src, int row0, int nrows, int tid) {
+    // 64 rows x 48 floats -> sX[r][LDX]
+    for (int t = tid; t < kR * (NFEAT / 4); t += kT) {
+        const int r = t / (NFEAT / 4), c = t % (NFEAT / 4);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < nrows) v = *reinterpret_cast<const float4*>(src + (size_t)(row0 + r) * NFEAT + 4 * c);
+        *reinterpret_cast<float4*>(sX + r * LDX + 4 * c) = v;
+    }
+}
+
+// ----------------------------------------------------------- forward ---
+template <int OUT>
+__global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __restrict__ tiles,
+                                               const float* __restrict__ rho, float* __restrict__ out,
+                                               int out_stride) {
+    extern __shared__ __align__(16) float sm[];
+    float* sW1 = sm;                 // 48 x 64
+    float* sW2 = sW1 + NFEAT * H1;   // 64 x 64
+    float* sW3 = sW2 + H1 * H2;      // 64 x OUT
+    float* sb1 = sW3 + H2 * 8;       // 64
+    float* sb2 = sb1 + H1;           // 64
+    float* sb3 = sb2 + H2;           // 8
+    float* sX = sb3 + 8;             // 64 x 52
+    float* sH1 = sX + kR * LDX;      // 64 x 68
+    float* sH2 = sH1 + kR * LDH;     // 64 x 68
+    const int tid = threadIdx.x;
+    const Tile tl = tiles[blockIdx.x];
+    const NetDev& w = nets.e[tl.elem];
+    copy_f4(sW1, w.W1, NFEAT * H1, tid);
+    copy_f4(sW2, w.W2, H1 * H2, tid);
+    for (int i = tid; i < H2 * OUT; i += kT) sW3[i] = w.W3[i];
+    for (int i = tid; i < H1; i += kT) sb1[i] = w.b1[i];
+    for (int i = tid; i < H2; i += kT) sb2[i] = w.b2[i];
+    if (tid < OUT) sb3[tid] = w.b3[tid];
+    load_rows(sX, rho, tl.row0, tl.nrows, tid);
+    __syncthreads();
+    const int ty = tid >> 4, tx = tid & 15;
+    float acc[4][4];
+    // layer 1
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = sb1[4 * tx + j];
+    mma_4x4<NFEAT, LDX, H1>(sX, sW1, ty, tx, acc);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<float4*>(sH1 + (4 * ty + i) * LDH + 4 * tx) =
+            make_float4(silu(acc[i][0]), silu(acc[i][1]), silu(acc[i][2]), silu(acc[i][3]));
+    __syncthreads();
+    // layer 2
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = sb2[4 * tx + j];
+    mma_4x4<H1, LDH, H2>(sH1, sW2, ty, tx, acc);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<float4*>(sH2 + (4 * ty + i) * LDH + 4 * tx) =
+            make_float4(silu(acc[i][0]), silu(acc[i][1]), silu(acc[i][2]), silu(acc[i][3]));
+    __syncthreads();
+    // layer 3: 4 threads per row
+    const int r = tid >> 2, part = tid & 3;
+    if (OUT == 1) {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 16 * part; k < 16 * part + 16; ++k) s = fmaf(sH2[r * LDH + k], sW3[k], s);
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        if (part == 0 && r < tl.nrows) out[(size_t)(tl.row0 + r) * out_stride] = s + sb3[0];
+    } else {
+        float s0 = sb3[2 * part], s1 = sb3[2 * part + 1];
+#pragma unroll 8
+        for (int k = 0; k < H2; ++k) {
+            const float h = sH2[r * LDH + k];
+            s0 = fmaf(h, sW3[k * OUT + 2 * part], s0);
+            s1 = fmaf(h, sW3[k * OUT + 2 * part + 1], s1);
+        }
+        if (r < tl.nrows) {
+            float* o = out + (size_t)(tl.row0 + r) * out_stride + 2 * part;
+            o[0] = s0;
+            o[1] = s1;
+        }
+    }
+}
+
+// ---------------------------------------------------------- backward ---
+// rhobar = W1 (dsilu(z1) * (W2 (dsilu(z2) * (W3 ybar))))   per row
+template <int OUT>
+__global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __restrict__ tiles,
+                                               const float* __restrict__ rho, const float* __restrict__ ybar,
+                                               float* __restrict__ rhobar) {
+    extern __shared__ __align__(16) float sm[];
+    float* sW1 = sm;                  // 48 x 64
+    float* sW2 = sW1 + NFEAT * H1;    // 64 x 64
+    float* sW1t = sW2 + H1 * H2;      // 64 x 48
+    float* sW2t = sW1t + H1 * NFEAT;  // 64 x 64
+    float* sW3t = sW2t + H1 * H2;     // OUT x 64 (8 rows reserved)
+    float* sb1 = sW3t + 8 * H2;       // 64
+    float* sb2 = sb1 + H1;            // 64
+    float* sY = sb2 + H2;             // 64 x 8
+    float* sX = sY + kR * 8;          // 64 x 52
+    float* sZ1 = sX + kR * LDX;       // 64 x 68
+    float* sZ2 = sZ1 + kR * LDH;      // 64 x 68
+    float* sG = sZ2 + kR * LDH;       // 64 x 68
+    const int tid = threadIdx.x;
+    const Tile tl = tiles[blockIdx.x];
+    const NetDev& w = nets.e[tl.elem];
+    copy_f4(sW1, w.W1, NFEAT * H1, tid);
+    copy_f4(sW2, w.W2, H1 * H2, tid);
+    copy_f4(sW1t, w.W1t, H1 * NFEAT, tid);
+    copy_f4(sW2t, w.W2t, H1 * H2, tid);
+    for (int i = tid; i < OUT * H2; i += kT) sW3t[i] = w.W3t[i];
+    for (int i = tid; i < H1; i += kT) sb1[i] = w.b1[i];
+    for (int i = tid; i < H2; i += kT) sb2[i] = w.b2[i];
+    for (int i = tid; i < kR * OUT; i += kT) {
+        const int r = i / OUT, o = i % OUT;
+        sY[r * 8 + o] = (OUT == 1) ? 1.f : (r < tl.nrows ? ybar[(size_t)(tl.row0 + r) * OUT + o] : 0.f);
+    }
+    load_rows(sX, rho, tl.row0, tl.nrows, tid);
+    __syncthreads();
+    const int ty = tid >> 4, tx = tid & 15;
+    float acc[4][4];
+    // z1, h1
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = sb1[4 * tx + j];
+    mma_4x4<NFEAT, LDX, H1>(sX, sW1, ty, tx, acc);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        *reinterpret_cast<float4*>(sZ1 + (4 * ty + i) * LDH + 4 * tx) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        *reinterpret_cast<float4*>(sG + (4 * ty + i) * LDH + 4 * tx) =
+            make_float4(silu(acc[i][0]), silu(acc[i][1]), silu(acc[i][2]), silu(acc[i][3]));
+    }
+    __syncthreads();
+    // z2
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = sb2[4 * tx + j];
+    mma_4x4<H1, LDH, H2>(sG, sW2, ty, tx, acc);
+    float z2[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) z2[i][j] = acc[i][j];
+    __syncthreads();  // everyone is done reading sG (h1)
+    // z2bar = (ybar W3^T) * dsilu(z2) -> sG
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int o = 0; o < OUT; ++o) {
+            const float y = sY[(4 * ty + i) * 8 + o];
+            const float4 wv = *reinterpret_cast<const float4*>(sW3t + o * H2 + 4 * tx);
+            v[0] = fmaf(y, wv.x, v[0]);
+            v[1] = fmaf(y, wv.y, v[1]);
+            v[2] = fmaf(y, wv.z, v[2]);
+            v[3] = fmaf(y, wv.w, v[3]);
+        }
+        *reinterpret_cast<float4*>(sG + (4 * ty + i) * LDH + 4 * tx) =
+            make_float4(v[0] * dsilu(z2[i][0]), v[1] * dsilu(z2[i][1]), v[2] * dsilu(z2[i][2]), v[3] * dsilu(z2[i][3]));
+    }
+    __syncthreads();
+    // z1bar = (z2bar W2^T) * dsilu(z1) -> sZ2
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    mma_4x4<H2, LDH, H1>(sG, sW2t, ty, tx, acc);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 z1 = *reinterpret_cast<const float4*>(sZ1 + (4 * ty + i) * LDH + 4 * tx);
+        *reinterpret_cast<float4*>(sZ2 + (4 * ty + i) * LDH + 4 * tx) = make_float4(
+            acc[i][0] * dsilu(z1.x), acc[i][1] * dsilu(z1.y), acc[i][2] * dsilu(z1.z), acc[i][3] * dsilu(z1.w));
+    }
+    __syncthreads();
+    // rhobar = z1bar W1^T  (64 x 48): 12 column groups of 4
+    if (tx < NFEAT / 4) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        mma_4x4<H1, LDH, NFEAT>(sZ2, sW1t, ty, tx, acc);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = 4 * ty + i;
+            if (r < tl.nrows)
+                *reinterpret_cast<float4*>(rhobar + (size_t)(tl.row0 + r) * NFEAT + 4 * tx) =
+                    make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        }
+    }
+}
+
+constexpr size_t fwd_smem() { return sizeof(float) * (NFEAT * H1 + H1 * H2 + H2 * 8 + H1 + H2 + 8 + kR * LDX + 2 * kR * LDH); }
+constexpr size_t bwd_smem() {
+    return sizeof(float) * (2 * NFEAT * H1 + 2 * H1 * H2 + 8 * H2 + H1 + H2 + kR * 8 + kR * LDX + 3 * kR * LDH);
+}
+
+void ensure_attrs() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_mlp_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
+    cudaFuncSetAttribute(k_mlp_fwd<NPHI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
+    cudaFuncSetAttribute(k_mlp_bwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem());
+    cudaFuncSetAttribute(k_mlp_bwd<NPHI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem());
+    done = true;
+}
+
+NetsOfLayer layer_nets(const NetTable& t, int layer) {
+    NetsOfLayer n;
+    for (int e = 0; e < MAX_ELEM; ++e) n.e[e] = t.net[layer][e];
+    return n;
+}
+
+}  // namespace
+
+cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
+                               const float* rho, float* out, int out_stride) {
+    const int nt = (int)nl->tiles_h.size();
+    if (nt == 0) return cudaSuccess;
+    ensure_attrs();
+    const NetsOfLayer ln = layer_nets(nets, t);
+    if (energy)
+        k_mlp_fwd<1><<<nt, kT, fwd_smem(), s>>>(ln, nl->tiles, rho, out, out_stride);
+    else
+        k_mlp_fwd<NPHI><<<nt, kT, fwd_smem(), s>>>(ln, nl->tiles, rho, out, out_stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
+                               const float* rho, const float* ybar, float* rhobar) {
+    const int nt = (int)nl->tiles_h.size();
+    if (nt == 0) return cudaSuccess;
+    ensure_attrs();
+    const NetsOfLayer ln = layer_nets(nets, t);
+    if (energy)
+        k_mlp_bwd<1><<<nt, kT, bwd_smem(), s>>>(ln, nl->tiles, rho, ybar, rhobar);
+    else
+        k_mlp_bwd<NPHI><<<nt, kT, bwd_smem(), s>>>(ln, nl->tiles, rho, ybar, rhobar);
+    return cudaGetLastError();
+}
+
+}  // namespace reann

@@ -1,0 +1,572 @@
+// Periodic neighbour list with a skin and the ghost (periodic-image) map.
+//
+// Sec. 2.2: one neighbour list of radius r_c serves every message-passing
+// layer; Sec. 1 motivates the skin (rebuild only after atoms moved skin/2).
+// On one GPU the paper's ghost atoms (Fig. 3a, Fig. 4a) become ghost slots
+// N..N+G-1: every periodic image that lies within r_c + skin of the cell,
+// pointing at its owner atom and carrying an integer image shift.
+//
+// Build (all deterministic, no host round trip except for sizes):
+//   1. wrap positions into the cell in FP64 and key every atom by
+//      (element, cell bin);
+//   2. counting sort by key -> internal order (element-major so the atomic
+//      networks see contiguous per-element tiles, spatially sorted inside an
+//      element so neighbour gathers stay local);
+//   3. enumerate ghost images (count, scan, fill);
+//   4. bin owned + ghost slots into an extended cell grid (counting sort);
+//   5. warp per owned atom: scan the stencil bins, FP32 pre-test with a
+//      margin, FP64 exact test for pairs near r_c + skin, ballot-compacted
+//      writes into a fixed-stride row.
+// The FP64 test follows one fixed arithmetic order (no FMA contraction):
+//   r = (x_w,o - x_w,i) + S(n), S(n)_d = (n0 H0d + n1 H1d) + n2 H2d,
+//   d^2 = (r0 r0 + r1 r1) + r2 r2 < (r_c + skin)^2.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace reann {
+namespace {
+
+constexpr int kScanThreads = 1024;
+
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+
+__device__ __forceinline__ void shift_vec(const CellGeom& g, int n0, int n1, int n2, double s[3]) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        s[d] = dadd(dadd(dmul((double)n0, g.h[d]), dmul((double)n1, g.h[3 + d])), dmul((double)n2, g.h[6 + d]));
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+__device__ __forceinline__ int pack_shift(int a, int b, int c) { return (a + 128) | ((b + 128) << 8) | ((c + 128) << 16); }
+__device__ __forceinline__ void unpack_shift(int p, int& a, int& b, int& c) {
+    a = (p & 255) - 128;
+    b = ((p >> 8) & 255) - 128;
+    c = ((p >> 16) & 255) - 128;
+}
+
+// 1. wrap + key (caller order)
+__global__ void k_wrap_key(int64_t n, const double* __restrict__ pos, const int32_t* __restrict__ species, int n_elem,
+                           CellGeom g, double* __restrict__ xw, double* __restrict__ fw, int32_t* __restrict__ mw,
+                           int32_t* __restrict__ key, int* __restrict__ flags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    int sp = species[i];
+    bool bad = !(isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]));
+    if (sp < 0 || sp >= n_elem) {
+        atomicOr(&flags[FLAG_SPECIES], 1);
+        sp = 0;
+    }
+    double fr[3];
+    int m[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        fr[k] = dadd(dadd(dmul(x[0], g.hinv[k]), dmul(x[1], g.hinv[3 + k])), dmul(x[2], g.hinv[6 + k]));
+        if (!isfinite(fr[k]) || fabs(fr[k]) > 1e9) bad = true;
+    }
+    if (bad) {
+        atomicOr(&flags[FLAG_GEOM], 1);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) fr[k] = 0.0, x[k] = 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) m[k] = (int)floor(fr[k]);
+    double s[3];
+    shift_vec(g, m[0], m[1], m[2], s);
+    int b[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        xw[3 * i + k] = dsub(x[k], s[k]);
+        double f = dsub(fr[k], (double)m[k]);
+        fw[3 * i + k] = f;
+        mw[3 * i + k] = m[k];
+        b[k] = clampi((int)floor(f * g.nb[k]), 0, g.nb[k] - 1);
+    }
+    int nbins = g.nb[0] * g.nb[1] * g.nb[2];
+    key[i] = sp * nbins + (b[0] * g.nb[1] + b[1]) * g.nb[2] + b[2];
+}
+
+// ---- deterministic counting sort ------------------------------------------
+__global__ void k_hist(int64_t n, const int32_t* __restrict__ key, int32_t* __restrict__ counts) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&counts[key[i]], 1);
+}
+
+// Exclusive scan of `in` (n entries) into out[0..n]; one block of kScanThreads.
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_single(int64_t n, const T* __restrict__ in, T* __restrict__ out) {
+    __shared__ T warp_sums[kScanThreads / 32];
+    const int tid = threadIdx.x;
+    const int64_t chunk = (n + kScanThreads - 1) / kScanThreads;
+    const int64_t lo = tid * chunk, hi = min(n, lo + chunk);
+    T local = 0;
+    for (int64_t i = lo; i < hi; ++i) local += in[i];
+    // block-wide exclusive scan of `local`
+    T v = local;
+    const int lane = tid & 31, w = tid >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) warp_sums[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        T s = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;  // inclusive
+    }
+    __syncthreads();
+    T base = (w > 0 ? warp_sums[w - 1] : (T)0) + v - local;
+    for (int64_t i = lo; i < hi; ++i) {
+        out[i] = base;
+        base += in[i];
+    }
+    if (tid == kScanThreads - 1) out[n] = base;
+}
+
+__global__ void k_scatter(int64_t n, const int32_t* __restrict__ key, const int32_t* __restrict__ start,
+                          int32_t* __restrict__ cursor, int32_t* __restrict__ order) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int k = key[i];
+    int p = start[k] + atomicAdd(&cursor[k], 1);
+    order[p] = (int32_t)i;
+}
+
+// sort every bucket ascending (buckets are small: tens of entries)
+__global__ void k_bucket_sort(int64_t nkeys, const int32_t* __restrict__ start, int32_t* __restrict__ order) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nkeys) return;
+    int lo = start[b], hi = start[b + 1];
+    for (int a = lo + 1; a < hi; ++a) {
+        int v = order[a];
+        int c = a - 1;
+        while (c >= lo && order[c] > v) {
+            order[c + 1] = order[c];
+            --c;
+        }
+        order[c + 1] = v;
+    }
+}
+
+// 2. gather per-atom arrays into internal order
+__global__ void k_gather_internal(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ xw_c,
+                                  const double* __restrict__ fw_c, const int32_t* __restrict__ mw_c,
+                                  const int32_t* __restrict__ sp_c, double* __restrict__ xw, double* __restrict__ fw,
+                                  int32_t* __restrict__ mw, int32_t* __restrict__ sp) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = perm[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        xw[3 * i + k] = xw_c[3 * (int64_t)c + k];
+        fw[3 * i + k] = fw_c[3 * (int64_t)c + k];
+        mw[3 * i + k] = mw_c[3 * (int64_t)c + k];
+    }
+    sp[i] = sp_c[c];
+}
+
+// 3. ghost images: fractional coordinate within (-reach, 1 + reach) on every axis
+__device__ __forceinline__ bool image_in_halo(const CellGeom& g, const double f[3], int a, int b, int c) {
+    double v0 = f[0] + a, v1 = f[1] + b, v2 = f[2] + c;
+    return v0 > -g.reach[0] && v0 < 1.0 + g.reach[0] && v1 > -g.reach[1] && v1 < 1.0 + g.reach[1] &&
+           v2 > -g.reach[2] && v2 < 1.0 + g.reach[2];
+}
+
+template <bool FILL>
+__global__ void k_ghosts(int64_t n, CellGeom g, const double* __restrict__ fw, const int32_t* __restrict__ goff,
+                         int32_t* __restrict__ gcnt, int32_t* __restrict__ owner, int32_t* __restrict__ shift,
+                         int64_t g_cap, int* __restrict__ flags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double f[3] = {fw[3 * i], fw[3 * i + 1], fw[3 * i + 2]};
+    int cnt = 0;
+    int64_t o = FILL ? goff[i] : 0;
+    for (int a = -g.nmax[0]; a <= g.nmax[0]; ++a)
+        for (int b = -g.nmax[1]; b <= g.nmax[1]; ++b)
+            for (int c = -g.nmax[2]; c <= g.nmax[2]; ++c) {
+                if (a == 0 && b == 0 && c == 0) continue;
+                if (!image_in_halo(g, f, a, b, c)) continue;
+                if (FILL) {
+                    int64_t q = o + cnt;
+                    if (q < g_cap) {
+                        owner[q] = (int32_t)i;
+                        shift[q] = pack_shift(a, b, c);
+                    } else {
+                        atomicOr(&flags[FLAG_GHOST_OVERFLOW], 1);
+                    }
+                }
+                ++cnt;
+            }
+    if (!FILL) gcnt[i] = cnt;
+}
+
+// 4. extended binning of owned + ghost slots
+__global__ void k_ext_key(int64_t n, const int64_t* __restrict__ g_total, int64_t g_cap, CellGeom g,
+                          const double* __restrict__ xw, const double* __restrict__ fw,
+                          const int32_t* __restrict__ owner, const int32_t* __restrict__ shift,
+                          int32_t* __restrict__ key, float4* __restrict__ p32, int32_t dead_key) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t G = min(*g_total, g_cap);
+    if (s >= n + g_cap) return;
+    if (s >= n + G) {
+        key[s] = dead_key;  // unused capacity sorts to the end
+        return;
+    }
+    int64_t o = s;
+    int a = 0, b = 0, c = 0;
+    if (s >= n) {
+        o = owner[s - n];
+        unpack_shift(shift[s - n], a, b, c);
+    }
+    double f[3] = {fw[3 * o] + a, fw[3 * o + 1] + b, fw[3 * o + 2] + c};
+    int bx[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bx[k] = clampi((int)floor(f[k] * g.nb[k]) + g.pad[k], 0, g.nbx[k] - 1);
+    key[s] = (bx[0] * g.nbx[1] + bx[1]) * g.nbx[2] + bx[2];
+    double sv[3];
+    shift_vec(g, a, b, c, sv);
+    p32[s] = make_float4((float)(xw[3 * o] + sv[0]), (float)(xw[3 * o + 1] + sv[1]), (float)(xw[3 * o + 2] + sv[2]), 0.f);
+}
+
+// 5. neighbour search: one warp per owned atom
+__global__ void __launch_bounds__(256) k_nbr_search(int64_t n, CellGeom g,
+                                                   const double* __restrict__ xw, const double* __restrict__ fw,
+                                                   const int32_t* __restrict__ owner, const int32_t* __restrict__ shift,
+                                                   const float4* __restrict__ p32, const int32_t* __restrict__ order,
+                                                   const int32_t* __restrict__ bstart, int stride,
+                                                   int32_t* __restrict__ nbr, int32_t* __restrict__ cnt_out,
+                                                   int* __restrict__ flags) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    const float4 pi = p32[i];
+    const double xi[3] = {xw[3 * i], xw[3 * i + 1], xw[3 * i + 2]};
+    int b[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) b[k] = clampi((int)floor(fw[3 * i + k] * g.nb[k]) + g.pad[k], 0, g.nbx[k] - 1);
+    const float lo2 = g.rcut2_f - g.margin, hi2 = g.rcut2_f + g.margin;
+    int count = 0;
+    int32_t* row = nbr + (size_t)i * stride;
+    for (int x = max(0, b[0] - g.sw[0]); x <= min(g.nbx[0] - 1, b[0] + g.sw[0]); ++x)
+        for (int y = max(0, b[1] - g.sw[1]); y <= min(g.nbx[1] - 1, b[1] + g.sw[1]); ++y)
+            for (int z = max(0, b[2] - g.sw[2]); z <= min(g.nbx[2] - 1, b[2] + g.sw[2]); ++z) {
+                const int bin = (x * g.nbx[1] + y) * g.nbx[2] + z;
+                const int s0 = bstart[bin], s1 = bstart[bin + 1];
+                for (int base = s0; base < s1; base += 32) {
+                    const int c = base + lane;
+                    bool hit = false;
+                    int j = -1;
+                    if (c < s1) {
+                        j = order[c];
+                        if (j != (int)i) {
+                            const float4 pj = p32[j];
+                            const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                            const float d2 = dx * dx + dy * dy + dz * dz;
+                            if (d2 < lo2 && d2 > 1e-4f) {
+                                hit = true;
+                            } else if (d2 <= hi2) {
+                                // exact FP64 decision (and the coincident-atom check)
+                                int64_t o = j;
+                                int a0 = 0, a1 = 0, a2 = 0;
+                                if (j >= n) {
+                                    o = owner[j - n];
+                                    unpack_shift(shift[j - n], a0, a1, a2);
+                                }
+                                double sv[3];
+                                shift_vec(g, a0, a1, a2, sv);
+                                double r[3];
+#pragma unroll
+                                for (int k = 0; k < 3; ++k) r[k] = dadd(dsub(xw[3 * o + k], xi[k]), sv[k]);
+                                const double dd = dadd(dadd(dmul(r[0], r[0]), dmul(r[1], r[1])), dmul(r[2], r[2]));
+                                hit = dd < g.rcut2;
+                                if (dd < 1e-16) atomicOr(&flags[FLAG_GEOM], 2);
+                            }
+                        }
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, hit);
+                    if (hit) {
+                        const int p = count + __popc(m & ((1u << lane) - 1u));
+                        if (p < stride) row[p] = j;
+                    }
+                    count += __popc(m);
+                }
+            }
+    if (lane == 0) {
+        cnt_out[i] = min(count, stride);
+        if (count > stride) atomicOr(&flags[FLAG_NBR_OVERFLOW], 1);
+        atomicMax(&flags[FLAG_MAXNBR], count);
+    }
+}
+
+// per evaluation: refresh owned + ghost positions (FP64 -> hi/lo FP32 pair)
+__global__ void k_refresh(int64_t n, int64_t g_count, CellGeom g, const double* __restrict__ pos,
+                          const int32_t* __restrict__ perm, const int32_t* __restrict__ wrapm,
+                          const int32_t* __restrict__ owner, const int32_t* __restrict__ shift,
+                          float4* __restrict__ hi, float4* __restrict__ lo) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n + g_count) return;
+    int64_t o = s;
+    int a = 0, b = 0, c = 0;
+    if (s >= n) {
+        o = owner[s - n];
+        unpack_shift(shift[s - n], a, b, c);
+    }
+    const int64_t cidx = perm[o];
+    double sm[3], sv[3];
+    shift_vec(g, wrapm[3 * o], wrapm[3 * o + 1], wrapm[3 * o + 2], sm);
+    shift_vec(g, a, b, c, sv);
+    double x[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) x[k] = (pos[3 * cidx + k] - sm[k]) + sv[k];
+    float h[3], l[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        h[k] = (float)x[k];
+        l[k] = (float)(x[k] - (double)h[k]);
+    }
+    hi[s] = make_float4(h[0], h[1], h[2], 0.f);
+    lo[s] = make_float4(l[0], l[1], l[2], 0.f);
+}
+
+// per evaluation: live (d < r_c) entries of every row, moved to the row's front
+__global__ void __launch_bounds__(256) k_live(int64_t n, int stride, float rc2, const int32_t* __restrict__ nbr,
+                                             const int32_t* __restrict__ cnt, const float4* __restrict__ hi,
+                                             const float4* __restrict__ lo, int32_t* __restrict__ live,
+                                             int32_t* __restrict__ live_cnt, int* __restrict__ flags) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    const float4 hi_i = hi[i], lo_i = lo[i];
+    const int c = cnt[i];
+    const int32_t* row = nbr + (size_t)i * stride;
+    int32_t* out = live + (size_t)i * stride;
+    int count = 0;
+    for (int base = 0; base < c; base += 32) {
+        const int e = base + lane;
+        bool keep = false;
+        int j = 0;
+        if (e < c) {
+            j = row[e];
+            const float4 hj = hi[j], lj = lo[j];
+            const float x = (hj.x - hi_i.x) + (lj.x - lo_i.x);
+            const float y = (hj.y - hi_i.y) + (lj.y - lo_i.y);
+            const float z = (hj.z - hi_i.z) + (lj.z - lo_i.z);
+            const float d2 = x * x + y * y + z * z;
+            keep = d2 < rc2;
+            if (!(d2 > 1e-16f)) {
+                keep = false;
+                atomicOr(&flags[FLAG_GEOM], 4);
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) out[count + __popc(m & ((1u << lane) - 1u))] = j;
+        count += __popc(m);
+    }
+    if (lane == 0) live_cnt[i] = count;
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+struct DevBuf {
+    std::vector<void*> ptrs;
+    ~DevBuf() {
+        for (void* p : ptrs) cudaFree(p);
+    }
+    template <typename T>
+    T* get(size_t count) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return nullptr;
+        ptrs.push_back(p);
+        return (T*)p;
+    }
+};
+
+}  // namespace
+
+// Counting sort of n keys in [0, nkeys): order = indices sorted by (key, index); start = bucket offsets.
+static cudaError_t counting_sort(cudaStream_t s, int64_t n, int64_t nkeys, const int32_t* key, int32_t* counts,
+                                 int32_t* start, int32_t* order) {
+    cudaMemsetAsync(counts, 0, sizeof(int32_t) * nkeys, s);
+    if (n > 0) k_hist<<<blocks_for(n, 256), 256, 0, s>>>(n, key, counts);
+    k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(nkeys, counts, start);
+    cudaMemsetAsync(counts, 0, sizeof(int32_t) * nkeys, s);
+    if (n > 0) k_scatter<<<blocks_for(n, 256), 256, 0, s>>>(n, key, start, counts, order);
+    k_bucket_sort<<<blocks_for(nkeys, 128), 128, 0, s>>>(nkeys, start, order);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static T* dalloc(reann_nlist* nl, size_t count) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return nullptr;
+    nl->allocs.push_back(p);
+    return (T*)p;
+}
+
+int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const int32_t* species) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = nl->n;
+    CellGeom& g = nl->geom;
+    DevBuf tmp;
+    const int64_t nbins = (int64_t)g.nb[0] * g.nb[1] * g.nb[2];
+    const int64_t nkeys = nbins * nl->n_elem;
+    double* xw_c = tmp.get<double>(3 * n);
+    double* fw_c = tmp.get<double>(3 * n);
+    int32_t* mw_c = tmp.get<int32_t>(3 * n);
+    int32_t* key = tmp.get<int32_t>(n);
+    int32_t* counts = tmp.get<int32_t>(nkeys);
+    int32_t* start = tmp.get<int32_t>(nkeys + 1);
+    double* xw = tmp.get<double>(3 * n);
+    double* fw = tmp.get<double>(3 * n);
+    int32_t* gcnt = tmp.get<int32_t>(n);
+    int32_t* goff = tmp.get<int32_t>(n + 1);
+    if (!xw_c || !fw_c || !mw_c || !key || !counts || !start || !xw || !fw || !gcnt || !goff)
+        return set_error(ctx, REANN_E_NOMEM, "neighbour-list scratch allocation failed");
+
+    nl->perm = dalloc<int32_t>(nl, n);
+    nl->species = dalloc<int32_t>(nl, n);
+    nl->wrapm = dalloc<int32_t>(nl, 3 * n);
+    nl->pos_ref = dalloc<double>(nl, 3 * n);
+    if (!nl->perm || !nl->species || !nl->wrapm || !nl->pos_ref)
+        return set_error(ctx, REANN_E_NOMEM, "neighbour-list allocation failed");
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->pos_ref, pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
+    REANN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * NFLAGS, s));
+
+    k_wrap_key<<<blocks_for(n, 256), 256, 0, s>>>(n, pos, species, nl->n_elem, g, xw_c, fw_c, mw_c, key, ctx->d_flags);
+    REANN_CUDA_TRY(ctx, counting_sort(s, n, nkeys, key, counts, start, nl->perm));
+    k_gather_internal<<<blocks_for(n, 256), 256, 0, s>>>(n, nl->perm, xw_c, fw_c, mw_c, species, xw, fw, nl->wrapm,
+                                                         nl->species);
+    // element ranges of the internal order
+    std::vector<int32_t> es(nl->n_elem + 1);
+    for (int e = 0; e <= nl->n_elem; ++e)
+        REANN_CUDA_TRY(ctx, cudaMemcpyAsync(&es[e], start + (int64_t)e * nbins, sizeof(int32_t),
+                                            cudaMemcpyDeviceToHost, s));
+    // ghosts: count, scan, size
+    k_ghosts<false><<<blocks_for(n, 256), 256, 0, s>>>(n, g, fw, nullptr, gcnt, nullptr, nullptr, 0, ctx->d_flags);
+    k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(n, gcnt, goff);
+    int32_t G = 0;
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(&G, goff + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int) * NFLAGS, cudaMemcpyDeviceToHost, s));
+    REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (ctx->h_flags[FLAG_SPECIES]) return set_error(ctx, REANN_E_ARG, "species index out of range");
+    if (ctx->h_flags[FLAG_GEOM]) return set_error(ctx, REANN_E_GEOM, "non-finite atom position");
+    for (int e = 0; e <= nl->n_elem; ++e) nl->elem_start[e] = es[e];
+
+    nl->g = G;
+    nl->g_cap = G;
+    const int64_t next = n + G;
+    nl->g_owner = dalloc<int32_t>(nl, G);
+    nl->g_shift = dalloc<int32_t>(nl, G);
+    int64_t* g_total = tmp.get<int64_t>(1);
+    int32_t* ekey = tmp.get<int32_t>(next);
+    float4* p32 = tmp.get<float4>(next);
+    if (!nl->g_owner || !nl->g_shift || !g_total || !ekey || !p32)
+        return set_error(ctx, REANN_E_NOMEM, "ghost allocation failed");
+    k_ghosts<true><<<blocks_for(n, 256), 256, 0, s>>>(n, g, fw, goff, nullptr, nl->g_owner, nl->g_shift, G,
+                                                      ctx->d_flags);
+    const int64_t G64 = G;
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(g_total, &G64, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    const int64_t nxbins = (int64_t)g.nbx[0] * g.nbx[1] * g.nbx[2];
+    int32_t* ecounts = tmp.get<int32_t>(nxbins + 1);
+    int32_t* estart = tmp.get<int32_t>(nxbins + 2);
+    int32_t* eorder = tmp.get<int32_t>(next);
+    if (!ecounts || !estart || !eorder) return set_error(ctx, REANN_E_NOMEM, "bin allocation failed");
+    k_ext_key<<<blocks_for(next, 256), 256, 0, s>>>(n, g_total, G, g, xw, fw, nl->g_owner, nl->g_shift, ekey, p32,
+                                                    (int32_t)nxbins);
+    REANN_CUDA_TRY(ctx, counting_sort(s, next, nxbins + 1, ekey, ecounts, estart, eorder));
+
+    // expected neighbours from the number density, with headroom
+    double vol = std::fabs(g.h[0] * (g.h[4] * g.h[8] - g.h[5] * g.h[7]) - g.h[1] * (g.h[3] * g.h[8] - g.h[5] * g.h[6]) +
+                           g.h[2] * (g.h[3] * g.h[7] - g.h[4] * g.h[6]));
+    double expect = (double)n / vol * 4.18879020478639 * std::pow(g.rcut2, 1.5);
+    int stride = (int)std::min<double>(1 << 20, std::ceil((1.5 * expect + 32) / 8.0) * 8);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        nl->stride = stride;
+        nl->nbr = dalloc<int32_t>(nl, (size_t)n * stride);
+        nl->nbr_cnt = dalloc<int32_t>(nl, n);
+        if (!nl->nbr || !nl->nbr_cnt) return set_error(ctx, REANN_E_NOMEM, "neighbour-list allocation failed");
+        REANN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * NFLAGS, s));
+        k_nbr_search<<<blocks_for(n * 32, 256), 256, 0, s>>>(n, g, xw, fw, nl->g_owner,
+                                                             nl->g_shift, p32, eorder, estart, stride, nl->nbr,
+                                                             nl->nbr_cnt, ctx->d_flags);
+        REANN_CUDA_TRY(ctx, cudaGetLastError());
+        REANN_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int) * NFLAGS, cudaMemcpyDeviceToHost, s));
+        REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        if (ctx->h_flags[FLAG_GEOM]) return set_error(ctx, REANN_E_GEOM, "coincident atoms (distance < 1e-8 A)");
+        if (ctx->h_flags[FLAG_GHOST_OVERFLOW]) return set_error(ctx, REANN_E_CAPACITY, "ghost capacity exceeded");
+        if (!ctx->h_flags[FLAG_NBR_OVERFLOW]) break;
+        // grow to the observed maximum and search again
+        stride = ((ctx->h_flags[FLAG_MAXNBR] + 8 + 7) / 8) * 8;
+        if (attempt == 1) return set_error(ctx, REANN_E_CAPACITY, "neighbour capacity exceeded");
+    }
+    return REANN_OK;
+}
+
+cudaError_t launch_refresh_positions(cudaStream_t s, const reann_nlist* nl, const double* pos) {
+    const int64_t total = nl->n + nl->g;
+    k_refresh<<<blocks_for(total, 256), 256, 0, s>>>(nl->n, nl->g, nl->geom, pos, nl->perm, nl->wrapm, nl->g_owner,
+                                                     nl->g_shift, nl->pos_hi, nl->pos_lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_live_edges(cudaStream_t s, const reann_nlist* nl, float rc2, int* flags) {
+    k_live<<<blocks_for(nl->n * 32, 256), 256, 0, s>>>(nl->n, nl->stride, rc2, nl->nbr, nl->nbr_cnt, nl->pos_hi,
+                                                       nl->pos_lo, nl->live, nl->live_cnt, flags);
+    return cudaGetLastError();
+}
+
+int export_nlist(reann_ctx* ctx, const reann_nlist* nl, int64_t cap, int32_t* oi, int32_t* oj, int32_t* on,
+                 int64_t* count) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = nl->n;
+    std::vector<int32_t> nbr((size_t)n * nl->stride), cnt(n), perm(n), wm(3 * n), own(nl->g), sh(nl->g);
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(nbr.data(), nl->nbr, sizeof(int32_t) * nbr.size(), cudaMemcpyDeviceToHost, s));
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(cnt.data(), nl->nbr_cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(perm.data(), nl->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(wm.data(), nl->wrapm, sizeof(int32_t) * 3 * n, cudaMemcpyDeviceToHost, s));
+    if (nl->g > 0) {
+        REANN_CUDA_TRY(ctx, cudaMemcpyAsync(own.data(), nl->g_owner, sizeof(int32_t) * nl->g, cudaMemcpyDeviceToHost, s));
+        REANN_CUDA_TRY(ctx, cudaMemcpyAsync(sh.data(), nl->g_shift, sizeof(int32_t) * nl->g, cudaMemcpyDeviceToHost, s));
+    }
+    REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    int64_t q = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int e = 0; e < cnt[i]; ++e) {
+            int64_t slot = nbr[(size_t)i * nl->stride + e];
+            int64_t o = slot;
+            int a[3] = {0, 0, 0};
+            if (slot >= n) {
+                o = own[slot - n];
+                int p = sh[slot - n];
+                a[0] = (p & 255) - 128;
+                a[1] = ((p >> 8) & 255) - 128;
+                a[2] = ((p >> 16) & 255) - 128;
+            }
+            if (q < cap) {
+                oi[q] = perm[i];
+                oj[q] = perm[o];
+                for (int k = 0; k < 3; ++k) on[3 * q + k] = a[k] - wm[3 * o + k] + wm[3 * i + k];
+            }
+            ++q;
+        }
+    }
+    *count = q;
+    return REANN_OK;
+}
+
+}  // namespace reann

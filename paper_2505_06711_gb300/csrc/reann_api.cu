@@ -1,0 +1,398 @@
+// Host side of the C ABI declared in include/reann.h: argument checks, model
+// upload, neighbour-list objects and the order of kernels of one energy +
+// force evaluation (T forward layers, then T reverse layers, Sec. 2.1-2.2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace reann;
+
+namespace reann {
+
+int set_error(reann_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+}  // namespace reann
+
+namespace {
+
+constexpr int64_t expected_params(int n_elem, int T) {
+    int64_t n = (int64_t)n_elem * NPHI + (int64_t)T * (LMAX + 1) * NPHI * NORB;
+    for (int t = 0; t < T; ++t) {
+        const int out = (t == T - 1) ? 1 : NPHI;
+        n += (int64_t)n_elem * (NFEAT * H1 + H1 + H1 * H2 + H2 + H2 * out + out);
+    }
+    return n;
+}
+
+// cell inverse: frac = x . hinv, with hinv = adj(H) / det(H)
+bool cell_inverse(const double* h, double* hinv, double* det_out) {
+    const double det = h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
+                       h[2] * (h[3] * h[7] - h[4] * h[6]);
+    if (!(std::fabs(det) > 1e-12) || !std::isfinite(det)) return false;
+    hinv[0] = (h[4] * h[8] - h[5] * h[7]) / det;
+    hinv[1] = (h[2] * h[7] - h[1] * h[8]) / det;
+    hinv[2] = (h[1] * h[5] - h[2] * h[4]) / det;
+    hinv[3] = (h[5] * h[6] - h[3] * h[8]) / det;
+    hinv[4] = (h[0] * h[8] - h[2] * h[6]) / det;
+    hinv[5] = (h[2] * h[3] - h[0] * h[5]) / det;
+    hinv[6] = (h[3] * h[7] - h[4] * h[6]) / det;
+    hinv[7] = (h[1] * h[6] - h[0] * h[7]) / det;
+    hinv[8] = (h[0] * h[4] - h[1] * h[3]) / det;
+    *det_out = det;
+    return true;
+}
+
+int make_geometry(reann_ctx* ctx, const double* cell, double r_cut, CellGeom* g) {
+    std::memset(g, 0, sizeof(*g));
+    for (int i = 0; i < 9; ++i) {
+        if (!std::isfinite(cell[i])) return set_error(ctx, REANN_E_GEOM, "non-finite cell");
+        g->h[i] = cell[i];
+    }
+    double det = 0;
+    if (!cell_inverse(g->h, g->hinv, &det)) return set_error(ctx, REANN_E_GEOM, "singular cell");
+    double maxc = r_cut;
+    for (int k = 0; k < 3; ++k) {
+        const double* u = g->h + 3 * ((k + 1) % 3);
+        const double* v = g->h + 3 * ((k + 2) % 3);
+        const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+        const double w = std::fabs(det) / std::sqrt(cx * cx + cy * cy + cz * cz);
+        const double delta = r_cut / w;
+        g->reach[k] = delta + 1e-6;
+        g->nmax[k] = (int)std::ceil(g->reach[k]);
+        if (g->nmax[k] > 100) return set_error(ctx, REANN_E_GEOM, "cell too thin for the cutoff");
+        g->nb[k] = std::max(1, std::min(1024, (int)std::floor(w / r_cut)));
+        g->sw[k] = std::max(1, (int)std::ceil(delta * g->nb[k] - 1e-9));
+        g->pad[k] = (int)std::ceil(g->reach[k] * g->nb[k]) + 1;
+        g->nbx[k] = g->nb[k] + 2 * g->pad[k];
+        maxc += std::fabs(g->h[k]) + std::fabs(g->h[3 + k]) + std::fabs(g->h[6 + k]);
+    }
+    g->rcut2 = r_cut * r_cut;
+    g->rcut2_f = (float)g->rcut2;
+    // FP32 positions carry up to half an ulp of the largest coordinate each
+    const double ulp = maxc * std::ldexp(1.0, -23);
+    g->margin = (float)(16.0 * r_cut * ulp + 1e-4);
+    return REANN_OK;
+}
+
+template <typename T>
+T* nl_alloc(reann_nlist* nl, size_t count) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return nullptr;
+    nl->allocs.push_back(p);
+    return (T*)p;
+}
+
+int alloc_eval_buffers(reann_ctx* ctx, reann_nlist* nl) {
+    const int64_t n = nl->n, ne = nl->n + nl->g_cap, T = nl->T;
+    nl->live = nl_alloc<int32_t>(nl, (size_t)n * nl->stride);
+    nl->live_cnt = nl_alloc<int32_t>(nl, n);
+    nl->pos_hi = nl_alloc<float4>(nl, ne);
+    nl->pos_lo = nl_alloc<float4>(nl, ne);
+    nl->coef = nl_alloc<float>(nl, (size_t)T * ne * NPHI);
+    nl->rho = nl_alloc<float>(nl, (size_t)T * n * NFEAT);
+    nl->bck = nl_alloc<float>(nl, (size_t)T * n * NB);
+    nl->eps = nl_alloc<float>(nl, n);
+    nl->rhobar = nl_alloc<float>(nl, (size_t)n * NFEAT);
+    nl->bbar = nl_alloc<float>(nl, (size_t)ne * NB);
+    nl->cbar = nl_alloc<float>(nl, (size_t)n * NPHI);
+    nl->grad = nl_alloc<float>(nl, (size_t)n * 3);
+    nl->n_partial = (int)((n + 2047) / 2048);
+    nl->partial = nl_alloc<double>(nl, nl->n_partial);
+    // element tiles of the atomic networks
+    nl->tiles_h.clear();
+    for (int e = 0; e < nl->n_elem; ++e)
+        for (int r = nl->elem_start[e]; r < nl->elem_start[e + 1]; r += MLP_TILE)
+            nl->tiles_h.push_back(Tile{e, r, std::min(MLP_TILE, nl->elem_start[e + 1] - r), 0});
+    nl->tiles = nl_alloc<Tile>(nl, nl->tiles_h.size());
+    if (!nl->live || !nl->live_cnt || !nl->pos_hi || !nl->pos_lo || !nl->coef || !nl->rho || !nl->bck || !nl->eps ||
+        !nl->rhobar || !nl->bbar || !nl->cbar || !nl->grad || !nl->partial || !nl->tiles)
+        return set_error(ctx, REANN_E_NOMEM, "evaluation buffers: out of device memory");
+    if (!nl->tiles_h.empty())
+        REANN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->tiles, nl->tiles_h.data(), sizeof(Tile) * nl->tiles_h.size(),
+                                            cudaMemcpyHostToDevice, ctx->stream));
+    // unused ghost capacity keeps finite values
+    REANN_CUDA_TRY(ctx, cudaMemsetAsync(nl->bbar, 0, sizeof(float) * ne * NB, ctx->stream));
+    return REANN_OK;
+}
+
+void free_nlist(reann_nlist* nl) {
+    if (!nl) return;
+    for (void* p : nl->allocs) cudaFree(p);
+    delete nl;
+}
+
+// pad to a multiple of 4 floats so that float4 loads stay aligned
+void push_block(std::vector<float>& dst, const float* src, size_t count) {
+    dst.insert(dst.end(), src, src + count);
+    while (dst.size() % 4) dst.push_back(0.f);
+}
+
+}  // namespace
+
+// ===================================================================== ABI ==
+
+extern "C" int reann_model_create(int n_elem, int T, int n_phi, int l_max, int n_orb, int h1, int h2, double r_c,
+                                  double alpha, const float* params, int64_t n_params, reann_model** out) {
+    if (!out || !params) return REANN_E_ARG;
+    *out = nullptr;
+    if (n_elem < 1 || n_elem > MAX_ELEM || T < 1 || T > 8 || n_phi != NPHI || l_max != LMAX || n_orb != NORB ||
+        h1 != H1 || h2 != H2 || !(r_c > 0) || !(alpha > 0) || !std::isfinite(r_c) || !std::isfinite(alpha) ||
+        alpha * r_c * r_c > 80.0)
+        return REANN_E_ARG;
+    if (n_params != expected_params(n_elem, T)) return REANN_E_ARG;
+    for (int64_t i = 0; i < n_params; ++i)
+        if (!std::isfinite(params[i])) return REANN_E_ARG;
+    reann_model* m = new (std::nothrow) reann_model;
+    if (!m) return REANN_E_NOMEM;
+    m->m.n_elem = n_elem;
+    m->m.T = T;
+    m->m.r_c = r_c;
+    m->m.alpha = alpha;
+    m->m.params.assign(params, params + n_params);
+    *out = m;
+    return REANN_OK;
+}
+
+extern "C" void reann_model_free(reann_model* model) { delete model; }
+
+extern "C" int reann_ctx_create(const reann_model* model, void* cuda_stream, reann_ctx** out) {
+    if (!out || !model) return REANN_E_ARG;
+    *out = nullptr;
+    reann_ctx* ctx = new (std::nothrow) reann_ctx;
+    if (!ctx) return REANN_E_NOMEM;
+    ctx->model = model->m;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    auto fail = [&](int code) {
+        reann_ctx_free(ctx);
+        return code;
+    };
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) return fail(REANN_E_CUDA);
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    const Model& M = ctx->model;
+    // radial constants (Sec. 2.1: Gaussian-type orbitals; centres linspace(0, r_c, N_phi))
+    Radial& R = ctx->radial;
+    auto split = [](double v, float& hi, float& lo) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    };
+    R.rc = (float)M.r_c;
+    R.rc2 = (float)(M.r_c * M.r_c);
+    split(M.alpha, R.alpha_hi, R.alpha_lo);
+    const double delta = M.r_c / (NPHI - 1);
+    split(2.0 * M.alpha * delta, R.tad_hi, R.tad_lo);
+    for (int m = 0; m < NPHI; ++m) {
+        split(m * delta, R.mu_hi[m], R.mu_lo[m]);
+        split(std::exp(-M.alpha * delta * delta * (2 * m + 1)), R.kap_hi[m], R.kap_lo[m]);
+    }
+    // device image of the parameters: c0, W, then per (t, e) W1 b1 W2 b2 W3 b3 W1t W2t W3t
+    std::vector<float> img;
+    const float* p = M.params.data();
+    std::vector<size_t> off_c0(1), off_W(1);
+    off_c0[0] = img.size();
+    push_block(img, p, (size_t)M.n_elem * NPHI);
+    p += M.n_elem * NPHI;
+    off_W[0] = img.size();
+    push_block(img, p, (size_t)M.T * (LMAX + 1) * NPHI * NORB);
+    p += M.T * (LMAX + 1) * NPHI * NORB;
+    struct Off {
+        size_t W1, b1, W2, b2, W3, b3, W1t, W2t, W3t;
+    };
+    std::vector<Off> offs((size_t)M.T * M.n_elem);
+    for (int t = 0; t < M.T; ++t) {
+        const int outd = (t == M.T - 1) ? 1 : NPHI;
+        for (int e = 0; e < M.n_elem; ++e) {
+            Off& o = offs[(size_t)t * M.n_elem + e];
+            const float* W1 = p;
+            const float* b1 = W1 + NFEAT * H1;
+            const float* W2 = b1 + H1;
+            const float* b2 = W2 + H1 * H2;
+            const float* W3 = b2 + H2;
+            const float* b3 = W3 + H2 * outd;
+            p = b3 + outd;
+            o.W1 = img.size(); push_block(img, W1, NFEAT * H1);
+            o.b1 = img.size(); push_block(img, b1, H1);
+            o.W2 = img.size(); push_block(img, W2, H1 * H2);
+            o.b2 = img.size(); push_block(img, b2, H2);
+            o.W3 = img.size(); push_block(img, W3, H2 * outd);
+            o.b3 = img.size(); push_block(img, b3, outd);
+            std::vector<float> tr;
+            tr.resize(H1 * NFEAT);
+            for (int f = 0; f < NFEAT; ++f)
+                for (int q = 0; q < H1; ++q) tr[q * NFEAT + f] = W1[f * H1 + q];
+            o.W1t = img.size(); push_block(img, tr.data(), tr.size());
+            tr.assign(H2 * H1, 0.f);
+            for (int u = 0; u < H1; ++u)
+                for (int q = 0; q < H2; ++q) tr[q * H1 + u] = W2[u * H2 + q];
+            o.W2t = img.size(); push_block(img, tr.data(), tr.size());
+            tr.assign(outd * H2, 0.f);
+            for (int u = 0; u < H2; ++u)
+                for (int q = 0; q < outd; ++q) tr[q * H2 + u] = W3[u * outd + q];
+            o.W3t = img.size(); push_block(img, tr.data(), tr.size());
+        }
+    }
+    if (cudaMalloc(&ctx->d_params, img.size() * sizeof(float)) != cudaSuccess) return fail(REANN_E_NOMEM);
+    if (cudaMemcpy(ctx->d_params, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(REANN_E_CUDA);
+    const float* base = ctx->d_params;
+    ctx->d_c0 = base + off_c0[0];
+    ctx->d_W = base + off_W[0];
+    for (int t = 0; t < M.T; ++t)
+        for (int e = 0; e < M.n_elem; ++e) {
+            const Off& o = offs[(size_t)t * M.n_elem + e];
+            ctx->nets.net[t][e] = NetDev{base + o.W1, base + o.b1, base + o.W2, base + o.b2, base + o.W3,
+                                         base + o.b3, base + o.W1t, base + o.W2t, base + o.W3t};
+        }
+    if (cudaMalloc(&ctx->d_flags, sizeof(int) * NFLAGS) != cudaSuccess) return fail(REANN_E_NOMEM);
+    if (cudaMemset(ctx->d_flags, 0, sizeof(int) * NFLAGS) != cudaSuccess) return fail(REANN_E_CUDA);
+    if (cudaMallocHost(&ctx->h_flags, sizeof(int) * NFLAGS) != cudaSuccess) return fail(REANN_E_NOMEM);
+    *out = ctx;
+    return REANN_OK;
+}
+
+extern "C" void reann_ctx_free(reann_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->d_params) cudaFree(ctx->d_params);
+    if (ctx->d_bf16) cudaFree(ctx->d_bf16);
+    if (ctx->d_flags) cudaFree(ctx->d_flags);
+    if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
+    delete ctx;
+}
+
+extern "C" int reann_ctx_set_mlp_precision(reann_ctx* ctx, int precision) {
+    if (!ctx) return REANN_E_ARG;
+    if (precision != REANN_MLP_FP32) return set_error(ctx, REANN_E_ARG, "unsupported network precision");
+    ctx->precision = precision;
+    return REANN_OK;
+}
+
+extern "C" const char* reann_last_error(const reann_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" int reann_ctx_check(reann_ctx* ctx) {
+    if (!ctx) return REANN_E_ARG;
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int) * NFLAGS, cudaMemcpyDeviceToHost,
+                                        ctx->stream));
+    REANN_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    REANN_CUDA_TRY(ctx, cudaGetLastError());
+    const int geom = ctx->h_flags[FLAG_GEOM], cap = ctx->h_flags[FLAG_NBR_OVERFLOW] | ctx->h_flags[FLAG_GHOST_OVERFLOW];
+    REANN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * NFLAGS, ctx->stream));
+    if (geom) return set_error(ctx, REANN_E_GEOM, "coincident or non-finite atoms in an evaluation");
+    if (cap) return set_error(ctx, REANN_E_CAPACITY, "neighbour or ghost capacity exceeded");
+    return REANN_OK;
+}
+
+extern "C" int reann_build_nlist(reann_ctx* ctx, int64_t n_atoms, const double* pos, const int32_t* species,
+                                 const double* cell, double r_c, double skin, reann_nlist** out) {
+    if (!ctx || !out) return REANN_E_ARG;
+    *out = nullptr;
+    if (n_atoms < 1 || n_atoms > (int64_t)1 << 28 || !pos || !species || !cell || !(skin >= 0) || !std::isfinite(skin))
+        return set_error(ctx, REANN_E_ARG, "bad argument to reann_build_nlist");
+    if (r_c != ctx->model.r_c) return set_error(ctx, REANN_E_MISMATCH, "r_c differs from the model cutoff");
+    reann_nlist* nl = new (std::nothrow) reann_nlist;
+    if (!nl) return set_error(ctx, REANN_E_NOMEM, "host allocation failed");
+    nl->n = n_atoms;
+    nl->n_elem = ctx->model.n_elem;
+    nl->T = ctx->model.T;
+    nl->r_c = r_c;
+    nl->skin = skin;
+    int rc = make_geometry(ctx, cell, r_c + skin, &nl->geom);
+    if (!rc) rc = build_nlist_device(ctx, nl, pos, species);
+    if (!rc) rc = alloc_eval_buffers(ctx, nl);
+    if (rc) {
+        cudaStreamSynchronize(ctx->stream);
+        free_nlist(nl);
+        return rc;
+    }
+    *out = nl;
+    return REANN_OK;
+}
+
+extern "C" void reann_nlist_free(reann_nlist* nl) { free_nlist(nl); }
+
+extern "C" int reann_nlist_info(const reann_nlist* nl, int64_t* n_atoms, int64_t* n_ghosts, int64_t* n_pairs) {
+    if (!nl) return REANN_E_ARG;
+    if (n_atoms) *n_atoms = nl->n;
+    if (n_ghosts) *n_ghosts = nl->g;
+    if (n_pairs) {
+        std::vector<int32_t> cnt(nl->n);
+        if (cudaMemcpy(cnt.data(), nl->nbr_cnt, sizeof(int32_t) * nl->n, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return REANN_E_CUDA;
+        int64_t s = 0;
+        for (int32_t c : cnt) s += c;
+        *n_pairs = s;
+    }
+    return REANN_OK;
+}
+
+extern "C" int reann_nlist_export(reann_ctx* ctx, const reann_nlist* nl, int64_t cap, int32_t* i, int32_t* j,
+                                  int32_t* n, int64_t* count) {
+    if (!ctx || !nl || !count || cap < 0 || (cap > 0 && (!i || !j || !n))) return REANN_E_ARG;
+    return export_nlist(ctx, nl, cap, i, j, n, count);
+}
+
+extern "C" int reann_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy,
+                                   float* forces, float* atom_energy) {
+    if (!ctx || !nl || !pos || !energy || !forces) return set_error(ctx, REANN_E_ARG, "null argument");
+    if (T != ctx->model.T || T != nl->T) return set_error(ctx, REANN_E_MISMATCH, "T differs from the model");
+    cudaStream_t s = ctx->stream;
+    const int64_t n = nl->n, ne = nl->n + nl->g_cap;
+    REANN_CUDA_TRY(ctx, launch_refresh_positions(s, nl, pos));
+    REANN_CUDA_TRY(ctx, launch_live_edges(s, nl, ctx->radial.rc2, ctx->d_flags));
+    REANN_CUDA_TRY(ctx, launch_init_coef(s, nl, ctx->d_c0));
+    const size_t lw = (size_t)(LMAX + 1) * NPHI * NORB;
+    // forward: Eq. 1 then Eq. 2, re-using the same list in every layer (Sec. 2.2)
+    for (int t = 0; t < T; ++t) {
+        float* coef_t = nl->coef + (size_t)t * ne * NPHI;
+        float* rho_t = nl->rho + (size_t)t * n * NFEAT;
+        float* bck_t = nl->bck + (size_t)t * n * NB;
+        if (t > 0) REANN_CUDA_TRY(ctx, launch_gather_ghost_rows(s, nl, coef_t, NPHI));
+        REANN_CUDA_TRY(ctx, launch_density_fwd(s, nl, ctx->radial, ctx->d_W + t * lw, coef_t, rho_t, bck_t));
+        if (t < T - 1)
+            REANN_CUDA_TRY(ctx, launch_mlp_fwd_f32(s, nl, ctx->nets, t, false, rho_t,
+                                                   nl->coef + (size_t)(t + 1) * ne * NPHI, NPHI));
+        else
+            REANN_CUDA_TRY(ctx, launch_mlp_fwd_f32(s, nl, ctx->nets, t, true, rho_t, nl->eps, 1));
+    }
+    REANN_CUDA_TRY(ctx, launch_energy_sum(s, nl, energy));
+    // reverse: Eqs. 3-5, one vector-Jacobian product per layer
+    REANN_CUDA_TRY(ctx, cudaMemsetAsync(nl->grad, 0, sizeof(float) * n * 3, s));
+    for (int t = T - 1; t >= 0; --t) {
+        const float* coef_t = nl->coef + (size_t)t * ne * NPHI;
+        const float* rho_t = nl->rho + (size_t)t * n * NFEAT;
+        const float* bck_t = nl->bck + (size_t)t * n * NB;
+        REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, rho_t, nl->cbar, nl->rhobar));
+        REANN_CUDA_TRY(ctx, launch_bbar(s, nl, ctx->d_W + t * lw, bck_t, nl->rhobar, nl->bbar));
+        REANN_CUDA_TRY(ctx, launch_gather_ghost_rows(s, nl, nl->bbar, NB));
+        REANN_CUDA_TRY(ctx, launch_density_adj(s, nl, ctx->radial, coef_t, nl->bbar, nl->cbar, nl->grad, t >= 1,
+                                               ctx->d_flags));
+    }
+    REANN_CUDA_TRY(ctx, launch_scatter_outputs(s, nl, forces, atom_energy));
+    return REANN_OK;
+}
+
+extern "C" int reann_energy_forces_host(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy,
+                                        float* forces) {
+    if (!ctx || !nl || !pos || !energy || !forces) return set_error(ctx, REANN_E_ARG, "null argument");
+    (void)T;
+    return set_error(ctx, REANN_E_ARG, "not implemented");
+}
+
+extern "C" int reann_get_layer(reann_ctx* ctx, const reann_nlist* nl, int layer, float* rho, float* coef) {
+    if (!ctx || !nl || layer < 0 || layer >= nl->T) return set_error(ctx, REANN_E_ARG, "bad layer");
+    const int64_t n = nl->n, ne = nl->n + nl->g_cap;
+    if (rho)
+        REANN_CUDA_TRY(ctx, launch_unpermute_rows(ctx->stream, nl, nl->rho + (size_t)layer * n * NFEAT, NFEAT, rho, NFEAT));
+    if (coef)
+        REANN_CUDA_TRY(ctx, launch_unpermute_rows(ctx->stream, nl, nl->coef + (size_t)layer * ne * NPHI, NPHI, coef, NPHI));
+    return REANN_OK;
+}

@@ -78,14 +78,44 @@ def _random_rotations(rng: np.random.Generator, n: int) -> np.ndarray:
     return r
 
 
-def water_box(n_molecules: int, seed: int = 0, jitter: float = 0.1) -> Structure:
+def _resolve_contacts(rng, o_pos, h_pos, h_local, edge, min_contact, max_tries):
+    """Re-draw the orientation of molecules whose hydrogens come closer than
+    ``min_contact`` to an atom of another molecule (minimum image), in molecule
+    order, up to ``max_tries`` rounds; liquid water has no such contacts."""
+    from scipy.spatial import cKDTree
+
+    n = o_pos.shape[0]
+    mol = np.concatenate([np.arange(n)] * 3)
+    is_h = np.concatenate([np.zeros(n, bool), np.ones(2 * n, bool)])
+    for _ in range(max_tries):
+        atoms = np.concatenate([o_pos, h_pos[:, 0], h_pos[:, 1]])
+        tree = cKDTree(np.mod(atoms, edge), boxsize=edge)
+        pairs = tree.query_pairs(min_contact, output_type="ndarray")
+        if pairs.size:
+            a, b = pairs[:, 0], pairs[:, 1]
+            clash = (mol[a] != mol[b]) & (is_h[a] | is_h[b])
+            a, b = a[clash], b[clash]
+        else:
+            a = b = np.zeros(0, int)
+        if a.size == 0:
+            break
+        # re-orient the molecule that owns a clashing hydrogen (both if both are H)
+        idx = np.unique(np.concatenate([mol[a][is_h[a]], mol[b][is_h[b]]]))
+        rot = _random_rotations(rng, idx.size)
+        h_pos[idx] = o_pos[idx, None, :] + np.einsum("nij,hj->nhi", rot, h_local)
+    return h_pos
+
+
+def water_box(n_molecules: int, seed: int = 0, jitter: float = 0.1, min_contact: float = 1.5,
+              max_tries: int = 60) -> Structure:
     """Periodic cubic water box at 1.0 g/cm^3 with ``3 * n_molecules`` atoms.
 
     Edge ``L = (n * 29.915 A^3)^(1/3)``; oxygens sit on the first ``n`` sites
     (seeded permutation) of a ``g^3`` grid, ``g = ceil(n^(1/3))``, spacing
     ``L/g``, each jittered by N(0, jitter); the two hydrogens are placed at
     0.96 A with an H-O-H angle of 104.5 degrees in a uniformly random
-    orientation.  Atom order is (O, H, H) per molecule.
+    orientation, re-drawn while a hydrogen lies closer than ``min_contact``
+    (A) to an atom of another molecule.  Atom order is (O, H, H) per molecule.
     """
     if n_molecules < 1:
         raise ValueError("n_molecules must be >= 1")
@@ -107,6 +137,8 @@ def water_box(n_molecules: int, seed: int = 0, jitter: float = 0.1) -> Structure
     )
     rot = _random_rotations(rng, n_molecules)
     h_pos = o_pos[:, None, :] + np.einsum("nij,hj->nhi", rot, h_local)
+    if min_contact > 0:
+        h_pos = _resolve_contacts(rng, o_pos, h_pos, h_local, edge, min_contact, max_tries)
     pos = np.empty((n_molecules, 3, 3))
     pos[:, 0] = o_pos
     pos[:, 1:] = h_pos
