@@ -1,0 +1,413 @@
+#!/usr/bin/env python
+"""REANN energy + force throughput on GB300 (atom-evaluations per second, T = 3).
+
+One step is one pass of the whole hot path over the 8,192-molecule periodic
+water box (24,576 atoms, 1.0 g/cm^3, skin 1 A, T = 3): device-side neighbour
+list rebuild (cell list, ghost slots), then the energy/force evaluation
+(T density layers with per-layer ghost refresh, per-element networks, FP64
+energy sum, reverse pass).  Inputs are synthetic (seeded water box, seeded
+random-weight model); the paper's datasets and trained weights are not used.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+* ``value``: atoms x ranks / device time per step, device time from CUDA events
+  around each step on the library's stream; the L2 cache (129 MB) is flushed by
+  writing a 256 MiB buffer before every timed step (outside the events).
+* ``e2e``: the same step through the C ABI with host buffers
+  (``reann_energy_forces_host`` with a forced rebuild): pinned host positions
+  in, host forces and energy out, copies inside the timed region.
+* ``roofline``: the region with the largest device time, its algorithmic FLOPs
+  per launch (counts in the design doc) over its mean launch time, against the FP32
+  SIMT peak of the GPU (SMs x 128 lanes x 2 FLOP x max SM clock).
+* ``cpu_baseline``: the FP64 oracle (test infrastructure) evaluating the same
+  box once on the host cores, rank 0 only.
+* ``--impl reference``: the oracle is the reference arm; each step is one full
+  oracle evaluation of the same box.
+
+With N > 1 (torchrun) every rank runs an independent replica (the path needs
+no data exchange on one structure per GPU); timing is max over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_MOLECULES = 8192
+T_LAYERS = 3
+SKIN = 1.0
+FLUSH_BYTES = 256 << 20
+
+# Algorithmic FP32 FLOPs (FMA = 2) of each timed region, from the formulas of
+# Eq. 1 (forward), Eqs. 3-5 (reverse) and the 48-64-64-{8,1} networks (Eq. 2).
+FLOP_PER_LIVE_EDGE_FWD = 176          # 80 FMA of b += c phi A, 8 c*phi, 8 phi*f_c
+FLOP_PER_ATOM_FWD = 2880              # contraction 10x16x8 FMA + 160 squares
+FLOP_PER_LIVE_EDGE_ADJ = 640          # 80 x (2 FMA combination + 2 FMA radial/angular sums)
+FLOP_PER_LIVE_EDGE_ADJ_CBAR = 160     # 80 FMA of cbar (layers t >= 1)
+FLOP_PER_ATOM_MLP_FWD = {8: 15360, 1: 14464}
+FLOP_PER_ATOM_MLP_BWD = {8: 29696, 1: 28800}
+FLOP_PER_ATOM_BBAR = 5440             # g (1280 FMA) + gbar (160) + bbar (1280 FMA)
+
+# DRAM traffic per launch of the dominant kernel from one ncu capture of this
+# workload (profiles/), valid only for the source it was taken on.
+TRAFFIC = {  # {(region, sha1[:12] of the kernel source): bytes per launch}
+    ("density_adj", "b631ded605f6"): 21508608,  # profiles/density_adj_water24576_T3.md
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """Largest value of x over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(n_atoms_per_rank: int, ms_per_step: float, ws: int) -> float:
+    """Whole-job atom-evaluations per second: every rank evaluates its own replica."""
+    return ws * n_atoms_per_rank / (ms_per_step * 1e-3)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = (
+        "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+        "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+    )
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL,
+            )
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {
+            "sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons,
+            "samples": len(rows),
+        }
+
+
+def source_sha(name: str) -> str:
+    path = os.path.join(ROOT, "paper_2505_06711_gb300", "csrc", name)
+    return hashlib.sha1(open(path, "rb").read()).hexdigest()[:12]
+
+
+REGION_SOURCE = {
+    "density_fwd": "density.cu", "density_adj": "density.cu", "bbar": "density.cu", "mlp_fwd": "mlp_fp32.cu",
+    "mlp_bwd": "mlp_fp32.cu", "nlist_rebuild": "nlist.cu", "live_edges": "nlist.cu",
+}
+
+
+def region_flops(region: str, n_atoms: int, n_live: int, T: int, launches: int) -> float | None:
+    """Algorithmic FLOPs of all launches of one region in one step."""
+    if region == "density_fwd":
+        return T * (n_live * FLOP_PER_LIVE_EDGE_FWD + n_atoms * FLOP_PER_ATOM_FWD)
+    if region == "density_adj":
+        return T * n_live * FLOP_PER_LIVE_EDGE_ADJ + (T - 1) * n_live * FLOP_PER_LIVE_EDGE_ADJ_CBAR
+    if region == "mlp_fwd":
+        return n_atoms * ((T - 1) * FLOP_PER_ATOM_MLP_FWD[8] + FLOP_PER_ATOM_MLP_FWD[1])
+    if region == "mlp_bwd":
+        return n_atoms * ((T - 1) * FLOP_PER_ATOM_MLP_BWD[8] + FLOP_PER_ATOM_MLP_BWD[1])
+    if region == "bbar":
+        return T * n_atoms * FLOP_PER_ATOM_BBAR
+    return None
+
+
+def launches_per_step(T: int) -> int:
+    """Library kernels per step: rebuild 15, evaluation 3 + (3T - 1) + 2 + 4T + 1."""
+    return 15 + 3 + (3 * T - 1) + 2 + 4 * T + 1
+
+
+def cpu_baseline(structure, spec):
+    import oracle
+
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < 4 and (time.perf_counter() - t_start) < 10.0:
+        t0 = time.perf_counter()
+        oracle.energy_forces(spec, structure.pos, structure.species, structure.cell, n_threads=cores)
+        times.append(time.perf_counter() - t0)
+    t = statistics.mean(times)
+    return {
+        "value": structure.n_atoms / t,
+        "unit": "atom-evals/s",
+        "cores": cores,
+        "kind": "oracle",
+        "sample": f"{len(times)} full FP64 evaluations (brute-force list + forward + reverse) of the "
+                  f"{structure.n_atoms}-atom water box, mean {t:.2f} s each",
+    }
+
+
+def base_line(args, ws, value, ms, dtype):
+    return {
+        "metric": "energy+force atom-evals/s at T=3",
+        "value": value,
+        "unit": "atom-evals/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": dtype,
+        "data": "synthetic (seeded water box, seeded random-weight REANN model)",
+        "config": {
+            "workload": f"water box {N_MOLECULES} H2O ({3 * N_MOLECULES} atoms), 1.0 g/cm^3, T={T_LAYERS}, "
+                        f"r_c=5 A, skin={SKIN} A, 8 Gaussians, L=2, 16 orbitals, networks 48-64-64 SiLU",
+            "atoms_per_gpu": 3 * N_MOLECULES,
+            "step": "device neighbour-list rebuild + energy/forces (forward T layers + reverse)",
+            "cache": "L2 flushed (256 MiB write) before every timed step",
+            "parallelism": f"replicas x{ws}",
+        },
+    }
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from synth import make_model, water_box
+
+    s = water_box(N_MOLECULES, seed=0)
+    spec = make_model(T=T_LAYERS)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    for _ in range(args.warmup):
+        oracle.energy_forces(spec, s.pos, s.species, s.cell, n_threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.energy_forces(spec, s.pos, s.species, s.cell, n_threads=cores)
+        times.append(time.perf_counter() - t0)
+    t = statistics.mean(times)
+    value = s.n_atoms / t
+    line = base_line(args, 1, value, t * 1e3, "f64")
+    line["impl"] = "reference"
+    line["config"]["step"] = "one FP64 oracle evaluation (brute-force list + forward + reverse) on the host cores"
+    line["cpu_baseline"] = {"value": value, "unit": "atom-evals/s", "cores": cores, "kind": "oracle",
+                            "sample": f"full {s.n_atoms}-atom box per step, {args.steps} steps"}
+    line["e2e"] = {"value": value, "unit": "atom-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2505_06711_gb300 import Potential, binding
+    from synth import make_model, water_box
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    s = water_box(N_MOLECULES, seed=0)
+    spec = make_model(T=T_LAYERS)
+    pot = Potential(spec)
+    sy = pot.system(s.pos, s.species, s.cell, skin=SKIN)
+    ctx, nl = pot.ctx, sy.nl
+    pos = sy.pos
+    energy = torch.zeros(1, dtype=torch.float64, device="cuda")
+    forces = torch.zeros((s.n_atoms, 3), dtype=torch.float32, device="cuda")
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        binding.reann_nlist_rebuild(ctx, nl, pos)
+        binding.reann_energy_forces(ctx, nl, pos, T_LAYERS, energy, forces, None)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    binding.reann_ctx_check(ctx)
+    n_atoms, n_ghosts, n_pairs, n_live = binding.reann_nlist_info(nl)
+
+    def timed(profile: bool):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        binding.reann_ctx_profile(ctx, profile)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if dist:
+            dist.barrier()
+        prof = binding.reann_ctx_profile_read(ctx)
+        binding.reann_ctx_profile(ctx, False)
+        binding.reann_ctx_check(ctx)
+        return sum(a.elapsed_time(b) for a, b in ev) / args.steps, wall, prof
+
+    # pass 1: the reported step time (no per-region events); pass 2: per-region events for the roofline
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, wall, _ = timed(False)
+    clk = clocks.stop()
+    ms_prof, _, prof = timed(True)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = aggregate(n_atoms, ms, ws)
+
+    # roofline of the dominant region
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    region, (tot_ms, nl_launch) = dom
+    per_step_ms = tot_ms / args.steps
+    launches = nl_launch / args.steps
+    flops = region_flops(region, n_atoms, n_live, T_LAYERS, launches)
+    props = torch.cuda.get_device_properties(local)
+    max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak_tflops = props.multi_processor_count * 128 * 2 * max_mhz * 1e6 / 1e12
+    roof = None
+    if flops is not None and launches > 0:
+        achieved = flops / launches / (per_step_ms / launches * 1e-3) / 1e12
+        key = (region, source_sha(REGION_SOURCE.get(region, "density.cu")))
+        roof = {
+            "bound": "alu",
+            "kernel": region,
+            "achieved": achieved,
+            "peak": peak_tflops,
+            "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops,
+            "traffic": TRAFFIC.get(key),
+            "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 FLOP x {max_mhz:.0f} MHz",
+            "launches_per_step": launches,
+            "mean_launch_ms": per_step_ms / launches,
+            "timed_in": "second timed pass of the same steps with per-region CUDA events on the library stream",
+            "ms_per_step_with_events": ms_prof,
+        }
+    breakdown = {k: round(v[0] / args.steps, 5) for k, v in prof.items() if v[1]}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_pos = torch.from_numpy(np.ascontiguousarray(s.pos)).pin_memory()
+        h_en = torch.zeros(1, dtype=torch.float64).pin_memory()
+        h_f = torch.zeros((s.n_atoms, 3), dtype=torch.float32).pin_memory()
+        for _ in range(args.warmup):
+            binding.reann_energy_forces_host(ctx, nl, h_pos, T_LAYERS, h_en, h_f, 1)
+        tt = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            binding.reann_energy_forces_host(ctx, nl, h_pos, T_LAYERS, h_en, h_f, 1)
+            tt.append(time.perf_counter() - t1)
+        e_ms = statistics.mean(tt) * 1e3
+        e_ms = max_over_ranks(e_ms, dist, "cuda")
+        e2e = {
+            "value": aggregate(n_atoms, e_ms, ws),
+            "unit": "atom-evals/s",
+            "ms_per_step": e_ms,
+            "h2d_bytes_per_step": int(h_pos.numel() * 8),
+            "d2h_bytes_per_step": int(h_f.numel() * 4 + 8),
+        }
+
+    if rank == 0:
+        line = base_line(args, ws, value, ms, "f32")
+        line["e2e"] = e2e
+        line["roofline"] = roof
+        line["gpu_launches"] = launches_per_step(T_LAYERS) * args.steps
+        line["clocks"] = clk
+        line["wall_s_timed_region"] = wall
+        line["breakdown_ms_per_step"] = breakdown
+        line["structure"] = {"atoms": n_atoms, "ghosts": n_ghosts, "pairs_rc_skin": n_pairs, "pairs_rc": n_live}
+        line["energy_eV"] = float(energy.item())
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(s, spec)
+        print(json.dumps(line), flush=True)
+    sy.close()
+    pot.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    from paper_2505_06711_gb300 import build
+
+    build.build()  # no-op when up to date
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

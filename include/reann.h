@@ -133,8 +133,23 @@ int reann_build_nlist(reann_ctx* ctx, int64_t n_atoms, const double* pos, const 
                       double r_c, double skin, reann_nlist** out);
 void reann_nlist_free(reann_nlist* nl);
 
-/* Sizes: atoms, ghost slots and listed (i, j, n) entries (host outputs, nullable). */
-int reann_nlist_info(const reann_nlist* nl, int64_t* n_atoms, int64_t* n_ghosts, int64_t* n_pairs);
+/*
+ * Rebuild the list of `nl` for new positions (dev, N x 3 FP64) on the device,
+ * re-using the capacities sized by reann_build_nlist: no allocation and no
+ * host synchronisation, so it can be enqueued between evaluations or inside
+ * a captured CUDA graph.  Same pair definition as reann_build_nlist.  If atom
+ * motion needs more ghost slots or row entries than were sized, the affected
+ * entries are dropped and reann_ctx_check() reports REANN_E_CAPACITY; build a
+ * new list then.  Asynchronous.  Errors: REANN_E_ARG, REANN_E_CUDA.
+ */
+int reann_nlist_rebuild(reann_ctx* ctx, reann_nlist* nl, const double* pos);
+
+/*
+ * Sizes (host outputs, each nullable): atoms, ghost slots in use, listed
+ * (i, j, n) entries within r_c + skin, and the entries within r_c found by the
+ * last evaluation (0 before the first).  Synchronous.
+ */
+int reann_nlist_info(const reann_nlist* nl, int64_t* n_atoms, int64_t* n_ghosts, int64_t* n_pairs, int64_t* n_live);
 
 /*
  * Copy the list to host arrays as (i, j, n) triples in the caller's atom
@@ -163,13 +178,32 @@ int reann_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int 
 
 /*
  * Same as reann_energy_forces with HOST buffers: copies pos (host, N x 3
- * FP64) to the device, rebuilds the neighbour list when any atom moved more
- * than skin/2 since the last build, evaluates, and copies energy (host, 1
- * FP64) and forces (host, N x 3 FP32) back.  Synchronous.  Pinned host memory
- * makes the copies asynchronous DMA; pageable memory works but is slower.
+ * FP64) to the device, rebuilds the neighbour list on the device (always if
+ * `rebuild` is non-zero, otherwise only when an atom moved more than skin/2
+ * since the last build), evaluates, and copies energy (host, 1 FP64) and
+ * forces (host, N x 3 FP32, caller order) back.  Synchronous; includes the
+ * reann_ctx_check() of the evaluation.  Pinned host memory makes the copies
+ * DMA transfers; pageable memory works but is slower.
  */
 int reann_energy_forces_host(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy,
-                             float* forces);
+                             float* forces, int rebuild);
+
+/* ------------------------------------------------------------- profiling --- */
+
+/*
+ * Per-region event profile: when enabled, every region of the evaluation
+ * (neighbour rebuild, position refresh, live-edge filter, coefficient init,
+ * ghost gathers, density forward, networks forward, energy sum, networks
+ * backward, bbar, density adjoint, output scatter) is bracketed by CUDA events
+ * on the context's stream.  Enabling or disabling resets the totals.
+ * reann_ctx_profile_read() waits for the stream and writes, per region, the
+ * summed device time (ms) and the number of timed launches into arrays of
+ * reann_profile_regions() entries; reann_profile_region_name() names them.
+ */
+int reann_ctx_profile(reann_ctx* ctx, int enable);
+int reann_profile_regions(void);
+const char* reann_profile_region_name(int region);
+int reann_ctx_profile_read(reann_ctx* ctx, double* total_ms, int64_t* launches);
 
 /*
  * Per-layer intermediates of the last evaluation of `nl`, in caller order

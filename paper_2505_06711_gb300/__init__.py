@@ -71,9 +71,13 @@ class System:
         self.forces = torch.zeros((self.n, 3), dtype=torch.float32, device=pot.device)
         self.atom_energy = torch.zeros(self.n, dtype=torch.float32, device=pot.device)
 
-    def rebuild(self) -> None:
-        binding.reann_nlist_free(self.nl)
-        self.nl = binding.reann_build_nlist(self.pot.ctx, self.pos, self.species, self.cell, self.pot.r_c, self.skin)
+    def rebuild(self, pos=None) -> None:
+        """Enqueue a device-side neighbour-list rebuild at ``pos`` (default: the build positions)."""
+        binding.reann_nlist_rebuild(self.pot.ctx, self.nl, self.pos if pos is None else pos)
+
+    def evaluate_host(self, pos, energy, forces, rebuild: bool = False) -> None:
+        """Host-buffer evaluation (synchronous): copies in, rebuilds if needed, evaluates, copies out."""
+        binding.reann_energy_forces_host(self.pot.ctx, self.nl, pos, self.pot.T, energy, forces, int(rebuild))
 
     def evaluate(self, pos=None, atom_energy: bool = True) -> None:
         """Enqueue one energy + force evaluation (results in .energy/.forces/.atom_energy)."""

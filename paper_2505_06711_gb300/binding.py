@@ -56,11 +56,16 @@ _SIGS = {
     "reann_ctx_check": ([_vp], _int),
     "reann_build_nlist": ([_vp, _i64, _vp, _vp, _vp, _dbl, _dbl, ctypes.POINTER(_vp)], _int),
     "reann_nlist_free": ([_vp], None),
-    "reann_nlist_info": ([_vp, _vp, _vp, _vp], _int),
+    "reann_nlist_info": ([_vp, _vp, _vp, _vp, _vp], _int),
     "reann_nlist_export": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp], _int),
     "reann_energy_forces": ([_vp, _vp, _vp, _int, _vp, _vp, _vp], _int),
-    "reann_energy_forces_host": ([_vp, _vp, _vp, _int, _vp, _vp], _int),
+    "reann_energy_forces_host": ([_vp, _vp, _vp, _int, _vp, _vp, _int], _int),
     "reann_get_layer": ([_vp, _vp, _int, _vp, _vp], _int),
+    "reann_nlist_rebuild": ([_vp, _vp, _vp], _int),
+    "reann_ctx_profile": ([_vp, _int], _int),
+    "reann_profile_regions": ([], _int),
+    "reann_profile_region_name": ([_int], ctypes.c_char_p),
+    "reann_ctx_profile_read": ([_vp, _vp, _vp], _int),
 }
 
 
@@ -173,10 +178,11 @@ def reann_nlist_free(nl) -> None:
     lib().reann_nlist_free(nl)
 
 
-def reann_nlist_info(nl) -> tuple[int, int, int]:
-    a, g, p = (np.zeros(1, np.int64) for _ in range(3))
-    _check(lib().reann_nlist_info(nl, _ptr(a), _ptr(g), _ptr(p)))
-    return int(a[0]), int(g[0]), int(p[0])
+def reann_nlist_info(nl) -> tuple[int, int, int, int]:
+    """(atoms, ghost slots, listed pairs within r_c + skin, live pairs within r_c of the last evaluation)."""
+    a, g, p, v = (np.zeros(1, np.int64) for _ in range(4))
+    _check(lib().reann_nlist_info(nl, _ptr(a), _ptr(g), _ptr(p), _ptr(v)))
+    return int(a[0]), int(g[0]), int(p[0]), int(v[0])
 
 
 def reann_nlist_export(ctx, nl):
@@ -204,12 +210,45 @@ def reann_energy_forces(ctx, nl, pos, T: int, energy, forces, atom_energy=None) 
     _check(lib().reann_energy_forces(ctx, nl, _ptr(pos), int(T), _ptr(energy), _ptr(forces), _ptr(atom_energy)), ctx)
 
 
-def reann_energy_forces_host(ctx, nl, pos: np.ndarray, T: int, energy: np.ndarray, forces: np.ndarray) -> None:
-    for a, dt in ((pos, np.float64), (energy, np.float64), (forces, np.float32)):
-        if not isinstance(a, np.ndarray) or a.dtype != dt or not a.flags.c_contiguous:
-            raise TypeError("host buffers must be contiguous numpy arrays (pos f64, energy f64, forces f32)")
-    _check(lib().reann_energy_forces_host(ctx, nl, _ptr(pos), int(T), _ptr(energy), _ptr(forces)), ctx)
+def reann_energy_forces_host(ctx, nl, pos, T: int, energy, forces, rebuild: int = 0) -> None:
+    """Host buffers: numpy arrays or pinned CPU torch tensors (pos f64 N x 3, energy f64 [1], forces f32 N x 3)."""
+    for a in (pos, energy, forces):
+        if isinstance(a, np.ndarray):
+            if not a.flags.c_contiguous:
+                raise TypeError("host buffers must be contiguous")
+        elif getattr(a, "is_cuda", True) or not a.is_contiguous():
+            raise TypeError("host buffers must be contiguous numpy arrays or CPU tensors")
+    _check(lib().reann_energy_forces_host(ctx, nl, _ptr(pos), int(T), _ptr(energy), _ptr(forces), int(rebuild)), ctx)
 
 
 def reann_get_layer(ctx, nl, layer: int, rho=None, coef=None) -> None:
     _check(lib().reann_get_layer(ctx, nl, int(layer), _ptr(rho), _ptr(coef)), ctx)
+
+
+def reann_nlist_rebuild(ctx, nl, pos) -> None:
+    import torch
+
+    _dev(pos, torch.float64, None, "pos")
+    _check(lib().reann_nlist_rebuild(ctx, nl, _ptr(pos)), ctx)
+
+
+# --------------------------------------------------------------- profiling --
+def reann_ctx_profile(ctx, enable: bool) -> None:
+    _check(lib().reann_ctx_profile(ctx, int(bool(enable))), ctx)
+
+
+def reann_profile_regions() -> int:
+    return int(lib().reann_profile_regions())
+
+
+def reann_profile_region_name(region: int) -> str:
+    return lib().reann_profile_region_name(int(region)).decode()
+
+
+def reann_ctx_profile_read(ctx) -> dict:
+    """{region name: (total ms, launches)} since profiling was enabled (synchronous)."""
+    k = reann_profile_regions()
+    ms = np.zeros(k, np.float64)
+    cnt = np.zeros(k, np.int64)
+    _check(lib().reann_ctx_profile_read(ctx, _ptr(ms), _ptr(cnt)), ctx)
+    return {reann_profile_region_name(r): (float(ms[r]), int(cnt[r])) for r in range(k)}

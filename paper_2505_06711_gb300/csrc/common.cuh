@@ -29,7 +29,32 @@ constexpr int MLP_TILE = 64;  // rows per FP32 network tile
 // l(a), multinomial weight l!/(lx! ly! lz!) and parity (-1)^l.
 
 // Device-side error flags (ctx->d_flags)
-enum Flag { FLAG_GEOM = 0, FLAG_NBR_OVERFLOW = 1, FLAG_GHOST_OVERFLOW = 2, FLAG_MAXNBR = 3, FLAG_SPECIES = 4, NFLAGS = 8 };
+enum Flag {
+    FLAG_GEOM = 0,
+    FLAG_NBR_OVERFLOW = 1,
+    FLAG_GHOST_OVERFLOW = 2,
+    FLAG_MAXNBR = 3,
+    FLAG_SPECIES = 4,
+    FLAG_MOVED = 5,
+    NFLAGS = 8
+};
+
+// Named regions of the optional per-kernel event profile (reann_ctx_profile).
+enum ProfRegion {
+    PR_REBUILD = 0,
+    PR_REFRESH,
+    PR_LIVE,
+    PR_INIT,
+    PR_GATHER,
+    PR_DENSITY_FWD,
+    PR_MLP_FWD,
+    PR_ENERGY,
+    PR_MLP_BWD,
+    PR_BBAR,
+    PR_DENSITY_ADJ,
+    PR_OUTPUT,
+    PR_COUNT
+};
 
 // Constants of the radial basis, passed by value to kernels.  Constants that
 // enter every edge identically are split into a float pair (hi + lo) so that
@@ -86,6 +111,17 @@ struct Tile {
     int elem, row0, nrows, pad;
 };
 
+// Resident scratch of the neighbour build, kept so that rebuilds neither
+// allocate nor synchronise.
+struct NlistScratch {
+    double *xw_c = nullptr, *fw_c = nullptr, *xw = nullptr, *fw = nullptr;  // wrapped Cartesian / fractional
+    int32_t *mw_c = nullptr, *key = nullptr, *counts = nullptr, *start = nullptr;
+    int32_t *gcnt = nullptr, *goff = nullptr;  // ghosts per atom and offsets; goff[n] = ghost count
+    int32_t* species_c = nullptr;              // caller-order species
+    int32_t *ekey = nullptr, *ecounts = nullptr, *estart = nullptr, *eorder = nullptr;
+    float4* p32 = nullptr;  // FP32 positions of owned + ghost slots for the pre-test
+};
+
 }  // namespace reann
 
 struct reann_model {
@@ -125,6 +161,11 @@ struct reann_nlist {
     float* grad = nullptr;         // N x 3
     double* partial = nullptr;     // energy partial sums
     int n_partial = 0;
+    reann::NlistScratch w;
+    // host-buffer entry point staging
+    double* h2d_pos = nullptr;     // N x 3
+    double* d_energy = nullptr;    // 1
+    float* d_forces = nullptr;     // N x 3
     std::vector<void*> allocs;
 };
 
@@ -143,6 +184,12 @@ struct reann_ctx {
     int* h_flags = nullptr;        // pinned mirror
     std::string err;
     int num_sms = 0;
+    // optional per-region event profile
+    bool prof_on = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[reann::PR_COUNT] = {0};
+    int64_t prof_n[reann::PR_COUNT] = {0};
 };
 
 namespace reann {
@@ -159,6 +206,9 @@ int set_error(reann_ctx* ctx, int code, const std::string& msg);
 // ---- launchers (defined in the .cu files) ----
 // neighbour list (nlist.cu)
 int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const int32_t* species);
+cudaError_t launch_rebuild(cudaStream_t s, reann_nlist* nl, const double* pos, int* flags);
+cudaError_t launch_moved(cudaStream_t s, const reann_nlist* nl, const double* pos, int* flags);
+const int32_t* ghost_count_ptr(const reann_nlist* nl);
 cudaError_t launch_refresh_positions(cudaStream_t s, const reann_nlist* nl, const double* pos);
 cudaError_t launch_live_edges(cudaStream_t s, const reann_nlist* nl, float rc2, int* flags);
 int export_nlist(reann_ctx* ctx, const reann_nlist* nl, int64_t cap, int32_t* i, int32_t* j, int32_t* n, int64_t* count);

@@ -386,10 +386,16 @@ __global__ void __launch_bounds__(kWarps * 32) k_density_adj(int64_t n, int stri
 }
 
 // ------------------------------------------------------- small kernels ---
-__global__ void k_init_coef(int64_t n, int64_t g, const int32_t* __restrict__ species,
-                            const int32_t* __restrict__ owner, const float* __restrict__ c0, float* __restrict__ coef) {
+__device__ __forceinline__ int64_t ghosts_in_use(const int32_t* g_count, int64_t g_cap) {
+    const int64_t g = *g_count;
+    return g < g_cap ? g : g_cap;
+}
+
+__global__ void k_init_coef(int64_t n, const int32_t* __restrict__ g_count, int64_t g_cap,
+                            const int32_t* __restrict__ species, const int32_t* __restrict__ owner,
+                            const float* __restrict__ c0, float* __restrict__ coef) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n + g) return;
+    if (s >= n + ghosts_in_use(g_count, g_cap)) return;
     const int64_t o = s < n ? s : owner[s - n];
     const int e = species[o];
     const float4* src = reinterpret_cast<const float4*>(c0 + e * NPHI);
@@ -399,9 +405,10 @@ __global__ void k_init_coef(int64_t n, int64_t g, const int32_t* __restrict__ sp
 }
 
 // ghost rows <- owner rows (the per-layer ghost refresh of Fig. 4a), width in floats, multiple of 4
-__global__ void k_gather_rows(int64_t n, int64_t g, int w4, const int32_t* __restrict__ owner, float* __restrict__ base) {
+__global__ void k_gather_rows(int64_t n, const int32_t* __restrict__ g_count, int64_t g_cap, int w4,
+                              const int32_t* __restrict__ owner, float* __restrict__ base) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= g * w4) return;
+    if (t >= ghosts_in_use(g_count, g_cap) * w4) return;
     const int64_t gi = t / w4;
     const int c = (int)(t - gi * w4);
     float4* b = reinterpret_cast<float4*>(base);
@@ -469,15 +476,17 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 }  // namespace
 
 cudaError_t launch_init_coef(cudaStream_t s, const reann_nlist* nl, const float* c0) {
-    const int64_t total = nl->n + nl->g;
-    k_init_coef<<<blocks_for(total, 256), 256, 0, s>>>(nl->n, nl->g, nl->species, nl->g_owner, c0, nl->coef);
+    const int64_t total = nl->n + nl->g_cap;
+    k_init_coef<<<blocks_for(total, 256), 256, 0, s>>>(nl->n, ghost_count_ptr(nl), nl->g_cap, nl->species, nl->g_owner,
+                                                       c0, nl->coef);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather_ghost_rows(cudaStream_t s, const reann_nlist* nl, float* base, int width) {
-    if (nl->g == 0) return cudaSuccess;
+    if (nl->g_cap == 0) return cudaSuccess;
     const int w4 = width / 4;
-    k_gather_rows<<<blocks_for(nl->g * w4, 256), 256, 0, s>>>(nl->n, nl->g, w4, nl->g_owner, base);
+    k_gather_rows<<<blocks_for(nl->g_cap * w4, 256), 256, 0, s>>>(nl->n, ghost_count_ptr(nl), nl->g_cap, w4,
+                                                                  nl->g_owner, base);
     return cudaGetLastError();
 }
 

@@ -6,7 +6,7 @@
 // N..N+G-1: every periodic image that lies within r_c + skin of the cell,
 // pointing at its owner atom and carrying an integer image shift.
 //
-// Build (all deterministic, no host round trip except for sizes):
+// Build (all deterministic):
 //   1. wrap positions into the cell in FP64 and key every atom by
 //      (element, cell bin);
 //   2. counting sort by key -> internal order (element-major so the atomic
@@ -17,6 +17,9 @@
 //   5. warp per owned atom: scan the stencil bins, FP32 pre-test with a
 //      margin, FP64 exact test for pairs near r_c + skin, ballot-compacted
 //      writes into a fixed-stride row.
+// The first build sizes the ghost and row capacities (one host round trip);
+// every later rebuild re-runs the same kernels into the resident buffers
+// without allocating or synchronising, so it can sit inside a CUDA graph.
 // The FP64 test follows one fixed arithmetic order (no FMA contraction):
 //   r = (x_w,o - x_w,i) + S(n), S(n)_d = (n0 H0d + n1 H1d) + n2 H2d,
 //   d^2 = (r0 r0 + r1 r1) + r2 r2 < (r_c + skin)^2.
@@ -51,6 +54,12 @@ __device__ __forceinline__ void unpack_shift(int p, int& a, int& b, int& c) {
     a = (p & 255) - 128;
     b = ((p >> 8) & 255) - 128;
     c = ((p >> 16) & 255) - 128;
+}
+
+// ghosts in use: the device count clamped to the capacity
+__device__ __forceinline__ int64_t ghosts_in_use(const int32_t* g_count, int64_t g_cap) {
+    const int64_t g = *g_count;
+    return g < g_cap ? g : g_cap;
 }
 
 // 1. wrap + key (caller order)
@@ -110,7 +119,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_single(int64_t n, const T
     const int64_t lo = tid * chunk, hi = min(n, lo + chunk);
     T local = 0;
     for (int64_t i = lo; i < hi; ++i) local += in[i];
-    // block-wide exclusive scan of `local`
     T v = local;
     const int lane = tid & 31, w = tid >> 5;
 #pragma unroll
@@ -215,16 +223,17 @@ __global__ void k_ghosts(int64_t n, CellGeom g, const double* __restrict__ fw, c
     if (!FILL) gcnt[i] = cnt;
 }
 
-// 4. extended binning of owned + ghost slots
-__global__ void k_ext_key(int64_t n, const int64_t* __restrict__ g_total, int64_t g_cap, CellGeom g,
+// 4. extended binning of owned + ghost slots (unused ghost capacity sorts last)
+__global__ void k_ext_key(int64_t n, const int32_t* __restrict__ g_count, int64_t g_cap, CellGeom g,
                           const double* __restrict__ xw, const double* __restrict__ fw,
                           const int32_t* __restrict__ owner, const int32_t* __restrict__ shift,
                           int32_t* __restrict__ key, float4* __restrict__ p32, int32_t dead_key) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t G = min(*g_total, g_cap);
     if (s >= n + g_cap) return;
+    const int64_t G = ghosts_in_use(g_count, g_cap);
     if (s >= n + G) {
-        key[s] = dead_key;  // unused capacity sorts to the end
+        key[s] = dead_key;
+        p32[s] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
     int64_t o = s;
@@ -244,12 +253,11 @@ __global__ void k_ext_key(int64_t n, const int64_t* __restrict__ g_total, int64_
 }
 
 // 5. neighbour search: one warp per owned atom
-__global__ void __launch_bounds__(256) k_nbr_search(int64_t n, CellGeom g,
-                                                   const double* __restrict__ xw, const double* __restrict__ fw,
-                                                   const int32_t* __restrict__ owner, const int32_t* __restrict__ shift,
-                                                   const float4* __restrict__ p32, const int32_t* __restrict__ order,
-                                                   const int32_t* __restrict__ bstart, int stride,
-                                                   int32_t* __restrict__ nbr, int32_t* __restrict__ cnt_out,
+__global__ void __launch_bounds__(256) k_nbr_search(int64_t n, CellGeom g, const double* __restrict__ xw,
+                                                   const double* __restrict__ fw, const int32_t* __restrict__ owner,
+                                                   const int32_t* __restrict__ shift, const float4* __restrict__ p32,
+                                                   const int32_t* __restrict__ order, const int32_t* __restrict__ bstart,
+                                                   int stride, int32_t* __restrict__ nbr, int32_t* __restrict__ cnt_out,
                                                    int* __restrict__ flags) {
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -314,12 +322,12 @@ __global__ void __launch_bounds__(256) k_nbr_search(int64_t n, CellGeom g,
 }
 
 // per evaluation: refresh owned + ghost positions (FP64 -> hi/lo FP32 pair)
-__global__ void k_refresh(int64_t n, int64_t g_count, CellGeom g, const double* __restrict__ pos,
-                          const int32_t* __restrict__ perm, const int32_t* __restrict__ wrapm,
-                          const int32_t* __restrict__ owner, const int32_t* __restrict__ shift,
-                          float4* __restrict__ hi, float4* __restrict__ lo) {
+__global__ void k_refresh(int64_t n, const int32_t* __restrict__ g_count, int64_t g_cap, CellGeom g,
+                          const double* __restrict__ pos, const int32_t* __restrict__ perm,
+                          const int32_t* __restrict__ wrapm, const int32_t* __restrict__ owner,
+                          const int32_t* __restrict__ shift, float4* __restrict__ hi, float4* __restrict__ lo) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n + g_count) return;
+    if (s >= n + ghosts_in_use(g_count, g_cap)) return;
     int64_t o = s;
     int a = 0, b = 0, c = 0;
     if (s >= n) {
@@ -380,33 +388,30 @@ __global__ void __launch_bounds__(256) k_live(int64_t n, int stride, float rc2, 
     if (lane == 0) live_cnt[i] = count;
 }
 
-inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+// largest displacement since the build: flag when any atom moved more than half the skin
+__global__ void k_moved(int64_t n, const double* __restrict__ pos, const double* __restrict__ ref, double thr2,
+                        int* __restrict__ flags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double dx = pos[3 * i] - ref[3 * i], dy = pos[3 * i + 1] - ref[3 * i + 1], dz = pos[3 * i + 2] - ref[3 * i + 2];
+    if (!(dx * dx + dy * dy + dz * dz <= thr2)) atomicOr(&flags[FLAG_MOVED], 1);
+}
 
-struct DevBuf {
-    std::vector<void*> ptrs;
-    ~DevBuf() {
-        for (void* p : ptrs) cudaFree(p);
-    }
-    template <typename T>
-    T* get(size_t count) {
-        void* p = nullptr;
-        if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return nullptr;
-        ptrs.push_back(p);
-        return (T*)p;
-    }
-};
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-// Counting sort of n keys in [0, nkeys): order = indices sorted by (key, index); start = bucket offsets.
+// Counting sort of n keys in [0, nkeys): order = indices sorted by (key, index) within the first
+// `sorted_keys` buckets (later buckets hold unused capacity whose order does not matter);
+// start = bucket offsets.
 static cudaError_t counting_sort(cudaStream_t s, int64_t n, int64_t nkeys, const int32_t* key, int32_t* counts,
-                                 int32_t* start, int32_t* order) {
+                                 int32_t* start, int32_t* order, int64_t sorted_keys) {
     cudaMemsetAsync(counts, 0, sizeof(int32_t) * nkeys, s);
     if (n > 0) k_hist<<<blocks_for(n, 256), 256, 0, s>>>(n, key, counts);
     k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(nkeys, counts, start);
     cudaMemsetAsync(counts, 0, sizeof(int32_t) * nkeys, s);
     if (n > 0) k_scatter<<<blocks_for(n, 256), 256, 0, s>>>(n, key, start, counts, order);
-    k_bucket_sort<<<blocks_for(nkeys, 128), 128, 0, s>>>(nkeys, start, order);
+    if (sorted_keys > 0) k_bucket_sort<<<blocks_for(sorted_keys, 128), 128, 0, s>>>(sorted_keys, start, order);
     return cudaGetLastError();
 }
 
@@ -418,82 +423,111 @@ static T* dalloc(reann_nlist* nl, size_t count) {
     return (T*)p;
 }
 
+static int64_t owned_keys(const reann_nlist* nl) {
+    const CellGeom& g = nl->geom;
+    return (int64_t)g.nb[0] * g.nb[1] * g.nb[2] * nl->n_elem;
+}
+static int64_t ext_bins(const reann_nlist* nl) {
+    const CellGeom& g = nl->geom;
+    return (int64_t)g.nbx[0] * g.nbx[1] * g.nbx[2];
+}
+
+// steps 1-3a: wrap, sort, gather, ghost count + scan (goff[n] = ghost count on the device)
+static cudaError_t stage_sort_and_count(cudaStream_t s, reann_nlist* nl, const double* pos, int* flags) {
+    const int64_t n = nl->n;
+    NlistScratch& w = nl->w;
+    cudaMemcpyAsync(nl->pos_ref, pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s);
+    k_wrap_key<<<blocks_for(n, 256), 256, 0, s>>>(n, pos, w.species_c, nl->n_elem, nl->geom, w.xw_c, w.fw_c, w.mw_c,
+                                                  w.key, flags);
+    counting_sort(s, n, owned_keys(nl), w.key, w.counts, w.start, nl->perm, owned_keys(nl));
+    k_gather_internal<<<blocks_for(n, 256), 256, 0, s>>>(n, nl->perm, w.xw_c, w.fw_c, w.mw_c, w.species_c, w.xw, w.fw,
+                                                         nl->wrapm, nl->species);
+    k_ghosts<false><<<blocks_for(n, 256), 256, 0, s>>>(n, nl->geom, w.fw, nullptr, w.gcnt, nullptr, nullptr, 0, flags);
+    k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(n, w.gcnt, w.goff);
+    return cudaGetLastError();
+}
+
+// steps 3b-4: ghost fill and the extended bins (needs the ghost capacity)
+static cudaError_t stage_ghosts_and_bins(cudaStream_t s, reann_nlist* nl, int* flags) {
+    const int64_t n = nl->n, next = n + nl->g_cap;
+    NlistScratch& w = nl->w;
+    k_ghosts<true><<<blocks_for(n, 256), 256, 0, s>>>(n, nl->geom, w.fw, w.goff, nullptr, nl->g_owner, nl->g_shift,
+                                                      nl->g_cap, flags);
+    const int64_t nx = ext_bins(nl);
+    k_ext_key<<<blocks_for(next, 256), 256, 0, s>>>(n, w.goff + n, nl->g_cap, nl->geom, w.xw, w.fw, nl->g_owner,
+                                                    nl->g_shift, w.ekey, w.p32, (int32_t)nx);
+    counting_sort(s, next, nx + 1, w.ekey, w.ecounts, w.estart, w.eorder, nx);
+    return cudaGetLastError();
+}
+
+static cudaError_t stage_search(cudaStream_t s, reann_nlist* nl, int* flags) {
+    const int64_t n = nl->n;
+    NlistScratch& w = nl->w;
+    k_nbr_search<<<blocks_for(n * 32, 256), 256, 0, s>>>(n, nl->geom, w.xw, w.fw, nl->g_owner, nl->g_shift, w.p32,
+                                                         w.eorder, w.estart, nl->stride, nl->nbr, nl->nbr_cnt, flags);
+    return cudaGetLastError();
+}
+
 int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const int32_t* species) {
     cudaStream_t s = ctx->stream;
     const int64_t n = nl->n;
-    CellGeom& g = nl->geom;
-    DevBuf tmp;
-    const int64_t nbins = (int64_t)g.nb[0] * g.nb[1] * g.nb[2];
-    const int64_t nkeys = nbins * nl->n_elem;
-    double* xw_c = tmp.get<double>(3 * n);
-    double* fw_c = tmp.get<double>(3 * n);
-    int32_t* mw_c = tmp.get<int32_t>(3 * n);
-    int32_t* key = tmp.get<int32_t>(n);
-    int32_t* counts = tmp.get<int32_t>(nkeys);
-    int32_t* start = tmp.get<int32_t>(nkeys + 1);
-    double* xw = tmp.get<double>(3 * n);
-    double* fw = tmp.get<double>(3 * n);
-    int32_t* gcnt = tmp.get<int32_t>(n);
-    int32_t* goff = tmp.get<int32_t>(n + 1);
-    if (!xw_c || !fw_c || !mw_c || !key || !counts || !start || !xw || !fw || !gcnt || !goff)
-        return set_error(ctx, REANN_E_NOMEM, "neighbour-list scratch allocation failed");
-
+    NlistScratch& w = nl->w;
+    const int64_t nkeys = owned_keys(nl);
+    w.xw_c = dalloc<double>(nl, 3 * n);
+    w.fw_c = dalloc<double>(nl, 3 * n);
+    w.mw_c = dalloc<int32_t>(nl, 3 * n);
+    w.key = dalloc<int32_t>(nl, n);
+    w.counts = dalloc<int32_t>(nl, nkeys);
+    w.start = dalloc<int32_t>(nl, nkeys + 1);
+    w.xw = dalloc<double>(nl, 3 * n);
+    w.fw = dalloc<double>(nl, 3 * n);
+    w.gcnt = dalloc<int32_t>(nl, n);
+    w.goff = dalloc<int32_t>(nl, n + 1);
+    w.species_c = dalloc<int32_t>(nl, n);
     nl->perm = dalloc<int32_t>(nl, n);
     nl->species = dalloc<int32_t>(nl, n);
     nl->wrapm = dalloc<int32_t>(nl, 3 * n);
     nl->pos_ref = dalloc<double>(nl, 3 * n);
-    if (!nl->perm || !nl->species || !nl->wrapm || !nl->pos_ref)
+    if (!w.xw_c || !w.fw_c || !w.mw_c || !w.key || !w.counts || !w.start || !w.xw || !w.fw || !w.gcnt || !w.goff ||
+        !w.species_c || !nl->perm || !nl->species || !nl->wrapm || !nl->pos_ref)
         return set_error(ctx, REANN_E_NOMEM, "neighbour-list allocation failed");
-    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->pos_ref, pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s));
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(w.species_c, species, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     REANN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * NFLAGS, s));
-
-    k_wrap_key<<<blocks_for(n, 256), 256, 0, s>>>(n, pos, species, nl->n_elem, g, xw_c, fw_c, mw_c, key, ctx->d_flags);
-    REANN_CUDA_TRY(ctx, counting_sort(s, n, nkeys, key, counts, start, nl->perm));
-    k_gather_internal<<<blocks_for(n, 256), 256, 0, s>>>(n, nl->perm, xw_c, fw_c, mw_c, species, xw, fw, nl->wrapm,
-                                                         nl->species);
-    // element ranges of the internal order
+    REANN_CUDA_TRY(ctx, stage_sort_and_count(s, nl, pos, ctx->d_flags));
+    // sizes: element ranges of the internal order and the ghost count
     std::vector<int32_t> es(nl->n_elem + 1);
+    const int64_t nbins = nkeys / nl->n_elem;
     for (int e = 0; e <= nl->n_elem; ++e)
-        REANN_CUDA_TRY(ctx, cudaMemcpyAsync(&es[e], start + (int64_t)e * nbins, sizeof(int32_t),
+        REANN_CUDA_TRY(ctx, cudaMemcpyAsync(&es[e], w.start + (int64_t)e * nbins, sizeof(int32_t),
                                             cudaMemcpyDeviceToHost, s));
-    // ghosts: count, scan, size
-    k_ghosts<false><<<blocks_for(n, 256), 256, 0, s>>>(n, g, fw, nullptr, gcnt, nullptr, nullptr, 0, ctx->d_flags);
-    k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(n, gcnt, goff);
     int32_t G = 0;
-    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(&G, goff + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(&G, w.goff + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int) * NFLAGS, cudaMemcpyDeviceToHost, s));
     REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     if (ctx->h_flags[FLAG_SPECIES]) return set_error(ctx, REANN_E_ARG, "species index out of range");
     if (ctx->h_flags[FLAG_GEOM]) return set_error(ctx, REANN_E_GEOM, "non-finite atom position");
     for (int e = 0; e <= nl->n_elem; ++e) nl->elem_start[e] = es[e];
-
     nl->g = G;
-    nl->g_cap = G;
-    const int64_t next = n + G;
-    nl->g_owner = dalloc<int32_t>(nl, G);
-    nl->g_shift = dalloc<int32_t>(nl, G);
-    int64_t* g_total = tmp.get<int64_t>(1);
-    int32_t* ekey = tmp.get<int32_t>(next);
-    float4* p32 = tmp.get<float4>(next);
-    if (!nl->g_owner || !nl->g_shift || !g_total || !ekey || !p32)
+    // capacity with headroom so that rebuilds after atom motion fit
+    nl->g_cap = G + G / 4 + 64;
+    const int64_t next = n + nl->g_cap;
+    const int64_t nx = ext_bins(nl);
+    nl->g_owner = dalloc<int32_t>(nl, nl->g_cap);
+    nl->g_shift = dalloc<int32_t>(nl, nl->g_cap);
+    w.ekey = dalloc<int32_t>(nl, next);
+    w.p32 = dalloc<float4>(nl, next);
+    w.ecounts = dalloc<int32_t>(nl, nx + 1);
+    w.estart = dalloc<int32_t>(nl, nx + 2);
+    w.eorder = dalloc<int32_t>(nl, next);
+    if (!nl->g_owner || !nl->g_shift || !w.ekey || !w.p32 || !w.ecounts || !w.estart || !w.eorder)
         return set_error(ctx, REANN_E_NOMEM, "ghost allocation failed");
-    k_ghosts<true><<<blocks_for(n, 256), 256, 0, s>>>(n, g, fw, goff, nullptr, nl->g_owner, nl->g_shift, G,
-                                                      ctx->d_flags);
-    const int64_t G64 = G;
-    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(g_total, &G64, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    const int64_t nxbins = (int64_t)g.nbx[0] * g.nbx[1] * g.nbx[2];
-    int32_t* ecounts = tmp.get<int32_t>(nxbins + 1);
-    int32_t* estart = tmp.get<int32_t>(nxbins + 2);
-    int32_t* eorder = tmp.get<int32_t>(next);
-    if (!ecounts || !estart || !eorder) return set_error(ctx, REANN_E_NOMEM, "bin allocation failed");
-    k_ext_key<<<blocks_for(next, 256), 256, 0, s>>>(n, g_total, G, g, xw, fw, nl->g_owner, nl->g_shift, ekey, p32,
-                                                    (int32_t)nxbins);
-    REANN_CUDA_TRY(ctx, counting_sort(s, next, nxbins + 1, ekey, ecounts, estart, eorder));
-
-    // expected neighbours from the number density, with headroom
-    double vol = std::fabs(g.h[0] * (g.h[4] * g.h[8] - g.h[5] * g.h[7]) - g.h[1] * (g.h[3] * g.h[8] - g.h[5] * g.h[6]) +
-                           g.h[2] * (g.h[3] * g.h[7] - g.h[4] * g.h[6]));
-    double expect = (double)n / vol * 4.18879020478639 * std::pow(g.rcut2, 1.5);
+    REANN_CUDA_TRY(ctx, stage_ghosts_and_bins(s, nl, ctx->d_flags));
+    // row capacity: expected neighbours from the number density, with headroom
+    const CellGeom& g = nl->geom;
+    const double vol = std::fabs(g.h[0] * (g.h[4] * g.h[8] - g.h[5] * g.h[7]) -
+                                 g.h[1] * (g.h[3] * g.h[8] - g.h[5] * g.h[6]) +
+                                 g.h[2] * (g.h[3] * g.h[7] - g.h[4] * g.h[6]));
+    const double expect = (double)n / vol * 4.18879020478639 * std::pow(g.rcut2, 1.5);
     int stride = (int)std::min<double>(1 << 20, std::ceil((1.5 * expect + 32) / 8.0) * 8);
     for (int attempt = 0; attempt < 2; ++attempt) {
         nl->stride = stride;
@@ -501,26 +535,38 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
         nl->nbr_cnt = dalloc<int32_t>(nl, n);
         if (!nl->nbr || !nl->nbr_cnt) return set_error(ctx, REANN_E_NOMEM, "neighbour-list allocation failed");
         REANN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * NFLAGS, s));
-        k_nbr_search<<<blocks_for(n * 32, 256), 256, 0, s>>>(n, g, xw, fw, nl->g_owner,
-                                                             nl->g_shift, p32, eorder, estart, stride, nl->nbr,
-                                                             nl->nbr_cnt, ctx->d_flags);
-        REANN_CUDA_TRY(ctx, cudaGetLastError());
+        REANN_CUDA_TRY(ctx, stage_search(s, nl, ctx->d_flags));
         REANN_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int) * NFLAGS, cudaMemcpyDeviceToHost, s));
         REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         if (ctx->h_flags[FLAG_GEOM]) return set_error(ctx, REANN_E_GEOM, "coincident atoms (distance < 1e-8 A)");
         if (ctx->h_flags[FLAG_GHOST_OVERFLOW]) return set_error(ctx, REANN_E_CAPACITY, "ghost capacity exceeded");
         if (!ctx->h_flags[FLAG_NBR_OVERFLOW]) break;
-        // grow to the observed maximum and search again
-        stride = ((ctx->h_flags[FLAG_MAXNBR] + 8 + 7) / 8) * 8;
         if (attempt == 1) return set_error(ctx, REANN_E_CAPACITY, "neighbour capacity exceeded");
+        // grow to the observed maximum (plus headroom for later motion) and search again
+        stride = ((ctx->h_flags[FLAG_MAXNBR] + ctx->h_flags[FLAG_MAXNBR] / 8 + 16 + 7) / 8) * 8;
     }
     return REANN_OK;
 }
 
+cudaError_t launch_rebuild(cudaStream_t s, reann_nlist* nl, const double* pos, int* flags) {
+    cudaError_t e = stage_sort_and_count(s, nl, pos, flags);
+    if (e == cudaSuccess) e = stage_ghosts_and_bins(s, nl, flags);
+    if (e == cudaSuccess) e = stage_search(s, nl, flags);
+    return e;
+}
+
+cudaError_t launch_moved(cudaStream_t s, const reann_nlist* nl, const double* pos, int* flags) {
+    const double half = 0.5 * nl->skin;
+    k_moved<<<blocks_for(nl->n, 256), 256, 0, s>>>(nl->n, pos, nl->pos_ref, half * half, flags);
+    return cudaGetLastError();
+}
+
+const int32_t* ghost_count_ptr(const reann_nlist* nl) { return nl->w.goff + nl->n; }
+
 cudaError_t launch_refresh_positions(cudaStream_t s, const reann_nlist* nl, const double* pos) {
-    const int64_t total = nl->n + nl->g;
-    k_refresh<<<blocks_for(total, 256), 256, 0, s>>>(nl->n, nl->g, nl->geom, pos, nl->perm, nl->wrapm, nl->g_owner,
-                                                     nl->g_shift, nl->pos_hi, nl->pos_lo);
+    const int64_t total = nl->n + nl->g_cap;
+    k_refresh<<<blocks_for(total, 256), 256, 0, s>>>(nl->n, ghost_count_ptr(nl), nl->g_cap, nl->geom, pos, nl->perm,
+                                                     nl->wrapm, nl->g_owner, nl->g_shift, nl->pos_hi, nl->pos_lo);
     return cudaGetLastError();
 }
 
@@ -534,14 +580,18 @@ int export_nlist(reann_ctx* ctx, const reann_nlist* nl, int64_t cap, int32_t* oi
                  int64_t* count) {
     cudaStream_t s = ctx->stream;
     const int64_t n = nl->n;
-    std::vector<int32_t> nbr((size_t)n * nl->stride), cnt(n), perm(n), wm(3 * n), own(nl->g), sh(nl->g);
+    int32_t G = 0;
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(&G, ghost_count_ptr(nl), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    const int64_t g = std::min<int64_t>(G, nl->g_cap);
+    std::vector<int32_t> nbr((size_t)n * nl->stride), cnt(n), perm(n), wm(3 * n), own(g), sh(g);
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(nbr.data(), nl->nbr, sizeof(int32_t) * nbr.size(), cudaMemcpyDeviceToHost, s));
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(cnt.data(), nl->nbr_cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(perm.data(), nl->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(wm.data(), nl->wrapm, sizeof(int32_t) * 3 * n, cudaMemcpyDeviceToHost, s));
-    if (nl->g > 0) {
-        REANN_CUDA_TRY(ctx, cudaMemcpyAsync(own.data(), nl->g_owner, sizeof(int32_t) * nl->g, cudaMemcpyDeviceToHost, s));
-        REANN_CUDA_TRY(ctx, cudaMemcpyAsync(sh.data(), nl->g_shift, sizeof(int32_t) * nl->g, cudaMemcpyDeviceToHost, s));
+    if (g > 0) {
+        REANN_CUDA_TRY(ctx, cudaMemcpyAsync(own.data(), nl->g_owner, sizeof(int32_t) * g, cudaMemcpyDeviceToHost, s));
+        REANN_CUDA_TRY(ctx, cudaMemcpyAsync(sh.data(), nl->g_shift, sizeof(int32_t) * g, cudaMemcpyDeviceToHost, s));
     }
     REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     int64_t q = 0;

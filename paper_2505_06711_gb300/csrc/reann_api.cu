@@ -121,8 +121,9 @@ int alloc_eval_buffers(reann_ctx* ctx, reann_nlist* nl) {
     if (!nl->tiles_h.empty())
         REANN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->tiles, nl->tiles_h.data(), sizeof(Tile) * nl->tiles_h.size(),
                                             cudaMemcpyHostToDevice, ctx->stream));
-    // unused ghost capacity keeps finite values
+    // unused ghost capacity keeps finite values; no live edges before the first evaluation
     REANN_CUDA_TRY(ctx, cudaMemsetAsync(nl->bbar, 0, sizeof(float) * ne * NB, ctx->stream));
+    REANN_CUDA_TRY(ctx, cudaMemsetAsync(nl->live_cnt, 0, sizeof(int32_t) * n, ctx->stream));
     return REANN_OK;
 }
 
@@ -262,6 +263,12 @@ extern "C" int reann_ctx_create(const reann_model* model, void* cuda_stream, rea
 
 extern "C" void reann_ctx_free(reann_ctx* ctx) {
     if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& r : ctx->prof_recs) {
+        cudaEventDestroy(r.second.first);
+        cudaEventDestroy(r.second.second);
+    }
+    for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
     if (ctx->d_params) cudaFree(ctx->d_params);
     if (ctx->d_bf16) cudaFree(ctx->d_bf16);
     if (ctx->d_flags) cudaFree(ctx->d_flags);
@@ -319,18 +326,27 @@ extern "C" int reann_build_nlist(reann_ctx* ctx, int64_t n_atoms, const double* 
 
 extern "C" void reann_nlist_free(reann_nlist* nl) { free_nlist(nl); }
 
-extern "C" int reann_nlist_info(const reann_nlist* nl, int64_t* n_atoms, int64_t* n_ghosts, int64_t* n_pairs) {
+extern "C" int reann_nlist_info(const reann_nlist* nl, int64_t* n_atoms, int64_t* n_ghosts, int64_t* n_pairs,
+                                int64_t* n_live) {
     if (!nl) return REANN_E_ARG;
     if (n_atoms) *n_atoms = nl->n;
-    if (n_ghosts) *n_ghosts = nl->g;
-    if (n_pairs) {
+    if (n_ghosts) {
+        int32_t g = 0;
+        if (cudaMemcpy(&g, ghost_count_ptr(nl), sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return REANN_E_CUDA;
+        *n_ghosts = std::min<int64_t>(g, nl->g_cap);
+    }
+    auto sum_counts = [&](const int32_t* d, int64_t* out) {
         std::vector<int32_t> cnt(nl->n);
-        if (cudaMemcpy(cnt.data(), nl->nbr_cnt, sizeof(int32_t) * nl->n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        if (cudaMemcpy(cnt.data(), d, sizeof(int32_t) * nl->n, cudaMemcpyDeviceToHost) != cudaSuccess)
             return REANN_E_CUDA;
         int64_t s = 0;
         for (int32_t c : cnt) s += c;
-        *n_pairs = s;
-    }
+        *out = s;
+        return REANN_OK;
+    };
+    if (n_pairs && sum_counts(nl->nbr_cnt, n_pairs)) return REANN_E_CUDA;
+    if (n_live && sum_counts(nl->live_cnt, n_live)) return REANN_E_CUDA;
     return REANN_OK;
 }
 
@@ -340,51 +356,205 @@ extern "C" int reann_nlist_export(reann_ctx* ctx, const reann_nlist* nl, int64_t
     return export_nlist(ctx, nl, cap, i, j, n, count);
 }
 
-extern "C" int reann_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy,
-                                   float* forces, float* atom_energy) {
-    if (!ctx || !nl || !pos || !energy || !forces) return set_error(ctx, REANN_E_ARG, "null argument");
-    if (T != ctx->model.T || T != nl->T) return set_error(ctx, REANN_E_MISMATCH, "T differs from the model");
+namespace {
+
+// ---- optional per-region event profile -----------------------------------
+cudaEvent_t prof_event(reann_ctx* ctx) {
+    if (!ctx->prof_pool.empty()) {
+        cudaEvent_t e = ctx->prof_pool.back();
+        ctx->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct ProfScope {
+    reann_ctx* ctx;
+    int region;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(reann_ctx* c, int r) : ctx(c), region(r) {
+        if (!ctx->prof_on) return;
+        a = prof_event(ctx);
+        b = prof_event(ctx);
+        cudaEventRecord(a, ctx->stream);
+    }
+    ~ProfScope() {
+        if (!ctx->prof_on || !a) return;
+        cudaEventRecord(b, ctx->stream);
+        ctx->prof_recs.push_back({region, {a, b}});
+    }
+};
+
+// harvest recorded event pairs into the per-region totals (synchronous)
+void prof_collect(reann_ctx* ctx) {
+    if (ctx->prof_recs.empty()) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& r : ctx->prof_recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.second.first, r.second.second) == cudaSuccess) {
+            ctx->prof_ms[r.first] += ms;
+            ctx->prof_n[r.first] += 1;
+        }
+        ctx->prof_pool.push_back(r.second.first);
+        ctx->prof_pool.push_back(r.second.second);
+    }
+    ctx->prof_recs.clear();
+}
+
+const char* kRegionNames[PR_COUNT] = {"nlist_rebuild", "refresh_positions", "live_edges",   "init_coef",
+                                      "ghost_gather",  "density_fwd",       "mlp_fwd",      "energy_sum",
+                                      "mlp_bwd",       "bbar",              "density_adj",  "scatter_outputs"};
+
+int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy, float* forces,
+                      float* atom_energy) {
     cudaStream_t s = ctx->stream;
     const int64_t n = nl->n, ne = nl->n + nl->g_cap;
-    REANN_CUDA_TRY(ctx, launch_refresh_positions(s, nl, pos));
-    REANN_CUDA_TRY(ctx, launch_live_edges(s, nl, ctx->radial.rc2, ctx->d_flags));
-    REANN_CUDA_TRY(ctx, launch_init_coef(s, nl, ctx->d_c0));
+    {
+        ProfScope p(ctx, PR_REFRESH);
+        REANN_CUDA_TRY(ctx, launch_refresh_positions(s, nl, pos));
+    }
+    {
+        ProfScope p(ctx, PR_LIVE);
+        REANN_CUDA_TRY(ctx, launch_live_edges(s, nl, ctx->radial.rc2, ctx->d_flags));
+    }
+    {
+        ProfScope p(ctx, PR_INIT);
+        REANN_CUDA_TRY(ctx, launch_init_coef(s, nl, ctx->d_c0));
+    }
     const size_t lw = (size_t)(LMAX + 1) * NPHI * NORB;
     // forward: Eq. 1 then Eq. 2, re-using the same list in every layer (Sec. 2.2)
     for (int t = 0; t < T; ++t) {
         float* coef_t = nl->coef + (size_t)t * ne * NPHI;
         float* rho_t = nl->rho + (size_t)t * n * NFEAT;
         float* bck_t = nl->bck + (size_t)t * n * NB;
-        if (t > 0) REANN_CUDA_TRY(ctx, launch_gather_ghost_rows(s, nl, coef_t, NPHI));
-        REANN_CUDA_TRY(ctx, launch_density_fwd(s, nl, ctx->radial, ctx->d_W + t * lw, coef_t, rho_t, bck_t));
+        if (t > 0) {
+            ProfScope p(ctx, PR_GATHER);  // ghost slots receive their owners' coefficients (Fig. 4a)
+            REANN_CUDA_TRY(ctx, launch_gather_ghost_rows(s, nl, coef_t, NPHI));
+        }
+        {
+            ProfScope p(ctx, PR_DENSITY_FWD);
+            REANN_CUDA_TRY(ctx, launch_density_fwd(s, nl, ctx->radial, ctx->d_W + t * lw, coef_t, rho_t, bck_t));
+        }
+        ProfScope p(ctx, PR_MLP_FWD);
         if (t < T - 1)
             REANN_CUDA_TRY(ctx, launch_mlp_fwd_f32(s, nl, ctx->nets, t, false, rho_t,
                                                    nl->coef + (size_t)(t + 1) * ne * NPHI, NPHI));
         else
             REANN_CUDA_TRY(ctx, launch_mlp_fwd_f32(s, nl, ctx->nets, t, true, rho_t, nl->eps, 1));
     }
-    REANN_CUDA_TRY(ctx, launch_energy_sum(s, nl, energy));
+    {
+        ProfScope p(ctx, PR_ENERGY);
+        REANN_CUDA_TRY(ctx, launch_energy_sum(s, nl, energy));
+    }
     // reverse: Eqs. 3-5, one vector-Jacobian product per layer
     REANN_CUDA_TRY(ctx, cudaMemsetAsync(nl->grad, 0, sizeof(float) * n * 3, s));
     for (int t = T - 1; t >= 0; --t) {
         const float* coef_t = nl->coef + (size_t)t * ne * NPHI;
         const float* rho_t = nl->rho + (size_t)t * n * NFEAT;
         const float* bck_t = nl->bck + (size_t)t * n * NB;
-        REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, rho_t, nl->cbar, nl->rhobar));
-        REANN_CUDA_TRY(ctx, launch_bbar(s, nl, ctx->d_W + t * lw, bck_t, nl->rhobar, nl->bbar));
-        REANN_CUDA_TRY(ctx, launch_gather_ghost_rows(s, nl, nl->bbar, NB));
+        {
+            ProfScope p(ctx, PR_MLP_BWD);
+            REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, rho_t, nl->cbar, nl->rhobar));
+        }
+        {
+            ProfScope p(ctx, PR_BBAR);
+            REANN_CUDA_TRY(ctx, launch_bbar(s, nl, ctx->d_W + t * lw, bck_t, nl->rhobar, nl->bbar));
+        }
+        {
+            ProfScope p(ctx, PR_GATHER);  // ghost slots receive their owners' adjoints (vector-Jacobian product)
+            REANN_CUDA_TRY(ctx, launch_gather_ghost_rows(s, nl, nl->bbar, NB));
+        }
+        ProfScope p(ctx, PR_DENSITY_ADJ);
         REANN_CUDA_TRY(ctx, launch_density_adj(s, nl, ctx->radial, coef_t, nl->bbar, nl->cbar, nl->grad, t >= 1,
                                                ctx->d_flags));
     }
+    ProfScope p(ctx, PR_OUTPUT);
     REANN_CUDA_TRY(ctx, launch_scatter_outputs(s, nl, forces, atom_energy));
     return REANN_OK;
 }
 
-extern "C" int reann_energy_forces_host(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy,
-                                        float* forces) {
+int run_rebuild(reann_ctx* ctx, reann_nlist* nl, const double* pos) {
+    ProfScope p(ctx, PR_REBUILD);
+    REANN_CUDA_TRY(ctx, launch_rebuild(ctx->stream, nl, pos, ctx->d_flags));
+    return REANN_OK;
+}
+
+}  // namespace
+
+extern "C" int reann_nlist_rebuild(reann_ctx* ctx, reann_nlist* nl, const double* pos) {
+    if (!ctx || !nl || !pos) return set_error(ctx, REANN_E_ARG, "null argument");
+    return run_rebuild(ctx, nl, pos);
+}
+
+extern "C" int reann_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy,
+                                   float* forces, float* atom_energy) {
     if (!ctx || !nl || !pos || !energy || !forces) return set_error(ctx, REANN_E_ARG, "null argument");
-    (void)T;
-    return set_error(ctx, REANN_E_ARG, "not implemented");
+    if (T != ctx->model.T || T != nl->T) return set_error(ctx, REANN_E_MISMATCH, "T differs from the model");
+    return run_energy_forces(ctx, nl, pos, T, energy, forces, atom_energy);
+}
+
+extern "C" int reann_energy_forces_host(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy,
+                                        float* forces, int rebuild) {
+    if (!ctx || !nl || !pos || !energy || !forces) return set_error(ctx, REANN_E_ARG, "null argument");
+    if (T != ctx->model.T || T != nl->T) return set_error(ctx, REANN_E_MISMATCH, "T differs from the model");
+    cudaStream_t s = ctx->stream;
+    const int64_t n = nl->n;
+    if (!nl->h2d_pos) {
+        nl->h2d_pos = nl_alloc<double>(nl, 3 * n);
+        nl->d_forces = nl_alloc<float>(nl, 3 * n);
+        nl->d_energy = nl_alloc<double>(nl, 1);
+        if (!nl->h2d_pos || !nl->d_forces || !nl->d_energy) return set_error(ctx, REANN_E_NOMEM, "staging buffers");
+    }
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->h2d_pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+    if (rebuild) {
+        int rc = run_rebuild(ctx, nl, nl->h2d_pos);
+        if (rc) return rc;
+    } else {
+        REANN_CUDA_TRY(ctx, launch_moved(s, nl, nl->h2d_pos, ctx->d_flags));
+        REANN_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int) * NFLAGS, cudaMemcpyDeviceToHost, s));
+        REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        if (ctx->h_flags[FLAG_MOVED]) {
+            int zero = 0;
+            REANN_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->d_flags + FLAG_MOVED, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+            int rc = run_rebuild(ctx, nl, nl->h2d_pos);
+            if (rc) return rc;
+        }
+    }
+    int rc = run_energy_forces(ctx, nl, nl->h2d_pos, T, nl->d_energy, nl->d_forces, nullptr);
+    if (rc) return rc;
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(forces, nl->d_forces, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(energy, nl->d_energy, sizeof(double), cudaMemcpyDeviceToHost, s));
+    REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    return reann_ctx_check(ctx);
+}
+
+extern "C" int reann_ctx_profile(reann_ctx* ctx, int enable) {
+    if (!ctx) return REANN_E_ARG;
+    prof_collect(ctx);
+    ctx->prof_on = enable != 0;
+    for (int r = 0; r < PR_COUNT; ++r) {
+        ctx->prof_ms[r] = 0.0;
+        ctx->prof_n[r] = 0;
+    }
+    return REANN_OK;
+}
+
+extern "C" int reann_profile_regions(void) { return PR_COUNT; }
+
+extern "C" const char* reann_profile_region_name(int region) {
+    return (region >= 0 && region < PR_COUNT) ? kRegionNames[region] : "";
+}
+
+extern "C" int reann_ctx_profile_read(reann_ctx* ctx, double* total_ms, int64_t* launches) {
+    if (!ctx || !total_ms || !launches) return REANN_E_ARG;
+    prof_collect(ctx);
+    for (int r = 0; r < PR_COUNT; ++r) {
+        total_ms[r] = ctx->prof_ms[r];
+        launches[r] = ctx->prof_n[r];
+    }
+    return REANN_OK;
 }
 
 extern "C" int reann_get_layer(reann_ctx* ctx, const reann_nlist* nl, int layer, float* rho, float* coef) {

@@ -1,0 +1,127 @@
+"""GPU tests of the C ABI beyond plain parity: device-side rebuild, the host-buffer
+entry point, the per-region profile, and the error paths (all through ctypes)."""
+
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import fcc_box, make_model, water_box
+from synth.structures import Structure
+
+from gpu_helpers import assert_parity, potential
+
+pytestmark = pytest.mark.gpu
+
+
+def _set(i, j, s):
+    return set(zip(i.tolist(), j.tolist(), map(tuple, s.tolist())))
+
+
+def test_device_rebuild_matches_oracle_after_motion():
+    import torch
+
+    s = water_box(64, seed=3)
+    spec = make_model(T=3)
+    pot = potential(spec)
+    sy = pot.system(s.pos, s.species, s.cell, skin=1.0)
+    rng = np.random.default_rng(1)
+    moved = s.pos + rng.normal(0, 0.3, size=s.pos.shape)  # beyond skin/2: neighbours change
+    p1 = torch.as_tensor(moved, device="cuda").contiguous()
+    sy.rebuild(p1)
+    sy.check()
+    gi, gj, gs = sy.neighbors()
+    oi, oj, osh = oracle.neighbors(moved, s.cell, spec.r_c + 1.0)
+    assert _set(gi, gj, gs) == _set(oi, oj, osh)
+    sy.evaluate(p1)
+    sy.check()
+    torch.cuda.synchronize()
+    ref = oracle.energy_forces(spec, moved, s.species, s.cell)
+    assert_parity({"energy": sy.energy.item(), "forces": sy.forces.double().cpu().numpy(),
+                   "atom_energy": sy.atom_energy.double().cpu().numpy()}, ref, s.n_atoms)
+    sy.close()
+
+
+@pytest.mark.parametrize("shift,rebuild", [(0.1, 0), (0.8, 0), (0.1, 1)])
+def test_host_entry_point(shift, rebuild):
+    """Host buffers in/out; a motion beyond skin/2 triggers the rebuild on its own."""
+    s = fcc_box(4, seed=5)
+    spec = make_model(T=3)
+    pot = potential(spec)
+    sy = pot.system(s.pos, s.species, s.cell, skin=1.0)
+    rng = np.random.default_rng(2)
+    moved = np.ascontiguousarray(s.pos + rng.uniform(-shift, shift, size=s.pos.shape))
+    e = np.zeros(1, np.float64)
+    f = np.zeros((s.n_atoms, 3), np.float32)
+    sy.evaluate_host(moved, e, f, rebuild=bool(rebuild))
+    ref = oracle.energy_forces(spec, moved, s.species, s.cell)
+    assert_parity({"energy": float(e[0]), "forces": f.astype(np.float64)}, {k: ref[k] for k in ("energy", "forces")},
+                  s.n_atoms)
+    sy.close()
+
+
+def test_profile_regions_cover_the_step():
+    import torch
+
+    from paper_2505_06711_gb300 import binding
+
+    s = water_box(64, seed=0)
+    spec = make_model(T=3)
+    pot = potential(spec)
+    sy = pot.system(s.pos, s.species, s.cell)
+    binding.reann_ctx_profile(pot.ctx, True)
+    sy.rebuild()
+    sy.evaluate()
+    prof = binding.reann_ctx_profile_read(pot.ctx)
+    binding.reann_ctx_profile(pot.ctx, False)
+    assert prof["density_fwd"][1] == 3 and prof["density_adj"][1] == 3
+    assert prof["mlp_fwd"][1] == 3 and prof["mlp_bwd"][1] == 3
+    assert prof["nlist_rebuild"][1] == 1
+    assert all(v[0] >= 0 for v in prof.values())
+    torch.cuda.synchronize()
+    sy.close()
+
+
+def _expect(code, fn):
+    from paper_2505_06711_gb300 import ReannError
+
+    with pytest.raises(ReannError) as e:
+        fn()
+    assert e.value.code == code, e.value
+
+
+def test_error_paths():
+    import torch
+
+    from paper_2505_06711_gb300 import binding
+
+    spec = make_model(T=3)
+    pot = potential(spec)
+    s = water_box(16, seed=0)
+    bad = s.pos.copy()
+    bad[5, 1] = np.nan
+    _expect(binding.REANN_E_GEOM, lambda: pot.system(bad, s.species, s.cell))
+    sp = s.species.copy()
+    sp[3] = 7
+    _expect(binding.REANN_E_ARG, lambda: pot.system(s.pos, sp, s.cell))
+    coinc = s.pos.copy()
+    coinc[1] = coinc[0]
+    _expect(binding.REANN_E_GEOM, lambda: pot.system(coinc, s.species, s.cell))
+    _expect(binding.REANN_E_GEOM, lambda: pot.system(s.pos, s.species, np.zeros((3, 3))))
+    # r_c and T must match the model
+    p = torch.as_tensor(s.pos, device="cuda").contiguous()
+    spc = torch.as_tensor(s.species, device="cuda").contiguous()
+    _expect(binding.REANN_E_MISMATCH, lambda: binding.reann_build_nlist(pot.ctx, p, spc, s.cell, 4.0, 1.0))
+    sy = pot.system(s.pos, s.species, s.cell)
+    _expect(binding.REANN_E_MISMATCH,
+            lambda: binding.reann_energy_forces(pot.ctx, sy.nl, p, 2, sy.energy, sy.forces, None))
+    # coincident atoms appearing after the build are reported by the check
+    q = s.pos.copy()
+    q[1] = q[0]
+    sy.evaluate(torch.as_tensor(q, device="cuda").contiguous())
+    _expect(binding.REANN_E_GEOM, sy.check)
+    # the context stays usable afterwards
+    sy.evaluate()
+    sy.check()
+    sy.close()
