@@ -188,6 +188,36 @@ int reann_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int 
 int reann_energy_forces_host(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy,
                              float* forces, int rebuild);
 
+/* ------------------------------------------------------ no-allocation sum --- */
+
+/*
+ * Total energy E = sum_i eps_i in FP64 from per-atom energies the caller
+ * already holds, without allocating any device memory.  The paper has no
+ * counterpart; this exists for callers that cannot allocate at that moment:
+ * code running while a CUDA stream is captured into a graph in the global
+ * capture mode (cudaMalloc is not permitted there), and force back-ends hosted
+ * by a molecular-dynamics engine whose force callback must not allocate
+ * because the engine owns the device-memory budget.
+ *   atom_energy  dev, n_atoms FP32 (e.g. the atom_energy output of
+ *                reann_energy_forces); NULL only when n_atoms == 0
+ *   n_atoms      0 <= n_atoms <= reann_energy_sum_noalloc_max_atoms()
+ *                (8,388,608); larger sizes return REANN_E_CAPACITY, no work
+ *   energy       dev, 1 FP64, overwritten
+ *   cuda_stream  cudaStream_t to enqueue on (NULL = legacy default stream)
+ * The same two-level summation order as reann_energy_forces, so the result
+ * equals that call's energy bit for bit on the same atom energies.
+ * Scratch is a fixed 32 KiB array inside the library, held by every GPU that
+ * loads it until the process exits.  The first call on each device looks up
+ * that array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (each call writes every entry it reads): calls that overlap
+ * on the GPU race and must be serialised by the caller.  Asynchronous.
+ * Errors: REANN_E_ARG, REANN_E_CAPACITY, REANN_E_CUDA (returned directly; no
+ * context message).
+ */
+int reann_energy_sum_noalloc(const float* atom_energy, int64_t n_atoms, double* energy, void* cuda_stream);
+int64_t reann_energy_sum_noalloc_max_atoms(void);
+
 /* ------------------------------------------------------------- profiling --- */
 
 /*

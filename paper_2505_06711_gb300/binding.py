@@ -66,6 +66,8 @@ _SIGS = {
     "reann_profile_regions": ([], _int),
     "reann_profile_region_name": ([_int], ctypes.c_char_p),
     "reann_ctx_profile_read": ([_vp, _vp, _vp], _int),
+    "reann_energy_sum_noalloc": ([_vp, _i64, _vp, _vp], _int),
+    "reann_energy_sum_noalloc_max_atoms": ([], _i64),
 }
 
 
@@ -230,6 +232,25 @@ def reann_nlist_rebuild(ctx, nl, pos) -> None:
 
     _dev(pos, torch.float64, None, "pos")
     _check(lib().reann_nlist_rebuild(ctx, nl, _ptr(pos)), ctx)
+
+
+# ---------------------------------------------------------- no-allocation --
+def reann_energy_sum_noalloc(atom_energy, n_atoms: int, energy, stream=None) -> int:
+    """FP64 sum of per-atom energies with the library's fixed scratch (no device allocation).
+
+    For callers that must not allocate (graph capture, engine-owned memory);
+    returns the C return code instead of raising, so those callers can branch on it.
+    """
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    return int(lib().reann_energy_sum_noalloc(_ptr(atom_energy), int(n_atoms), _ptr(energy), _vp(handle)))
+
+
+def reann_energy_sum_noalloc_max_atoms() -> int:
+    return int(lib().reann_energy_sum_noalloc_max_atoms())
 
 
 # --------------------------------------------------------------- profiling --
