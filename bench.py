@@ -379,8 +379,26 @@ def run_ours(args):
             "d2h_bytes_per_step": int(h_f.numel() * 4 + 8),
         }
 
+    # the same step with the atomic networks on tcgen05 tensor cores
+    variants = {"fp32": {"value": value, "ms_per_step": ms, "mlp_ms_per_step": breakdown.get("mlp_fwd", 0.0)
+                         + breakdown.get("mlp_bwd", 0.0)}}
+    for name, prec in (("bf16_mlp", binding.REANN_MLP_BF16), ("bf16x3_mlp", binding.REANN_MLP_BF16X3)):
+        binding.reann_ctx_set_mlp_precision(ctx, prec)
+        for _ in range(args.warmup):
+            step()
+        v_ms, _, _ = timed(False)
+        _, _, v_prof = timed(True)
+        v_ms = max_over_ranks(v_ms, dist, "cuda")
+        variants[name] = {
+            "value": aggregate(n_atoms, v_ms, ws),
+            "ms_per_step": v_ms,
+            "mlp_ms_per_step": (v_prof["mlp_fwd"][0] + v_prof["mlp_bwd"][0]) / args.steps,
+        }
+    binding.reann_ctx_set_mlp_precision(ctx, binding.REANN_MLP_FP32)
+
     if rank == 0:
         line = base_line(args, ws, value, ms, "f32")
+        line["variants"] = variants
         line["e2e"] = e2e
         line["roofline"] = roof
         line["gpu_launches"] = launches_per_step(T_LAYERS) * args.steps

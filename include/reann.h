@@ -57,8 +57,10 @@ extern "C" {
 #define REANN_E_TIMEOUT (-6)  /* a bounded device wait ran out                */
 #define REANN_E_CAPACITY (-7) /* a neighbour/ghost capacity was exceeded (rebuild) */
 
-#define REANN_MLP_FP32 0 /* atomic networks in FP32 SIMT arithmetic                    */
-#define REANN_MLP_BF16 1 /* atomic networks on tcgen05 tensor cores, BF16 in, FP32 acc */
+#define REANN_MLP_FP32 0   /* atomic networks in FP32 SIMT arithmetic                        */
+#define REANN_MLP_BF16 1   /* tcgen05 tensor cores, BF16 operands, FP32 accumulation         */
+#define REANN_MLP_BF16X3 2 /* tcgen05, every operand a BF16 hi + lo pair, 3 MMAs per K step,
+                              FP32 accumulation (about 16 significant bits per operand)      */
 
 typedef struct reann_model reann_model;
 typedef struct reann_ctx reann_ctx;
@@ -93,7 +95,11 @@ void reann_model_free(reann_model* model);
 int reann_ctx_create(const reann_model* model, void* cuda_stream, reann_ctx** out);
 void reann_ctx_free(reann_ctx* ctx);
 
-/* Precision of the atomic networks (REANN_MLP_FP32 default, REANN_MLP_BF16). */
+/*
+ * Precision of the atomic networks: REANN_MLP_FP32 (default), REANN_MLP_BF16
+ * or REANN_MLP_BF16X3.  The density and reverse-pass edge arithmetic stays
+ * FP32 and the energy sum FP64 in every mode.  Errors: REANN_E_ARG.
+ */
 int reann_ctx_set_mlp_precision(reann_ctx* ctx, int precision);
 
 /* Message of the last failure on `ctx` (static storage of the context). */

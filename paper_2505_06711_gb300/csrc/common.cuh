@@ -36,6 +36,7 @@ enum Flag {
     FLAG_MAXNBR = 3,
     FLAG_SPECIES = 4,
     FLAG_MOVED = 5,
+    FLAG_TIMEOUT = 6,
     NFLAGS = 8
 };
 
@@ -111,6 +112,18 @@ struct Tile {
     int elem, row0, nrows, pad;
 };
 
+// BF16 weight images of one (layer, element) network for the tensor-core path,
+// 64 KiB: forward hi | forward lo | backward hi | backward lo, each 16 KiB in the
+// K-major core-matrix layout; forward = W1^T 64x48 | W2^T 64x64 | W3^T 16x64,
+// backward = W3 64x16 | W2 64x64 | W1 48x64; lo = BF16 rounding of w - hi.
+struct TcImg {
+    const uint8_t* img;
+    const float *b1, *b2, *b3;
+};
+struct TcTable {
+    TcImg img[8][MAX_ELEM];
+};
+
 // Resident scratch of the neighbour build, kept so that rebuilds neither
 // allocate nor synchronise.
 struct NlistScratch {
@@ -119,6 +132,7 @@ struct NlistScratch {
     int32_t *gcnt = nullptr, *goff = nullptr;  // ghosts per atom and offsets; goff[n] = ghost count
     int32_t* species_c = nullptr;              // caller-order species
     int32_t *ekey = nullptr, *ecounts = nullptr, *estart = nullptr, *eorder = nullptr;
+    int32_t *scat = nullptr, *escat = nullptr;  // atomic-order scatter before the in-bucket ranking
     float4* p32 = nullptr;  // FP32 positions of owned + ghost slots for the pre-test
 };
 
@@ -146,7 +160,9 @@ struct reann_nlist {
     int32_t* nbr_cnt = nullptr;    // N
     int32_t* live = nullptr;       // N x stride, live (d < r_c) entries first
     int32_t* live_cnt = nullptr;   // N
-    reann::Tile* tiles = nullptr;  // MLP tiles
+    reann::Tile* tiles = nullptr;  // MLP tiles (64 rows, FP32 networks)
+    std::vector<reann::Tile> tiles128_h;
+    reann::Tile* tiles128 = nullptr;  // 128-row tiles of the tensor-core networks
     double* pos_ref = nullptr;     // N x 3 FP64 caller positions at build (caller order)
     // per-evaluation state (resident)
     float4* pos_hi = nullptr;      // N + g_cap
@@ -180,6 +196,7 @@ struct reann_ctx {
     const float* d_c0 = nullptr;   // [n_elem][8]
     const float* d_W = nullptr;    // [T][3][8][16]
     void* d_bf16 = nullptr;        // BF16 weight images for the tensor-core networks
+    reann::TcTable tc{};
     int* d_flags = nullptr;        // reann::NFLAGS ints
     int* h_flags = nullptr;        // pinned mirror
     std::string err;
@@ -230,6 +247,12 @@ cudaError_t launch_unpermute_rows(cudaStream_t s, const reann_nlist* nl, const f
 // atomic networks, FP32 SIMT (mlp_fp32.cu)
 cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
                                const float* rho, float* out, int out_stride);
+// atomic networks, BF16 on tcgen05 tensor cores (mlp_tc.cu)
+cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
+                              bool split, const float* rho, float* out, int out_stride, int* flags);
+cudaError_t launch_mlp_bwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
+                              bool split, const float* rho, const float* ybar, float* rhobar, int* flags);
+
 cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
                                const float* rho, const float* ybar, float* rhobar);
 

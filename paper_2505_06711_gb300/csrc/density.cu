@@ -111,7 +111,7 @@ __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast
 __device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 
 // ------------------------------------------------------------- forward ---
-__global__ void __launch_bounds__(kWarps * 32) k_density_fwd(int64_t n, int stride, Radial R,
+__global__ void __launch_bounds__(kWarps * 32, 2) k_density_fwd(int64_t n, int stride, Radial R,
                                                             const int32_t* __restrict__ live,
                                                             const int32_t* __restrict__ live_cnt,
                                                             const float4* __restrict__ phi_hi,

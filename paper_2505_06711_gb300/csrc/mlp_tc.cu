@@ -1,0 +1,552 @@
+// Per-element atomic networks on the 5th-generation tensor cores (tcgen05),
+// BF16 operands, FP32 accumulation in tensor memory (TMEM).
+//
+// Sec. 2.1, Eq. 2: c^{t+1}_i = M^t_{Z_i}(rho^t_i), 48 -> 64 -> 64 -> 8, and the
+// energy network 48 -> 64 -> 64 -> 1, SiLU between layers; the reverse pass
+// (Eqs. 4-5) needs rhobar = J^T ybar only (a vector-Jacobian product).
+//
+// One CTA of 128 threads takes a tile of 128 consecutive atoms of one element
+// (atoms are stored element-major).  Per layer, thread 0 issues
+// tcgen05.mma.cta_group::1.kind::f16 (M = 128, K = 16 per instruction) with A
+// (activations) and B (weights, N x K) in shared memory in the K-major
+// no-swizzle core-matrix layout and D in TMEM; tcgen05.commit arrives on an
+// mbarrier that all threads wait on.  Thread r then reads TMEM lane r
+// (tcgen05.ld 32x32b), applies bias and SiLU (or its derivative) in FP32,
+// rounds to BF16 and writes the next layer's A tile.  Weight images are laid
+// out once on the host in the same core-matrix layout and copied to shared
+// memory with bulk asynchronous copies (cp.async.bulk, TMA engine).
+//
+// Two precisions share the kernels:
+//   plain BF16 (SPLIT = false): one MMA per K step, BF16 operands;
+//   split BF16 (SPLIT = true): every operand is a BF16 pair x = hi + lo and
+//     each K step issues hi*hi + hi*lo + lo*hi, still BF16 tensor-core MMAs
+//     with FP32 accumulation but with ~16 significant bits per operand.  In a
+//     crystal every atom feeds the networks nearly the same inputs, so plain
+//     BF16 rounding shifts every atomic energy the same way; the split form
+//     removes that shift.
+//
+// Core-matrix layout of an R x K BF16 tile: 8 x 8 blocks of 128 contiguous
+// bytes (8 rows of 16 bytes); block (r/8, k/8) at byte (r/8 * K/8 + k/8) * 128.
+// Descriptor: LBO = 128 B (next block along K), SBO = 16 K bytes (next 8-row
+// group).
+//
+// Every wait is bounded: after kSpinLimit polls a CTA records FLAG_TIMEOUT in
+// the context flags, frees its TMEM and returns (reann_ctx_check reports
+// REANN_E_TIMEOUT).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace reann {
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kRows = 128;
+constexpr uint32_t kTmemCols = 256;
+constexpr long long kSpinLimit = 1ll << 26;
+
+// ------------------------------------------------------------- PTX glue ---
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// K-major, no swizzle, sm_100-family descriptor (version field = 1 at bit 46)
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
+    d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;  // base offset 0, relative LBO, layout type 0 (no swizzle)
+}
+
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+    return (1u << 4)                      // D format F32
+           | (1u << 7)                    // A format BF16
+           | (1u << 10)                   // B format BF16
+           | ((uint32_t)(N >> 3) << 17)   // N / 8
+           | ((uint32_t)(M >> 4) << 24);  // M / 16
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(mbar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// bounded wait for phase `parity`; returns false when the limit ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+    const uint32_t a = smem_addr(mbar);
+    for (long long it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// global -> shared bulk copy (TMA engine), completion counted on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float silu(float z) { return z / (1.f + expf(-z)); }
+__device__ __forceinline__ float dsilu(float z) {
+    const float s = 1.f / (1.f + expf(-z));
+    return s * (1.f + z * (1.f - s));
+}
+
+// Write 8 values (k = 8 kc .. 8 kc + 7) of row r into a core-matrix tile with K
+// columns: the BF16 rounding into `hi` and, when `lo` is given, the BF16
+// rounding of the remainder into `lo` (so that hi + lo carries ~16 bits).
+__device__ __forceinline__ void put8(uint8_t* hi, uint8_t* lo, int K, int r, int kc, const float* v) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * p], v[2 * p + 1]);
+        h[p] = *reinterpret_cast<const uint32_t*>(&b);
+        if (lo) {
+            const float2 f = __bfloat1622float2(b);
+            const __nv_bfloat162 c = __floats2bfloat162_rn(v[2 * p] - f.x, v[2 * p + 1] - f.y);
+            l[p] = *reinterpret_cast<const uint32_t*>(&c);
+        }
+    }
+    const size_t off = (size_t)((r >> 3) * (K >> 3) + kc) * 128 + (r & 7) * 16;
+    *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    if (lo) *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// 16 KiB weight images per (layer, element), laid out by the host:
+//   forward  (W1^T 64x48 | W2^T 64x64 | W3^T 16x64), backward (W3 64x16 | W2 64x64 | W1 48x64);
+// in memory: forward hi | forward lo | backward hi | backward lo (lo = BF16 remainder).
+constexpr uint32_t kImg = 16384;
+constexpr uint32_t kF_W1t = 0, kF_W2t = 6144, kF_W3t = 14336;
+constexpr uint32_t kB_W3p = 0, kB_W2 = 2048, kB_W1 = 10240;
+
+// shared-memory layouts (bytes); lo tiles exist only in the split form
+template <bool SPLIT>
+struct FwdSmem {
+    static constexpr uint32_t S = SPLIT ? 2 : 1;
+    static constexpr uint32_t W = 0, A = kImg * S, H = A + 12288 * S, BAR = H + 16384 * S;
+    static constexpr uint32_t WLO = W + kImg, ALO = A + 12288, HLO = H + 16384;
+    static constexpr int BYTES = BAR + 64;
+    static constexpr int REQUEST = 110 * 1024;  // > 1/3 of an SM's shared memory: at most 2 CTAs (2 x 256 TMEM columns)
+};
+template <bool SPLIT>
+struct BwdSmem {
+    static constexpr uint32_t S = SPLIT ? 2 : 1;
+    static constexpr uint32_t WF = 0, WB = kImg * S, A = 2 * kImg * S, H = A + 12288 * S, Y = H + 16384 * S,
+                              BAR = Y + 4096 * S;
+    static constexpr uint32_t WFLO = WF + kImg, WBLO = WB + kImg, ALO = A + 12288, HLO = H + 16384, YLO = Y + 4096;
+    static constexpr int BYTES = BAR + 64;
+    static constexpr int REQUEST = SPLIT ? 132 * 1024 : 110 * 1024;  // split: one CTA per SM
+};
+static_assert(FwdSmem<true>::BYTES <= FwdSmem<true>::REQUEST, "forward shared memory");
+static_assert(BwdSmem<true>::BYTES <= BwdSmem<true>::REQUEST, "backward shared memory");
+
+struct TcNet {
+    const uint8_t* img;  // forward hi | forward lo | backward hi | backward lo
+    const float *b1, *b2, *b3;
+};
+struct TcLayer {
+    TcNet e[MAX_ELEM];
+};
+
+__device__ __forceinline__ uint32_t lane_addr(uint32_t tmem, int warp, int col) {
+    return tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col;
+}
+
+// uniform bounded wait: every thread polls; the CTA agrees on the outcome
+__device__ __forceinline__ bool wait_all(uint64_t* bar, uint32_t parity) {
+    const bool ok = mbar_wait(bar, parity);
+    return __syncthreads_and(ok);
+}
+
+__device__ __forceinline__ void fail(int* flags, uint64_t* bar, uint32_t parity) {
+    if (threadIdx.x == 0) atomicOr(&flags[FLAG_TIMEOUT], 1);
+    mbar_wait(bar, parity);  // give work in flight one more bounded chance to land
+    __syncthreads();
+}
+
+// rows [row0, row0 + nrows) of a row-major FP32 [.][48] array -> BF16 core-matrix tile(s) (K = 48)
+__device__ __forceinline__ void load_x_tile(uint8_t* hi, uint8_t* lo, const float* __restrict__ x, const Tile& tl,
+                                            int r) {
+#pragma unroll
+    for (int kc = 0; kc < NFEAT / 8; ++kc) {
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (r < tl.nrows) {
+            const float4 a = *reinterpret_cast<const float4*>(x + (size_t)(tl.row0 + r) * NFEAT + 8 * kc);
+            const float4 b = *reinterpret_cast<const float4*>(x + (size_t)(tl.row0 + r) * NFEAT + 8 * kc + 4);
+            v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+        }
+        put8(hi, lo, NFEAT, r, kc, v);
+    }
+}
+
+// D[cols] (+)= A (K = 16 ks_count) x B^T for one 128-row tile; split form adds hi*lo + lo*hi
+template <bool SPLIT>
+__device__ __forceinline__ void issue(uint32_t tmem_d, const uint8_t* A, const uint8_t* Alo, int KA,
+                                      const uint8_t* B, const uint8_t* Blo, int N, int ks_count) {
+    const uint32_t idesc = make_idesc(kRows, N);
+    const uint32_t a0 = smem_addr(A), b0 = smem_addr(B);
+    const uint32_t a1 = SPLIT ? smem_addr(Alo) : 0u, b1 = SPLIT ? smem_addr(Blo) : 0u;
+    for (int ks = 0; ks < ks_count; ++ks) {
+        const uint64_t ah = make_desc(a0 + ks * 256, 128, 16 * KA), bh = make_desc(b0 + ks * 256, 128, 16 * KA);
+        mma_bf16(tmem_d, ah, bh, idesc, ks > 0 ? 1u : 0u);
+        if (SPLIT) {
+            mma_bf16(tmem_d, ah, make_desc(b1 + ks * 256, 128, 16 * KA), idesc, 1u);
+            mma_bf16(tmem_d, make_desc(a1 + ks * 256, 128, 16 * KA), bh, idesc, 1u);
+        }
+    }
+}
+
+// between "threads wrote shared memory / read TMEM" and "thread 0 issues MMAs"
+__device__ __forceinline__ void handoff() {
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+__device__ __forceinline__ uint32_t setup(uint32_t* tslot, uint64_t* bar) {
+    if ((threadIdx.x >> 5) == 0) tmem_alloc(tslot, kTmemCols);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    return *tslot;
+}
+
+__device__ __forceinline__ void teardown(uint32_t tmem) {
+    tc_fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// TMEM columns [c, c + 64) of this lane -> act(v + bias) -> row r of an A tile (K = 64)
+template <bool SPLIT>
+__device__ __forceinline__ void silu_to_tile(uint32_t tmem, int warp, int c, const float* __restrict__ bias,
+                                             uint8_t* hi, uint8_t* lo, int r) {
+    float v[16], h[16];
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+        tmem_ld16(lane_addr(tmem, warp, c + c0), v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) h[i] = silu(v[i] + bias[c0 + i]);
+        put8(hi, SPLIT ? lo : nullptr, 64, r, c0 / 8, h);
+        put8(hi, SPLIT ? lo : nullptr, 64, r, c0 / 8 + 1, h + 8);
+    }
+}
+
+// g (columns [cg, cg + 64)) * silu'(z + bias) (z in columns [cz, cz + 64)) -> row r of an A tile
+template <bool SPLIT>
+__device__ __forceinline__ void dsilu_to_tile(uint32_t tmem, int warp, int cg, int cz, const float* __restrict__ bias,
+                                              uint8_t* hi, uint8_t* lo, int r) {
+    float g[16], z[16], h[16];
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+        tmem_ld16(lane_addr(tmem, warp, cg + c0), g);
+        tmem_ld16(lane_addr(tmem, warp, cz + c0), z);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) h[i] = g[i] * dsilu(z[i] + bias[c0 + i]);
+        put8(hi, SPLIT ? lo : nullptr, 64, r, c0 / 8, h);
+        put8(hi, SPLIT ? lo : nullptr, 64, r, c0 / 8 + 1, h + 8);
+    }
+}
+
+// forward: TMEM columns [0,64) z1, [64,128) z2, [128,144) y
+template <int OUT, bool SPLIT>
+__global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_fwd(TcLayer nets, const Tile* __restrict__ tiles,
+                                                           const float* __restrict__ rho, float* __restrict__ out,
+                                                           int out_stride, int* __restrict__ flags) {
+    using L = FwdSmem<SPLIT>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::BAR);  // [0] weights, [1] MMA
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, r = tid;
+    const Tile tl = tiles[blockIdx.x];
+    const TcNet& w = nets.e[tl.elem];
+    const uint32_t tmem = setup(tslot, bar);
+    if (tid == 0) {
+        mbar_expect_tx(&bar[0], kImg * L::S);
+        bulk_g2s(smem + L::W, w.img, kImg * L::S, &bar[0]);  // forward hi (| lo)
+    }
+    load_x_tile(smem + L::A, SPLIT ? smem + L::ALO : nullptr, rho, tl, r);
+    handoff();
+    bool ok = wait_all(&bar[0], 0);
+    if (!ok) {
+        fail(flags, &bar[0], 0);
+    } else {
+        if (tid == 0) {  // z1 = x W1
+            issue<SPLIT>(tmem, smem + L::A, smem + L::ALO, NFEAT, smem + L::W + kF_W1t, smem + L::WLO + kF_W1t, H1,
+                         NFEAT / 16);
+            mma_commit(&bar[1]);
+        }
+        ok = wait_all(&bar[1], 0);
+        if (!ok) fail(flags, &bar[1], 0);
+    }
+    if (ok) {
+        tc_fence_after();
+        silu_to_tile<SPLIT>(tmem, warp, 0, w.b1, smem + L::H, smem + L::HLO, r);
+        handoff();
+        if (tid == 0) {  // z2 = h1 W2
+            issue<SPLIT>(tmem + 64, smem + L::H, smem + L::HLO, H1, smem + L::W + kF_W2t, smem + L::WLO + kF_W2t, H2,
+                         H1 / 16);
+            mma_commit(&bar[1]);
+        }
+        ok = wait_all(&bar[1], 1);
+        if (!ok) fail(flags, &bar[1], 1);
+    }
+    if (ok) {
+        tc_fence_after();
+        silu_to_tile<SPLIT>(tmem, warp, 64, w.b2, smem + L::H, smem + L::HLO, r);
+        handoff();
+        if (tid == 0) {  // y = h2 W3 (N padded to 16)
+            issue<SPLIT>(tmem + 128, smem + L::H, smem + L::HLO, H2, smem + L::W + kF_W3t, smem + L::WLO + kF_W3t, 16,
+                         H2 / 16);
+            mma_commit(&bar[1]);
+        }
+        ok = wait_all(&bar[1], 0);
+        if (!ok) fail(flags, &bar[1], 0);
+    }
+    if (ok) {
+        tc_fence_after();
+        float v[16];
+        tmem_ld16(lane_addr(tmem, warp, 128), v);
+        if (r < tl.nrows) {
+            float* o = out + (size_t)(tl.row0 + r) * out_stride;
+#pragma unroll
+            for (int i = 0; i < OUT; ++i) o[i] = v[i] + w.b3[i];
+        }
+    }
+    teardown(tmem);
+}
+
+// rhobar = J^T ybar, recomputing z1, z2.  TMEM columns: [0,64) z1, [64,128) z2,
+// [128,192) ybar W3^T then rhobar (48), [192,256) z2bar W2^T.
+template <int OUT, bool SPLIT>
+__global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_bwd(TcLayer nets, const Tile* __restrict__ tiles,
+                                                           const float* __restrict__ rho,
+                                                           const float* __restrict__ ybar,
+                                                           float* __restrict__ rhobar, int* __restrict__ flags) {
+    using L = BwdSmem<SPLIT>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::BAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, r = tid;
+    const Tile tl = tiles[blockIdx.x];
+    const TcNet& w = nets.e[tl.elem];
+    const uint32_t tmem = setup(tslot, bar);
+    if (tid == 0) {
+        mbar_expect_tx(&bar[0], 2 * kImg * L::S);
+        bulk_g2s(smem + L::WF, w.img, kImg * L::S, &bar[0]);             // forward hi (| lo)
+        bulk_g2s(smem + L::WB, w.img + 2 * kImg, kImg * L::S, &bar[0]);  // backward hi (| lo)
+    }
+    load_x_tile(smem + L::A, SPLIT ? smem + L::ALO : nullptr, rho, tl, r);
+    {
+        float y[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) y[i] = 0.f;
+        if (r < tl.nrows) {
+            if (OUT == 1)
+                y[0] = 1.f;  // d eps_i / d eps_i
+            else
+#pragma unroll
+                for (int i = 0; i < OUT; ++i) y[i] = ybar[(size_t)(tl.row0 + r) * OUT + i];
+        }
+        put8(smem + L::Y, SPLIT ? smem + L::YLO : nullptr, 16, r, 0, y);
+        put8(smem + L::Y, SPLIT ? smem + L::YLO : nullptr, 16, r, 1, y + 8);
+    }
+    handoff();
+    bool ok = wait_all(&bar[0], 0);
+    if (!ok) {
+        fail(flags, &bar[0], 0);
+    } else {
+        if (tid == 0) {
+            issue<SPLIT>(tmem, smem + L::A, smem + L::ALO, NFEAT, smem + L::WF + kF_W1t, smem + L::WFLO + kF_W1t, H1,
+                         NFEAT / 16);  // z1
+            issue<SPLIT>(tmem + 128, smem + L::Y, smem + L::YLO, 16, smem + L::WB + kB_W3p, smem + L::WBLO + kB_W3p,
+                         H2, 1);  // ybar W3^T
+            mma_commit(&bar[1]);
+        }
+        ok = wait_all(&bar[1], 0);
+        if (!ok) fail(flags, &bar[1], 0);
+    }
+    if (ok) {
+        tc_fence_after();
+        silu_to_tile<SPLIT>(tmem, warp, 0, w.b1, smem + L::H, smem + L::HLO, r);
+        handoff();
+        if (tid == 0) {  // z2
+            issue<SPLIT>(tmem + 64, smem + L::H, smem + L::HLO, H1, smem + L::WF + kF_W2t, smem + L::WFLO + kF_W2t,
+                         H2, H1 / 16);
+            mma_commit(&bar[1]);
+        }
+        ok = wait_all(&bar[1], 1);
+        if (!ok) fail(flags, &bar[1], 1);
+    }
+    if (ok) {
+        tc_fence_after();
+        dsilu_to_tile<SPLIT>(tmem, warp, 128, 64, w.b2, smem + L::H, smem + L::HLO, r);  // z2bar
+        handoff();
+        if (tid == 0) {  // z2bar W2^T
+            issue<SPLIT>(tmem + 192, smem + L::H, smem + L::HLO, H2, smem + L::WB + kB_W2, smem + L::WBLO + kB_W2, H1,
+                         H2 / 16);
+            mma_commit(&bar[1]);
+        }
+        ok = wait_all(&bar[1], 0);
+        if (!ok) fail(flags, &bar[1], 0);
+    }
+    if (ok) {
+        tc_fence_after();
+        dsilu_to_tile<SPLIT>(tmem, warp, 192, 0, w.b1, smem + L::H, smem + L::HLO, r);  // z1bar
+        handoff();
+        if (tid == 0) {  // rhobar = z1bar W1^T
+            issue<SPLIT>(tmem + 128, smem + L::H, smem + L::HLO, H1, smem + L::WB + kB_W1, smem + L::WBLO + kB_W1,
+                         NFEAT, H1 / 16);
+            mma_commit(&bar[1]);
+        }
+        ok = wait_all(&bar[1], 1);
+        if (!ok) fail(flags, &bar[1], 1);
+    }
+    if (ok) {
+        tc_fence_after();
+        float v[16];
+#pragma unroll
+        for (int c0 = 0; c0 < NFEAT; c0 += 16) {
+            tmem_ld16(lane_addr(tmem, warp, 128 + c0), v);
+            if (r < tl.nrows) {
+                float4* dst = reinterpret_cast<float4*>(rhobar + (size_t)(tl.row0 + r) * NFEAT + c0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+        }
+    }
+    teardown(tmem);
+}
+
+TcLayer layer_of(const TcTable& t, int layer) {
+    TcLayer l;
+    for (int e = 0; e < MAX_ELEM; ++e) l.e[e] = TcNet{t.img[layer][e].img, t.img[layer][e].b1, t.img[layer][e].b2,
+                                                      t.img[layer][e].b3};
+    return l;
+}
+
+template <int OUT, bool SPLIT>
+void set_attrs() {
+    cudaFuncSetAttribute(k_mlp_tc_fwd<OUT, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         FwdSmem<SPLIT>::REQUEST);
+    cudaFuncSetAttribute(k_mlp_tc_bwd<OUT, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         BwdSmem<SPLIT>::REQUEST);
+}
+
+void ensure_tc_attrs() {
+    static bool done = false;
+    if (done) return;
+    set_attrs<1, false>();
+    set_attrs<NPHI, false>();
+    set_attrs<1, true>();
+    set_attrs<NPHI, true>();
+    done = true;
+}
+
+template <int OUT, bool SPLIT>
+void fwd_launch(cudaStream_t s, int nt, const TcLayer& l, const Tile* tiles, const float* rho, float* out,
+                int out_stride, int* flags) {
+    k_mlp_tc_fwd<OUT, SPLIT><<<nt, kThreads, FwdSmem<SPLIT>::REQUEST, s>>>(l, tiles, rho, out, out_stride, flags);
+}
+
+template <int OUT, bool SPLIT>
+void bwd_launch(cudaStream_t s, int nt, const TcLayer& l, const Tile* tiles, const float* rho, const float* ybar,
+                float* rhobar, int* flags) {
+    k_mlp_tc_bwd<OUT, SPLIT><<<nt, kThreads, BwdSmem<SPLIT>::REQUEST, s>>>(l, tiles, rho, ybar, rhobar, flags);
+}
+
+}  // namespace
+
+cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
+                              bool split, const float* rho, float* out, int out_stride, int* flags) {
+    const int nt = (int)nl->tiles128_h.size();
+    if (nt == 0) return cudaSuccess;
+    ensure_tc_attrs();
+    const TcLayer l = layer_of(nets, t);
+    if (energy)
+        (split ? fwd_launch<1, true> : fwd_launch<1, false>)(s, nt, l, nl->tiles128, rho, out, out_stride, flags);
+    else
+        (split ? fwd_launch<NPHI, true> : fwd_launch<NPHI, false>)(s, nt, l, nl->tiles128, rho, out, out_stride,
+                                                                    flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_bwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
+                              bool split, const float* rho, const float* ybar, float* rhobar, int* flags) {
+    const int nt = (int)nl->tiles128_h.size();
+    if (nt == 0) return cudaSuccess;
+    ensure_tc_attrs();
+    const TcLayer l = layer_of(nets, t);
+    if (energy)
+        (split ? bwd_launch<1, true> : bwd_launch<1, false>)(s, nt, l, nl->tiles128, rho, ybar, rhobar, flags);
+    else
+        (split ? bwd_launch<NPHI, true> : bwd_launch<NPHI, false>)(s, nt, l, nl->tiles128, rho, ybar, rhobar, flags);
+    return cudaGetLastError();
+}
+
+}  // namespace reann

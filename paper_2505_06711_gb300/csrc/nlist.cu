@@ -155,20 +155,25 @@ __global__ void k_scatter(int64_t n, const int32_t* __restrict__ key, const int3
     order[p] = (int32_t)i;
 }
 
-// sort every bucket ascending (buckets are small: tens of entries)
-__global__ void k_bucket_sort(int64_t nkeys, const int32_t* __restrict__ start, int32_t* __restrict__ order) {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nkeys) return;
-    int lo = start[b], hi = start[b + 1];
-    for (int a = lo + 1; a < hi; ++a) {
-        int v = order[a];
-        int c = a - 1;
-        while (c >= lo && order[c] > v) {
-            order[c + 1] = order[c];
-            --c;
-        }
-        order[c + 1] = v;
+// Deterministic placement inside each bucket: the entry at position p of the
+// atomic-order scatter moves to start[b] + (number of entries of its bucket with
+// a smaller index).  One thread per entry, each scanning its own bucket (buckets
+// hold tens of entries); entries of buckets >= sorted_keys keep their position.
+__global__ void k_bucket_rank(int64_t n, const int32_t* __restrict__ key, const int32_t* __restrict__ start,
+                              const int32_t* __restrict__ scattered, int64_t sorted_keys,
+                              int32_t* __restrict__ order) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int32_t v = scattered[p];
+    const int32_t b = key[v];
+    if (b >= sorted_keys) {
+        order[p] = v;
+        return;
     }
+    const int lo = start[b], hi = start[b + 1];
+    int rank = 0;
+    for (int q = lo; q < hi; ++q) rank += scattered[q] < v;
+    order[lo + rank] = v;
 }
 
 // 2. gather per-atom arrays into internal order
@@ -405,13 +410,15 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 // `sorted_keys` buckets (later buckets hold unused capacity whose order does not matter);
 // start = bucket offsets.
 static cudaError_t counting_sort(cudaStream_t s, int64_t n, int64_t nkeys, const int32_t* key, int32_t* counts,
-                                 int32_t* start, int32_t* order, int64_t sorted_keys) {
+                                 int32_t* start, int32_t* scattered, int32_t* order, int64_t sorted_keys) {
     cudaMemsetAsync(counts, 0, sizeof(int32_t) * nkeys, s);
     if (n > 0) k_hist<<<blocks_for(n, 256), 256, 0, s>>>(n, key, counts);
     k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(nkeys, counts, start);
     cudaMemsetAsync(counts, 0, sizeof(int32_t) * nkeys, s);
-    if (n > 0) k_scatter<<<blocks_for(n, 256), 256, 0, s>>>(n, key, start, counts, order);
-    if (sorted_keys > 0) k_bucket_sort<<<blocks_for(sorted_keys, 128), 128, 0, s>>>(sorted_keys, start, order);
+    if (n > 0) {
+        k_scatter<<<blocks_for(n, 256), 256, 0, s>>>(n, key, start, counts, scattered);
+        k_bucket_rank<<<blocks_for(n, 256), 256, 0, s>>>(n, key, start, scattered, sorted_keys, order);
+    }
     return cudaGetLastError();
 }
 
@@ -439,7 +446,7 @@ static cudaError_t stage_sort_and_count(cudaStream_t s, reann_nlist* nl, const d
     cudaMemcpyAsync(nl->pos_ref, pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s);
     k_wrap_key<<<blocks_for(n, 256), 256, 0, s>>>(n, pos, w.species_c, nl->n_elem, nl->geom, w.xw_c, w.fw_c, w.mw_c,
                                                   w.key, flags);
-    counting_sort(s, n, owned_keys(nl), w.key, w.counts, w.start, nl->perm, owned_keys(nl));
+    counting_sort(s, n, owned_keys(nl), w.key, w.counts, w.start, w.scat, nl->perm, owned_keys(nl));
     k_gather_internal<<<blocks_for(n, 256), 256, 0, s>>>(n, nl->perm, w.xw_c, w.fw_c, w.mw_c, w.species_c, w.xw, w.fw,
                                                          nl->wrapm, nl->species);
     k_ghosts<false><<<blocks_for(n, 256), 256, 0, s>>>(n, nl->geom, w.fw, nullptr, w.gcnt, nullptr, nullptr, 0, flags);
@@ -456,7 +463,7 @@ static cudaError_t stage_ghosts_and_bins(cudaStream_t s, reann_nlist* nl, int* f
     const int64_t nx = ext_bins(nl);
     k_ext_key<<<blocks_for(next, 256), 256, 0, s>>>(n, w.goff + n, nl->g_cap, nl->geom, w.xw, w.fw, nl->g_owner,
                                                     nl->g_shift, w.ekey, w.p32, (int32_t)nx);
-    counting_sort(s, next, nx + 1, w.ekey, w.ecounts, w.estart, w.eorder, nx);
+    counting_sort(s, next, nx + 1, w.ekey, w.ecounts, w.estart, w.escat, w.eorder, nx);
     return cudaGetLastError();
 }
 
@@ -484,12 +491,13 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
     w.gcnt = dalloc<int32_t>(nl, n);
     w.goff = dalloc<int32_t>(nl, n + 1);
     w.species_c = dalloc<int32_t>(nl, n);
+    w.scat = dalloc<int32_t>(nl, n);
     nl->perm = dalloc<int32_t>(nl, n);
     nl->species = dalloc<int32_t>(nl, n);
     nl->wrapm = dalloc<int32_t>(nl, 3 * n);
     nl->pos_ref = dalloc<double>(nl, 3 * n);
     if (!w.xw_c || !w.fw_c || !w.mw_c || !w.key || !w.counts || !w.start || !w.xw || !w.fw || !w.gcnt || !w.goff ||
-        !w.species_c || !nl->perm || !nl->species || !nl->wrapm || !nl->pos_ref)
+        !w.species_c || !w.scat || !nl->perm || !nl->species || !nl->wrapm || !nl->pos_ref)
         return set_error(ctx, REANN_E_NOMEM, "neighbour-list allocation failed");
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(w.species_c, species, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     REANN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * NFLAGS, s));
@@ -519,7 +527,8 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
     w.ecounts = dalloc<int32_t>(nl, nx + 1);
     w.estart = dalloc<int32_t>(nl, nx + 2);
     w.eorder = dalloc<int32_t>(nl, next);
-    if (!nl->g_owner || !nl->g_shift || !w.ekey || !w.p32 || !w.ecounts || !w.estart || !w.eorder)
+    w.escat = dalloc<int32_t>(nl, next);
+    if (!nl->g_owner || !nl->g_shift || !w.ekey || !w.p32 || !w.ecounts || !w.estart || !w.eorder || !w.escat)
         return set_error(ctx, REANN_E_NOMEM, "ghost allocation failed");
     REANN_CUDA_TRY(ctx, stage_ghosts_and_bins(s, nl, ctx->d_flags));
     // row capacity: expected neighbours from the number density, with headroom

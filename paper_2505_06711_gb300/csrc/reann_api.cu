@@ -115,6 +115,15 @@ int alloc_eval_buffers(reann_ctx* ctx, reann_nlist* nl) {
         for (int r = nl->elem_start[e]; r < nl->elem_start[e + 1]; r += MLP_TILE)
             nl->tiles_h.push_back(Tile{e, r, std::min(MLP_TILE, nl->elem_start[e + 1] - r), 0});
     nl->tiles = nl_alloc<Tile>(nl, nl->tiles_h.size());
+    nl->tiles128_h.clear();
+    for (int e = 0; e < nl->n_elem; ++e)
+        for (int r = nl->elem_start[e]; r < nl->elem_start[e + 1]; r += 128)
+            nl->tiles128_h.push_back(Tile{e, r, std::min(128, nl->elem_start[e + 1] - r), 0});
+    nl->tiles128 = nl_alloc<Tile>(nl, nl->tiles128_h.size());
+    if (!nl->tiles128) return set_error(ctx, REANN_E_NOMEM, "evaluation buffers: out of device memory");
+    if (!nl->tiles128_h.empty())
+        REANN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->tiles128, nl->tiles128_h.data(), sizeof(Tile) * nl->tiles128_h.size(),
+                                            cudaMemcpyHostToDevice, ctx->stream));
     if (!nl->live || !nl->live_cnt || !nl->pos_hi || !nl->pos_lo || !nl->coef || !nl->rho || !nl->bck || !nl->eps ||
         !nl->rhobar || !nl->bbar || !nl->cbar || !nl->grad || !nl->partial || !nl->tiles)
         return set_error(ctx, REANN_E_NOMEM, "evaluation buffers: out of device memory");
@@ -131,6 +140,39 @@ void free_nlist(reann_nlist* nl) {
     if (!nl) return;
     for (void* p : nl->allocs) cudaFree(p);
     delete nl;
+}
+
+// FP32 -> BF16, round to nearest even
+uint16_t to_bf16(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+float from_bf16(uint16_t h) {
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// Append an R x K BF16 tile (src row-major with leading dimension ld, entries
+// beyond rows x cols zero) in the K-major core-matrix layout used by
+// tcgen05.mma: 8 x 8 blocks of 128 bytes, block (r/8, k/8) at (r/8 * K/8 + k/8).
+// With lo = true the tile holds the BF16 rounding of w - bf16(w) instead.
+void push_core(std::vector<uint16_t>& dst, const float* src, int ld, int rows, int cols, int R, int K,
+               bool lo = false) {
+    const size_t base = dst.size();
+    dst.resize(base + (size_t)R * K, 0);
+    for (int r = 0; r < R; ++r)
+        for (int k = 0; k < K; ++k) {
+            const float v = (r < rows && k < cols) ? src[(size_t)r * ld + k] : 0.f;
+            const uint16_t h = to_bf16(v);
+            dst[base + ((size_t)(r / 8) * (K / 8) + k / 8) * 64 + (r % 8) * 8 + (k % 8)] =
+                lo ? to_bf16(v - from_bf16(h)) : h;
+        }
 }
 
 // pad to a multiple of 4 floats so that float4 loads stay aligned
@@ -210,6 +252,7 @@ extern "C" int reann_ctx_create(const reann_model* model, void* cuda_stream, rea
         size_t W1, b1, W2, b2, W3, b3, W1t, W2t, W3t;
     };
     std::vector<Off> offs((size_t)M.T * M.n_elem);
+    std::vector<uint16_t> tcimg;  // per (t, e): forward hi | forward lo | backward hi | backward lo, 16 KiB each
     for (int t = 0; t < M.T; ++t) {
         const int outd = (t == M.T - 1) ? 1 : NPHI;
         for (int e = 0; e < M.n_elem; ++e) {
@@ -240,8 +283,28 @@ extern "C" int reann_ctx_create(const reann_model* model, void* cuda_stream, rea
             for (int u = 0; u < H2; ++u)
                 for (int q = 0; q < outd; ++q) tr[q * H2 + u] = W3[u * outd + q];
             o.W3t = img.size(); push_block(img, tr.data(), tr.size());
+            // BF16 images for the tensor-core networks (B operands are N x K, K-major)
+            std::vector<float> w1t(H1 * NFEAT), w2t(H2 * H1);
+            for (int f = 0; f < NFEAT; ++f)
+                for (int q = 0; q < H1; ++q) w1t[q * NFEAT + f] = W1[f * H1 + q];
+            for (int u = 0; u < H1; ++u)
+                for (int q = 0; q < H2; ++q) w2t[q * H1 + u] = W2[u * H2 + q];
+            for (int lo = 0; lo < 2; ++lo) {
+                push_core(tcimg, w1t.data(), NFEAT, H1, NFEAT, H1, NFEAT, lo);  // forward: W1^T
+                push_core(tcimg, w2t.data(), H1, H2, H1, H2, H1, lo);           //          W2^T
+                push_core(tcimg, tr.data(), H2, outd, H2, 16, H2, lo);          //          W3^T (rows padded to 16)
+            }
+            for (int lo = 0; lo < 2; ++lo) {
+                push_core(tcimg, W3, outd, H2, outd, H2, 16, lo);    // backward: W3 (K padded to 16)
+                push_core(tcimg, W2, H2, H1, H2, H1, H2, lo);        //           W2
+                push_core(tcimg, W1, H1, NFEAT, H1, NFEAT, H1, lo);  //           W1
+            }
         }
     }
+    if (cudaMalloc(&ctx->d_bf16, tcimg.size() * sizeof(uint16_t)) != cudaSuccess) return fail(REANN_E_NOMEM);
+    if (cudaMemcpy(ctx->d_bf16, tcimg.data(), tcimg.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return fail(REANN_E_CUDA);
     if (cudaMalloc(&ctx->d_params, img.size() * sizeof(float)) != cudaSuccess) return fail(REANN_E_NOMEM);
     if (cudaMemcpy(ctx->d_params, img.data(), img.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(REANN_E_CUDA);
@@ -253,6 +316,8 @@ extern "C" int reann_ctx_create(const reann_model* model, void* cuda_stream, rea
             const Off& o = offs[(size_t)t * M.n_elem + e];
             ctx->nets.net[t][e] = NetDev{base + o.W1, base + o.b1, base + o.W2, base + o.b2, base + o.W3,
                                          base + o.b3, base + o.W1t, base + o.W2t, base + o.W3t};
+            const uint8_t* ib = static_cast<const uint8_t*>(ctx->d_bf16) + ((size_t)t * M.n_elem + e) * 4 * 16384;
+            ctx->tc.img[t][e] = TcImg{ib, base + o.b1, base + o.b2, base + o.b3};
         }
     if (cudaMalloc(&ctx->d_flags, sizeof(int) * NFLAGS) != cudaSuccess) return fail(REANN_E_NOMEM);
     if (cudaMemset(ctx->d_flags, 0, sizeof(int) * NFLAGS) != cudaSuccess) return fail(REANN_E_CUDA);
@@ -278,7 +343,8 @@ extern "C" void reann_ctx_free(reann_ctx* ctx) {
 
 extern "C" int reann_ctx_set_mlp_precision(reann_ctx* ctx, int precision) {
     if (!ctx) return REANN_E_ARG;
-    if (precision != REANN_MLP_FP32) return set_error(ctx, REANN_E_ARG, "unsupported network precision");
+    if (precision != REANN_MLP_FP32 && precision != REANN_MLP_BF16 && precision != REANN_MLP_BF16X3)
+        return set_error(ctx, REANN_E_ARG, "unsupported network precision");
     ctx->precision = precision;
     return REANN_OK;
 }
@@ -292,9 +358,11 @@ extern "C" int reann_ctx_check(reann_ctx* ctx) {
     REANN_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     REANN_CUDA_TRY(ctx, cudaGetLastError());
     const int geom = ctx->h_flags[FLAG_GEOM], cap = ctx->h_flags[FLAG_NBR_OVERFLOW] | ctx->h_flags[FLAG_GHOST_OVERFLOW];
+    const int timeout = ctx->h_flags[FLAG_TIMEOUT];
     REANN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * NFLAGS, ctx->stream));
     if (geom) return set_error(ctx, REANN_E_GEOM, "coincident or non-finite atoms in an evaluation");
     if (cap) return set_error(ctx, REANN_E_CAPACITY, "neighbour or ghost capacity exceeded");
+    if (timeout) return set_error(ctx, REANN_E_TIMEOUT, "a bounded device wait ran out (tensor-core network)");
     return REANN_OK;
 }
 
@@ -438,11 +506,14 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
             REANN_CUDA_TRY(ctx, launch_density_fwd(s, nl, ctx->radial, ctx->d_W + t * lw, coef_t, rho_t, bck_t));
         }
         ProfScope p(ctx, PR_MLP_FWD);
-        if (t < T - 1)
-            REANN_CUDA_TRY(ctx, launch_mlp_fwd_f32(s, nl, ctx->nets, t, false, rho_t,
-                                                   nl->coef + (size_t)(t + 1) * ne * NPHI, NPHI));
+        const bool energy_net = t == T - 1;
+        float* out = energy_net ? nl->eps : nl->coef + (size_t)(t + 1) * ne * NPHI;
+        const int out_stride = energy_net ? 1 : NPHI;
+        if (ctx->precision != REANN_MLP_FP32)
+            REANN_CUDA_TRY(ctx, launch_mlp_fwd_tc(s, nl, ctx->tc, t, energy_net, ctx->precision == REANN_MLP_BF16X3,
+                                                  rho_t, out, out_stride, ctx->d_flags));
         else
-            REANN_CUDA_TRY(ctx, launch_mlp_fwd_f32(s, nl, ctx->nets, t, true, rho_t, nl->eps, 1));
+            REANN_CUDA_TRY(ctx, launch_mlp_fwd_f32(s, nl, ctx->nets, t, energy_net, rho_t, out, out_stride));
     }
     {
         ProfScope p(ctx, PR_ENERGY);
@@ -456,7 +527,12 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
         const float* bck_t = nl->bck + (size_t)t * n * NB;
         {
             ProfScope p(ctx, PR_MLP_BWD);
-            REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, rho_t, nl->cbar, nl->rhobar));
+            if (ctx->precision != REANN_MLP_FP32)
+                REANN_CUDA_TRY(ctx, launch_mlp_bwd_tc(s, nl, ctx->tc, t, t == T - 1,
+                                                      ctx->precision == REANN_MLP_BF16X3, rho_t, nl->cbar, nl->rhobar,
+                                                      ctx->d_flags));
+            else
+                REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, rho_t, nl->cbar, nl->rhobar));
         }
         {
             ProfScope p(ctx, PR_BBAR);
