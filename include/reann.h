@@ -242,6 +242,33 @@ const char* reann_profile_region_name(int region);
 int reann_ctx_profile_read(reann_ctx* ctx, double* total_ms, int64_t* launches);
 
 /*
+ * NVE molecular dynamics: n_steps velocity-Verlet steps of dt_fs (fs) with
+ * REANN forces (the benchmark systems' MD of Sec. 2.3 / 4.1 without a
+ * thermostat), positions and velocities integrated in FP64:
+ *   v += dt/2 F/m;  x += dt v;  if any atom moved more than skin/2 since the
+ *   last build: rebuild the list on the device;  F = -dE/dx;  v += dt/2 F/m.
+ *   pos    dev, N x 3 FP64 (A), caller order, updated in place
+ *   vel    dev, N x 3 FP64 (A/fs), updated in place
+ *   mass   dev, N FP64 (amu)
+ *   e_pot  dev, n_steps FP64: E after each step (eV), or NULL
+ *   e_kin  dev, n_steps FP64: kinetic energy after each step (eV), or NULL
+ * The first call (and any call whose pointers, dt, n_steps or network
+ * precision differ from the previous one) evaluates the starting forces and
+ * captures one step as a CUDA graph on a library-owned stream, ordered after
+ * the context stream; every step is then one graph launch, the rebuild being
+ * a device-side decision.  Asynchronous with respect to the host; the context
+ * stream waits for the steps.  Capacity overflow during a rebuild is reported
+ * by reann_ctx_check() (REANN_E_CAPACITY: build a new list).
+ * Errors: REANN_E_ARG, REANN_E_NOMEM, REANN_E_CUDA.
+ */
+int reann_md_step(reann_ctx* ctx, reann_nlist* nl, double* pos, double* vel, const double* mass, double dt_fs,
+                  int n_steps, double* e_pot, double* e_kin);
+
+/* Steps run by the last reann_md_step call and neighbour-list rebuilds since the
+ * first one (host outputs, nullable).  Synchronous. */
+int reann_md_info(reann_ctx* ctx, const reann_nlist* nl, int64_t* steps, int64_t* rebuilds);
+
+/*
  * Per-layer intermediates of the last evaluation of `nl`, in caller order
  * (inspection and testing): rho (dev, N x F FP32) and c (dev, N x N_phi FP32)
  * of layer `layer` in [0, T).  Either output may be NULL.  Asynchronous.

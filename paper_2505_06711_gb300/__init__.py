@@ -86,6 +86,20 @@ class System:
             self.pot.ctx, self.nl, p, self.pot.T, self.energy, self.forces, self.atom_energy if atom_energy else None
         )
 
+    def md(self, vel, mass, dt_fs: float, n_steps: int, record: bool = True):
+        """Run NVE velocity Verlet in place on self.pos / vel; returns (E_pot, E_kin) per step or None."""
+        import torch
+
+        e_pot = e_kin = None
+        if record:
+            e_pot = torch.zeros(n_steps, dtype=torch.float64, device=self.pot.device)
+            e_kin = torch.zeros(n_steps, dtype=torch.float64, device=self.pot.device)
+        binding.reann_md_step(self.pot.ctx, self.nl, self.pos, vel, mass, dt_fs, n_steps, e_pot, e_kin)
+        return (e_pot, e_kin) if record else None
+
+    def md_info(self):
+        return binding.reann_md_info(self.pot.ctx, self.nl)
+
     def layer(self, t: int):
         import torch
 

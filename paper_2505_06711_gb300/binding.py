@@ -67,6 +67,8 @@ _SIGS = {
     "reann_profile_regions": ([], _int),
     "reann_profile_region_name": ([_int], ctypes.c_char_p),
     "reann_ctx_profile_read": ([_vp, _vp, _vp], _int),
+    "reann_md_step": ([_vp, _vp, _vp, _vp, _vp, _dbl, _int, _vp, _vp], _int),
+    "reann_md_info": ([_vp, _vp, _vp, _vp], _int),
     "reann_energy_sum_noalloc": ([_vp, _i64, _vp, _vp], _int),
     "reann_energy_sum_noalloc_max_atoms": ([], _i64),
 }
@@ -233,6 +235,30 @@ def reann_nlist_rebuild(ctx, nl, pos) -> None:
 
     _dev(pos, torch.float64, None, "pos")
     _check(lib().reann_nlist_rebuild(ctx, nl, _ptr(pos)), ctx)
+
+
+# --------------------------------------------------------------------- MD --
+def reann_md_step(ctx, nl, pos, vel, mass, dt_fs: float, n_steps: int, e_pot=None, e_kin=None) -> None:
+    import torch
+
+    n = pos.shape[0]
+    _dev(pos, torch.float64, (n, 3), "pos")
+    _dev(vel, torch.float64, (n, 3), "vel")
+    _dev(mass, torch.float64, (n,), "mass")
+    for name, a in (("e_pot", e_pot), ("e_kin", e_kin)):
+        if a is not None:
+            _dev(a, torch.float64, None, name)
+            if a.numel() < n_steps:
+                raise ValueError(f"{name} holds fewer than n_steps entries")
+    _check(lib().reann_md_step(ctx, nl, _ptr(pos), _ptr(vel), _ptr(mass), float(dt_fs), int(n_steps), _ptr(e_pot),
+                               _ptr(e_kin)), ctx)
+
+
+def reann_md_info(ctx, nl) -> tuple[int, int]:
+    """(steps of the last reann_md_step call, rebuilds since the first call)."""
+    s, r = np.zeros(1, np.int64), np.zeros(1, np.int64)
+    _check(lib().reann_md_info(ctx, nl, _ptr(s), _ptr(r)), ctx)
+    return int(s[0]), int(r[0])
 
 
 # ---------------------------------------------------------- no-allocation --

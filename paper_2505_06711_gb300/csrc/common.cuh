@@ -182,6 +182,18 @@ struct reann_nlist {
     double* h2d_pos = nullptr;     // N x 3
     double* d_energy = nullptr;    // 1
     float* d_forces = nullptr;     // N x 3
+    // MD state: forces of the current positions, per-step energies, rebuild gate, graph
+    float* md_forces = nullptr;    // N x 3 (caller order)
+    double* md_scalars = nullptr;  // [0] E_pot, [1] E_kin
+    double* md_partial = nullptr;
+    int* md_ints = nullptr;        // [0] rebuild gate, [1] step counter, [2] rebuild count
+    bool md_forces_valid = false;
+    const double* md_forces_at = nullptr;  // positions the forces belong to
+    cudaGraph_t md_graph = nullptr;
+    cudaGraphExec_t md_exec = nullptr;
+    const void* md_key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    double md_dt = 0.0;
+    int md_precision = -1, md_nsteps = -1;
     std::vector<void*> allocs;
 };
 
@@ -201,6 +213,9 @@ struct reann_ctx {
     int* h_flags = nullptr;        // pinned mirror
     std::string err;
     int num_sms = 0;
+    // MD: a non-blocking stream the step graph is captured on and replayed on
+    cudaStream_t md_stream = nullptr;
+    cudaEvent_t md_ev[2] = {nullptr, nullptr};
     // optional per-region event profile
     bool prof_on = false;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_recs;
@@ -223,8 +238,17 @@ int set_error(reann_ctx* ctx, int code, const std::string& msg);
 // ---- launchers (defined in the .cu files) ----
 // neighbour list (nlist.cu)
 int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const int32_t* species);
-cudaError_t launch_rebuild(cudaStream_t s, reann_nlist* nl, const double* pos, int* flags);
-cudaError_t launch_moved(cudaStream_t s, const reann_nlist* nl, const double* pos, int* flags);
+cudaError_t launch_rebuild(cudaStream_t s, reann_nlist* nl, const double* pos, int* flags, const int* gate);
+cudaError_t launch_moved(cudaStream_t s, const reann_nlist* nl, const double* pos, int* moved);
+
+// velocity Verlet (md.cu)
+cudaError_t launch_kick(cudaStream_t s, int64_t n, double* vel, const float* forces, const double* mass,
+                        double half_dt);
+cudaError_t launch_drift(cudaStream_t s, int64_t n, double* pos, const double* vel, double dt);
+cudaError_t launch_ekin(cudaStream_t s, int64_t n, const double* vel, const double* mass, double* partial,
+                        double* out);
+cudaError_t launch_record(cudaStream_t s, int* counter, const double* epot, const double* ekin, double* epot_out,
+                          double* ekin_out, int n_steps, const int* gate, int* rebuilds);
 const int32_t* ghost_count_ptr(const reann_nlist* nl);
 cudaError_t launch_refresh_positions(cudaStream_t s, const reann_nlist* nl, const double* pos);
 cudaError_t launch_live_edges(cudaStream_t s, const reann_nlist* nl, float rc2, int* flags);

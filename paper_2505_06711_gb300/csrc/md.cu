@@ -1,0 +1,110 @@
+// NVE velocity-Verlet integration in FP64 around the REANN force evaluation.
+//
+// One MD step (captured once as a CUDA graph and replayed):
+//   v += (dt/2) F/m;  x += dt v;  rebuild the neighbour list if any atom moved
+//   more than skin/2 since the last build (gated kernels, no host round trip);
+//   E, F = REANN(x);  v += (dt/2) F/m;  K = sum m v^2 / 2 (FP64);  record E, K.
+// Units: A, fs, amu, eV; 1 eV/(A amu) = 9.648533212e-3 A/fs^2.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace reann {
+namespace {
+
+constexpr double kAccel = 9.648533212e-3;  // (eV/A)/amu -> A/fs^2
+constexpr int kThreads = 256, kPer = 8;
+
+__global__ void k_kick(int64_t n, double* __restrict__ vel, const float* __restrict__ forces,
+                       const double* __restrict__ mass, double half_dt) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * n) return;
+    vel[t] += half_dt * kAccel * (double)forces[t] / mass[t / 3];
+}
+
+__global__ void k_drift(int64_t n, double* __restrict__ pos, const double* __restrict__ vel, double dt) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < 3 * n) pos[t] += dt * vel[t];
+}
+
+// kinetic energy in eV, two-level FP64 tree (fixed order, deterministic)
+__global__ void __launch_bounds__(kThreads) k_ekin_partial(int64_t n, const double* __restrict__ vel,
+                                                           const double* __restrict__ mass,
+                                                           double* __restrict__ partial) {
+    __shared__ double sm[kThreads];
+    const int64_t base = (int64_t)blockIdx.x * kThreads * kPer;
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const int64_t i = base + k * kThreads + threadIdx.x;
+        if (i < n) {
+            const double vx = vel[3 * i], vy = vel[3 * i + 1], vz = vel[3 * i + 2];
+            s += 0.5 * mass[i] * (vx * vx + vy * vy + vz * vz) / kAccel;
+        }
+    }
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+}
+
+__global__ void __launch_bounds__(kThreads) k_ekin_final(int np, const double* __restrict__ partial,
+                                                         double* __restrict__ out) {
+    __shared__ double sm[kThreads];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < np; i += kThreads) s += partial[i];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sm[0];
+}
+
+// append this step's energies at the device step counter, count rebuilds
+__global__ void k_record(int* __restrict__ counter, const double* __restrict__ epot, const double* __restrict__ ekin,
+                         double* __restrict__ epot_out, double* __restrict__ ekin_out, int n_steps,
+                         const int* __restrict__ gate, int* __restrict__ rebuilds) {
+    const int k = *counter;
+    if (k < n_steps) {
+        if (epot_out) epot_out[k] = *epot;
+        if (ekin_out) ekin_out[k] = *ekin;
+    }
+    *counter = k + 1;
+    if (*gate) *rebuilds += 1;
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_kick(cudaStream_t s, int64_t n, double* vel, const float* forces, const double* mass,
+                        double half_dt) {
+    k_kick<<<blocks_for(3 * n, 256), 256, 0, s>>>(n, vel, forces, mass, half_dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_drift(cudaStream_t s, int64_t n, double* pos, const double* vel, double dt) {
+    k_drift<<<blocks_for(3 * n, 256), 256, 0, s>>>(n, pos, vel, dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ekin(cudaStream_t s, int64_t n, const double* vel, const double* mass, double* partial,
+                        double* out) {
+    const int np = (int)blocks_for(n, kThreads * kPer);
+    k_ekin_partial<<<np, kThreads, 0, s>>>(n, vel, mass, partial);
+    k_ekin_final<<<1, kThreads, 0, s>>>(np, partial, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_record(cudaStream_t s, int* counter, const double* epot, const double* ekin, double* epot_out,
+                          double* ekin_out, int n_steps, const int* gate, int* rebuilds) {
+    k_record<<<1, 1, 0, s>>>(counter, epot, ekin, epot_out, ekin_out, n_steps, gate, rebuilds);
+    return cudaGetLastError();
+}
+
+}  // namespace reann

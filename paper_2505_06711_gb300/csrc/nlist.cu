@@ -63,9 +63,10 @@ __device__ __forceinline__ int64_t ghosts_in_use(const int32_t* g_count, int64_t
 }
 
 // 1. wrap + key (caller order)
-__global__ void k_wrap_key(int64_t n, const double* __restrict__ pos, const int32_t* __restrict__ species, int n_elem,
+__global__ void k_wrap_key(const int* __restrict__ gate, int64_t n, const double* __restrict__ pos, const int32_t* __restrict__ species, int n_elem,
                            CellGeom g, double* __restrict__ xw, double* __restrict__ fw, int32_t* __restrict__ mw,
                            int32_t* __restrict__ key, int* __restrict__ flags) {
+    if (gate && *gate == 0) return;  // rebuild not needed this step
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double x[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
@@ -105,14 +106,17 @@ __global__ void k_wrap_key(int64_t n, const double* __restrict__ pos, const int3
 }
 
 // ---- deterministic counting sort ------------------------------------------
-__global__ void k_hist(int64_t n, const int32_t* __restrict__ key, int32_t* __restrict__ counts) {
+__global__ void k_hist(const int* __restrict__ gate, int64_t n, const int32_t* __restrict__ key, int32_t* __restrict__ counts) {
+    if (gate && *gate == 0) return;  // rebuild not needed this step
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) atomicAdd(&counts[key[i]], 1);
 }
 
 // Exclusive scan of `in` (n entries) into out[0..n]; one block of kScanThreads.
 template <typename T>
-__global__ void __launch_bounds__(kScanThreads) k_scan_single(int64_t n, const T* __restrict__ in, T* __restrict__ out) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_single(const int* __restrict__ gate, int64_t n, const T* __restrict__ in,
+                                                                T* __restrict__ out) {
+    if (gate && *gate == 0) return;  // rebuild not needed this step
     __shared__ T warp_sums[kScanThreads / 32];
     const int tid = threadIdx.x;
     const int64_t chunk = (n + kScanThreads - 1) / kScanThreads;
@@ -146,8 +150,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_single(int64_t n, const T
     if (tid == kScanThreads - 1) out[n] = base;
 }
 
-__global__ void k_scatter(int64_t n, const int32_t* __restrict__ key, const int32_t* __restrict__ start,
+__global__ void k_scatter(const int* __restrict__ gate, int64_t n, const int32_t* __restrict__ key, const int32_t* __restrict__ start,
                           int32_t* __restrict__ cursor, int32_t* __restrict__ order) {
+    if (gate && *gate == 0) return;  // rebuild not needed this step
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int k = key[i];
@@ -159,9 +164,10 @@ __global__ void k_scatter(int64_t n, const int32_t* __restrict__ key, const int3
 // atomic-order scatter moves to start[b] + (number of entries of its bucket with
 // a smaller index).  One thread per entry, each scanning its own bucket (buckets
 // hold tens of entries); entries of buckets >= sorted_keys keep their position.
-__global__ void k_bucket_rank(int64_t n, const int32_t* __restrict__ key, const int32_t* __restrict__ start,
+__global__ void k_bucket_rank(const int* __restrict__ gate, int64_t n, const int32_t* __restrict__ key, const int32_t* __restrict__ start,
                               const int32_t* __restrict__ scattered, int64_t sorted_keys,
                               int32_t* __restrict__ order) {
+    if (gate && *gate == 0) return;  // rebuild not needed this step
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int32_t v = scattered[p];
@@ -177,10 +183,11 @@ __global__ void k_bucket_rank(int64_t n, const int32_t* __restrict__ key, const 
 }
 
 // 2. gather per-atom arrays into internal order
-__global__ void k_gather_internal(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ xw_c,
+__global__ void k_gather_internal(const int* __restrict__ gate, int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ xw_c,
                                   const double* __restrict__ fw_c, const int32_t* __restrict__ mw_c,
                                   const int32_t* __restrict__ sp_c, double* __restrict__ xw, double* __restrict__ fw,
                                   int32_t* __restrict__ mw, int32_t* __restrict__ sp) {
+    if (gate && *gate == 0) return;  // rebuild not needed this step
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c = perm[i];
@@ -201,9 +208,10 @@ __device__ __forceinline__ bool image_in_halo(const CellGeom& g, const double f[
 }
 
 template <bool FILL>
-__global__ void k_ghosts(int64_t n, CellGeom g, const double* __restrict__ fw, const int32_t* __restrict__ goff,
+__global__ void k_ghosts(const int* __restrict__ gate, int64_t n, CellGeom g, const double* __restrict__ fw, const int32_t* __restrict__ goff,
                          int32_t* __restrict__ gcnt, int32_t* __restrict__ owner, int32_t* __restrict__ shift,
                          int64_t g_cap, int* __restrict__ flags) {
+    if (gate && *gate == 0) return;  // rebuild not needed this step
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double f[3] = {fw[3 * i], fw[3 * i + 1], fw[3 * i + 2]};
@@ -229,10 +237,11 @@ __global__ void k_ghosts(int64_t n, CellGeom g, const double* __restrict__ fw, c
 }
 
 // 4. extended binning of owned + ghost slots (unused ghost capacity sorts last)
-__global__ void k_ext_key(int64_t n, const int32_t* __restrict__ g_count, int64_t g_cap, CellGeom g,
+__global__ void k_ext_key(const int* __restrict__ gate, int64_t n, const int32_t* __restrict__ g_count, int64_t g_cap, CellGeom g,
                           const double* __restrict__ xw, const double* __restrict__ fw,
                           const int32_t* __restrict__ owner, const int32_t* __restrict__ shift,
                           int32_t* __restrict__ key, float4* __restrict__ p32, int32_t dead_key) {
+    if (gate && *gate == 0) return;  // rebuild not needed this step
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n + g_cap) return;
     const int64_t G = ghosts_in_use(g_count, g_cap);
@@ -258,12 +267,13 @@ __global__ void k_ext_key(int64_t n, const int32_t* __restrict__ g_count, int64_
 }
 
 // 5. neighbour search: one warp per owned atom
-__global__ void __launch_bounds__(256) k_nbr_search(int64_t n, CellGeom g, const double* __restrict__ xw,
+__global__ void __launch_bounds__(256) k_nbr_search(const int* __restrict__ gate, int64_t n, CellGeom g, const double* __restrict__ xw,
                                                    const double* __restrict__ fw, const int32_t* __restrict__ owner,
                                                    const int32_t* __restrict__ shift, const float4* __restrict__ p32,
                                                    const int32_t* __restrict__ order, const int32_t* __restrict__ bstart,
                                                    int stride, int32_t* __restrict__ nbr, int32_t* __restrict__ cnt_out,
                                                    int* __restrict__ flags) {
+    if (gate && *gate == 0) return;  // rebuild not needed this step
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
@@ -395,11 +405,18 @@ __global__ void __launch_bounds__(256) k_live(int64_t n, int stride, float rc2, 
 
 // largest displacement since the build: flag when any atom moved more than half the skin
 __global__ void k_moved(int64_t n, const double* __restrict__ pos, const double* __restrict__ ref, double thr2,
-                        int* __restrict__ flags) {
+                        int* __restrict__ moved) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double dx = pos[3 * i] - ref[3 * i], dy = pos[3 * i + 1] - ref[3 * i + 1], dz = pos[3 * i + 2] - ref[3 * i + 2];
-    if (!(dx * dx + dy * dy + dz * dz <= thr2)) atomicOr(&flags[FLAG_MOVED], 1);
+    if (!(dx * dx + dy * dy + dz * dz <= thr2)) atomicOr(moved, 1);
+}
+
+__global__ void k_copy_ref(const int* __restrict__ gate, int64_t n3, const double* __restrict__ pos,
+                           double* __restrict__ ref) {
+    if (gate && *gate == 0) return;  // rebuild not needed this step
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n3) ref[i] = pos[i];
 }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -409,15 +426,16 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 // Counting sort of n keys in [0, nkeys): order = indices sorted by (key, index) within the first
 // `sorted_keys` buckets (later buckets hold unused capacity whose order does not matter);
 // start = bucket offsets.
-static cudaError_t counting_sort(cudaStream_t s, int64_t n, int64_t nkeys, const int32_t* key, int32_t* counts,
-                                 int32_t* start, int32_t* scattered, int32_t* order, int64_t sorted_keys) {
+static cudaError_t counting_sort(cudaStream_t s, const int* gate, int64_t n, int64_t nkeys, const int32_t* key,
+                                 int32_t* counts, int32_t* start, int32_t* scattered, int32_t* order,
+                                 int64_t sorted_keys) {
     cudaMemsetAsync(counts, 0, sizeof(int32_t) * nkeys, s);
-    if (n > 0) k_hist<<<blocks_for(n, 256), 256, 0, s>>>(n, key, counts);
-    k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(nkeys, counts, start);
+    if (n > 0) k_hist<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, key, counts);
+    k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(gate, nkeys, counts, start);
     cudaMemsetAsync(counts, 0, sizeof(int32_t) * nkeys, s);
     if (n > 0) {
-        k_scatter<<<blocks_for(n, 256), 256, 0, s>>>(n, key, start, counts, scattered);
-        k_bucket_rank<<<blocks_for(n, 256), 256, 0, s>>>(n, key, start, scattered, sorted_keys, order);
+        k_scatter<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, key, start, counts, scattered);
+        k_bucket_rank<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, key, start, scattered, sorted_keys, order);
     }
     return cudaGetLastError();
 }
@@ -440,37 +458,38 @@ static int64_t ext_bins(const reann_nlist* nl) {
 }
 
 // steps 1-3a: wrap, sort, gather, ghost count + scan (goff[n] = ghost count on the device)
-static cudaError_t stage_sort_and_count(cudaStream_t s, reann_nlist* nl, const double* pos, int* flags) {
+static cudaError_t stage_sort_and_count(cudaStream_t s, reann_nlist* nl, const double* pos, int* flags,
+                                        const int* gate) {
     const int64_t n = nl->n;
     NlistScratch& w = nl->w;
-    cudaMemcpyAsync(nl->pos_ref, pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, s);
-    k_wrap_key<<<blocks_for(n, 256), 256, 0, s>>>(n, pos, w.species_c, nl->n_elem, nl->geom, w.xw_c, w.fw_c, w.mw_c,
+    k_copy_ref<<<blocks_for(3 * n, 256), 256, 0, s>>>(gate, 3 * n, pos, nl->pos_ref);
+    k_wrap_key<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, pos, w.species_c, nl->n_elem, nl->geom, w.xw_c, w.fw_c, w.mw_c,
                                                   w.key, flags);
-    counting_sort(s, n, owned_keys(nl), w.key, w.counts, w.start, w.scat, nl->perm, owned_keys(nl));
-    k_gather_internal<<<blocks_for(n, 256), 256, 0, s>>>(n, nl->perm, w.xw_c, w.fw_c, w.mw_c, w.species_c, w.xw, w.fw,
+    counting_sort(s, gate, n, owned_keys(nl), w.key, w.counts, w.start, w.scat, nl->perm, owned_keys(nl));
+    k_gather_internal<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, nl->perm, w.xw_c, w.fw_c, w.mw_c, w.species_c, w.xw, w.fw,
                                                          nl->wrapm, nl->species);
-    k_ghosts<false><<<blocks_for(n, 256), 256, 0, s>>>(n, nl->geom, w.fw, nullptr, w.gcnt, nullptr, nullptr, 0, flags);
-    k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(n, w.gcnt, w.goff);
+    k_ghosts<false><<<blocks_for(n, 256), 256, 0, s>>>(gate, n, nl->geom, w.fw, nullptr, w.gcnt, nullptr, nullptr, 0, flags);
+    k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(gate, n, w.gcnt, w.goff);
     return cudaGetLastError();
 }
 
 // steps 3b-4: ghost fill and the extended bins (needs the ghost capacity)
-static cudaError_t stage_ghosts_and_bins(cudaStream_t s, reann_nlist* nl, int* flags) {
+static cudaError_t stage_ghosts_and_bins(cudaStream_t s, reann_nlist* nl, int* flags, const int* gate) {
     const int64_t n = nl->n, next = n + nl->g_cap;
     NlistScratch& w = nl->w;
-    k_ghosts<true><<<blocks_for(n, 256), 256, 0, s>>>(n, nl->geom, w.fw, w.goff, nullptr, nl->g_owner, nl->g_shift,
+    k_ghosts<true><<<blocks_for(n, 256), 256, 0, s>>>(gate, n, nl->geom, w.fw, w.goff, nullptr, nl->g_owner, nl->g_shift,
                                                       nl->g_cap, flags);
     const int64_t nx = ext_bins(nl);
-    k_ext_key<<<blocks_for(next, 256), 256, 0, s>>>(n, w.goff + n, nl->g_cap, nl->geom, w.xw, w.fw, nl->g_owner,
+    k_ext_key<<<blocks_for(next, 256), 256, 0, s>>>(gate, n, w.goff + n, nl->g_cap, nl->geom, w.xw, w.fw, nl->g_owner,
                                                     nl->g_shift, w.ekey, w.p32, (int32_t)nx);
-    counting_sort(s, next, nx + 1, w.ekey, w.ecounts, w.estart, w.escat, w.eorder, nx);
+    counting_sort(s, gate, next, nx + 1, w.ekey, w.ecounts, w.estart, w.escat, w.eorder, nx);
     return cudaGetLastError();
 }
 
-static cudaError_t stage_search(cudaStream_t s, reann_nlist* nl, int* flags) {
+static cudaError_t stage_search(cudaStream_t s, reann_nlist* nl, int* flags, const int* gate) {
     const int64_t n = nl->n;
     NlistScratch& w = nl->w;
-    k_nbr_search<<<blocks_for(n * 32, 256), 256, 0, s>>>(n, nl->geom, w.xw, w.fw, nl->g_owner, nl->g_shift, w.p32,
+    k_nbr_search<<<blocks_for(n * 32, 256), 256, 0, s>>>(gate, n, nl->geom, w.xw, w.fw, nl->g_owner, nl->g_shift, w.p32,
                                                          w.eorder, w.estart, nl->stride, nl->nbr, nl->nbr_cnt, flags);
     return cudaGetLastError();
 }
@@ -501,7 +520,7 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
         return set_error(ctx, REANN_E_NOMEM, "neighbour-list allocation failed");
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(w.species_c, species, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     REANN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * NFLAGS, s));
-    REANN_CUDA_TRY(ctx, stage_sort_and_count(s, nl, pos, ctx->d_flags));
+    REANN_CUDA_TRY(ctx, stage_sort_and_count(s, nl, pos, ctx->d_flags, nullptr));
     // sizes: element ranges of the internal order and the ghost count
     std::vector<int32_t> es(nl->n_elem + 1);
     const int64_t nbins = nkeys / nl->n_elem;
@@ -530,7 +549,7 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
     w.escat = dalloc<int32_t>(nl, next);
     if (!nl->g_owner || !nl->g_shift || !w.ekey || !w.p32 || !w.ecounts || !w.estart || !w.eorder || !w.escat)
         return set_error(ctx, REANN_E_NOMEM, "ghost allocation failed");
-    REANN_CUDA_TRY(ctx, stage_ghosts_and_bins(s, nl, ctx->d_flags));
+    REANN_CUDA_TRY(ctx, stage_ghosts_and_bins(s, nl, ctx->d_flags, nullptr));
     // row capacity: expected neighbours from the number density, with headroom
     const CellGeom& g = nl->geom;
     const double vol = std::fabs(g.h[0] * (g.h[4] * g.h[8] - g.h[5] * g.h[7]) -
@@ -544,7 +563,7 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
         nl->nbr_cnt = dalloc<int32_t>(nl, n);
         if (!nl->nbr || !nl->nbr_cnt) return set_error(ctx, REANN_E_NOMEM, "neighbour-list allocation failed");
         REANN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * NFLAGS, s));
-        REANN_CUDA_TRY(ctx, stage_search(s, nl, ctx->d_flags));
+        REANN_CUDA_TRY(ctx, stage_search(s, nl, ctx->d_flags, nullptr));
         REANN_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int) * NFLAGS, cudaMemcpyDeviceToHost, s));
         REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         if (ctx->h_flags[FLAG_GEOM]) return set_error(ctx, REANN_E_GEOM, "coincident atoms (distance < 1e-8 A)");
@@ -557,16 +576,17 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
     return REANN_OK;
 }
 
-cudaError_t launch_rebuild(cudaStream_t s, reann_nlist* nl, const double* pos, int* flags) {
-    cudaError_t e = stage_sort_and_count(s, nl, pos, flags);
-    if (e == cudaSuccess) e = stage_ghosts_and_bins(s, nl, flags);
-    if (e == cudaSuccess) e = stage_search(s, nl, flags);
+// gate == nullptr: always rebuild; otherwise every kernel returns at once unless *gate != 0
+cudaError_t launch_rebuild(cudaStream_t s, reann_nlist* nl, const double* pos, int* flags, const int* gate) {
+    cudaError_t e = stage_sort_and_count(s, nl, pos, flags, gate);
+    if (e == cudaSuccess) e = stage_ghosts_and_bins(s, nl, flags, gate);
+    if (e == cudaSuccess) e = stage_search(s, nl, flags, gate);
     return e;
 }
 
-cudaError_t launch_moved(cudaStream_t s, const reann_nlist* nl, const double* pos, int* flags) {
+cudaError_t launch_moved(cudaStream_t s, const reann_nlist* nl, const double* pos, int* moved) {
     const double half = 0.5 * nl->skin;
-    k_moved<<<blocks_for(nl->n, 256), 256, 0, s>>>(nl->n, pos, nl->pos_ref, half * half, flags);
+    k_moved<<<blocks_for(nl->n, 256), 256, 0, s>>>(nl->n, pos, nl->pos_ref, half * half, moved);
     return cudaGetLastError();
 }
 

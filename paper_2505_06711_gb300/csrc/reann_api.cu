@@ -138,6 +138,8 @@ int alloc_eval_buffers(reann_ctx* ctx, reann_nlist* nl) {
 
 void free_nlist(reann_nlist* nl) {
     if (!nl) return;
+    if (nl->md_exec) cudaGraphExecDestroy(nl->md_exec);
+    if (nl->md_graph) cudaGraphDestroy(nl->md_graph);
     for (void* p : nl->allocs) cudaFree(p);
     delete nl;
 }
@@ -334,6 +336,12 @@ extern "C" void reann_ctx_free(reann_ctx* ctx) {
         cudaEventDestroy(r.second.second);
     }
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+    if (ctx->md_stream) {
+        cudaStreamSynchronize(ctx->md_stream);
+        cudaStreamDestroy(ctx->md_stream);
+    }
+    for (cudaEvent_t e : ctx->md_ev)
+        if (e) cudaEventDestroy(e);
     if (ctx->d_params) cudaFree(ctx->d_params);
     if (ctx->d_bf16) cudaFree(ctx->d_bf16);
     if (ctx->d_flags) cudaFree(ctx->d_flags);
@@ -553,7 +561,7 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
 
 int run_rebuild(reann_ctx* ctx, reann_nlist* nl, const double* pos) {
     ProfScope p(ctx, PR_REBUILD);
-    REANN_CUDA_TRY(ctx, launch_rebuild(ctx->stream, nl, pos, ctx->d_flags));
+    REANN_CUDA_TRY(ctx, launch_rebuild(ctx->stream, nl, pos, ctx->d_flags, nullptr));
     return REANN_OK;
 }
 
@@ -588,7 +596,7 @@ extern "C" int reann_energy_forces_host(reann_ctx* ctx, reann_nlist* nl, const d
         int rc = run_rebuild(ctx, nl, nl->h2d_pos);
         if (rc) return rc;
     } else {
-        REANN_CUDA_TRY(ctx, launch_moved(s, nl, nl->h2d_pos, ctx->d_flags));
+        REANN_CUDA_TRY(ctx, launch_moved(s, nl, nl->h2d_pos, ctx->d_flags + FLAG_MOVED));
         REANN_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int) * NFLAGS, cudaMemcpyDeviceToHost, s));
         REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         if (ctx->h_flags[FLAG_MOVED]) {
@@ -604,6 +612,119 @@ extern "C" int reann_energy_forces_host(reann_ctx* ctx, reann_nlist* nl, const d
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(energy, nl->d_energy, sizeof(double), cudaMemcpyDeviceToHost, s));
     REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
     return reann_ctx_check(ctx);
+}
+
+namespace {
+
+// enqueue one velocity-Verlet step on ctx->stream (captured into the step graph)
+int md_step_body(reann_ctx* ctx, reann_nlist* nl, double* pos, double* vel, const double* mass, double dt,
+                 int n_steps, double* e_pot, double* e_kin) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = nl->n;
+    int* gate = nl->md_ints;
+    REANN_CUDA_TRY(ctx, launch_kick(s, n, vel, nl->md_forces, mass, 0.5 * dt));
+    REANN_CUDA_TRY(ctx, launch_drift(s, n, pos, vel, dt));
+    REANN_CUDA_TRY(ctx, cudaMemsetAsync(gate, 0, sizeof(int), s));
+    REANN_CUDA_TRY(ctx, launch_moved(s, nl, pos, gate));
+    REANN_CUDA_TRY(ctx, launch_rebuild(s, nl, pos, ctx->d_flags, gate));  // kernels return at once unless gate != 0
+    int rc = run_energy_forces(ctx, nl, pos, nl->T, nl->md_scalars, nl->md_forces, nullptr);
+    if (rc) return rc;
+    REANN_CUDA_TRY(ctx, launch_kick(s, n, vel, nl->md_forces, mass, 0.5 * dt));
+    REANN_CUDA_TRY(ctx, launch_ekin(s, n, vel, mass, nl->md_partial, nl->md_scalars + 1));
+    REANN_CUDA_TRY(ctx, launch_record(s, nl->md_ints + 1, nl->md_scalars, nl->md_scalars + 1, e_pot, e_kin, n_steps,
+                                      gate, nl->md_ints + 2));
+    return REANN_OK;
+}
+
+int md_run(reann_ctx* ctx, reann_nlist* nl, double* pos, double* vel, const double* mass, double dt, int n_steps,
+           double* e_pot, double* e_kin) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = nl->n;
+    if (!nl->md_forces) {
+        nl->md_forces = nl_alloc<float>(nl, 3 * n);
+        nl->md_scalars = nl_alloc<double>(nl, 2);
+        nl->md_partial = nl_alloc<double>(nl, (n + 2047) / 2048);
+        nl->md_ints = nl_alloc<int>(nl, 3);
+        if (!nl->md_forces || !nl->md_scalars || !nl->md_partial || !nl->md_ints)
+            return set_error(ctx, REANN_E_NOMEM, "MD buffers: out of device memory");
+        REANN_CUDA_TRY(ctx, cudaMemsetAsync(nl->md_ints, 0, 3 * sizeof(int), s));
+    }
+    int* gate = nl->md_ints;
+    // forces at the starting positions (rebuilding first if atoms moved beyond skin/2)
+    if (!nl->md_forces_valid || nl->md_forces_at != pos || nl->md_precision != ctx->precision) {
+        REANN_CUDA_TRY(ctx, cudaMemsetAsync(gate, 0, sizeof(int), s));
+        REANN_CUDA_TRY(ctx, launch_moved(s, nl, pos, gate));
+        REANN_CUDA_TRY(ctx, launch_rebuild(s, nl, pos, ctx->d_flags, gate));
+        int rc = run_energy_forces(ctx, nl, pos, nl->T, nl->md_scalars, nl->md_forces, nullptr);
+        if (rc) return rc;
+        nl->md_forces_valid = true;
+        nl->md_forces_at = pos;
+    }
+    const void* key[6] = {pos, vel, mass, e_pot, e_kin, nullptr};
+    const bool same = nl->md_exec && std::memcmp(key, nl->md_key, sizeof(key)) == 0 && nl->md_dt == dt &&
+                      nl->md_precision == ctx->precision && nl->md_nsteps == n_steps;
+    if (!same) {
+        if (nl->md_exec) cudaGraphExecDestroy(nl->md_exec);
+        if (nl->md_graph) cudaGraphDestroy(nl->md_graph);
+        nl->md_exec = nullptr;
+        nl->md_graph = nullptr;
+        REANN_CUDA_TRY(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const int rc = md_step_body(ctx, nl, pos, vel, mass, dt, n_steps, e_pot, e_kin);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(s, &g);
+        if (rc || ec != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return rc ? rc : set_error(ctx, REANN_E_CUDA, std::string("MD step capture: ") + cudaGetErrorString(ec));
+        }
+        nl->md_graph = g;
+        REANN_CUDA_TRY(ctx, cudaGraphInstantiate(&nl->md_exec, g, 0));
+        std::memcpy(nl->md_key, key, sizeof(key));
+        nl->md_dt = dt;
+        nl->md_precision = ctx->precision;
+        nl->md_nsteps = n_steps;
+    }
+    REANN_CUDA_TRY(ctx, cudaMemsetAsync(nl->md_ints + 1, 0, sizeof(int), s));
+    for (int k = 0; k < n_steps; ++k) REANN_CUDA_TRY(ctx, cudaGraphLaunch(nl->md_exec, s));
+    return REANN_OK;
+}
+
+}  // namespace
+
+extern "C" int reann_md_step(reann_ctx* ctx, reann_nlist* nl, double* pos, double* vel, const double* mass,
+                             double dt_fs, int n_steps, double* e_pot, double* e_kin) {
+    if (!ctx || !nl || !pos || !vel || !mass || !(dt_fs > 0) || !std::isfinite(dt_fs) || n_steps < 0)
+        return set_error(ctx, REANN_E_ARG, "bad argument to reann_md_step");
+    if (n_steps == 0) return REANN_OK;
+    if (!ctx->md_stream) {
+        REANN_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->md_stream, cudaStreamNonBlocking));
+        REANN_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->md_ev[0], cudaEventDisableTiming));
+        REANN_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->md_ev[1], cudaEventDisableTiming));
+    }
+    // run on the MD stream, ordered after and before the caller's stream
+    cudaStream_t user = ctx->stream;
+    REANN_CUDA_TRY(ctx, cudaEventRecord(ctx->md_ev[0], user));
+    REANN_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->md_stream, ctx->md_ev[0], 0));
+    const bool prof = ctx->prof_on;
+    ctx->stream = ctx->md_stream;
+    ctx->prof_on = false;
+    const int rc = md_run(ctx, nl, pos, vel, mass, dt_fs, n_steps, e_pot, e_kin);
+    ctx->stream = user;
+    ctx->prof_on = prof;
+    REANN_CUDA_TRY(ctx, cudaEventRecord(ctx->md_ev[1], ctx->md_stream));
+    REANN_CUDA_TRY(ctx, cudaStreamWaitEvent(user, ctx->md_ev[1], 0));
+    return rc;
+}
+
+extern "C" int reann_md_info(reann_ctx* ctx, const reann_nlist* nl, int64_t* steps, int64_t* rebuilds) {
+    if (!ctx || !nl) return REANN_E_ARG;
+    int h[3] = {0, 0, 0};
+    if (nl->md_ints) {
+        REANN_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        REANN_CUDA_TRY(ctx, cudaMemcpy(h, nl->md_ints, sizeof(h), cudaMemcpyDeviceToHost));
+    }
+    if (steps) *steps = h[1];
+    if (rebuilds) *rebuilds = h[2];
+    return REANN_OK;
 }
 
 extern "C" int reann_ctx_profile(reann_ctx* ctx, int enable) {

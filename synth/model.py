@@ -29,7 +29,10 @@ them; random ones need them so that values stay O(1)):
   is multiplied by ``FEATURE_SCALE[t][e][l]`` so that the network inputs stay
   within about [0, 1] in every layer (Eq. 1 squares the coefficients, so
   without it the features grow or decay geometrically with ``t``);
-* every energy-network ``W3`` is multiplied by ``ENERGY_SCALE`` so that forces
+* every energy-network ``W3`` is drawn Xavier-normal, made non-negative (so
+  that each atomic energy is bounded from below by -0.28 sum W3: with random
+  signs the model is unbounded below and MD trajectories collapse into ever
+  denser clusters) and multiplied by ``ENERGY_SCALE`` so that forces
   are O(1) eV/A.
 
 No REANN arithmetic happens here: the module only draws and lays out numbers.
@@ -60,9 +63,9 @@ FEATURE_SCALE = (
     ((7.7, 8.7, 4.2), (4.6, 10.0, 4.3), (15.0, 15.0, 1.6)),
 )
 # Multiplier on the energy network's output weights (eV): gives forces of
-# about 1 eV/A (99th percentile) on the water box and 0.5 eV/A (median) on
+# about 2 eV/A (99th percentile) on the water box and 0.5 eV/A (median) on
 # the Cu box at T = 3.
-ENERGY_SCALE = 8.0
+ENERGY_SCALE = 4.0
 
 
 @dataclasses.dataclass
@@ -162,7 +165,9 @@ def make_model(
             put((t, e, "b2"), np.zeros(h2))
             w3 = _xavier(stream(4 if t < T - 1 else 5, t, e), h2, out)
             if t == T - 1:
-                w3 = w3 * es
+                # non-negative output weights: SiLU >= -0.28 then bounds every atomic
+                # energy from below, so clustering cannot release unbounded energy
+                w3 = np.abs(w3) * es
             put((t, e, "W3"), w3)
             put((t, e, "b3"), np.zeros(out))
     return ModelSpec(n_elem, T, n_phi, l_max, n_orb, h1, h2, float(r_c), float(alpha), p.astype(np.float32))
