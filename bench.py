@@ -74,7 +74,56 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-md", action="store_true")
+    p.add_argument("--md-steps", type=int, default=1000)
     return p.parse_args()
+
+
+def run_md(structure, pot, args, dt_fs: float = 0.5, temperature_k: float = 300.0):
+    """NVE velocity Verlet on the same box (Maxwell-Boltzmann start): drift and atom-steps/s.
+
+    A first call of the same length captures the step graph and equilibrates
+    briefly; the second call is timed (CUDA events on the context stream) and
+    its energies give the drift (slope of a linear fit of E_tot/N vs time).
+    """
+    import numpy as np
+    import torch
+
+    from synth import MASS_AMU, maxwell_boltzmann
+
+    n = structure.n_atoms
+    sy = pot.system(structure.pos, structure.species, structure.cell, skin=SKIN)
+    m = MASS_AMU[structure.species]
+    vel = torch.as_tensor(maxwell_boltzmann(m, temperature_k, seed=0), device="cuda").contiguous()
+    mass = torch.as_tensor(m, device="cuda").contiguous()
+    k = args.md_steps
+    sy.md(vel, mass, dt_fs, k)  # capture + first stretch
+    _, r0 = sy.md_info()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    e_pot, e_kin = sy.md(vel, mass, dt_fs, k)
+    b.record()
+    torch.cuda.synchronize()
+    sy.check()
+    steps, r1 = sy.md_info()
+    ms = a.elapsed_time(b)
+    etot = ((e_pot + e_kin) / n).cpu().numpy()
+    t_ps = np.arange(1, k + 1) * dt_fs * 1e-3
+    slope = float(np.polyfit(t_ps, etot, 1)[0])
+    out = {
+        "workload": f"NVE velocity Verlet, {n}-atom water box, dt {dt_fs} fs, {k} timed steps after {k} untimed, "
+                    f"Maxwell-Boltzmann {temperature_k:.0f} K start, FP64 integrator, FP32 networks",
+        "atom_steps_per_s": n * k / (ms * 1e-3),
+        "ms_per_step": ms / k,
+        "drift_meV_per_atom_per_ps": slope * 1e3,
+        "etot_std_meV_per_atom": float(etot.std() * 1e3),
+        "rebuilds_timed": r1 - r0,
+        "steps": steps,
+        "temperature_end_K": float(2 * e_kin[-1].item() / (3 * n - 3) / 8.617333262e-5),
+    }
+    sy.close()
+    return out
 
 
 def dist_env():
@@ -396,9 +445,12 @@ def run_ours(args):
         }
     binding.reann_ctx_set_mlp_precision(ctx, binding.REANN_MLP_FP32)
 
+    md = None if args.no_md else run_md(s, pot, args)
+
     if rank == 0:
         line = base_line(args, ws, value, ms, "f32")
         line["variants"] = variants
+        line["md"] = md
         line["e2e"] = e2e
         line["roofline"] = roof
         line["gpu_launches"] = launches_per_step(T_LAYERS) * args.steps
