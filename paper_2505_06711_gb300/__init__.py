@@ -14,7 +14,44 @@ import numpy as np
 from . import binding
 from .binding import ReannError  # noqa: F401
 
-__all__ = ["Potential", "System", "binding", "ReannError"]
+__all__ = ["Potential", "System", "binding", "ReannError", "ReannEnergy", "energy"]
+
+
+def _energy_function():
+    import torch
+
+    class ReannEnergy(torch.autograd.Function):
+        """E(pos) as a differentiable torch op over the library's hand-written adjoint.
+
+        forward runs reann_energy_forces (T forward layers, then the reverse
+        pass of Eqs. 3-5 in the same call) and keeps F = -dE/dpos; backward
+        returns -F * grad_E, so no autograd graph is ever built through the
+        message-passing layers.
+        """
+
+        @staticmethod
+        def forward(ctx, pos, system):
+            system.evaluate(pos.detach().contiguous(), atom_energy=False)
+            ctx.save_for_backward(system.forces.detach().to(pos.dtype).clone())
+            return system.energy.detach().clone().reshape(()).to(pos.dtype)
+
+        @staticmethod
+        def backward(ctx, grad_e):
+            (forces,) = ctx.saved_tensors
+            return -grad_e * forces, None
+
+    return ReannEnergy
+
+
+def energy(pos, system):
+    """Differentiable total energy (0-d FP64 tensor) of ``system`` at ``pos`` (N x 3 FP64 CUDA)."""
+    global ReannEnergy
+    if ReannEnergy is None:
+        ReannEnergy = _energy_function()
+    return ReannEnergy.apply(pos, system)
+
+
+ReannEnergy = None
 
 
 class Potential:
