@@ -75,8 +75,58 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-md", action="store_true")
+    p.add_argument("--no-t-scaling", action="store_true")
     p.add_argument("--md-steps", type=int, default=1000)
     return p.parse_args()
+
+
+def run_t_scaling(args, steps: int = 10):
+    """1,048,576-atom fcc Cu (64^3 cells), same step at T = 3 and T = 5: cost linear in T (Sec. 2.2)."""
+    import torch
+
+    from paper_2505_06711_gb300 import Potential, binding
+    from synth import fcc_box, make_model
+
+    s = fcc_box(64, seed=0)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    out = {"workload": f"fcc Cu 64^3 cells ({s.n_atoms} atoms), skin {SKIN} A, step = rebuild + energy/forces"}
+    for T in (3, 5):
+        pot = Potential(make_model(T=T))
+        sy = pot.system(s.pos, s.species, s.cell, skin=SKIN)
+        ctx, nl = pot.ctx, sy.nl
+        res = {}
+        for name, prec in (("fp32", binding.REANN_MLP_FP32), ("bf16_mlp", binding.REANN_MLP_BF16)):
+            binding.reann_ctx_set_mlp_precision(ctx, prec)
+
+            def step():
+                binding.reann_nlist_rebuild(ctx, nl, sy.pos)
+                binding.reann_energy_forces(ctx, nl, sy.pos, T, sy.energy, sy.forces, None)
+
+            step()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for a, b in ev:
+                flush.zero_()
+                a.record()
+                step()
+                b.record()
+            torch.cuda.synchronize()
+            binding.reann_ctx_check(ctx)
+            ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+            res[name] = {"ms_per_step": ms, "atom_evals_per_s": s.n_atoms / (ms * 1e-3)}
+        binding.reann_ctx_profile(ctx, True)
+        step()
+        prof = binding.reann_ctx_profile_read(ctx)
+        binding.reann_ctx_profile(ctx, False)
+        res["rebuild_ms"] = prof["nlist_rebuild"][0]
+        out[f"T{T}"] = res
+        sy.close()
+        pot.close()
+    for name in ("fp32", "bf16_mlp"):
+        t3 = out["T3"][name]["ms_per_step"] - out["T3"]["rebuild_ms"]
+        t5 = out["T5"][name]["ms_per_step"] - out["T5"]["rebuild_ms"]
+        out[f"{name}_eval_cost_ratio_T5_over_T3"] = t5 / t3
+    out["ideal_ratio"] = 5.0 / 3.0
+    return out
 
 
 def run_md(structure, pot, args, dt_fs: float = 0.5, temperature_k: float = 300.0):
@@ -446,11 +496,13 @@ def run_ours(args):
     binding.reann_ctx_set_mlp_precision(ctx, binding.REANN_MLP_FP32)
 
     md = None if args.no_md else run_md(s, pot, args)
+    t_scaling = None if args.no_t_scaling else run_t_scaling(args)
 
     if rank == 0:
         line = base_line(args, ws, value, ms, "f32")
         line["variants"] = variants
         line["md"] = md
+        line["t_scaling_cu_1m"] = t_scaling
         line["e2e"] = e2e
         line["roofline"] = roof
         line["gpu_launches"] = launches_per_step(T_LAYERS) * args.steps
