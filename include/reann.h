@@ -194,6 +194,57 @@ int reann_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int 
 int reann_energy_forces_host(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy,
                              float* forces, int rebuild);
 
+/* ---------------------------------------------------------------- serving --- */
+
+/*
+ * Continuous-batching pool: many independent structures resident on the
+ * device and evaluated together by one launch sequence (one evaluation of the
+ * paper's path, Sec. 2.1-2.2, over all of them), with per-structure offsets.
+ *   reann_serve_create  reserve a pool of max_atoms owned slots, max_ghosts
+ *                       ghost slots, max_structures structures and neighbour
+ *                       rows of `stride` entries on ctx's device; its device
+ *                       memory (about 3.5 kB per atom at T = 3 plus 8 B per row
+ *                       entry) is the admission budget.  Synchronous.
+ *   reann_serve_submit  build the structure's list with build_ctx (its own
+ *                       stream, so builds overlap pool launches in flight),
+ *                       then, if free owned and ghost ranges and a structure
+ *                       slot remain, pack it into the pool (on the pool's
+ *                       stream, after any launch already enqueued) and return
+ *                       its slot; otherwise REANN_E_NOMEM (admission refused:
+ *                       retry after a release).  pos/species dev, caller
+ *                       order; cell host 9 FP64.  Rows longer than `stride`:
+ *                       REANN_E_CAPACITY.
+ *   reann_serve_launch  evaluate every structure submitted since the last
+ *                       launch: energies[slot] (dev FP64, max_structures
+ *                       entries) and forces (dev FP32, (max_atoms + 1) x 3:
+ *                       rows [offset, offset + n) of each launched slot in its
+ *                       caller order, the last row is scratch).  `slots`
+ *                       (host, max_structures, nullable) and *count receive the
+ *                       launched slots.  The sequence is captured as a CUDA
+ *                       graph on the first launch (per precision and output
+ *                       pointers) and replayed afterwards.  Asynchronous: the
+ *                       context stream waits for it.  A slot is evaluated
+ *                       once; later launches leave its energy entry and force
+ *                       rows untouched until it is released.
+ *   reann_serve_release free a slot's ranges once its results were read
+ *                       (REANN_E_ARG for a slot not in use).
+ * Each structure's arithmetic is independent of its batch mates (own rows,
+ * own network tiles, own FP64 energy segment), so results are bitwise the same
+ * alone and in any mix.
+ */
+typedef struct reann_serve reann_serve;
+int reann_serve_create(reann_ctx* ctx, int64_t max_atoms, int64_t max_ghosts, int max_structures, int stride,
+                       reann_serve** out);
+void reann_serve_free(reann_serve* srv);
+int reann_serve_submit(reann_serve* srv, reann_ctx* build_ctx, int64_t n_atoms, const double* pos,
+                       const int32_t* species, const double* cell, double skin, int* slot);
+int reann_serve_launch(reann_serve* srv, double* energies, float* forces, int* slots, int* count);
+int reann_serve_release(reann_serve* srv, int slot);
+/* atom offset and size of a used slot (host outputs, nullable) */
+int reann_serve_slot(const reann_serve* srv, int slot, int64_t* atom_offset, int64_t* n_atoms);
+/* largest free owned range, largest free ghost range, free structure slots */
+int reann_serve_usage(const reann_serve* srv, int64_t* free_atoms, int64_t* free_ghosts, int* free_slots);
+
 /* ------------------------------------------------------ no-allocation sum --- */
 
 /*

@@ -67,6 +67,13 @@ _SIGS = {
     "reann_profile_regions": ([], _int),
     "reann_profile_region_name": ([_int], ctypes.c_char_p),
     "reann_ctx_profile_read": ([_vp, _vp, _vp], _int),
+    "reann_serve_create": ([_vp, _i64, _i64, _int, _int, ctypes.POINTER(_vp)], _int),
+    "reann_serve_free": ([_vp], None),
+    "reann_serve_submit": ([_vp, _vp, _i64, _vp, _vp, _vp, _dbl, ctypes.POINTER(_int)], _int),
+    "reann_serve_launch": ([_vp, _vp, _vp, _vp, ctypes.POINTER(_int)], _int),
+    "reann_serve_release": ([_vp, _int], _int),
+    "reann_serve_slot": ([_vp, _int, _vp, _vp], _int),
+    "reann_serve_usage": ([_vp, _vp, _vp, _vp], _int),
     "reann_md_step": ([_vp, _vp, _vp, _vp, _vp, _dbl, _int, _vp, _vp], _int),
     "reann_md_info": ([_vp, _vp, _vp, _vp], _int),
     "reann_energy_sum_noalloc": ([_vp, _i64, _vp, _vp], _int),
@@ -235,6 +242,58 @@ def reann_nlist_rebuild(ctx, nl, pos) -> None:
 
     _dev(pos, torch.float64, None, "pos")
     _check(lib().reann_nlist_rebuild(ctx, nl, _ptr(pos)), ctx)
+
+
+# ---------------------------------------------------------------- serving --
+def reann_serve_create(ctx, max_atoms: int, max_ghosts: int, max_structures: int, stride: int):
+    out = _vp()
+    _check(lib().reann_serve_create(ctx, int(max_atoms), int(max_ghosts), int(max_structures), int(stride),
+                                    ctypes.byref(out)), ctx)
+    return out
+
+
+def reann_serve_free(srv) -> None:
+    lib().reann_serve_free(srv)
+
+
+def reann_serve_submit(srv, ctx, build_ctx, pos, species, cell, skin: float):
+    """Slot id, or None when the pool refuses admission (REANN_E_NOMEM)."""
+    import torch
+
+    n = pos.shape[0]
+    _dev(pos, torch.float64, (n, 3), "pos")
+    _dev(species, torch.int32, (n,), "species")
+    c = np.ascontiguousarray(cell, dtype=np.float64).reshape(9)
+    slot = _int(-1)
+    rc = lib().reann_serve_submit(srv, build_ctx, n, _ptr(pos), _ptr(species), _ptr(c), float(skin), ctypes.byref(slot))
+    if rc == REANN_E_NOMEM:
+        return None
+    _check(rc, ctx)
+    return int(slot.value)
+
+
+def reann_serve_launch(srv, ctx, energies, forces, max_structures: int) -> list[int]:
+    slots = np.zeros(max_structures, np.int32)
+    cnt = _int(0)
+    _check(lib().reann_serve_launch(srv, _ptr(energies), _ptr(forces), _ptr(slots), ctypes.byref(cnt)), ctx)
+    return slots[: cnt.value].tolist()
+
+
+def reann_serve_release(srv, ctx, slot: int) -> None:
+    _check(lib().reann_serve_release(srv, int(slot)), ctx)
+
+
+def reann_serve_slot(srv, slot: int) -> tuple[int, int]:
+    o, n = np.zeros(1, np.int64), np.zeros(1, np.int64)
+    _check(lib().reann_serve_slot(srv, int(slot), _ptr(o), _ptr(n)))
+    return int(o[0]), int(n[0])
+
+
+def reann_serve_usage(srv) -> tuple[int, int, int]:
+    a, g = np.zeros(1, np.int64), np.zeros(1, np.int64)
+    s = np.zeros(1, np.int32)
+    _check(lib().reann_serve_usage(srv, _ptr(a), _ptr(g), _ptr(s)))
+    return int(a[0]), int(g[0]), int(s[0])
 
 
 # --------------------------------------------------------------------- MD --

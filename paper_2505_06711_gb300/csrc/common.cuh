@@ -145,6 +145,7 @@ struct reann_model {
 struct reann_nlist {
     int64_t n = 0, g = 0, g_cap = 0;  // atoms, ghosts, ghost capacity
     int stride = 0;                   // neighbour row capacity
+    int max_count = 0;                // longest row found by the first build
     int n_elem = 0, T = 0;
     double r_c = 0, skin = 0;
     reann::CellGeom geom{};
@@ -240,6 +241,13 @@ int set_error(reann_ctx* ctx, int code, const std::string& msg);
 int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const int32_t* species);
 cudaError_t launch_rebuild(cudaStream_t s, reann_nlist* nl, const double* pos, int* flags, const int* gate);
 cudaError_t launch_moved(cudaStream_t s, const reann_nlist* nl, const double* pos, int* moved);
+
+// serving pool (serve.cu)
+cudaError_t launch_pack(cudaStream_t s, const reann_nlist* src, const double* caller_pos, reann_nlist* pool,
+                        int64_t ob, int64_t gb);
+cudaError_t launch_release(cudaStream_t s, reann_nlist* pool, int64_t ob, int64_t n);
+cudaError_t launch_retire(cudaStream_t s, const int4* seg, int nseg, reann_nlist* pool);
+cudaError_t launch_segment_energy(cudaStream_t s, const int4* seg, int nseg, const float* eps, double* energies);
 
 // velocity Verlet (md.cu)
 cudaError_t launch_kick(cudaStream_t s, int64_t n, double* vel, const float* forces, const double* mass,

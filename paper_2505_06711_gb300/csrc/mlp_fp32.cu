@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __
     float* sH2 = sH1 + kR * LDH;     // 64 x 68
     const int tid = threadIdx.x;
     const Tile tl = tiles[blockIdx.x];
+    if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list
     const NetDev& w = nets.e[tl.elem];
     copy_f4(sW1, w.W1, NFEAT * H1, tid);
     copy_f4(sW2, w.W2, H1 * H2, tid);
@@ -169,6 +170,7 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
     float* sG = sZ2 + kR * LDH;       // 64 x 68
     const int tid = threadIdx.x;
     const Tile tl = tiles[blockIdx.x];
+    if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list
     const NetDev& w = nets.e[tl.elem];
     copy_f4(sW1, w.W1, NFEAT * H1, tid);
     copy_f4(sW2, w.W2, H1 * H2, tid);

@@ -324,6 +324,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_fwd(TcLayer nets, const 
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
     const int tid = threadIdx.x, warp = tid >> 5, r = tid;
     const Tile tl = tiles[blockIdx.x];
+    if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list (before any TMEM allocation)
     const TcNet& w = nets.e[tl.elem];
     const uint32_t tmem = setup(tslot, bar);
     if (tid == 0) {
@@ -394,6 +395,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_bwd(TcLayer nets, const 
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
     const int tid = threadIdx.x, warp = tid >> 5, r = tid;
     const Tile tl = tiles[blockIdx.x];
+    if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list (before any TMEM allocation)
     const TcNet& w = nets.e[tl.elem];
     const uint32_t tmem = setup(tslot, bar);
     if (tid == 0) {

@@ -568,6 +568,7 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
         REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
         if (ctx->h_flags[FLAG_GEOM]) return set_error(ctx, REANN_E_GEOM, "coincident atoms (distance < 1e-8 A)");
         if (ctx->h_flags[FLAG_GHOST_OVERFLOW]) return set_error(ctx, REANN_E_CAPACITY, "ghost capacity exceeded");
+        nl->max_count = ctx->h_flags[FLAG_MAXNBR];
         if (!ctx->h_flags[FLAG_NBR_OVERFLOW]) break;
         if (attempt == 1) return set_error(ctx, REANN_E_CAPACITY, "neighbour capacity exceeded");
         // grow to the observed maximum (plus headroom for later motion) and search again

@@ -374,8 +374,11 @@ extern "C" int reann_ctx_check(reann_ctx* ctx) {
     return REANN_OK;
 }
 
-extern "C" int reann_build_nlist(reann_ctx* ctx, int64_t n_atoms, const double* pos, const int32_t* species,
-                                 const double* cell, double r_c, double skin, reann_nlist** out) {
+namespace {
+
+// neighbour list and ghost map only (no per-structure evaluation buffers)
+int build_list(reann_ctx* ctx, int64_t n_atoms, const double* pos, const int32_t* species, const double* cell,
+               double r_c, double skin, bool eval_buffers, reann_nlist** out) {
     if (!ctx || !out) return REANN_E_ARG;
     *out = nullptr;
     if (n_atoms < 1 || n_atoms > (int64_t)1 << 28 || !pos || !species || !cell || !(skin >= 0) || !std::isfinite(skin))
@@ -390,7 +393,7 @@ extern "C" int reann_build_nlist(reann_ctx* ctx, int64_t n_atoms, const double* 
     nl->skin = skin;
     int rc = make_geometry(ctx, cell, r_c + skin, &nl->geom);
     if (!rc) rc = build_nlist_device(ctx, nl, pos, species);
-    if (!rc) rc = alloc_eval_buffers(ctx, nl);
+    if (!rc && eval_buffers) rc = alloc_eval_buffers(ctx, nl);
     if (rc) {
         cudaStreamSynchronize(ctx->stream);
         free_nlist(nl);
@@ -398,6 +401,13 @@ extern "C" int reann_build_nlist(reann_ctx* ctx, int64_t n_atoms, const double* 
     }
     *out = nl;
     return REANN_OK;
+}
+
+}  // namespace
+
+extern "C" int reann_build_nlist(reann_ctx* ctx, int64_t n_atoms, const double* pos, const int32_t* species,
+                                 const double* cell, double r_c, double skin, reann_nlist** out) {
+    return build_list(ctx, n_atoms, pos, species, cell, r_c, skin, true, out);
 }
 
 extern "C" void reann_nlist_free(reann_nlist* nl) { free_nlist(nl); }
@@ -483,11 +493,13 @@ const char* kRegionNames[PR_COUNT] = {"nlist_rebuild", "refresh_positions", "liv
                                       "ghost_gather",  "density_fwd",       "mlp_fwd",      "energy_sum",
                                       "mlp_bwd",       "bbar",              "density_adj",  "scatter_outputs"};
 
+// pos == nullptr: positions already in place (serving pool); seg != nullptr: one FP64
+// energy per segment (structure) into energy[seg.z] instead of one total.
 int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy, float* forces,
-                      float* atom_energy) {
+                      float* atom_energy, const int4* seg = nullptr, int nseg = 0) {
     cudaStream_t s = ctx->stream;
     const int64_t n = nl->n, ne = nl->n + nl->g_cap;
-    {
+    if (pos) {
         ProfScope p(ctx, PR_REFRESH);
         REANN_CUDA_TRY(ctx, launch_refresh_positions(s, nl, pos));
     }
@@ -525,7 +537,10 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
     }
     {
         ProfScope p(ctx, PR_ENERGY);
-        REANN_CUDA_TRY(ctx, launch_energy_sum(s, nl, energy));
+        if (seg)
+            REANN_CUDA_TRY(ctx, launch_segment_energy(s, seg, nseg, nl->eps, energy));
+        else
+            REANN_CUDA_TRY(ctx, launch_energy_sum(s, nl, energy));
     }
     // reverse: Eqs. 3-5, one vector-Jacobian product per layer
     REANN_CUDA_TRY(ctx, cudaMemsetAsync(nl->grad, 0, sizeof(float) * n * 3, s));
@@ -761,5 +776,340 @@ extern "C" int reann_get_layer(reann_ctx* ctx, const reann_nlist* nl, int layer,
         REANN_CUDA_TRY(ctx, launch_unpermute_rows(ctx->stream, nl, nl->rho + (size_t)layer * n * NFEAT, NFEAT, rho, NFEAT));
     if (coef)
         REANN_CUDA_TRY(ctx, launch_unpermute_rows(ctx->stream, nl, nl->coef + (size_t)layer * ne * NPHI, NPHI, coef, NPHI));
+    return REANN_OK;
+}
+
+// ================================================================ serving ==
+
+namespace {
+
+// first-fit allocator of [start, start + len) ranges with coalescing
+struct RangeAlloc {
+    std::vector<std::pair<int64_t, int64_t>> free;  // sorted (start, len)
+    void init(int64_t n) { free.assign(1, {0, n}); }
+    bool take(int64_t len, int64_t* start) {
+        if (len == 0) {
+            *start = 0;
+            return true;
+        }
+        for (size_t k = 0; k < free.size(); ++k)
+            if (free[k].second >= len) {
+                *start = free[k].first;
+                free[k].first += len;
+                free[k].second -= len;
+                if (free[k].second == 0) free.erase(free.begin() + k);
+                return true;
+            }
+        return false;
+    }
+    void give(int64_t start, int64_t len) {
+        if (len == 0) return;
+        auto it = std::lower_bound(free.begin(), free.end(), std::make_pair(start, (int64_t)0));
+        it = free.insert(it, {start, len});
+        size_t k = it - free.begin();
+        if (k + 1 < free.size() && free[k].first + free[k].second == free[k + 1].first) {
+            free[k].second += free[k + 1].second;
+            free.erase(free.begin() + k + 1);
+        }
+        if (k > 0 && free[k - 1].first + free[k - 1].second == free[k].first) {
+            free[k - 1].second += free[k].second;
+            free.erase(free.begin() + k);
+        }
+    }
+};
+
+struct ServeSlot {
+    bool used = false, pending = false, retired = false;
+    int64_t ob = 0, n = 0, gb = 0, g = 0;
+    std::vector<Tile> t64, t128;
+};
+
+}  // namespace
+
+struct reann_serve {
+    reann_ctx* ctx = nullptr;
+    reann_nlist* pool = nullptr;
+    int max_slots = 0;
+    RangeAlloc owned, ghost;
+    std::vector<ServeSlot> slots;
+    int4* d_seg = nullptr;
+    int4* h_seg = nullptr;  // pinned staging
+    Tile *h_t64 = nullptr, *h_t128 = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t staged = nullptr, done = nullptr, user_ready = nullptr;
+    std::vector<std::pair<reann_nlist*, cudaEvent_t>> deferred;  // built lists freed once their pack has run
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_precision = -1;
+    const void* graph_out[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+void serve_reap(reann_serve* srv, bool wait) {
+    for (size_t k = 0; k < srv->deferred.size();) {
+        auto& d = srv->deferred[k];
+        if (wait) cudaEventSynchronize(d.second);
+        if (cudaEventQuery(d.second) == cudaSuccess) {
+            free_nlist(d.first);
+            cudaEventDestroy(d.second);
+            srv->deferred.erase(srv->deferred.begin() + k);
+        } else {
+            ++k;
+        }
+    }
+}
+
+// one evaluation of every structure in the segment table, then their retirement
+int pool_pass(reann_ctx* ctx, reann_serve* srv, double* energies, float* forces) {
+    reann_nlist* p = srv->pool;
+    int rc = run_energy_forces(ctx, p, nullptr, p->T, energies, forces, nullptr, srv->d_seg, srv->max_slots);
+    if (!rc) REANN_CUDA_TRY(ctx, launch_retire(ctx->stream, srv->d_seg, srv->max_slots, p));
+    return rc;
+}
+
+}  // namespace
+
+extern "C" void reann_serve_free(reann_serve* srv) {
+    if (!srv) return;
+    if (srv->stream) cudaStreamSynchronize(srv->stream);
+    serve_reap(srv, true);
+    if (srv->exec) cudaGraphExecDestroy(srv->exec);
+    if (srv->graph) cudaGraphDestroy(srv->graph);
+    free_nlist(srv->pool);
+    if (srv->d_seg) cudaFree(srv->d_seg);
+    if (srv->h_seg) cudaFreeHost(srv->h_seg);
+    if (srv->h_t64) cudaFreeHost(srv->h_t64);
+    if (srv->h_t128) cudaFreeHost(srv->h_t128);
+    for (cudaEvent_t e : {srv->staged, srv->done, srv->user_ready})
+        if (e) cudaEventDestroy(e);
+    if (srv->stream) cudaStreamDestroy(srv->stream);
+    delete srv;
+}
+
+extern "C" int reann_serve_create(reann_ctx* ctx, int64_t max_atoms, int64_t max_ghosts, int max_structures,
+                                  int stride, reann_serve** out) {
+    if (!ctx || !out || max_atoms < 1 || max_ghosts < 0 || max_structures < 1 || stride < 8 || stride > 4096 ||
+        max_atoms > ((int64_t)1 << 28))
+        return set_error(ctx, REANN_E_ARG, "bad argument to reann_serve_create");
+    *out = nullptr;
+    reann_serve* srv = new (std::nothrow) reann_serve;
+    if (!srv) return set_error(ctx, REANN_E_NOMEM, "host allocation failed");
+    auto fail = [&](int code, const char* msg) {
+        reann_serve_free(srv);
+        return set_error(ctx, code, msg);
+    };
+    srv->ctx = ctx;
+    srv->max_slots = max_structures;
+    srv->slots.resize(max_structures);
+    srv->owned.init(max_atoms);
+    srv->ghost.init(max_ghosts);
+    reann_nlist* p = new (std::nothrow) reann_nlist;
+    if (!p) return fail(REANN_E_NOMEM, "host allocation failed");
+    srv->pool = p;
+    p->n = max_atoms;
+    p->g = p->g_cap = max_ghosts;
+    p->stride = stride;
+    p->n_elem = ctx->model.n_elem;
+    p->T = ctx->model.T;
+    p->r_c = ctx->model.r_c;
+    p->perm = nl_alloc<int32_t>(p, max_atoms);
+    p->species = nl_alloc<int32_t>(p, max_atoms);
+    p->g_owner = nl_alloc<int32_t>(p, max_ghosts);
+    p->nbr = nl_alloc<int32_t>(p, (size_t)max_atoms * stride);
+    p->nbr_cnt = nl_alloc<int32_t>(p, max_atoms);
+    p->w.goff = nl_alloc<int32_t>(p, max_atoms + 1);
+    if (!p->perm || !p->species || !p->g_owner || !p->nbr || !p->nbr_cnt || !p->w.goff)
+        return fail(REANN_E_NOMEM, "serving pool: out of device memory");
+    if (alloc_eval_buffers(ctx, p)) return fail(REANN_E_NOMEM, "serving pool: out of device memory");
+    // tile lists of fixed capacity (padding entries have nrows = 0)
+    const int64_t cap64 = max_atoms / MLP_TILE + (int64_t)max_structures * p->n_elem + 1;
+    const int64_t cap128 = max_atoms / 128 + (int64_t)max_structures * p->n_elem + 1;
+    p->tiles_h.assign(cap64, Tile{0, 0, 0, 0});
+    p->tiles128_h.assign(cap128, Tile{0, 0, 0, 0});
+    p->tiles = nl_alloc<Tile>(p, cap64);
+    p->tiles128 = nl_alloc<Tile>(p, cap128);
+    if (!p->tiles || !p->tiles128 || cudaMalloc(&srv->d_seg, sizeof(int4) * max_structures) != cudaSuccess ||
+        cudaMallocHost(&srv->h_seg, sizeof(int4) * max_structures) != cudaSuccess ||
+        cudaMallocHost(&srv->h_t64, sizeof(Tile) * cap64) != cudaSuccess ||
+        cudaMallocHost(&srv->h_t128, sizeof(Tile) * cap128) != cudaSuccess)
+        return fail(REANN_E_NOMEM, "serving pool: out of memory");
+    if (cudaStreamCreateWithFlags(&srv->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&srv->staged, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&srv->done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&srv->user_ready, cudaEventDisableTiming) != cudaSuccess)
+        return fail(REANN_E_CUDA, "serving pool: stream/event creation failed");
+    // empty pool: no neighbours, outputs to the sink row, every ghost slot "in use" (all point at atom 0)
+    std::vector<int32_t> sink(max_atoms, (int32_t)max_atoms), goff(max_atoms + 1, 0);
+    goff[max_atoms] = (int32_t)max_ghosts;
+    bool ok = cudaMemcpy(p->perm, sink.data(), sizeof(int32_t) * max_atoms, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(p->w.goff, goff.data(), sizeof(int32_t) * (max_atoms + 1), cudaMemcpyHostToDevice) ==
+                  cudaSuccess &&
+              cudaMemset(p->nbr_cnt, 0, sizeof(int32_t) * max_atoms) == cudaSuccess &&
+              cudaMemset(p->species, 0, sizeof(int32_t) * max_atoms) == cudaSuccess &&
+              cudaMemset(p->g_owner, 0, sizeof(int32_t) * std::max<int64_t>(max_ghosts, 1)) == cudaSuccess &&
+              cudaMemset(p->pos_hi, 0, sizeof(float4) * (max_atoms + max_ghosts)) == cudaSuccess &&
+              cudaMemset(p->pos_lo, 0, sizeof(float4) * (max_atoms + max_ghosts)) == cudaSuccess &&
+              cudaDeviceSynchronize() == cudaSuccess;
+    if (!ok) return fail(REANN_E_CUDA, "serving pool: initialisation failed");
+    *out = srv;
+    return REANN_OK;
+}
+
+extern "C" int reann_serve_submit(reann_serve* srv, reann_ctx* build_ctx, int64_t n_atoms, const double* pos,
+                                  const int32_t* species, const double* cell, double skin, int* slot) {
+    if (!srv || !build_ctx || !slot) return REANN_E_ARG;
+    reann_ctx* ctx = srv->ctx;
+    if (build_ctx->model.T != ctx->model.T || build_ctx->model.n_elem != ctx->model.n_elem ||
+        build_ctx->model.r_c != ctx->model.r_c)
+        return set_error(ctx, REANN_E_MISMATCH, "build context holds a different model");
+    serve_reap(srv, false);
+    reann_nlist* tmp = nullptr;
+    int rc = build_list(build_ctx, n_atoms, pos, species, cell, ctx->model.r_c, skin, false, &tmp);
+    if (rc) return set_error(ctx, rc, std::string("structure build: ") + build_ctx->err);
+    if (tmp->max_count > srv->pool->stride) {
+        free_nlist(tmp);
+        return set_error(ctx, REANN_E_CAPACITY, "a neighbour row is longer than the pool stride");
+    }
+    int s = -1;
+    for (int k = 0; k < srv->max_slots; ++k)
+        if (!srv->slots[k].used) {
+            s = k;
+            break;
+        }
+    int64_t ob = 0, gb = 0;
+    if (s < 0 || !srv->owned.take(tmp->n, &ob)) {
+        free_nlist(tmp);
+        return set_error(ctx, REANN_E_NOMEM, "serving pool full (admission refused)");
+    }
+    if (!srv->ghost.take(tmp->g, &gb)) {
+        srv->owned.give(ob, tmp->n);
+        free_nlist(tmp);
+        return set_error(ctx, REANN_E_NOMEM, "serving pool full (admission refused)");
+    }
+    ServeSlot& sl = srv->slots[s];
+    sl.used = true;
+    sl.pending = true;
+    sl.ob = ob;
+    sl.n = tmp->n;
+    sl.gb = gb;
+    sl.g = tmp->g;
+    sl.t64.clear();
+    sl.t128.clear();
+    for (int e = 0; e < tmp->n_elem; ++e) {
+        for (int r = tmp->elem_start[e]; r < tmp->elem_start[e + 1]; r += MLP_TILE)
+            sl.t64.push_back(Tile{e, (int)(ob + r), std::min(MLP_TILE, tmp->elem_start[e + 1] - r), 0});
+        for (int r = tmp->elem_start[e]; r < tmp->elem_start[e + 1]; r += 128)
+            sl.t128.push_back(Tile{e, (int)(ob + r), std::min(128, tmp->elem_start[e + 1] - r), 0});
+    }
+    // pack on the pool stream (ordered with launches); the built list lives until the pack has run
+    REANN_CUDA_TRY(ctx, launch_pack(srv->stream, tmp, tmp->pos_ref, srv->pool, ob, gb));
+    cudaEvent_t ev = nullptr;
+    REANN_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    REANN_CUDA_TRY(ctx, cudaEventRecord(ev, srv->stream));
+    srv->deferred.push_back({tmp, ev});
+    *slot = s;
+    return REANN_OK;
+}
+
+extern "C" int reann_serve_launch(reann_serve* srv, double* energies, float* forces, int* slots, int* count) {
+    if (!srv || !energies || !forces || !count) return REANN_E_ARG;
+    reann_ctx* ctx = srv->ctx;
+    reann_nlist* p = srv->pool;
+    // the pinned staging buffers of the previous launch must have been copied
+    REANN_CUDA_TRY(ctx, cudaEventSynchronize(srv->staged));
+    size_t n64 = 0, n128 = 0;
+    int nseg = 0;
+    for (int k = 0; k < srv->max_slots; ++k) {
+        ServeSlot& sl = srv->slots[k];
+        if (!sl.used || !sl.pending) continue;
+        for (const Tile& t : sl.t64) srv->h_t64[n64++] = t;
+        for (const Tile& t : sl.t128) srv->h_t128[n128++] = t;
+        srv->h_seg[nseg] = make_int4((int)sl.ob, (int)sl.n, k, 0);
+        if (slots) slots[nseg] = k;
+        ++nseg;
+        sl.pending = false;
+        sl.retired = true;  // by the pass below
+    }
+    *count = nseg;
+    if (nseg == 0) return REANN_OK;
+    for (size_t k = n64; k < p->tiles_h.size(); ++k) srv->h_t64[k] = Tile{0, 0, 0, 0};
+    for (size_t k = n128; k < p->tiles128_h.size(); ++k) srv->h_t128[k] = Tile{0, 0, 0, 0};
+    for (int k = nseg; k < srv->max_slots; ++k) srv->h_seg[k] = make_int4(0, -1, 0, 0);
+    cudaStream_t s = srv->stream;
+    REANN_CUDA_TRY(ctx, cudaEventRecord(srv->user_ready, ctx->stream));
+    REANN_CUDA_TRY(ctx, cudaStreamWaitEvent(s, srv->user_ready, 0));
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(p->tiles, srv->h_t64, sizeof(Tile) * p->tiles_h.size(), cudaMemcpyHostToDevice, s));
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(p->tiles128, srv->h_t128, sizeof(Tile) * p->tiles128_h.size(),
+                                        cudaMemcpyHostToDevice, s));
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(srv->d_seg, srv->h_seg, sizeof(int4) * srv->max_slots, cudaMemcpyHostToDevice, s));
+    REANN_CUDA_TRY(ctx, cudaEventRecord(srv->staged, s));
+    // one evaluation of the whole pool, captured once per (precision, outputs) and replayed
+    cudaStream_t user = ctx->stream;
+    const bool prof = ctx->prof_on;
+    ctx->stream = s;
+    ctx->prof_on = false;
+    int rc = REANN_OK;
+    const bool same = srv->exec && srv->graph_precision == ctx->precision && srv->graph_out[0] == energies &&
+                      srv->graph_out[1] == forces;
+    if (!same) {
+        if (srv->exec) cudaGraphExecDestroy(srv->exec);
+        if (srv->graph) cudaGraphDestroy(srv->graph);
+        srv->exec = nullptr;
+        srv->graph = nullptr;
+        // one plain run first (sets kernel attributes outside capture), then capture the same sequence
+        rc = pool_pass(ctx, srv, energies, forces);
+        if (!rc && cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            rc = pool_pass(ctx, srv, energies, forces);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(s, &g);
+            if (!rc && ec == cudaSuccess && cudaGraphInstantiate(&srv->exec, g, 0) == cudaSuccess) {
+                srv->graph = g;
+                srv->graph_precision = ctx->precision;
+                srv->graph_out[0] = energies;
+                srv->graph_out[1] = forces;
+            } else {
+                if (g) cudaGraphDestroy(g);
+                if (!rc) rc = set_error(ctx, REANN_E_CUDA, "serving graph capture failed");
+            }
+        }
+    } else if (cudaGraphLaunch(srv->exec, s) != cudaSuccess) {
+        rc = set_error(ctx, REANN_E_CUDA, "serving graph launch failed");
+    }
+    ctx->stream = user;
+    ctx->prof_on = prof;
+    REANN_CUDA_TRY(ctx, cudaEventRecord(srv->done, s));
+    REANN_CUDA_TRY(ctx, cudaStreamWaitEvent(user, srv->done, 0));
+    serve_reap(srv, false);
+    return rc;
+}
+
+extern "C" int reann_serve_release(reann_serve* srv, int slot) {
+    if (!srv || slot < 0 || slot >= srv->max_slots || !srv->slots[slot].used) return REANN_E_ARG;
+    ServeSlot& sl = srv->slots[slot];
+    if (!sl.retired) REANN_CUDA_TRY(srv->ctx, launch_release(srv->stream, srv->pool, sl.ob, sl.n));
+    srv->owned.give(sl.ob, sl.n);
+    srv->ghost.give(sl.gb, sl.g);
+    sl = ServeSlot{};
+    return REANN_OK;
+}
+
+extern "C" int reann_serve_slot(const reann_serve* srv, int slot, int64_t* atom_offset, int64_t* n_atoms) {
+    if (!srv || slot < 0 || slot >= srv->max_slots || !srv->slots[slot].used) return REANN_E_ARG;
+    if (atom_offset) *atom_offset = srv->slots[slot].ob;
+    if (n_atoms) *n_atoms = srv->slots[slot].n;
+    return REANN_OK;
+}
+
+extern "C" int reann_serve_usage(const reann_serve* srv, int64_t* free_atoms, int64_t* free_ghosts, int* free_slots) {
+    if (!srv) return REANN_E_ARG;
+    int64_t fa = 0, fg = 0;
+    for (auto& r : srv->owned.free) fa = std::max(fa, r.second);
+    for (auto& r : srv->ghost.free) fg = std::max(fg, r.second);
+    int fs = 0;
+    for (auto& sl : srv->slots) fs += !sl.used;
+    if (free_atoms) *free_atoms = fa;
+    if (free_ghosts) *free_ghosts = fg;
+    if (free_slots) *free_slots = fs;
     return REANN_OK;
 }

@@ -47,7 +47,7 @@ def assert_parity(gpu, ref, n, e_tol=E_TOL_PER_ATOM, f_tol=F_TOL_MAX):
     print(f"[parity] N={n} |dE|/N={de:.3e} max|dF|={df:.3e} max|F|={fmax:.3e}")
     assert de <= e_tol, f"|dE|/N = {de:.3e} > {e_tol}"
     assert df <= f_tol, f"max|dF| = {df:.3e} > {f_tol}"
-    if "atom_energy" in ref:
+    if "atom_energy" in ref and "atom_energy" in gpu:
         da = float(np.abs(gpu["atom_energy"] - ref["atom_energy"]).max()) if n else 0.0
         assert da <= 10 * e_tol, f"max|d eps| = {da:.3e}"
     return de, df
