@@ -77,7 +77,64 @@ def parse():
     p.add_argument("--no-md", action="store_true")
     p.add_argument("--no-t-scaling", action="store_true")
     p.add_argument("--md-steps", type=int, default=1000)
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=10000)
     return p.parse_args()
+
+
+def run_serve(args):
+    """Continuous-batching serving: Poisson arrivals of mixed water / Cu structures, T = 3, BF16 networks.
+
+    Request mix: 50/50 water (16..2048 molecules) / fcc Cu (3..20 cells per
+    side), log-uniform sizes, per-request jitter.  Baseline: the same requests
+    served one at a time in FP32 (build, evaluate, read back), which also sets
+    the arrival rate of the main stream (70 % of that capacity).  Latency is
+    completion minus arrival, completion = results back on the host.
+    """
+    import math
+
+    from paper_2505_06711_gb300 import Potential, binding
+    from paper_2505_06711_gb300.serving import (Server, latency_stats, make_requests, make_templates, serve_alone,
+                                                serve_stream)
+    from synth import make_model
+
+    spec = make_model(T=3, seed=1234)
+    templates = make_templates(seed=0)
+    pot = Potential(spec)
+    serve_alone(pot, make_requests(templates, 16, math.inf, seed=100))  # warm-up
+    n_alone = max(64, min(1000, args.serve_requests // 10))
+    alone_reqs = make_requests(templates, n_alone, math.inf, seed=101)
+    _, st = serve_alone(pot, alone_reqs)
+    pot.close()
+    alone_rps = n_alone / st["wall_s"]
+    alone_atoms = sum(r.n_atoms for r in alone_reqs) / st["wall_s"]
+    pool = {"max_atoms": 1 << 17, "max_ghosts": 1 << 18, "max_structures": 256, "stride": 160}
+    server = Server(spec, pool["max_atoms"], pool["max_ghosts"], pool["max_structures"], pool["stride"],
+                    precision=binding.REANN_MLP_BF16)
+    try:
+        serve_stream(server, make_requests(templates, 64, alone_rps, seed=102))  # warm-up, graph capture
+        reqs = make_requests(templates, args.serve_requests, 0.7 * alone_rps, seed=103)
+        res, st = serve_stream(server, reqs)
+        main = {"load": 0.7, "rate_per_s": 0.7 * alone_rps, "requests": len(reqs), **latency_stats(res), **st}
+        sweep = []
+        n_sweep = max(200, args.serve_requests // 5)
+        for load in (1.0, 2.0, 4.0, math.inf):
+            rq = make_requests(templates, n_sweep, load * alone_rps, seed=104)
+            r, t = serve_stream(server, rq)
+            sweep.append({"load": load if math.isfinite(load) else "all at t=0", "requests": n_sweep,
+                          **latency_stats(r), **t})
+    finally:
+        server.close()
+    saturated = sweep[-1]["atom_evals_per_s"]
+    return {
+        "workload": "Poisson arrivals; 50/50 water 16..2048 molecules / Cu fcc 3..20 cells, log-uniform sizes, "
+                    "jitter N(0, 0.02 A); T = 3; pooled launches with BF16 atomic networks",
+        "pool": pool,
+        "alone_fp32": {"requests": n_alone, "requests_per_s": alone_rps, "atom_evals_per_s": alone_atoms},
+        "main": main,
+        "sweep": sweep,
+        "saturated_over_alone_atom_evals": saturated / alone_atoms,
+    }
 
 
 def run_t_scaling(args, steps: int = 10):
@@ -497,12 +554,14 @@ def run_ours(args):
 
     md = None if args.no_md else run_md(s, pot, args)
     t_scaling = None if args.no_t_scaling else run_t_scaling(args)
+    serve = None if args.no_serve or ws > 1 else run_serve(args)
 
     if rank == 0:
         line = base_line(args, ws, value, ms, "f32")
         line["variants"] = variants
         line["md"] = md
         line["t_scaling_cu_1m"] = t_scaling
+        line["serve"] = serve
         line["e2e"] = e2e
         line["roofline"] = roof
         line["gpu_launches"] = launches_per_step(T_LAYERS) * args.steps

@@ -228,6 +228,9 @@ int reann_energy_forces_host(reann_ctx* ctx, reann_nlist* nl, const double* pos,
  *                       rows untouched until it is released.
  *   reann_serve_release free a slot's ranges once its results were read
  *                       (REANN_E_ARG for a slot not in use).
+ * The reann_serve_* calls on one pool are thread-safe: several threads, each
+ * with its own build_ctx, may submit while another launches and releases; the
+ * builds themselves run concurrently.
  * Each structure's arithmetic is independent of its batch mates (own rows,
  * own network tiles, own FP64 energy segment), so results are bitwise the same
  * alone and in any mix.
@@ -241,9 +244,9 @@ int reann_serve_submit(reann_serve* srv, reann_ctx* build_ctx, int64_t n_atoms, 
 int reann_serve_launch(reann_serve* srv, double* energies, float* forces, int* slots, int* count);
 int reann_serve_release(reann_serve* srv, int slot);
 /* atom offset and size of a used slot (host outputs, nullable) */
-int reann_serve_slot(const reann_serve* srv, int slot, int64_t* atom_offset, int64_t* n_atoms);
+int reann_serve_slot(reann_serve* srv, int slot, int64_t* atom_offset, int64_t* n_atoms);
 /* largest free owned range, largest free ghost range, free structure slots */
-int reann_serve_usage(const reann_serve* srv, int64_t* free_atoms, int64_t* free_ghosts, int* free_slots);
+int reann_serve_usage(reann_serve* srv, int64_t* free_atoms, int64_t* free_ghosts, int* free_slots);
 
 /* ------------------------------------------------------ no-allocation sum --- */
 

@@ -196,6 +196,11 @@ struct reann_nlist {
     double md_dt = 0.0;
     int md_precision = -1, md_nsteps = -1;
     std::vector<void*> allocs;
+    // stream-ordered allocation (serving builds): blocks come from mem_pool on
+    // alloc_stream and go back with cudaFreeAsync on the same stream, so neither
+    // side waits for unrelated device work; null pool: cudaMalloc / cudaFree
+    cudaMemPool_t mem_pool = nullptr;
+    cudaStream_t alloc_stream = nullptr;
 };
 
 struct reann_ctx {
@@ -245,6 +250,11 @@ cudaError_t launch_moved(cudaStream_t s, const reann_nlist* nl, const double* po
 // serving pool (serve.cu)
 cudaError_t launch_pack(cudaStream_t s, const reann_nlist* src, const double* caller_pos, reann_nlist* pool,
                         int64_t ob, int64_t gb);
+void* nlist_alloc_bytes(reann_nlist* nl, size_t bytes);
+template <typename T>
+inline T* nlist_alloc(reann_nlist* nl, size_t count) {
+    return static_cast<T*>(nlist_alloc_bytes(nl, count * sizeof(T)));
+}
 cudaError_t launch_release(cudaStream_t s, reann_nlist* pool, int64_t ob, int64_t n);
 cudaError_t launch_retire(cudaStream_t s, const int4* seg, int nseg, reann_nlist* pool);
 cudaError_t launch_segment_energy(cudaStream_t s, const int4* seg, int nseg, const float* eps, double* energies);

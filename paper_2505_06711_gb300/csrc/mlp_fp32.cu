@@ -13,6 +13,8 @@
 // row-major activations and weights from shared memory.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace reann {
@@ -265,13 +267,18 @@ constexpr size_t bwd_smem() {
 }
 
 void ensure_attrs() {
-    static bool done = false;
-    if (done) return;
+    // once per device, safe under concurrent first calls
+    static std::mutex mu;
+    static uint64_t done = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 64 && ((done >> dev) & 1)) return;
     cudaFuncSetAttribute(k_mlp_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
     cudaFuncSetAttribute(k_mlp_fwd<NPHI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
     cudaFuncSetAttribute(k_mlp_bwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem());
     cudaFuncSetAttribute(k_mlp_bwd<NPHI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem());
-    done = true;
+    if (dev < 64) done |= (uint64_t)1 << dev;
 }
 
 NetsOfLayer layer_nets(const NetTable& t, int layer) {

@@ -36,6 +36,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace reann {
@@ -501,13 +503,18 @@ void set_attrs() {
 }
 
 void ensure_tc_attrs() {
-    static bool done = false;
-    if (done) return;
+    // once per device, safe under concurrent first calls
+    static std::mutex mu;
+    static uint64_t done = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 64 && ((done >> dev) & 1)) return;
     set_attrs<1, false>();
     set_attrs<NPHI, false>();
     set_attrs<1, true>();
     set_attrs<NPHI, true>();
-    done = true;
+    if (dev < 64) done |= (uint64_t)1 << dev;
 }
 
 template <int OUT, bool SPLIT>

@@ -440,12 +440,22 @@ static cudaError_t counting_sort(cudaStream_t s, const int* gate, int64_t n, int
     return cudaGetLastError();
 }
 
+void* nlist_alloc_bytes(reann_nlist* nl, size_t bytes) {
+    void* p = nullptr;
+    bytes = std::max<size_t>(bytes, 1);
+    const cudaError_t e = nl->mem_pool ? cudaMallocFromPoolAsync(&p, bytes, nl->mem_pool, nl->alloc_stream)
+                                       : cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    nl->allocs.push_back(p);
+    return p;
+}
+
 template <typename T>
 static T* dalloc(reann_nlist* nl, size_t count) {
-    void* p = nullptr;
-    if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return nullptr;
-    nl->allocs.push_back(p);
-    return (T*)p;
+    return nlist_alloc<T>(nl, count);
 }
 
 static int64_t owned_keys(const reann_nlist* nl) {

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -87,10 +88,7 @@ int make_geometry(reann_ctx* ctx, const double* cell, double r_cut, CellGeom* g)
 
 template <typename T>
 T* nl_alloc(reann_nlist* nl, size_t count) {
-    void* p = nullptr;
-    if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return nullptr;
-    nl->allocs.push_back(p);
-    return (T*)p;
+    return nlist_alloc<T>(nl, count);
 }
 
 int alloc_eval_buffers(reann_ctx* ctx, reann_nlist* nl) {
@@ -140,7 +138,12 @@ void free_nlist(reann_nlist* nl) {
     if (!nl) return;
     if (nl->md_exec) cudaGraphExecDestroy(nl->md_exec);
     if (nl->md_graph) cudaGraphDestroy(nl->md_graph);
-    for (void* p : nl->allocs) cudaFree(p);
+    for (void* p : nl->allocs) {
+        if (nl->mem_pool)
+            cudaFreeAsync(p, nl->alloc_stream);
+        else
+            cudaFree(p);
+    }
     delete nl;
 }
 
@@ -378,7 +381,7 @@ namespace {
 
 // neighbour list and ghost map only (no per-structure evaluation buffers)
 int build_list(reann_ctx* ctx, int64_t n_atoms, const double* pos, const int32_t* species, const double* cell,
-               double r_c, double skin, bool eval_buffers, reann_nlist** out) {
+               double r_c, double skin, bool eval_buffers, reann_nlist** out, cudaMemPool_t mem_pool = nullptr) {
     if (!ctx || !out) return REANN_E_ARG;
     *out = nullptr;
     if (n_atoms < 1 || n_atoms > (int64_t)1 << 28 || !pos || !species || !cell || !(skin >= 0) || !std::isfinite(skin))
@@ -391,6 +394,8 @@ int build_list(reann_ctx* ctx, int64_t n_atoms, const double* pos, const int32_t
     nl->T = ctx->model.T;
     nl->r_c = r_c;
     nl->skin = skin;
+    nl->mem_pool = mem_pool;
+    nl->alloc_stream = ctx->stream;
     int rc = make_geometry(ctx, cell, r_c + skin, &nl->geom);
     if (!rc) rc = build_nlist_device(ctx, nl, pos, species);
     if (!rc && eval_buffers) rc = alloc_eval_buffers(ctx, nl);
@@ -827,6 +832,7 @@ struct ServeSlot {
 }  // namespace
 
 struct reann_serve {
+    std::mutex mu;  // slots, ranges, staging and the pool stream; builds run outside it
     reann_ctx* ctx = nullptr;
     reann_nlist* pool = nullptr;
     int max_slots = 0;
@@ -836,6 +842,7 @@ struct reann_serve {
     int4* h_seg = nullptr;  // pinned staging
     Tile *h_t64 = nullptr, *h_t128 = nullptr;
     cudaStream_t stream = nullptr;
+    cudaMemPool_t build_pool = nullptr;  // stream-ordered blocks of the per-submission lists
     cudaEvent_t staged = nullptr, done = nullptr, user_ready = nullptr;
     std::vector<std::pair<reann_nlist*, cudaEvent_t>> deferred;  // built lists freed once their pack has run
     cudaGraph_t graph = nullptr;
@@ -851,6 +858,7 @@ void serve_reap(reann_serve* srv, bool wait) {
         auto& d = srv->deferred[k];
         if (wait) cudaEventSynchronize(d.second);
         if (cudaEventQuery(d.second) == cudaSuccess) {
+            d.first->alloc_stream = srv->stream;  // its last readers ran there
             free_nlist(d.first);
             cudaEventDestroy(d.second);
             srv->deferred.erase(srv->deferred.begin() + k);
@@ -874,6 +882,8 @@ extern "C" void reann_serve_free(reann_serve* srv) {
     if (!srv) return;
     if (srv->stream) cudaStreamSynchronize(srv->stream);
     serve_reap(srv, true);
+    if (srv->stream) cudaStreamSynchronize(srv->stream);
+    if (srv->build_pool) cudaMemPoolDestroy(srv->build_pool);
     if (srv->exec) cudaGraphExecDestroy(srv->exec);
     if (srv->graph) cudaGraphDestroy(srv->graph);
     free_nlist(srv->pool);
@@ -939,6 +949,18 @@ extern "C" int reann_serve_create(reann_ctx* ctx, int64_t max_atoms, int64_t max
         cudaEventCreateWithFlags(&srv->done, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&srv->user_ready, cudaEventDisableTiming) != cudaSuccess)
         return fail(REANN_E_CUDA, "serving pool: stream/event creation failed");
+    {
+        int dev = 0;
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        if (cudaGetDevice(&dev) != cudaSuccess) return fail(REANN_E_CUDA, "serving pool: no current device");
+        props.location.id = dev;
+        uint64_t keep = UINT64_MAX;  // released blocks stay mapped for the next submission
+        if (cudaMemPoolCreate(&srv->build_pool, &props) != cudaSuccess ||
+            cudaMemPoolSetAttribute(srv->build_pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess)
+            return fail(REANN_E_CUDA, "serving pool: memory pool creation failed");
+    }
     // empty pool: no neighbours, outputs to the sink row, every ghost slot "in use" (all point at atom 0)
     std::vector<int32_t> sink(max_atoms, (int32_t)max_atoms), goff(max_atoms + 1, 0);
     goff[max_atoms] = (int32_t)max_ghosts;
@@ -963,9 +985,19 @@ extern "C" int reann_serve_submit(reann_serve* srv, reann_ctx* build_ctx, int64_
     if (build_ctx->model.T != ctx->model.T || build_ctx->model.n_elem != ctx->model.n_elem ||
         build_ctx->model.r_c != ctx->model.r_c)
         return set_error(ctx, REANN_E_MISMATCH, "build context holds a different model");
-    serve_reap(srv, false);
+    {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        serve_reap(srv, false);
+        // refuse early when no structure slot or owned range can take it (ghosts are known only after the build)
+        bool slot_free = false;
+        for (const ServeSlot& sl : srv->slots) slot_free |= !sl.used;
+        int64_t widest = 0;
+        for (auto& r : srv->owned.free) widest = std::max(widest, r.second);
+        if (!slot_free || widest < n_atoms) return set_error(ctx, REANN_E_NOMEM, "serving pool full (admission refused)");
+    }
     reann_nlist* tmp = nullptr;
-    int rc = build_list(build_ctx, n_atoms, pos, species, cell, ctx->model.r_c, skin, false, &tmp);
+    int rc = build_list(build_ctx, n_atoms, pos, species, cell, ctx->model.r_c, skin, false, &tmp, srv->build_pool);
+    std::lock_guard<std::mutex> lock(srv->mu);
     if (rc) return set_error(ctx, rc, std::string("structure build: ") + build_ctx->err);
     if (tmp->max_count > srv->pool->stride) {
         free_nlist(tmp);
@@ -1014,6 +1046,7 @@ extern "C" int reann_serve_submit(reann_serve* srv, reann_ctx* build_ctx, int64_
 
 extern "C" int reann_serve_launch(reann_serve* srv, double* energies, float* forces, int* slots, int* count) {
     if (!srv || !energies || !forces || !count) return REANN_E_ARG;
+    std::lock_guard<std::mutex> lock(srv->mu);
     reann_ctx* ctx = srv->ctx;
     reann_nlist* p = srv->pool;
     // the pinned staging buffers of the previous launch must have been copied
@@ -1085,7 +1118,9 @@ extern "C" int reann_serve_launch(reann_serve* srv, double* energies, float* for
 }
 
 extern "C" int reann_serve_release(reann_serve* srv, int slot) {
-    if (!srv || slot < 0 || slot >= srv->max_slots || !srv->slots[slot].used) return REANN_E_ARG;
+    if (!srv) return REANN_E_ARG;
+    std::lock_guard<std::mutex> lock(srv->mu);
+    if (slot < 0 || slot >= srv->max_slots || !srv->slots[slot].used) return REANN_E_ARG;
     ServeSlot& sl = srv->slots[slot];
     if (!sl.retired) REANN_CUDA_TRY(srv->ctx, launch_release(srv->stream, srv->pool, sl.ob, sl.n));
     srv->owned.give(sl.ob, sl.n);
@@ -1094,15 +1129,18 @@ extern "C" int reann_serve_release(reann_serve* srv, int slot) {
     return REANN_OK;
 }
 
-extern "C" int reann_serve_slot(const reann_serve* srv, int slot, int64_t* atom_offset, int64_t* n_atoms) {
-    if (!srv || slot < 0 || slot >= srv->max_slots || !srv->slots[slot].used) return REANN_E_ARG;
+extern "C" int reann_serve_slot(reann_serve* srv, int slot, int64_t* atom_offset, int64_t* n_atoms) {
+    if (!srv) return REANN_E_ARG;
+    std::lock_guard<std::mutex> lock(srv->mu);
+    if (slot < 0 || slot >= srv->max_slots || !srv->slots[slot].used) return REANN_E_ARG;
     if (atom_offset) *atom_offset = srv->slots[slot].ob;
     if (n_atoms) *n_atoms = srv->slots[slot].n;
     return REANN_OK;
 }
 
-extern "C" int reann_serve_usage(const reann_serve* srv, int64_t* free_atoms, int64_t* free_ghosts, int* free_slots) {
+extern "C" int reann_serve_usage(reann_serve* srv, int64_t* free_atoms, int64_t* free_ghosts, int* free_slots) {
     if (!srv) return REANN_E_ARG;
+    std::lock_guard<std::mutex> lock(srv->mu);
     int64_t fa = 0, fg = 0;
     for (auto& r : srv->owned.free) fa = std::max(fa, r.second);
     for (auto& r : srv->ghost.free) fg = std::max(fg, r.second);
