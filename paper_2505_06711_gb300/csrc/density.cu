@@ -12,13 +12,14 @@
 //   (the second term of each line is the reverse edge j -> k, written with
 //   A_a(-r) = (-1)^l A_a(r); ghost slots j carry their owner's bbar, which is
 //   the paper's ghost-gradient exchange as a vector-Jacobian product, Sec. 2.2).
-// No atomics: every output row is written by the one quad that owns it.
+// No atomics: every output row is written by the lanes of its own centre atom.
 //
-// Layout: a quad of 4 lanes per centre atom (8 atoms per warp).  Each lane
-// walks every 4th live neighbour, gathers the neighbour's hi/lo FP32 position
-// (32 B) and coefficients (32 B) and accumulates the 80 products in
+// Forward layout: a quad of 4 lanes per centre atom (8 atoms per warp).  Each
+// lane walks every 4th live neighbour, gathers the neighbour's hi/lo FP32
+// position (32 B) and coefficients (32 B) and accumulates the 80 products in
 // registers; a butterfly reduce-scatter leaves 20 of the 80 b values in each
-// lane, which then contracts its 4 orbitals from shared memory.
+// lane, which then contracts its 4 orbitals from shared memory.  The adjoint
+// gathers 320 B of bbar per edge and uses 8 lanes per atom instead (below).
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -90,9 +91,6 @@ __device__ __forceinline__ void cutoff(const Radial& R, float d, float& fc, floa
     fc = c2 * c2;
     dfc = __fdiv_rn(-6.28318530717959f * c2 * c * s, R.rc);
 }
-
-// d - mu_m with the centre as a float pair
-__device__ __forceinline__ float dmu(const Radial& R, float d, int m) { return (d - R.mu_hi[m]) - R.mu_lo[m]; }
 
 __device__ __forceinline__ void monomials(float x, float y, float z, float A[NANG]) {
     A[0] = 1.f;
@@ -258,131 +256,143 @@ __global__ void __launch_bounds__(256) k_bbar(int64_t n, const float* __restrict
 }
 
 // ---------------------------------------------------------- adjoint ------
+// Reverse pass (header formulas), laid out for coalesced gathers: 8
+// lanes per centre atom k (4 atoms per warp), lane m owning radial channel m.
+// Per batch of 8 live edges each lane first computes the geometry of one edge
+// (d, f_c, f_c', the 8 Gaussians) into shared memory; then every lane walks the
+// 8 edges and, for its channel m, gathers bbar_{j,a,m} (a = 0..9: per load the
+// 8 lanes read one contiguous 32 B sector of row j) and c_{j,m}, and
+// accumulates its share of dE/dr_k; cbar_{k,m} is lane m's own sum.  The
+// force is reduced over the 8 lanes once per atom.
+constexpr int kAdjWarps = 8;
+constexpr int kAdjGroups = 4;  // centre atoms per warp
+// Edge record in shared memory: x y z 1/d | d fc fc' - | g_0..g_7 (16 floats).
+// Strides chosen bank-conflict free: a record every 20 floats (8 lanes' float4
+// stores hit 32 distinct banks), a group every 168 floats (the 4 groups'
+// reads of g_m land on disjoint banks).
+constexpr int kGeoStride = 20;
+constexpr int kGroupStride = 8 * kGeoStride + 8;
+
 template <bool WANT_CBAR>
-__global__ void __launch_bounds__(kWarps * 32) k_density_adj(int64_t n, int stride, Radial R,
-                                                            const int32_t* __restrict__ live,
-                                                            const int32_t* __restrict__ live_cnt,
-                                                            const float4* __restrict__ phi_hi,
-                                                            const float4* __restrict__ plo,
-                                                            const float* __restrict__ coef,
-                                                            const float* __restrict__ bbar, float* __restrict__ cbar,
-                                                            float* __restrict__ grad) {
-    __shared__ __align__(16) float sBk[kWarps][kAtomsPerWarp][kBStride];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, q = lane & 3, slot = lane >> 2;
-    const int64_t atom = ((int64_t)blockIdx.x * kWarps + warp) * kAtomsPerWarp + slot;
+__global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int stride, Radial R,
+                                                                const int32_t* __restrict__ live,
+                                                                const int32_t* __restrict__ live_cnt,
+                                                                const float4* __restrict__ phi_hi,
+                                                                const float4* __restrict__ plo,
+                                                                const float* __restrict__ coef,
+                                                                const float* __restrict__ bbar,
+                                                                float* __restrict__ cbar, float* __restrict__ grad) {
+    __shared__ __align__(16) float sGeo[kAdjWarps][kAdjGroups * kGroupStride];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, m = lane & 7, grp = lane >> 3;
+    const int64_t atom = ((int64_t)blockIdx.x * kAdjWarps + warp) * kAdjGroups + grp;
     const bool valid = atom < n;
-    float* sk = sBk[warp][slot];
+    float bk[NANG];
+    float ck = 0.f;
+    int cnt = 0;
+    float4 hi_i = make_float4(0.f, 0.f, 0.f, 0.f), lo_i = hi_i;
+    const int32_t* row = live;
     if (valid) {
 #pragma unroll
-        for (int v = 0; v < 20; v += 4)
-            *reinterpret_cast<float4*>(sk + 20 * q + v) = ldg4(bbar + (size_t)atom * NB + 20 * q + v);
+        for (int a = 0; a < NANG; ++a) bk[a] = __ldg(bbar + (size_t)atom * NB + a * NPHI + m);
+        ck = __ldg(coef + (size_t)atom * NPHI + m);
+        cnt = live_cnt[atom];
+        hi_i = phi_hi[atom];
+        lo_i = plo[atom];
+        row = live + (size_t)atom * stride;
+    } else {
+#pragma unroll
+        for (int a = 0; a < NANG; ++a) bk[a] = 0.f;
     }
-    __syncwarp();
-    float gx = 0.f, gy = 0.f, gz = 0.f;
-    float cb[NPHI];
-#pragma unroll
-    for (int m = 0; m < NPHI; ++m) cb[m] = 0.f;
-    if (valid) {
-        const float4 hi_i = phi_hi[atom], lo_i = plo[atom];
-        const float4 k0 = ldg4(coef + (size_t)atom * NPHI), k1 = ldg4(coef + (size_t)atom * NPHI + 4);
-        const float ck[NPHI] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
-        const int cnt = live_cnt[atom];
-        const int32_t* row = live + (size_t)atom * stride;
-        for (int e = q; e < cnt; e += 4) {
-            const int j = row[e];
+    int cmax = cnt;
+    cmax = max(cmax, __shfl_xor_sync(FULL, cmax, 8));
+    cmax = max(cmax, __shfl_xor_sync(FULL, cmax, 16));
+    const float mu_hi = R.mu_hi[m], mu_lo = R.mu_lo[m], two_alpha = 2.f * R.alpha_hi;
+    float* geo = sGeo[warp] + grp * kGroupStride;
+    float gx = 0.f, gy = 0.f, gz = 0.f, cb = 0.f;
+    for (int e0 = 0; e0 < cmax; e0 += 8) {
+        // geometry of edge e0 + m, one edge per lane
+        int j = 0;
+        if (e0 + m < cnt) {
+            j = row[e0 + m];
             const float4 hj = phi_hi[j], lj = plo[j];
             const float x = (hj.x - hi_i.x) + (lj.x - lo_i.x);
             const float y = (hj.y - hi_i.y) + (lj.y - lo_i.y);
             const float z = (hj.z - hi_i.z) + (lj.z - lo_i.z);
             const float d = sqrtf(x * x + y * y + z * z);
-            const float inv_d = 1.f / d;
             float gs[NPHI], fc, dfc;
             gaussians(R, d, gs);
             cutoff(R, d, fc, dfc);
-            const float4 c0 = ldg4(coef + (size_t)j * NPHI), c1 = ldg4(coef + (size_t)j * NPHI + 4);
-            const float cj[NPHI] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-            float phi[NPHI], p[NPHI], pt[NPHI], qv[NPHI], qt[NPHI];
+            float* g = geo + m * kGeoStride;
+            *reinterpret_cast<float4*>(g) = make_float4(x, y, z, 1.f / d);
+            *reinterpret_cast<float4*>(g + 4) = make_float4(d, fc, dfc, 0.f);
+            *reinterpret_cast<float4*>(g + 8) = make_float4(gs[0], gs[1], gs[2], gs[3]);
+            *reinterpret_cast<float4*>(g + 12) = make_float4(gs[4], gs[5], gs[6], gs[7]);
+        }
+        __syncwarp();
+        const int ns = cnt - e0;
+#pragma unroll 2
+        for (int s = 0; s < 8; ++s) {
+            const int js = __shfl_sync(FULL, j, (lane & ~7) | s);
+            if (s < ns) {
+                const float* g = geo + s * kGeoStride;
+                const float4 g0 = *reinterpret_cast<const float4*>(g);
+                const float4 g1 = *reinterpret_cast<const float4*>(g + 4);
+                const float gsm = g[8 + m];
+                const float* bj = bbar + (size_t)js * NB + m;
+                float bjv[NANG];
 #pragma unroll
-            for (int m = 0; m < NPHI; ++m) {
-                phi[m] = gs[m] * fc;
-                const float dphi = gs[m] * (dfc - 2.f * R.alpha_hi * dmu(R, d, m) * fc);
-                p[m] = cj[m] * dphi;
-                pt[m] = ck[m] * dphi;
-                qv[m] = cj[m] * phi[m];
-                qt[m] = ck[m] * phi[m];
-            }
-            float A[NANG];
-            monomials(x, y, z, A);
-            float sAU = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
-            float cacc[NPHI];
+                for (int a = 0; a < NANG; ++a) bjv[a] = __ldg(bj + a * NPHI);
+                const float cj = __ldg(coef + (size_t)js * NPHI + m);
+                const float x = g0.x, y = g0.y, z = g0.z, inv_d = g0.w;
+                const float d = g1.x, fc = g1.y, dfc = g1.z;
+                const float phi = gsm * fc;
+                const float dphi = gsm * (dfc - two_alpha * ((d - mu_hi) - mu_lo) * fc);  // d - mu_m as a float pair
+                const float p = cj * dphi, pt = ck * dphi, qv = cj * phi, qt = ck * phi;
+                float A[NANG];
+                monomials(x, y, z, A);
+                float sAU = 0.f, vx = 0.f, vy = 0.f, vz = 0.f, cacc = 0.f;
 #pragma unroll
-            for (int m = 0; m < NPHI; ++m) cacc[m] = 0.f;
-            const float* bj = bbar + (size_t)j * NB;
-#pragma unroll
-            for (int a = 0; a < NANG; ++a) {
-                const float sl = ang_sign(a);
-                const float4 k0a = ld4(sk + a * NPHI), k1a = ld4(sk + a * NPHI + 4);
-                const float bk[NPHI] = {k0a.x, k0a.y, k0a.z, k0a.w, k1a.x, k1a.y, k1a.z, k1a.w};
-                const float4 j0 = ldg4(bj + a * NPHI), j1 = ldg4(bj + a * NPHI + 4);
-                const float bjm[NPHI] = {j0.x, j0.y, j0.z, j0.w, j1.x, j1.y, j1.z, j1.w};
-                float u1 = 0.f, u2 = 0.f, v1 = 0.f, v2 = 0.f;
-#pragma unroll
-                for (int m = 0; m < NPHI; ++m) {
-                    u1 = fmaf(bk[m], p[m], u1);
-                    u2 = fmaf(bjm[m], pt[m], u2);
-                    if (a > 0) {
-                        v1 = fmaf(bk[m], qv[m], v1);
-                        v2 = fmaf(bjm[m], qt[m], v2);
+                for (int a = 0; a < NANG; ++a) {
+                    const float sl = ang_sign(a);
+                    sAU = fmaf(A[a], fmaf(bk[a], p, sl * bjv[a] * pt), sAU);
+                    const float v = fmaf(bk[a], qv, sl * bjv[a] * qt);
+                    switch (a) {
+                        case 1: vx += v; break;
+                        case 2: vy += v; break;
+                        case 3: vz += v; break;
+                        case 4: vx = fmaf(2.f * x, v, vx); break;
+                        case 5: vy = fmaf(2.f * y, v, vy); break;
+                        case 6: vz = fmaf(2.f * z, v, vz); break;
+                        case 7: vx = fmaf(y, v, vx); vy = fmaf(x, v, vy); break;
+                        case 8: vx = fmaf(z, v, vx); vz = fmaf(x, v, vz); break;
+                        case 9: vy = fmaf(z, v, vy); vz = fmaf(y, v, vz); break;
+                        default: break;
                     }
-                    if (WANT_CBAR) cacc[m] = fmaf(sl * A[a], bjm[m], cacc[m]);
+                    if (WANT_CBAR) cacc = fmaf(sl * A[a], bjv[a], cacc);
                 }
-                const float u = fmaf(sl, u2, u1);
-                sAU = fmaf(A[a], u, sAU);
-                const float v = fmaf(sl, v2, v1);
-                switch (a) {
-                    case 1: vx += v; break;
-                    case 2: vy += v; break;
-                    case 3: vz += v; break;
-                    case 4: vx = fmaf(2.f * x, v, vx); break;
-                    case 5: vy = fmaf(2.f * y, v, vy); break;
-                    case 6: vz = fmaf(2.f * z, v, vz); break;
-                    case 7: vx = fmaf(y, v, vx); vy = fmaf(x, v, vy); break;
-                    case 8: vx = fmaf(z, v, vx); vz = fmaf(x, v, vz); break;
-                    case 9: vy = fmaf(z, v, vy); vz = fmaf(y, v, vz); break;
-                    default: break;
-                }
-            }
-            const float s = sAU * inv_d;
-            gx -= fmaf(s, x, vx);
-            gy -= fmaf(s, y, vy);
-            gz -= fmaf(s, z, vz);
-            if (WANT_CBAR) {
-#pragma unroll
-                for (int m = 0; m < NPHI; ++m) cb[m] = fmaf(phi[m], cacc[m], cb[m]);
+                const float sc = sAU * inv_d;
+                gx -= fmaf(sc, x, vx);
+                gy -= fmaf(sc, y, vy);
+                gz -= fmaf(sc, z, vz);
+                if (WANT_CBAR) cb = fmaf(phi, cacc, cb);
             }
         }
+        __syncwarp();
     }
-    // quad all-reduce
 #pragma unroll
-    for (int o = 1; o <= 2; o <<= 1) {
+    for (int o = 1; o <= 4; o <<= 1) {
         gx += __shfl_xor_sync(FULL, gx, o);
         gy += __shfl_xor_sync(FULL, gy, o);
         gz += __shfl_xor_sync(FULL, gz, o);
-        if (WANT_CBAR) {
-#pragma unroll
-            for (int m = 0; m < NPHI; ++m) cb[m] += __shfl_xor_sync(FULL, cb[m], o);
-        }
     }
-    if (!valid || q != 0) return;
-    float* gr = grad + (size_t)atom * 3;
-    gr[0] += gx;
-    gr[1] += gy;
-    gr[2] += gz;
-    if (WANT_CBAR) {
-        float* dst = cbar + (size_t)atom * NPHI;
-        *reinterpret_cast<float4*>(dst) = make_float4(cb[0], cb[1], cb[2], cb[3]);
-        *reinterpret_cast<float4*>(dst + 4) = make_float4(cb[4], cb[5], cb[6], cb[7]);
+    if (!valid) return;
+    if (m == 0) {
+        float* gr = grad + (size_t)atom * 3;
+        gr[0] += gx;
+        gr[1] += gy;
+        gr[2] += gz;
     }
+    if (WANT_CBAR) cbar[(size_t)atom * NPHI + m] = cb;
 }
 
 // ------------------------------------------------------- small kernels ---
@@ -507,12 +517,12 @@ cudaError_t launch_bbar(cudaStream_t s, const reann_nlist* nl, const float* W, c
 cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* coef,
                                const float* bbar, float* cbar, float* grad, bool want_cbar, int* flags) {
     (void)flags;
-    const int64_t per_block = kWarps * kAtomsPerWarp;
+    const int64_t per_block = kAdjWarps * kAdjGroups;
     if (want_cbar)
-        k_density_adj<true><<<blocks_for(nl->n, per_block), kWarps * 32, 0, s>>>(
+        k_density_adj8<true><<<blocks_for(nl->n, per_block), kAdjWarps * 32, 0, s>>>(
             nl->n, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi, nl->pos_lo, coef, bbar, cbar, grad);
     else
-        k_density_adj<false><<<blocks_for(nl->n, per_block), kWarps * 32, 0, s>>>(
+        k_density_adj8<false><<<blocks_for(nl->n, per_block), kAdjWarps * 32, 0, s>>>(
             nl->n, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi, nl->pos_lo, coef, bbar, cbar, grad);
     return cudaGetLastError();
 }
