@@ -10,7 +10,9 @@
 // Atoms are stored element-major, so a tile of 64 consecutive rows uses one
 // element's weights.  A block of 256 threads computes a 64x64 layer output as
 // 16x16 threads x (4 rows x 4 columns), reading float4 fragments of the
-// row-major activations and weights from shared memory.
+// row-major activations and weights from shared memory.  Both kernels keep one
+// or two activation buffers only (48 KB / 68 KB of shared memory), so that
+// four / three blocks share an SM.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -75,7 +77,43 @@ __device__ __forceinline__ void load_rows(float* sX, const float* src, int row0,
     }
 }
 
+// Sum of 4 * OUT partial values over the 16 lanes of a half-warp (the tx of one
+// ty), as a butterfly reduce-scatter: with NV = 32 lane tx ends with values
+// 2 tx and 2 tx + 1, with NV = 4 every lane ends with value tx / 4.
+template <int NV>
+__device__ __forceinline__ void reduce16(float v[NV], int tx) {
+    int cnt = NV;
+#pragma unroll
+    for (int off = 8; off >= 1; off >>= 1) {
+        if (cnt > 1) {
+            const bool upper = tx & off;
+            const int half = cnt / 2;
+#pragma unroll
+            for (int k = 0; k < NV / 2; ++k) {
+                if (k < half) {
+                    const float send = upper ? v[k] : v[k + half];
+                    const float keep = upper ? v[k + half] : v[k];
+                    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                }
+            }
+            cnt = half;
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+        }
+    }
+}
+
+// W3 (64 x OUT) in shared memory with row k = 4 tx + j stored at (j * 16 + tx):
+// the 16 lanes of a half-warp read 16 different rows without bank conflicts
+template <int OUT>
+__device__ __forceinline__ int w3_row(int k) {
+    return (k & 3) * 16 + (k >> 2);
+}
+
 // ----------------------------------------------------------- forward ---
+// Shared memory: weights (31 KB) and one 64 x 68 activation buffer that holds
+// the input rows, then h1; h2 stays in registers and the output layer is a
+// half-warp reduction, so four blocks fit on an SM.
 template <int OUT>
 __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __restrict__ tiles,
                                                const float* __restrict__ rho, float* __restrict__ out,
@@ -83,24 +121,22 @@ __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __
     extern __shared__ __align__(16) float sm[];
     float* sW1 = sm;                 // 48 x 64
     float* sW2 = sW1 + NFEAT * H1;   // 64 x 64
-    float* sW3 = sW2 + H1 * H2;      // 64 x OUT
+    float* sW3 = sW2 + H1 * H2;      // 64 x OUT (8 reserved), rows permuted (w3_row)
     float* sb1 = sW3 + H2 * 8;       // 64
     float* sb2 = sb1 + H1;           // 64
     float* sb3 = sb2 + H2;           // 8
-    float* sX = sb3 + 8;             // 64 x 52
-    float* sH1 = sX + kR * LDX;      // 64 x 68
-    float* sH2 = sH1 + kR * LDH;     // 64 x 68
+    float* sA = sb3 + 8;             // 64 x 68: input rows (stride LDX), then h1 (stride LDH)
     const int tid = threadIdx.x;
     const Tile tl = tiles[blockIdx.x];
     if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list
     const NetDev& w = nets.e[tl.elem];
     copy_f4(sW1, w.W1, NFEAT * H1, tid);
     copy_f4(sW2, w.W2, H1 * H2, tid);
-    for (int i = tid; i < H2 * OUT; i += kT) sW3[i] = w.W3[i];
+    for (int i = tid; i < H2 * OUT; i += kT) sW3[w3_row<OUT>(i / OUT) * OUT + i % OUT] = w.W3[i];
     for (int i = tid; i < H1; i += kT) sb1[i] = w.b1[i];
     for (int i = tid; i < H2; i += kT) sb2[i] = w.b2[i];
     if (tid < OUT) sb3[tid] = w.b3[tid];
-    load_rows(sX, rho, tl.row0, tl.nrows, tid);
+    load_rows(sA, rho, tl.row0, tl.nrows, tid);
     __syncthreads();
     const int ty = tid >> 4, tx = tid & 15;
     float acc[4][4];
@@ -109,75 +145,81 @@ __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = sb1[4 * tx + j];
-    mma_4x4<NFEAT, LDX, H1>(sX, sW1, ty, tx, acc);
+    mma_4x4<NFEAT, LDX, H1>(sA, sW1, ty, tx, acc);
+    __syncthreads();  // every thread is done reading the input rows
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-        *reinterpret_cast<float4*>(sH1 + (4 * ty + i) * LDH + 4 * tx) =
+        *reinterpret_cast<float4*>(sA + (4 * ty + i) * LDH + 4 * tx) =
             make_float4(silu(acc[i][0]), silu(acc[i][1]), silu(acc[i][2]), silu(acc[i][3]));
     __syncthreads();
-    // layer 2
+    // layer 2 (h2 stays in registers)
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = sb2[4 * tx + j];
-    mma_4x4<H1, LDH, H2>(sH1, sW2, ty, tx, acc);
+    mma_4x4<H1, LDH, H2>(sA, sW2, ty, tx, acc);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-        *reinterpret_cast<float4*>(sH2 + (4 * ty + i) * LDH + 4 * tx) =
-            make_float4(silu(acc[i][0]), silu(acc[i][1]), silu(acc[i][2]), silu(acc[i][3]));
-    __syncthreads();
-    // layer 3: 4 threads per row
-    const int r = tid >> 2, part = tid & 3;
-    if (OUT == 1) {
-        float s = 0.f;
 #pragma unroll
-        for (int k = 16 * part; k < 16 * part + 16; ++k) s = fmaf(sH2[r * LDH + k], sW3[k], s);
-        s += __shfl_xor_sync(0xffffffffu, s, 1);
-        s += __shfl_xor_sync(0xffffffffu, s, 2);
-        if (part == 0 && r < tl.nrows) out[(size_t)(tl.row0 + r) * out_stride] = s + sb3[0];
-    } else {
-        float s0 = sb3[2 * part], s1 = sb3[2 * part + 1];
-#pragma unroll 8
-        for (int k = 0; k < H2; ++k) {
-            const float h = sH2[r * LDH + k];
-            s0 = fmaf(h, sW3[k * OUT + 2 * part], s0);
-            s1 = fmaf(h, sW3[k * OUT + 2 * part + 1], s1);
+        for (int j = 0; j < 4; ++j) acc[i][j] = silu(acc[i][j]);
+    // layer 3: per-thread partial dot products over its 4 columns, reduced over tx
+    float v[4 * OUT];
+#pragma unroll
+    for (int q = 0; q < 4 * OUT; ++q) v[q] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float* w3 = sW3 + (j * 16 + tx) * OUT;
+#pragma unroll
+        for (int o = 0; o < OUT; ++o) {
+            const float wv = w3[o];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i * OUT + o] = fmaf(acc[i][j], wv, v[i * OUT + o]);
         }
+    }
+    reduce16<4 * OUT>(v, tx);
+    if (OUT == 1) {
+        const int r = 4 * ty + (tx >> 2);
+        if ((tx & 3) == 0 && r < tl.nrows) out[(size_t)(tl.row0 + r) * out_stride] = v[0] + sb3[0];
+    } else {
+        const int r = 4 * ty + (tx >> 2), o = 2 * (tx & 3);
         if (r < tl.nrows) {
-            float* o = out + (size_t)(tl.row0 + r) * out_stride + 2 * part;
-            o[0] = s0;
-            o[1] = s1;
+            float* dst = out + (size_t)(tl.row0 + r) * out_stride + o;
+            dst[0] = v[0] + sb3[o];
+            dst[1] = v[1] + sb3[o + 1];
         }
     }
 }
 
 // ---------------------------------------------------------- backward ---
 // rhobar = W1 (dsilu(z1) * (W2 (dsilu(z2) * (W3 ybar))))   per row
+// Shared memory: the forward weights, replaced by their transposes (cp.async,
+// overlapping the z2bar step) once the forward recompute is done, and two
+// 64 x 68 activation buffers (input rows -> h1 -> z2bar -> z1bar, and z1), so
+// three blocks fit on an SM.
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
 template <int OUT>
 __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __restrict__ tiles,
                                                const float* __restrict__ rho, const float* __restrict__ ybar,
                                                float* __restrict__ rhobar) {
     extern __shared__ __align__(16) float sm[];
-    float* sW1 = sm;                  // 48 x 64
-    float* sW2 = sW1 + NFEAT * H1;    // 64 x 64
-    float* sW1t = sW2 + H1 * H2;      // 64 x 48
-    float* sW2t = sW1t + H1 * NFEAT;  // 64 x 64
-    float* sW3t = sW2t + H1 * H2;     // OUT x 64 (8 rows reserved)
+    float* sW1 = sm;                  // 48 x 64, later W1^T 64 x 48
+    float* sW2 = sW1 + NFEAT * H1;    // 64 x 64, later W2^T
+    float* sW3t = sW2 + H1 * H2;      // OUT x 64 (8 rows reserved)
     float* sb1 = sW3t + 8 * H2;       // 64
     float* sb2 = sb1 + H1;            // 64
     float* sY = sb2 + H2;             // 64 x 8
-    float* sX = sY + kR * 8;          // 64 x 52
-    float* sZ1 = sX + kR * LDX;       // 64 x 68
-    float* sZ2 = sZ1 + kR * LDH;      // 64 x 68
-    float* sG = sZ2 + kR * LDH;       // 64 x 68
+    float* sG = sY + kR * 8;          // 64 x 68: input rows, h1, z2bar, z1bar
+    float* sZ1 = sG + kR * LDH;       // 64 x 68: z1
     const int tid = threadIdx.x;
     const Tile tl = tiles[blockIdx.x];
     if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list
     const NetDev& w = nets.e[tl.elem];
     copy_f4(sW1, w.W1, NFEAT * H1, tid);
     copy_f4(sW2, w.W2, H1 * H2, tid);
-    copy_f4(sW1t, w.W1t, H1 * NFEAT, tid);
-    copy_f4(sW2t, w.W2t, H1 * H2, tid);
     for (int i = tid; i < OUT * H2; i += kT) sW3t[i] = w.W3t[i];
     for (int i = tid; i < H1; i += kT) sb1[i] = w.b1[i];
     for (int i = tid; i < H2; i += kT) sb2[i] = w.b2[i];
@@ -185,7 +227,7 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
         const int r = i / OUT, o = i % OUT;
         sY[r * 8 + o] = (OUT == 1) ? 1.f : (r < tl.nrows ? ybar[(size_t)(tl.row0 + r) * OUT + o] : 0.f);
     }
-    load_rows(sX, rho, tl.row0, tl.nrows, tid);
+    load_rows(sG, rho, tl.row0, tl.nrows, tid);
     __syncthreads();
     const int ty = tid >> 4, tx = tid & 15;
     float acc[4][4];
@@ -194,7 +236,8 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = sb1[4 * tx + j];
-    mma_4x4<NFEAT, LDX, H1>(sX, sW1, ty, tx, acc);
+    mma_4x4<NFEAT, LDX, H1>(sG, sW1, ty, tx, acc);
+    __syncthreads();  // every thread is done reading the input rows
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         *reinterpret_cast<float4*>(sZ1 + (4 * ty + i) * LDH + 4 * tx) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
@@ -213,7 +256,11 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) z2[i][j] = acc[i][j];
-    __syncthreads();  // everyone is done reading sG (h1)
+    __syncthreads();  // everyone is done reading h1, W1 and W2
+    // bring in the transposes while z2bar is computed
+    for (int i = tid; i < H1 * H2 / 4; i += kT) cp_async16(sW2 + 4 * i, w.W2t + 4 * i);
+    for (int i = tid; i < H1 * NFEAT / 4; i += kT) cp_async16(sW1 + 4 * i, w.W1t + 4 * i);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
     // z2bar = (ybar W3^T) * dsilu(z2) -> sG
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -230,17 +277,19 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
         *reinterpret_cast<float4*>(sG + (4 * ty + i) * LDH + 4 * tx) =
             make_float4(v[0] * dsilu(z2[i][0]), v[1] * dsilu(z2[i][1]), v[2] * dsilu(z2[i][2]), v[3] * dsilu(z2[i][3]));
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    // z1bar = (z2bar W2^T) * dsilu(z1) -> sZ2
+    // z1bar = (z2bar W2^T) * dsilu(z1)
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    mma_4x4<H2, LDH, H1>(sG, sW2t, ty, tx, acc);
+    mma_4x4<H2, LDH, H1>(sG, sW2, ty, tx, acc);
+    __syncthreads();  // everyone is done reading z2bar
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const float4 z1 = *reinterpret_cast<const float4*>(sZ1 + (4 * ty + i) * LDH + 4 * tx);
-        *reinterpret_cast<float4*>(sZ2 + (4 * ty + i) * LDH + 4 * tx) = make_float4(
+        *reinterpret_cast<float4*>(sG + (4 * ty + i) * LDH + 4 * tx) = make_float4(
             acc[i][0] * dsilu(z1.x), acc[i][1] * dsilu(z1.y), acc[i][2] * dsilu(z1.z), acc[i][3] * dsilu(z1.w));
     }
     __syncthreads();
@@ -250,7 +299,7 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-        mma_4x4<H1, LDH, NFEAT>(sZ2, sW1t, ty, tx, acc);
+        mma_4x4<H1, LDH, NFEAT>(sG, sW1, ty, tx, acc);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int r = 4 * ty + i;
@@ -261,10 +310,8 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
     }
 }
 
-constexpr size_t fwd_smem() { return sizeof(float) * (NFEAT * H1 + H1 * H2 + H2 * 8 + H1 + H2 + 8 + kR * LDX + 2 * kR * LDH); }
-constexpr size_t bwd_smem() {
-    return sizeof(float) * (2 * NFEAT * H1 + 2 * H1 * H2 + 8 * H2 + H1 + H2 + kR * 8 + kR * LDX + 3 * kR * LDH);
-}
+constexpr size_t fwd_smem() { return sizeof(float) * (NFEAT * H1 + H1 * H2 + H2 * 8 + H1 + H2 + 8 + kR * LDH); }
+constexpr size_t bwd_smem() { return sizeof(float) * (NFEAT * H1 + H1 * H2 + 8 * H2 + H1 + H2 + kR * 8 + 2 * kR * LDH); }
 
 void ensure_attrs() {
     // once per device, safe under concurrent first calls
