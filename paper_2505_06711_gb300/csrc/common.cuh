@@ -133,7 +133,8 @@ struct NlistScratch {
     int32_t* species_c = nullptr;              // caller-order species
     int32_t *ekey = nullptr, *ecounts = nullptr, *estart = nullptr, *eorder = nullptr;
     int32_t *scat = nullptr, *escat = nullptr;  // atomic-order scatter before the in-bucket ranking
-    float4* p32 = nullptr;  // FP32 positions of owned + ghost slots for the pre-test
+    float4* p32 = nullptr;   // FP32 positions of owned + ghost slots for the pre-test
+    float4* p32s = nullptr;  // the same in bin-sorted order, slot index in .w
 };
 
 }  // namespace reann

@@ -164,22 +164,28 @@ __global__ void k_scatter(const int* __restrict__ gate, int64_t n, const int32_t
 // atomic-order scatter moves to start[b] + (number of entries of its bucket with
 // a smaller index).  One thread per entry, each scanning its own bucket (buckets
 // hold tens of entries); entries of buckets >= sorted_keys keep their position.
+// With `pin`, the entry's FP32 position follows it into sorted order, its index
+// carried in .w (bit pattern), so that the search reads candidates contiguously.
 __global__ void k_bucket_rank(const int* __restrict__ gate, int64_t n, const int32_t* __restrict__ key, const int32_t* __restrict__ start,
                               const int32_t* __restrict__ scattered, int64_t sorted_keys,
-                              int32_t* __restrict__ order) {
+                              int32_t* __restrict__ order, const float4* __restrict__ pin, float4* __restrict__ pout) {
     if (gate && *gate == 0) return;  // rebuild not needed this step
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int32_t v = scattered[p];
     const int32_t b = key[v];
-    if (b >= sorted_keys) {
-        order[p] = v;
-        return;
+    int64_t dst = p;
+    if (b < sorted_keys) {
+        const int lo = start[b], hi = start[b + 1];
+        int rank = 0;
+        for (int q = lo; q < hi; ++q) rank += scattered[q] < v;
+        dst = lo + rank;
     }
-    const int lo = start[b], hi = start[b + 1];
-    int rank = 0;
-    for (int q = lo; q < hi; ++q) rank += scattered[q] < v;
-    order[lo + rank] = v;
+    order[dst] = v;
+    if (pin) {
+        const float4 x = pin[v];
+        pout[dst] = make_float4(x.x, x.y, x.z, __int_as_float(v));
+    }
 }
 
 // 2. gather per-atom arrays into internal order
@@ -200,11 +206,20 @@ __global__ void k_gather_internal(const int* __restrict__ gate, int64_t n, const
     sp[i] = sp_c[c];
 }
 
-// 3. ghost images: fractional coordinate within (-reach, 1 + reach) on every axis
-__device__ __forceinline__ bool image_in_halo(const CellGeom& g, const double f[3], int a, int b, int c) {
-    double v0 = f[0] + a, v1 = f[1] + b, v2 = f[2] + c;
-    return v0 > -g.reach[0] && v0 < 1.0 + g.reach[0] && v1 > -g.reach[1] && v1 < 1.0 + g.reach[1] &&
-           v2 > -g.reach[2] && v2 < 1.0 + g.reach[2];
+// 3. ghost images: fractional coordinate within (-reach, 1 + reach) on every axis.
+// The admissible shifts of one axis form an interval (the test is monotone in
+// the shift), so each axis is tested once per shift and only the admissible
+// box is enumerated, in the order a, b, c.
+__device__ __forceinline__ void halo_interval(const CellGeom& g, int k, double f, int& lo, int& hi) {
+    lo = 1;
+    hi = 0;
+    for (int a = -g.nmax[k]; a <= g.nmax[k]; ++a) {
+        const double v = f + a;
+        if (v > -g.reach[k] && v < 1.0 + g.reach[k]) {
+            if (lo > hi) lo = a;
+            hi = a;
+        }
+    }
 }
 
 template <bool FILL>
@@ -214,26 +229,29 @@ __global__ void k_ghosts(const int* __restrict__ gate, int64_t n, CellGeom g, co
     if (gate && *gate == 0) return;  // rebuild not needed this step
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double f[3] = {fw[3 * i], fw[3 * i + 1], fw[3 * i + 2]};
+    int lo[3], hi[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) halo_interval(g, k, fw[3 * i + k], lo[k], hi[k]);
+    if (!FILL) {
+        // the zero shift always lies in the interval (wrapped coordinates are in [0, 1))
+        gcnt[i] = (hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1) - 1;
+        return;
+    }
     int cnt = 0;
-    int64_t o = FILL ? goff[i] : 0;
-    for (int a = -g.nmax[0]; a <= g.nmax[0]; ++a)
-        for (int b = -g.nmax[1]; b <= g.nmax[1]; ++b)
-            for (int c = -g.nmax[2]; c <= g.nmax[2]; ++c) {
+    const int64_t o = goff[i];
+    for (int a = lo[0]; a <= hi[0]; ++a)
+        for (int b = lo[1]; b <= hi[1]; ++b)
+            for (int c = lo[2]; c <= hi[2]; ++c) {
                 if (a == 0 && b == 0 && c == 0) continue;
-                if (!image_in_halo(g, f, a, b, c)) continue;
-                if (FILL) {
-                    int64_t q = o + cnt;
-                    if (q < g_cap) {
-                        owner[q] = (int32_t)i;
-                        shift[q] = pack_shift(a, b, c);
-                    } else {
-                        atomicOr(&flags[FLAG_GHOST_OVERFLOW], 1);
-                    }
+                const int64_t q = o + cnt;
+                if (q < g_cap) {
+                    owner[q] = (int32_t)i;
+                    shift[q] = pack_shift(a, b, c);
+                } else {
+                    atomicOr(&flags[FLAG_GHOST_OVERFLOW], 1);
                 }
                 ++cnt;
             }
-    if (!FILL) gcnt[i] = cnt;
 }
 
 // 4. extended binning of owned + ghost slots (unused ghost capacity sorts last)
@@ -266,14 +284,21 @@ __global__ void k_ext_key(const int* __restrict__ gate, int64_t n, const int32_t
     p32[s] = make_float4((float)(xw[3 * o] + sv[0]), (float)(xw[3 * o + 1] + sv[1]), (float)(xw[3 * o + 2] + sv[2]), 0.f);
 }
 
-// 5. neighbour search: one warp per owned atom
+// 5. neighbour search: one warp per owned atom.  For each (x, y) column of the
+// stencil the z-run of bins is one contiguous range of the bin-sorted slots;
+// lane l takes column l of a batch of 32, a warp scan of the run lengths
+// concatenates them, and the warp walks the concatenation 32 candidates at a
+// time (a binary search over the scanned lengths maps a candidate to its
+// column), reading the sorted FP32 positions with their slot index in .w.
+// Candidates come in the same order as a bin-by-bin walk (x, then y, then z).
 __global__ void __launch_bounds__(256) k_nbr_search(const int* __restrict__ gate, int64_t n, CellGeom g, const double* __restrict__ xw,
                                                    const double* __restrict__ fw, const int32_t* __restrict__ owner,
                                                    const int32_t* __restrict__ shift, const float4* __restrict__ p32,
-                                                   const int32_t* __restrict__ order, const int32_t* __restrict__ bstart,
+                                                   const float4* __restrict__ p32s, const int32_t* __restrict__ bstart,
                                                    int stride, int32_t* __restrict__ nbr, int32_t* __restrict__ cnt_out,
                                                    int* __restrict__ flags) {
     if (gate && *gate == 0) return;  // rebuild not needed this step
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
@@ -282,53 +307,77 @@ __global__ void __launch_bounds__(256) k_nbr_search(const int* __restrict__ gate
     int b[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) b[k] = clampi((int)floor(fw[3 * i + k] * g.nb[k]) + g.pad[k], 0, g.nbx[k] - 1);
+    const int x0 = max(0, b[0] - g.sw[0]), x1 = min(g.nbx[0] - 1, b[0] + g.sw[0]);
+    const int y0 = max(0, b[1] - g.sw[1]), y1 = min(g.nbx[1] - 1, b[1] + g.sw[1]);
+    const int z0 = max(0, b[2] - g.sw[2]), z1 = min(g.nbx[2] - 1, b[2] + g.sw[2]);
+    const int ny = y1 - y0 + 1, ncol = (x1 - x0 + 1) * ny;
     const float lo2 = g.rcut2_f - g.margin, hi2 = g.rcut2_f + g.margin;
     int count = 0;
     int32_t* row = nbr + (size_t)i * stride;
-    for (int x = max(0, b[0] - g.sw[0]); x <= min(g.nbx[0] - 1, b[0] + g.sw[0]); ++x)
-        for (int y = max(0, b[1] - g.sw[1]); y <= min(g.nbx[1] - 1, b[1] + g.sw[1]); ++y)
-            for (int z = max(0, b[2] - g.sw[2]); z <= min(g.nbx[2] - 1, b[2] + g.sw[2]); ++z) {
-                const int bin = (x * g.nbx[1] + y) * g.nbx[2] + z;
-                const int s0 = bstart[bin], s1 = bstart[bin + 1];
-                for (int base = s0; base < s1; base += 32) {
-                    const int c = base + lane;
-                    bool hit = false;
-                    int j = -1;
-                    if (c < s1) {
-                        j = order[c];
-                        if (j != (int)i) {
-                            const float4 pj = p32[j];
-                            const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-                            const float d2 = dx * dx + dy * dy + dz * dz;
-                            if (d2 < lo2 && d2 > 1e-4f) {
-                                hit = true;
-                            } else if (d2 <= hi2) {
-                                // exact FP64 decision (and the coincident-atom check)
-                                int64_t o = j;
-                                int a0 = 0, a1 = 0, a2 = 0;
-                                if (j >= n) {
-                                    o = owner[j - n];
-                                    unpack_shift(shift[j - n], a0, a1, a2);
-                                }
-                                double sv[3];
-                                shift_vec(g, a0, a1, a2, sv);
-                                double r[3];
+    for (int cb = 0; cb < ncol; cb += 32) {
+        int st = 0, len = 0;
+        if (cb + lane < ncol) {
+            const int col = cb + lane;
+            const int bin0 = ((x0 + col / ny) * g.nbx[1] + (y0 + col % ny)) * g.nbx[2];
+            st = bstart[bin0 + z0];
+            len = bstart[bin0 + z1 + 1] - st;
+        }
+        int pref = len;  // inclusive scan of the run lengths
 #pragma unroll
-                                for (int k = 0; k < 3; ++k) r[k] = dadd(dsub(xw[3 * o + k], xi[k]), sv[k]);
-                                const double dd = dadd(dadd(dmul(r[0], r[0]), dmul(r[1], r[1])), dmul(r[2], r[2]));
-                                hit = dd < g.rcut2;
-                                if (dd < 1e-16) atomicOr(&flags[FLAG_GEOM], 2);
-                            }
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, pref, o);
+            if (lane >= o) pref += y;
+        }
+        const int total = __shfl_sync(FULL, pref, 31);
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            // column r of candidate t: the first lane whose inclusive prefix exceeds t
+            int lo = 0, hi = 31;
+#pragma unroll
+            for (int step = 0; step < 5; ++step) {
+                const int mid = (lo + hi) >> 1;
+                if (__shfl_sync(FULL, pref, mid) > t) hi = mid;
+                else lo = mid + 1;
+            }
+            const int r = min(lo, 31);
+            const int c = __shfl_sync(FULL, st, r) + t - (__shfl_sync(FULL, pref, r) - __shfl_sync(FULL, len, r));
+            bool hit = false;
+            int j = -1;
+            if (t < total) {
+                const float4 pj = p32s[c];
+                j = __float_as_int(pj.w);
+                if (j != (int)i) {
+                    const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                    const float d2 = dx * dx + dy * dy + dz * dz;
+                    if (d2 < lo2 && d2 > 1e-4f) {
+                        hit = true;
+                    } else if (d2 <= hi2) {
+                        // exact FP64 decision (and the coincident-atom check)
+                        int64_t o = j;
+                        int a0 = 0, a1 = 0, a2 = 0;
+                        if (j >= n) {
+                            o = owner[j - n];
+                            unpack_shift(shift[j - n], a0, a1, a2);
                         }
+                        double sv[3];
+                        shift_vec(g, a0, a1, a2, sv);
+                        double rr[3];
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) rr[k] = dadd(dsub(xw[3 * o + k], xi[k]), sv[k]);
+                        const double dd = dadd(dadd(dmul(rr[0], rr[0]), dmul(rr[1], rr[1])), dmul(rr[2], rr[2]));
+                        hit = dd < g.rcut2;
+                        if (dd < 1e-16) atomicOr(&flags[FLAG_GEOM], 2);
                     }
-                    const unsigned m = __ballot_sync(0xffffffffu, hit);
-                    if (hit) {
-                        const int p = count + __popc(m & ((1u << lane) - 1u));
-                        if (p < stride) row[p] = j;
-                    }
-                    count += __popc(m);
                 }
             }
+            const unsigned m = __ballot_sync(FULL, hit);
+            if (hit) {
+                const int p = count + __popc(m & ((1u << lane) - 1u));
+                if (p < stride) row[p] = j;
+            }
+            count += __popc(m);
+        }
+    }
     if (lane == 0) {
         cnt_out[i] = min(count, stride);
         if (count > stride) atomicOr(&flags[FLAG_NBR_OVERFLOW], 1);
@@ -428,14 +477,14 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 // start = bucket offsets.
 static cudaError_t counting_sort(cudaStream_t s, const int* gate, int64_t n, int64_t nkeys, const int32_t* key,
                                  int32_t* counts, int32_t* start, int32_t* scattered, int32_t* order,
-                                 int64_t sorted_keys) {
+                                 int64_t sorted_keys, const float4* pin = nullptr, float4* pout = nullptr) {
     cudaMemsetAsync(counts, 0, sizeof(int32_t) * nkeys, s);
     if (n > 0) k_hist<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, key, counts);
     k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(gate, nkeys, counts, start);
     cudaMemsetAsync(counts, 0, sizeof(int32_t) * nkeys, s);
     if (n > 0) {
         k_scatter<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, key, start, counts, scattered);
-        k_bucket_rank<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, key, start, scattered, sorted_keys, order);
+        k_bucket_rank<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, key, start, scattered, sorted_keys, order, pin, pout);
     }
     return cudaGetLastError();
 }
@@ -492,7 +541,7 @@ static cudaError_t stage_ghosts_and_bins(cudaStream_t s, reann_nlist* nl, int* f
     const int64_t nx = ext_bins(nl);
     k_ext_key<<<blocks_for(next, 256), 256, 0, s>>>(gate, n, w.goff + n, nl->g_cap, nl->geom, w.xw, w.fw, nl->g_owner,
                                                     nl->g_shift, w.ekey, w.p32, (int32_t)nx);
-    counting_sort(s, gate, next, nx + 1, w.ekey, w.ecounts, w.estart, w.escat, w.eorder, nx);
+    counting_sort(s, gate, next, nx + 1, w.ekey, w.ecounts, w.estart, w.escat, w.eorder, nx, w.p32, w.p32s);
     return cudaGetLastError();
 }
 
@@ -500,7 +549,7 @@ static cudaError_t stage_search(cudaStream_t s, reann_nlist* nl, int* flags, con
     const int64_t n = nl->n;
     NlistScratch& w = nl->w;
     k_nbr_search<<<blocks_for(n * 32, 256), 256, 0, s>>>(gate, n, nl->geom, w.xw, w.fw, nl->g_owner, nl->g_shift, w.p32,
-                                                         w.eorder, w.estart, nl->stride, nl->nbr, nl->nbr_cnt, flags);
+                                                         w.p32s, w.estart, nl->stride, nl->nbr, nl->nbr_cnt, flags);
     return cudaGetLastError();
 }
 
@@ -553,11 +602,12 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
     nl->g_shift = dalloc<int32_t>(nl, nl->g_cap);
     w.ekey = dalloc<int32_t>(nl, next);
     w.p32 = dalloc<float4>(nl, next);
+    w.p32s = dalloc<float4>(nl, next);
     w.ecounts = dalloc<int32_t>(nl, nx + 1);
     w.estart = dalloc<int32_t>(nl, nx + 2);
     w.eorder = dalloc<int32_t>(nl, next);
     w.escat = dalloc<int32_t>(nl, next);
-    if (!nl->g_owner || !nl->g_shift || !w.ekey || !w.p32 || !w.ecounts || !w.estart || !w.eorder || !w.escat)
+    if (!nl->g_owner || !nl->g_shift || !w.ekey || !w.p32 || !w.p32s || !w.ecounts || !w.estart || !w.eorder || !w.escat)
         return set_error(ctx, REANN_E_NOMEM, "ghost allocation failed");
     REANN_CUDA_TRY(ctx, stage_ghosts_and_bins(s, nl, ctx->d_flags, nullptr));
     // row capacity: expected neighbours from the number density, with headroom
