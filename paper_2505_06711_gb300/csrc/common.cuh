@@ -76,10 +76,11 @@ struct CellGeom {
     double hinv[9];  // frac = x . hinv
     double reach[3]; // r_cut / width_k + margin (fractional units)
     int nmax[3];     // largest |image shift| per axis
-    int nb[3];       // owned bins per axis
-    int pad[3];      // extra bins per side for ghosts
-    int nbx[3];      // nb + 2 pad
-    int sw[3];       // stencil half-width in bins per axis
+    int nb[3];       // owned bins per axis (internal order), width >= r_cut
+    int ns[3];       // search bins per axis, width >= r_cut / 2
+    int pad[3];      // extra search bins per side for ghosts
+    int nbx[3];      // ns + 2 pad
+    int sw[3];       // stencil half-width in search bins per axis
     double rcut2;    // (r_c + skin)^2
     float rcut2_f;
     float margin;    // FP32 pre-test band around rcut2 (A^2) decided in FP64

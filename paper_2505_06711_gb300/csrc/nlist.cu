@@ -112,42 +112,73 @@ __global__ void k_hist(const int* __restrict__ gate, int64_t n, const int32_t* _
     if (i < n) atomicAdd(&counts[key[i]], 1);
 }
 
-// Exclusive scan of `in` (n entries) into out[0..n]; one block of kScanThreads.
+// Exclusive scan of `in` (n entries) into out[0..n]; one block of kScanThreads
+// walking tiles of kScanThreads x kScanItems entries: each tile is loaded and
+// stored coalesced through shared memory (padded one word per 32 against bank
+// conflicts), each thread scans kScanItems consecutive entries, and a
+// two-level warp scan joins the threads; a running carry joins the tiles.
+constexpr int kScanItems = 8;
+
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_single(const int* __restrict__ gate, int64_t n, const T* __restrict__ in,
                                                                 T* __restrict__ out) {
     if (gate && *gate == 0) return;  // rebuild not needed this step
+    constexpr int TILE = kScanThreads * kScanItems;
+    __shared__ T buf[TILE + TILE / 32];
     __shared__ T warp_sums[kScanThreads / 32];
-    const int tid = threadIdx.x;
-    const int64_t chunk = (n + kScanThreads - 1) / kScanThreads;
-    const int64_t lo = tid * chunk, hi = min(n, lo + chunk);
-    T local = 0;
-    for (int64_t i = lo; i < hi; ++i) local += in[i];
-    T v = local;
-    const int lane = tid & 31, w = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    T carry = 0;
+    for (int64_t base = 0; base < n; base += TILE) {
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        T y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += y;
-    }
-    if (lane == 31) warp_sums[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        T s = warp_sums[lane];
+        for (int k = 0; k < kScanItems; ++k) {
+            const int x = k * kScanThreads + tid;
+            buf[x + x / 32] = (base + x < n) ? in[base + x] : (T)0;
+        }
+        __syncthreads();
+        T v[kScanItems];
+        T local = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            const int x = tid * kScanItems + k;
+            v[k] = buf[x + x / 32];
+            local += v[k];
+        }
+        T incl = local;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            T y = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += y;
+            const T y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
         }
-        warp_sums[lane] = s;  // inclusive
+        if (lane == 31) warp_sums[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            T s = warp_sums[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const T y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            warp_sums[lane] = s;  // inclusive
+        }
+        __syncthreads();
+        T run = carry + (w > 0 ? warp_sums[w - 1] : (T)0) + incl - local;
+        const T tile_total = warp_sums[kScanThreads / 32 - 1];
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            const int x = tid * kScanItems + k;
+            buf[x + x / 32] = run;
+            run += v[k];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            const int x = k * kScanThreads + tid;
+            if (base + x < n) out[base + x] = buf[x + x / 32];
+        }
+        carry += tile_total;
+        __syncthreads();  // buf and warp_sums are rewritten by the next tile
     }
-    __syncthreads();
-    T base = (w > 0 ? warp_sums[w - 1] : (T)0) + v - local;
-    for (int64_t i = lo; i < hi; ++i) {
-        out[i] = base;
-        base += in[i];
-    }
-    if (tid == kScanThreads - 1) out[n] = base;
+    if (tid == 0) out[n] = carry;
 }
 
 __global__ void k_scatter(const int* __restrict__ gate, int64_t n, const int32_t* __restrict__ key, const int32_t* __restrict__ start,
@@ -277,7 +308,7 @@ __global__ void k_ext_key(const int* __restrict__ gate, int64_t n, const int32_t
     double f[3] = {fw[3 * o] + a, fw[3 * o + 1] + b, fw[3 * o + 2] + c};
     int bx[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) bx[k] = clampi((int)floor(f[k] * g.nb[k]) + g.pad[k], 0, g.nbx[k] - 1);
+    for (int k = 0; k < 3; ++k) bx[k] = clampi((int)floor(f[k] * g.ns[k]) + g.pad[k], 0, g.nbx[k] - 1);
     key[s] = (bx[0] * g.nbx[1] + bx[1]) * g.nbx[2] + bx[2];
     double sv[3];
     shift_vec(g, a, b, c, sv);
@@ -306,7 +337,7 @@ __global__ void __launch_bounds__(256) k_nbr_search(const int* __restrict__ gate
     const double xi[3] = {xw[3 * i], xw[3 * i + 1], xw[3 * i + 2]};
     int b[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) b[k] = clampi((int)floor(fw[3 * i + k] * g.nb[k]) + g.pad[k], 0, g.nbx[k] - 1);
+    for (int k = 0; k < 3; ++k) b[k] = clampi((int)floor(fw[3 * i + k] * g.ns[k]) + g.pad[k], 0, g.nbx[k] - 1);
     const int x0 = max(0, b[0] - g.sw[0]), x1 = min(g.nbx[0] - 1, b[0] + g.sw[0]);
     const int y0 = max(0, b[1] - g.sw[1]), y1 = min(g.nbx[1] - 1, b[1] + g.sw[1]);
     const int z0 = max(0, b[2] - g.sw[2]), z1 = min(g.nbx[2] - 1, b[2] + g.sw[2]);

@@ -73,9 +73,11 @@ int make_geometry(reann_ctx* ctx, const double* cell, double r_cut, CellGeom* g)
         g->nmax[k] = (int)std::ceil(g->reach[k]);
         if (g->nmax[k] > 100) return set_error(ctx, REANN_E_GEOM, "cell too thin for the cutoff");
         g->nb[k] = std::max(1, std::min(1024, (int)std::floor(w / r_cut)));
-        g->sw[k] = std::max(1, (int)std::ceil(delta * g->nb[k] - 1e-9));
-        g->pad[k] = (int)std::ceil(g->reach[k] * g->nb[k]) + 1;
-        g->nbx[k] = g->nb[k] + 2 * g->pad[k];
+        // half-width search bins: a 5 x 5 x 5 stencil covers 42 % less volume than 3 x 3 x 3 full bins
+        g->ns[k] = std::max(1, std::min(1024, (int)std::floor(2.0 * w / r_cut)));
+        g->sw[k] = std::max(1, (int)std::ceil(delta * g->ns[k] - 1e-9));
+        g->pad[k] = (int)std::ceil(g->reach[k] * g->ns[k]) + 1;
+        g->nbx[k] = g->ns[k] + 2 * g->pad[k];
         maxc += std::fabs(g->h[k]) + std::fabs(g->h[3 + k]) + std::fabs(g->h[6 + k]);
     }
     g->rcut2 = r_cut * r_cut;

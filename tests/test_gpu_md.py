@@ -8,7 +8,7 @@ import pytest
 import oracle
 from synth import MASS_AMU, make_model, maxwell_boltzmann, water_box
 
-from gpu_helpers import assert_parity, potential
+from gpu_helpers import F_TOL_MAX, assert_parity, potential
 
 pytestmark = pytest.mark.gpu
 
@@ -78,7 +78,13 @@ def test_nve_conserves_energy_across_device_rebuilds():
     fresh.evaluate()
     fresh.check()
     torch.cuda.synchronize()
+    # After 1 ps the random model has heated the box to ~1,100 K and the end state
+    # holds close contacts (down to ~0.1 A) with forces up to ~8 eV/A.  FP32
+    # rounding in the edge sums is relative to the force (measured <= 2e-5 |F|
+    # per atom), so the absolute bar, set for forces of order 1 eV/A, scales with
+    # the largest force here.
+    f_scale = max(1.0, float(np.abs(ref["forces"]).max()))
     assert_parity({"energy": fresh.energy.item(), "forces": fresh.forces.double().cpu().numpy()},
-                  {k: ref[k] for k in ("energy", "forces")}, s.n_atoms)
+                  {k: ref[k] for k in ("energy", "forces")}, s.n_atoms, f_tol=F_TOL_MAX * f_scale)
     fresh.close()
     sy.close()
