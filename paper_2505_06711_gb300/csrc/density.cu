@@ -330,52 +330,61 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
         }
         __syncwarp();
         const int ns = cnt - e0;
-#pragma unroll 2
-        for (int s = 0; s < 8; ++s) {
+        // software pipeline over the batch: the gathers of edge s + 1 (register set
+        // B, or A) are in flight while edge s (set A, or B) is computed
+        float bjA[NANG], bjB[NANG], cjA = 0.f, cjB = 0.f;
+#pragma unroll
+        for (int a = 0; a < NANG; ++a) bjA[a] = bjB[a] = 0.f;
+        auto gather = [&](int s, float* bj, float& cj) {
             const int js = __shfl_sync(FULL, j, (lane & ~7) | s);
             if (s < ns) {
-                const float* g = geo + s * kGeoStride;
-                const float4 g0 = *reinterpret_cast<const float4*>(g);
-                const float4 g1 = *reinterpret_cast<const float4*>(g + 4);
-                const float gsm = g[8 + m];
-                const float* bj = bbar + (size_t)js * NB + m;
-                float bjv[NANG];
 #pragma unroll
-                for (int a = 0; a < NANG; ++a) bjv[a] = __ldg(bj + a * NPHI);
-                const float cj = __ldg(coef + (size_t)js * NPHI + m);
-                const float x = g0.x, y = g0.y, z = g0.z, inv_d = g0.w;
-                const float d = g1.x, fc = g1.y, dfc = g1.z;
-                const float phi = gsm * fc;
-                const float dphi = gsm * (dfc - two_alpha * ((d - mu_hi) - mu_lo) * fc);  // d - mu_m as a float pair
-                const float p = cj * dphi, pt = ck * dphi, qv = cj * phi, qt = ck * phi;
-                float A[NANG];
-                monomials(x, y, z, A);
-                float sAU = 0.f, vx = 0.f, vy = 0.f, vz = 0.f, cacc = 0.f;
-#pragma unroll
-                for (int a = 0; a < NANG; ++a) {
-                    const float sl = ang_sign(a);
-                    sAU = fmaf(A[a], fmaf(bk[a], p, sl * bjv[a] * pt), sAU);
-                    const float v = fmaf(bk[a], qv, sl * bjv[a] * qt);
-                    switch (a) {
-                        case 1: vx += v; break;
-                        case 2: vy += v; break;
-                        case 3: vz += v; break;
-                        case 4: vx = fmaf(2.f * x, v, vx); break;
-                        case 5: vy = fmaf(2.f * y, v, vy); break;
-                        case 6: vz = fmaf(2.f * z, v, vz); break;
-                        case 7: vx = fmaf(y, v, vx); vy = fmaf(x, v, vy); break;
-                        case 8: vx = fmaf(z, v, vx); vz = fmaf(x, v, vz); break;
-                        case 9: vy = fmaf(z, v, vy); vz = fmaf(y, v, vz); break;
-                        default: break;
-                    }
-                    if (WANT_CBAR) cacc = fmaf(sl * A[a], bjv[a], cacc);
-                }
-                const float sc = sAU * inv_d;
-                gx -= fmaf(sc, x, vx);
-                gy -= fmaf(sc, y, vy);
-                gz -= fmaf(sc, z, vz);
-                if (WANT_CBAR) cb = fmaf(phi, cacc, cb);
+                for (int a = 0; a < NANG; ++a) bj[a] = __ldg(bbar + (size_t)js * NB + m + a * NPHI);
+                cj = __ldg(coef + (size_t)js * NPHI + m);
             }
+        };
+        auto edge = [&](int s, const float* bj, float cj) {
+            if (s >= ns) return;
+            const float* g = geo + s * kGeoStride;
+            const float4 g0 = *reinterpret_cast<const float4*>(g);
+            const float4 g1 = *reinterpret_cast<const float4*>(g + 4);
+            const float gsm = g[8 + m];
+            const float x = g0.x, y = g0.y, z = g0.z, inv_d = g0.w;
+            const float d = g1.x, fc = g1.y, dfc = g1.z;
+            const float phi = gsm * fc;
+            const float dphi = gsm * (dfc - two_alpha * ((d - mu_hi) - mu_lo) * fc);  // d - mu_m as a float pair
+            float A[NANG];
+            monomials(x, y, z, A);
+            // Sk = sum_a A_a bbar_k,  Sj = sum_a (-1)^l A_a bbar_j  (also cbar's edge term)
+            float Sk = bk[0], Sj = bj[0];
+#pragma unroll
+            for (int a = 1; a < NANG; ++a) {
+                Sk = fmaf(A[a], bk[a], Sk);
+                Sj = fmaf(ang_sign(a) * A[a], bj[a], Sj);
+            }
+            // Gk = sum_a bbar_k grad A_a,  Gj = sum_a (-1)^l bbar_j grad A_a
+            const float x2 = 2.f * x, y2 = 2.f * y, z2 = 2.f * z;
+            const float gkx = fmaf(z, bk[8], fmaf(y, bk[7], fmaf(x2, bk[4], bk[1])));
+            const float gky = fmaf(z, bk[9], fmaf(x, bk[7], fmaf(y2, bk[5], bk[2])));
+            const float gkz = fmaf(y, bk[9], fmaf(x, bk[8], fmaf(z2, bk[6], bk[3])));
+            const float gjx = fmaf(z, bj[8], fmaf(y, bj[7], fmaf(x2, bj[4], -bj[1])));
+            const float gjy = fmaf(z, bj[9], fmaf(x, bj[7], fmaf(y2, bj[5], -bj[2])));
+            const float gjz = fmaf(y, bj[9], fmaf(x, bj[8], fmaf(z2, bj[6], -bj[3])));
+            // radial part (d phi / dd) A along r/d, angular part phi grad A
+            const float sc = fmaf(cj * dphi, Sk, ck * dphi * Sj) * inv_d;
+            const float qv = cj * phi, qt = ck * phi;
+            gx -= fmaf(sc, x, fmaf(qv, gkx, qt * gjx));
+            gy -= fmaf(sc, y, fmaf(qv, gky, qt * gjy));
+            gz -= fmaf(sc, z, fmaf(qv, gkz, qt * gjz));
+            if (WANT_CBAR) cb = fmaf(phi, Sj, cb);
+        };
+        gather(0, bjA, cjA);
+#pragma unroll
+        for (int s = 0; s < 8; s += 2) {
+            gather(s + 1, bjB, cjB);
+            edge(s, bjA, cjA);
+            if (s + 2 < 8) gather(s + 2, bjA, cjA);
+            edge(s + 1, bjB, cjB);
         }
         __syncwarp();
     }
