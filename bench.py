@@ -78,8 +78,56 @@ def parse():
     p.add_argument("--no-t-scaling", action="store_true")
     p.add_argument("--md-steps", type=int, default=1000)
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-decomp", action="store_true")
     p.add_argument("--serve-requests", type=int, default=10000)
     return p.parse_args()
+
+
+def run_decomp(args, steps: int = 100):
+    """The paper's spatial decomposition (Sec. 2.2) as virtual ranks on one GPU.
+
+    Same 24,576-atom water box and T = 3 evaluation; the undivided list against
+    2x2x2 and 4x4x4 subdomains, whose ghost slots are refreshed from their
+    owners before every layer (c) and in the reverse pass (bbar).  Reports the
+    evaluation time (no rebuild) and the halo sizes; forces are bitwise those
+    of the undivided list (tests/test_gpu_decomp.py).
+    """
+    import torch
+
+    from paper_2505_06711_gb300 import Potential
+    from synth import make_model, water_box
+
+    s = water_box(8192, seed=0)
+    pot = Potential(make_model(T=T_LAYERS))
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    out = {"workload": f"water box 8192 H2O ({s.n_atoms} atoms), T = {T_LAYERS}, evaluation only"}
+    for label, ranks in (("1x1x1", None), ("2x2x2", (2, 2, 2)), ("4x4x4", (4, 4, 4))):
+        sy = pot.system(s.pos, s.species, s.cell, skin=SKIN, ranks=ranks)
+        for _ in range(5):
+            sy.evaluate(atom_energy=False)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record()
+            sy.evaluate(atom_energy=False)
+            b.record()
+        torch.cuda.synchronize()
+        sy.check()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        info = sy.ranks()
+        remote = int(info["remote"].sum())
+        out[label] = {
+            "ranks": len(info["local"]),
+            "ms_per_eval": ms,
+            "atom_evals_per_s": s.n_atoms / (ms * 1e-3),
+            "ghost_slots": int(info["ghosts"].sum()),
+            "remote_ghost_slots": remote,
+            # per layer: c (8 FP32) forward and bbar (80 FP32) backward for every remote ghost
+            "exchange_bytes_per_layer": {"forward_c": remote * 32, "reverse_bbar": remote * 320},
+        }
+        sy.close()
+    pot.close()
+    return out
 
 
 def run_serve(args):
@@ -555,6 +603,7 @@ def run_ours(args):
     md = None if args.no_md else run_md(s, pot, args)
     t_scaling = None if args.no_t_scaling else run_t_scaling(args)
     serve = None if args.no_serve or ws > 1 else run_serve(args)
+    decomp = None if args.no_decomp else run_decomp(args)
 
     if rank == 0:
         line = base_line(args, ws, value, ms, "f32")
@@ -562,6 +611,7 @@ def run_ours(args):
         line["md"] = md
         line["t_scaling_cu_1m"] = t_scaling
         line["serve"] = serve
+        line["decomposition"] = decomp
         line["e2e"] = e2e
         line["roofline"] = roof
         line["gpu_launches"] = launches_per_step(T_LAYERS) * args.steps

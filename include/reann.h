@@ -166,6 +166,40 @@ int reann_nlist_info(const reann_nlist* nl, int64_t* n_atoms, int64_t* n_ghosts,
 int reann_nlist_export(reann_ctx* ctx, const reann_nlist* nl, int64_t cap, int32_t* i, int32_t* j, int32_t* n,
                        int64_t* count);
 
+/* ------------------------------------------------- spatial decomposition --- */
+
+/*
+ * The paper's parallel scheme (Sec. 2.2, Figs. 3-5) as virtual ranks on one
+ * device.  The cell is cut into ranks[0] x ranks[1] x ranks[2] subdomains in
+ * fractional coordinates (ranks host, each 1..64).  Rank r owns the atoms of
+ * its subdomain (local atoms) and holds a ghost slot for every atom or
+ * periodic image within r_c + skin of one of its local atoms that is not a
+ * zero-shift local atom of r (owned by another rank, or an image); its
+ * neighbour rows reference only its own local atoms and ghost slots.  The
+ * returned list evaluates through reann_energy_forces unchanged: before each
+ * layer every ghost slot receives its owner's coefficients (the per-layer
+ * exchange of Fig. 4a), and in the reverse pass its owner's bbar (the ghost
+ * gradient exchange of Sec. 2.2 in vector-Jacobian-product form), so the halo
+ * is r_c + skin for every T.  Rows keep the single-domain entry order and ghost
+ * slots hold bit-identical copies, so forces equal the single-domain list's
+ * bit for bit (energies to the order of the FP64 sum).  Other arguments as
+ * reann_build_nlist; synchronous (the subdomain bookkeeping runs on the host
+ * once).  Such a list is not rebuilt in place: reann_nlist_rebuild, an
+ * automatic rebuild in reann_energy_forces_host and reann_md_step return
+ * REANN_E_ARG.  Errors: as reann_build_nlist; REANN_E_ARG for bad ranks.
+ */
+int reann_build_nlist_decomposed(reann_ctx* ctx, int64_t n_atoms, const double* pos, const int32_t* species,
+                                 const double* cell, double r_c, double skin, const int32_t ranks[3],
+                                 reann_nlist** out);
+
+/*
+ * Per-rank sizes of a decomposed list (a single-domain list reports one rank):
+ * *n_ranks, and for each rank (host arrays of n_ranks entries, each nullable)
+ * its local atoms, ghost slots, and ghost slots owned by another rank (the
+ * slots the per-layer exchange fills across ranks).  Synchronous.
+ */
+int reann_decomp_info(const reann_nlist* nl, int32_t* n_ranks, int64_t* local, int64_t* ghosts, int64_t* remote);
+
 /* ------------------------------------------------------------ evaluation --- */
 
 /*

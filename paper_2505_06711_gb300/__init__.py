@@ -76,8 +76,9 @@ class Potential:
     def set_precision(self, precision: int) -> None:
         binding.reann_ctx_set_mlp_precision(self.ctx, precision)
 
-    def system(self, pos, species, cell, skin: float = 1.0) -> "System":
-        return System(self, pos, species, cell, skin)
+    def system(self, pos, species, cell, skin: float = 1.0, ranks=None) -> "System":
+        """One structure; ``ranks`` = (kx, ky, kz) builds the virtual-rank decomposed list."""
+        return System(self, pos, species, cell, skin, ranks)
 
     def close(self) -> None:
         if getattr(self, "ctx", None) is not None:
@@ -94,7 +95,7 @@ class Potential:
 class System:
     """One periodic structure with its resident neighbour list and buffers."""
 
-    def __init__(self, pot: Potential, pos, species, cell, skin: float = 1.0):
+    def __init__(self, pot: Potential, pos, species, cell, skin: float = 1.0, ranks=None):
         import torch
 
         self.pot = pot
@@ -103,7 +104,11 @@ class System:
         self.pos = torch.as_tensor(np.asarray(pos, dtype=np.float64), device=pot.device).contiguous()
         self.species = torch.as_tensor(np.asarray(species, dtype=np.int32), device=pot.device).contiguous()
         self.n = int(self.pos.shape[0])
-        self.nl = binding.reann_build_nlist(pot.ctx, self.pos, self.species, self.cell, pot.r_c, self.skin)
+        if ranks is None:
+            self.nl = binding.reann_build_nlist(pot.ctx, self.pos, self.species, self.cell, pot.r_c, self.skin)
+        else:
+            self.nl = binding.reann_build_nlist_decomposed(pot.ctx, self.pos, self.species, self.cell, pot.r_c,
+                                                           self.skin, ranks)
         self.energy = torch.zeros(1, dtype=torch.float64, device=pot.device)
         self.forces = torch.zeros((self.n, 3), dtype=torch.float32, device=pot.device)
         self.atom_energy = torch.zeros(self.n, dtype=torch.float32, device=pot.device)
@@ -150,6 +155,10 @@ class System:
 
     def info(self):
         return binding.reann_nlist_info(self.nl)
+
+    def ranks(self) -> dict:
+        """Per virtual rank: local atoms, ghost slots, ghost slots owned by another rank."""
+        return binding.reann_decomp_info(self.nl)
 
     def check(self) -> None:
         binding.reann_ctx_check(self.pot.ctx)

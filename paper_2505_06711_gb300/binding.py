@@ -62,6 +62,8 @@ _SIGS = {
     "reann_energy_forces": ([_vp, _vp, _vp, _int, _vp, _vp, _vp], _int),
     "reann_energy_forces_host": ([_vp, _vp, _vp, _int, _vp, _vp, _int], _int),
     "reann_get_layer": ([_vp, _vp, _int, _vp, _vp], _int),
+    "reann_build_nlist_decomposed": ([_vp, _i64, _vp, _vp, _vp, _dbl, _dbl, _vp, ctypes.POINTER(_vp)], _int),
+    "reann_decomp_info": ([_vp, _vp, _vp, _vp, _vp], _int),
     "reann_nlist_rebuild": ([_vp, _vp, _vp], _int),
     "reann_ctx_profile": ([_vp, _int], _int),
     "reann_profile_regions": ([], _int),
@@ -184,6 +186,29 @@ def reann_build_nlist(ctx, pos, species, cell, r_c: float, skin: float):
     out = _vp()
     _check(lib().reann_build_nlist(ctx, n, _ptr(pos), _ptr(species), _ptr(c), float(r_c), float(skin), ctypes.byref(out)), ctx)
     return out
+
+
+def reann_build_nlist_decomposed(ctx, pos, species, cell, r_c: float, skin: float, ranks):
+    import torch
+
+    n = pos.shape[0]
+    _dev(pos, torch.float64, (n, 3), "pos")
+    _dev(species, torch.int32, (n,), "species")
+    c = np.ascontiguousarray(cell, dtype=np.float64).reshape(9)
+    rk = np.ascontiguousarray(ranks, dtype=np.int32).reshape(3)
+    out = _vp()
+    _check(lib().reann_build_nlist_decomposed(ctx, n, _ptr(pos), _ptr(species), _ptr(c), float(r_c), float(skin),
+                                              _ptr(rk), ctypes.byref(out)), ctx)
+    return out
+
+
+def reann_decomp_info(nl) -> dict:
+    """{'local', 'ghosts', 'remote'}: per-rank counts (numpy int64 arrays)."""
+    k = np.zeros(1, np.int32)
+    _check(lib().reann_decomp_info(nl, _ptr(k), None, None, None))
+    loc, gh, rem = (np.zeros(int(k[0]), np.int64) for _ in range(3))
+    _check(lib().reann_decomp_info(nl, _ptr(k), _ptr(loc), _ptr(gh), _ptr(rem)))
+    return {"local": loc, "ghosts": gh, "remote": rem}
 
 
 def reann_nlist_free(nl) -> None:

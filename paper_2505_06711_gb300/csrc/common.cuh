@@ -197,6 +197,11 @@ struct reann_nlist {
     const void* md_key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     double md_dt = 0.0;
     int md_precision = -1, md_nsteps = -1;
+    // spatial decomposition into virtual ranks (reann_build_nlist_decomposed):
+    // per rank its local atoms, ghost slots, and ghost slots owned by another rank
+    bool decomposed = false;
+    int rank_grid[3] = {1, 1, 1};
+    std::vector<int64_t> rank_local, rank_ghost, rank_remote;
     std::vector<void*> allocs;
     // stream-ordered allocation (serving builds): blocks come from mem_pool on
     // alloc_stream and go back with cudaFreeAsync on the same stream, so neither

@@ -4,12 +4,15 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <numeric>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -93,7 +96,8 @@ T* nl_alloc(reann_nlist* nl, size_t count) {
     return nlist_alloc<T>(nl, count);
 }
 
-int alloc_eval_buffers(reann_ctx* ctx, reann_nlist* nl) {
+// ranges: (element, first row, end row) of the network tiles; default the element ranges
+int alloc_eval_buffers(reann_ctx* ctx, reann_nlist* nl, const std::vector<std::array<int, 3>>* ranges = nullptr) {
     const int64_t n = nl->n, ne = nl->n + nl->g_cap, T = nl->T;
     nl->live = nl_alloc<int32_t>(nl, (size_t)n * nl->stride);
     nl->live_cnt = nl_alloc<int32_t>(nl, n);
@@ -110,15 +114,18 @@ int alloc_eval_buffers(reann_ctx* ctx, reann_nlist* nl) {
     nl->n_partial = (int)((n + 2047) / 2048);
     nl->partial = nl_alloc<double>(nl, nl->n_partial);
     // element tiles of the atomic networks
+    std::vector<std::array<int, 3>> own;
+    if (!ranges) {
+        for (int e = 0; e < nl->n_elem; ++e) own.push_back({e, nl->elem_start[e], nl->elem_start[e + 1]});
+        ranges = &own;
+    }
     nl->tiles_h.clear();
-    for (int e = 0; e < nl->n_elem; ++e)
-        for (int r = nl->elem_start[e]; r < nl->elem_start[e + 1]; r += MLP_TILE)
-            nl->tiles_h.push_back(Tile{e, r, std::min(MLP_TILE, nl->elem_start[e + 1] - r), 0});
-    nl->tiles = nl_alloc<Tile>(nl, nl->tiles_h.size());
     nl->tiles128_h.clear();
-    for (int e = 0; e < nl->n_elem; ++e)
-        for (int r = nl->elem_start[e]; r < nl->elem_start[e + 1]; r += 128)
-            nl->tiles128_h.push_back(Tile{e, r, std::min(128, nl->elem_start[e + 1] - r), 0});
+    for (const auto& rg : *ranges) {
+        for (int r = rg[1]; r < rg[2]; r += MLP_TILE) nl->tiles_h.push_back(Tile{rg[0], r, std::min(MLP_TILE, rg[2] - r), 0});
+        for (int r = rg[1]; r < rg[2]; r += 128) nl->tiles128_h.push_back(Tile{rg[0], r, std::min(128, rg[2] - r), 0});
+    }
+    nl->tiles = nl_alloc<Tile>(nl, nl->tiles_h.size());
     nl->tiles128 = nl_alloc<Tile>(nl, nl->tiles128_h.size());
     if (!nl->tiles128) return set_error(ctx, REANN_E_NOMEM, "evaluation buffers: out of device memory");
     if (!nl->tiles128_h.empty())
@@ -417,6 +424,223 @@ extern "C" int reann_build_nlist(reann_ctx* ctx, int64_t n_atoms, const double* 
     return build_list(ctx, n_atoms, pos, species, cell, r_c, skin, true, out);
 }
 
+// ------------------------------------------------ spatial decomposition ---
+// Virtual ranks on one device (Sec. 2.2, Figs. 3-5).  The single-domain list is
+// built first and read back; every atom is assigned to the subdomain of its
+// wrapped fractional coordinates; atoms are re-ordered rank-major (element-
+// major inside a rank, the spatial order kept); every neighbour entry that is
+// not a zero-shift atom of the same rank becomes a ghost slot of that rank,
+// one slot per distinct (owner, image shift) in order of first use.  The rows
+// keep their entries' order, and a ghost slot receives bit-identical copies of
+// its owner's position, coefficients and bbar, so each atom's arithmetic is
+// the single-domain arithmetic.
+namespace {
+
+constexpr int32_t kZeroShift = 128 | (128 << 8) | (128 << 16);
+
+int build_decomposed(reann_ctx* ctx, reann_nlist* src, const int32_t ranks[3], reann_nlist** out) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = src->n;
+    const int stride = src->stride;
+    int32_t G = 0;
+    std::vector<int32_t> nbr((size_t)n * stride), cnt(n), perm(n), spc(n), wm(3 * n);
+    std::vector<double> fw(3 * n), pref(3 * n);
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(&G, src->w.goff + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    std::vector<int32_t> own(std::max<int32_t>(G, 1)), sh(std::max<int32_t>(G, 1));
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(nbr.data(), src->nbr, sizeof(int32_t) * nbr.size(), cudaMemcpyDeviceToHost, s));
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(cnt.data(), src->nbr_cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(perm.data(), src->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(spc.data(), src->species, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(wm.data(), src->wrapm, sizeof(int32_t) * 3 * n, cudaMemcpyDeviceToHost, s));
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(fw.data(), src->w.fw, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    REANN_CUDA_TRY(ctx, cudaMemcpyAsync(pref.data(), src->pos_ref, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    if (G > 0) {
+        REANN_CUDA_TRY(ctx, cudaMemcpyAsync(own.data(), src->g_owner, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, s));
+        REANN_CUDA_TRY(ctx, cudaMemcpyAsync(sh.data(), src->g_shift, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, s));
+    }
+    REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    // subdomain of every atom (internal order)
+    const int K = ranks[0] * ranks[1] * ranks[2];
+    std::vector<int32_t> rank(n);
+    for (int64_t i = 0; i < n; ++i) {
+        int b[3];
+        for (int k = 0; k < 3; ++k)
+            b[k] = std::min(ranks[k] - 1, std::max(0, (int)std::floor(fw[3 * i + k] * ranks[k])));
+        rank[i] = (b[0] * ranks[1] + b[1]) * ranks[2] + b[2];
+    }
+    // rank-major, then element-major; the existing (spatially sorted) order inside
+    std::vector<int64_t> order(n), newidx(n);
+    std::iota(order.begin(), order.end(), (int64_t)0);
+    const int ne = src->n_elem;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        return (int64_t)rank[a] * ne + spc[a] < (int64_t)rank[b] * ne + spc[b];
+    });
+    for (int64_t p = 0; p < n; ++p) newidx[order[p]] = p;
+    // ghost slots per rank and remapped rows (ghost entries first as -(local id + 1))
+    std::vector<std::unordered_map<int64_t, int32_t>> gmap(K);
+    std::vector<std::vector<int32_t>> gown(K), gsh(K);
+    std::vector<int32_t> row_new((size_t)n * stride, 0), cnt_new(n);
+    for (int64_t p = 0; p < n; ++p) {
+        const int64_t i = order[p];
+        const int r = rank[i];
+        cnt_new[p] = cnt[i];
+        for (int e = 0; e < cnt[i]; ++e) {
+            const int64_t sl = nbr[(size_t)i * stride + e];
+            int64_t o = sl;
+            int32_t shift = kZeroShift;
+            if (sl >= n) {
+                o = own[sl - n];
+                shift = sh[sl - n];
+            }
+            int32_t entry;
+            if (shift == kZeroShift && rank[o] == r) {
+                entry = (int32_t)newidx[o];
+            } else {
+                const int64_t key = (o << 24) | (int64_t)(shift & 0xFFFFFF);
+                auto it = gmap[r].find(key);
+                int32_t id;
+                if (it == gmap[r].end()) {
+                    id = (int32_t)gown[r].size();
+                    gmap[r].emplace(key, id);
+                    gown[r].push_back((int32_t)newidx[o]);
+                    gsh[r].push_back(shift);
+                } else {
+                    id = it->second;
+                }
+                entry = -(id + 1);
+            }
+            row_new[(size_t)p * stride + e] = entry;
+        }
+    }
+    std::vector<int64_t> gbase(K + 1, 0);
+    for (int r = 0; r < K; ++r) gbase[r + 1] = gbase[r] + (int64_t)gown[r].size();
+    const int64_t Gt = gbase[K];
+    if (n + Gt > ((int64_t)1 << 31) - 1) return set_error(ctx, REANN_E_CAPACITY, "decomposed list too large");
+    for (int64_t p = 0; p < n; ++p) {
+        const int r = rank[order[p]];
+        for (int e = 0; e < cnt_new[p]; ++e) {
+            int32_t& v = row_new[(size_t)p * stride + e];
+            if (v < 0) v = (int32_t)(n + gbase[r] + (-v - 1));
+        }
+    }
+    std::vector<int32_t> g_own(std::max<int64_t>(Gt, 1)), g_sh(std::max<int64_t>(Gt, 1));
+    for (int r = 0; r < K; ++r)
+        for (size_t q = 0; q < gown[r].size(); ++q) {
+            g_own[gbase[r] + q] = gown[r][q];
+            g_sh[gbase[r] + q] = gsh[r][q];
+        }
+    std::vector<int32_t> perm_new(n), spc_new(n), wm_new(3 * n), goff(n + 1, 0);
+    for (int64_t p = 0; p < n; ++p) {
+        const int64_t i = order[p];
+        perm_new[p] = perm[i];
+        spc_new[p] = spc[i];
+        for (int k = 0; k < 3; ++k) wm_new[3 * p + k] = wm[3 * i + k];
+    }
+    goff[n] = (int32_t)Gt;
+    // tiles: one run per (rank, element)
+    std::vector<std::array<int, 3>> ranges;
+    for (int64_t p = 0; p < n;) {
+        int64_t q = p;
+        while (q < n && rank[order[q]] == rank[order[p]] && spc_new[q] == spc_new[p]) ++q;
+        ranges.push_back({spc_new[p], (int)p, (int)q});
+        p = q;
+    }
+    // the new list
+    reann_nlist* nl = new (std::nothrow) reann_nlist;
+    if (!nl) return set_error(ctx, REANN_E_NOMEM, "host allocation failed");
+    nl->n = n;
+    nl->g = nl->g_cap = Gt;
+    nl->stride = stride;
+    nl->max_count = src->max_count;
+    nl->n_elem = ne;
+    nl->T = src->T;
+    nl->r_c = src->r_c;
+    nl->skin = src->skin;
+    nl->geom = src->geom;
+    for (int e = 0; e <= MAX_ELEM; ++e) nl->elem_start[e] = 0;
+    nl->decomposed = true;
+    for (int k = 0; k < 3; ++k) nl->rank_grid[k] = ranks[k];
+    nl->rank_local.assign(K, 0);
+    nl->rank_ghost.assign(K, 0);
+    nl->rank_remote.assign(K, 0);
+    for (int64_t i = 0; i < n; ++i) nl->rank_local[rank[i]]++;
+    for (int r = 0; r < K; ++r) {
+        nl->rank_ghost[r] = (int64_t)gown[r].size();
+        for (int32_t o : gown[r]) nl->rank_remote[r] += rank[order[o]] != r;
+    }
+    auto fail = [&](int code, const char* msg) {
+        cudaStreamSynchronize(s);
+        free_nlist(nl);
+        return set_error(ctx, code, msg);
+    };
+    nl->perm = nl_alloc<int32_t>(nl, n);
+    nl->species = nl_alloc<int32_t>(nl, n);
+    nl->wrapm = nl_alloc<int32_t>(nl, 3 * n);
+    nl->g_owner = nl_alloc<int32_t>(nl, std::max<int64_t>(Gt, 1));
+    nl->g_shift = nl_alloc<int32_t>(nl, std::max<int64_t>(Gt, 1));
+    nl->nbr = nl_alloc<int32_t>(nl, (size_t)n * stride);
+    nl->nbr_cnt = nl_alloc<int32_t>(nl, n);
+    nl->w.goff = nl_alloc<int32_t>(nl, n + 1);
+    nl->pos_ref = nl_alloc<double>(nl, 3 * n);
+    if (!nl->perm || !nl->species || !nl->wrapm || !nl->g_owner || !nl->g_shift || !nl->nbr || !nl->nbr_cnt ||
+        !nl->w.goff || !nl->pos_ref)
+        return fail(REANN_E_NOMEM, "decomposed list: out of device memory");
+    bool ok = cudaMemcpyAsync(nl->perm, perm_new.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+              cudaMemcpyAsync(nl->species, spc_new.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+              cudaMemcpyAsync(nl->wrapm, wm_new.data(), sizeof(int32_t) * 3 * n, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+              cudaMemcpyAsync(nl->g_owner, g_own.data(), sizeof(int32_t) * g_own.size(), cudaMemcpyHostToDevice, s) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(nl->g_shift, g_sh.data(), sizeof(int32_t) * g_sh.size(), cudaMemcpyHostToDevice, s) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(nl->nbr, row_new.data(), sizeof(int32_t) * row_new.size(), cudaMemcpyHostToDevice, s) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(nl->nbr_cnt, cnt_new.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+              cudaMemcpyAsync(nl->w.goff, goff.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(nl->pos_ref, pref.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    if (!ok) return fail(REANN_E_CUDA, "decomposed list: upload failed");
+    if (int rc = alloc_eval_buffers(ctx, nl, &ranges)) {
+        cudaStreamSynchronize(s);
+        free_nlist(nl);
+        return rc;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(REANN_E_CUDA, "decomposed list: upload failed");
+    *out = nl;
+    return REANN_OK;
+}
+
+}  // namespace
+
+extern "C" int reann_build_nlist_decomposed(reann_ctx* ctx, int64_t n_atoms, const double* pos, const int32_t* species,
+                                            const double* cell, double r_c, double skin, const int32_t ranks[3],
+                                            reann_nlist** out) {
+    if (!ctx || !out || !ranks) return set_error(ctx, REANN_E_ARG, "null argument");
+    *out = nullptr;
+    for (int k = 0; k < 3; ++k)
+        if (ranks[k] < 1 || ranks[k] > 64) return set_error(ctx, REANN_E_ARG, "ranks per axis must be in 1..64");
+    reann_nlist* src = nullptr;
+    int rc = build_list(ctx, n_atoms, pos, species, cell, r_c, skin, false, &src);
+    if (rc) return rc;
+    rc = build_decomposed(ctx, src, ranks, out);
+    cudaStreamSynchronize(ctx->stream);
+    free_nlist(src);
+    return rc;
+}
+
+extern "C" int reann_decomp_info(const reann_nlist* nl, int32_t* n_ranks, int64_t* local, int64_t* ghosts,
+                                 int64_t* remote) {
+    if (!nl) return REANN_E_ARG;
+    const int K = nl->decomposed ? (int)nl->rank_local.size() : 1;
+    if (n_ranks) *n_ranks = K;
+    for (int r = 0; r < K; ++r) {
+        if (local) local[r] = nl->decomposed ? nl->rank_local[r] : nl->n;
+        if (ghosts) ghosts[r] = nl->decomposed ? nl->rank_ghost[r] : nl->g;
+        if (remote) remote[r] = nl->decomposed ? nl->rank_remote[r] : 0;
+    }
+    return REANN_OK;
+}
+
 extern "C" void reann_nlist_free(reann_nlist* nl) { free_nlist(nl); }
 
 extern "C" int reann_nlist_info(const reann_nlist* nl, int64_t* n_atoms, int64_t* n_ghosts, int64_t* n_pairs,
@@ -582,6 +806,8 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
 }
 
 int run_rebuild(reann_ctx* ctx, reann_nlist* nl, const double* pos) {
+    if (nl->decomposed)
+        return set_error(ctx, REANN_E_ARG, "a decomposed list is not rebuilt in place: build it anew");
     ProfScope p(ctx, PR_REBUILD);
     REANN_CUDA_TRY(ctx, launch_rebuild(ctx->stream, nl, pos, ctx->d_flags, nullptr));
     return REANN_OK;
@@ -716,6 +942,7 @@ extern "C" int reann_md_step(reann_ctx* ctx, reann_nlist* nl, double* pos, doubl
                              double dt_fs, int n_steps, double* e_pot, double* e_kin) {
     if (!ctx || !nl || !pos || !vel || !mass || !(dt_fs > 0) || !std::isfinite(dt_fs) || n_steps < 0)
         return set_error(ctx, REANN_E_ARG, "bad argument to reann_md_step");
+    if (nl->decomposed) return set_error(ctx, REANN_E_ARG, "MD needs device rebuilds: use a single-domain list");
     if (n_steps == 0) return REANN_OK;
     if (!ctx->md_stream) {
         REANN_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->md_stream, cudaStreamNonBlocking));
