@@ -79,8 +79,51 @@ def parse():
     p.add_argument("--md-steps", type=int, default=1000)
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-decomp", action="store_true")
+    p.add_argument("--no-hea", action="store_true")
     p.add_argument("--serve-requests", type=int, default=10000)
     return p.parse_args()
+
+
+def run_hea(args, steps: int = 10):
+    """Five-element fcc high-entropy alloy (eight-element model), T = 3: the same step
+    (rebuild + energy/forces) on 32,000 and 1,048,576 atoms, FP32 and BF16 networks."""
+    import torch
+
+    from paper_2505_06711_gb300 import Potential, binding
+    from synth import hea_box, make_model
+
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    out = {"workload": "fcc random solid solution of Co, Cr, Fe, Mn, Ni in equal shares, a = 3.59 A, "
+                       f"skin {SKIN} A, T = {T_LAYERS}, step = rebuild + energy/forces"}
+    pot = Potential(make_model(T=T_LAYERS, n_elem=8))
+    for k in (20, 64):
+        s = hea_box(k, seed=0)
+        sy = pot.system(s.pos, s.species, s.cell, skin=SKIN)
+        res = {"atoms": s.n_atoms}
+        for name, prec in (("fp32", binding.REANN_MLP_FP32), ("bf16_mlp", binding.REANN_MLP_BF16)):
+            binding.reann_ctx_set_mlp_precision(pot.ctx, prec)
+
+            def step():
+                binding.reann_nlist_rebuild(pot.ctx, sy.nl, sy.pos)
+                binding.reann_energy_forces(pot.ctx, sy.nl, sy.pos, T_LAYERS, sy.energy, sy.forces, None)
+
+            for _ in range(3):
+                step()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for a, b in ev:
+                flush.zero_()
+                a.record()
+                step()
+                b.record()
+            torch.cuda.synchronize()
+            binding.reann_ctx_check(pot.ctx)
+            ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+            res[name] = {"ms_per_step": ms, "atom_evals_per_s": s.n_atoms / (ms * 1e-3)}
+        binding.reann_ctx_set_mlp_precision(pot.ctx, binding.REANN_MLP_FP32)
+        out[f"hea{k}"] = res
+        sy.close()
+    pot.close()
+    return out
 
 
 def run_decomp(args, steps: int = 100):
@@ -604,6 +647,7 @@ def run_ours(args):
     t_scaling = None if args.no_t_scaling else run_t_scaling(args)
     serve = None if args.no_serve or ws > 1 else run_serve(args)
     decomp = None if args.no_decomp else run_decomp(args)
+    hea = None if args.no_hea else run_hea(args)
 
     if rank == 0:
         line = base_line(args, ws, value, ms, "f32")
@@ -612,6 +656,7 @@ def run_ours(args):
         line["t_scaling_cu_1m"] = t_scaling
         line["serve"] = serve
         line["decomposition"] = decomp
+        line["hea"] = hea
         line["e2e"] = e2e
         line["roofline"] = roof
         line["gpu_launches"] = launches_per_step(T_LAYERS) * args.steps

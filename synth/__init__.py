@@ -4,7 +4,8 @@ This package draws random numbers and lays them out; it holds none of the
 REANN arithmetic (no distances, orbitals, densities or networks).  Both the
 oracle (``oracle/``) and the GPU library consume what it produces:
 
-* :mod:`synth.structures` -- periodic water boxes and fcc metal boxes
+* :mod:`synth.structures` -- periodic water boxes, fcc metal and high-entropy
+  alloy boxes
   (the paper's benchmark system types, Sec. 2.3 and Sec. 4.1), Maxwell-Boltzmann
   velocities for NVE runs.
 * :mod:`synth.model` -- a seeded REANN parameter set in the flat FP32 layout
@@ -16,11 +17,13 @@ from .structures import (  # noqa: F401
     Structure,
     water_box,
     fcc_box,
+    hea_box,
     supercell,
     maxwell_boltzmann,
     SPECIES_H,
     SPECIES_O,
     SPECIES_CU,
+    SPECIES_HEA,
     MASS_AMU,
 )
 from .model import ModelSpec, make_model, param_layout  # noqa: F401

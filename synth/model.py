@@ -48,19 +48,25 @@ import numpy as np
 # Input scale folded into the W1 rows of angular momentum l, per layer t and
 # element e: FEATURE_SCALE[t][e][l].  Chosen once, layer by layer, so that the
 # largest network input of every feature block is 1 on the 8,192-molecule
-# water box (H, O; seed 0) and the 32,000-atom fcc Cu box (Cu; seed 0) with the
-# default model seed (two significant digits; the Cu l=1 block, suppressed by
-# the fcc symmetry, takes the l=0 value).  Eq. 1 squares the coefficients, so
+# water box (H, O; seed 0), the 32,000-atom fcc Cu box (Cu; seed 0) and the
+# 4,000-atom high-entropy-alloy box (Co, Cr, Fe, Mn, Ni; seed 0, eight-element
+# model) with the default model seed (two significant digits; the Cu l=1
+# block, suppressed by the fcc symmetry, takes the l=0 value).  Eq. 1 squares the coefficients, so
 # the layer recursion maps an outlier ratio r to about r^2 per layer; scaling
 # by the maximum (not the RMS) keeps the random networks in their mildly
 # non-linear range on large boxes instead of letting outliers grow without
 # bound.  Layers beyond the table reuse its last row.
 FEATURE_SCALE = (
-    ((0.054, 0.16, 0.0017), (0.046, 0.21, 0.0019), (0.35, 0.35, 0.014)),
-    ((19.0, 46.0, 2.7), (16.0, 53.0, 3.3), (5.5, 5.5, 0.14)),
-    ((26.0, 24.0, 0.78), (17.0, 27.0, 0.87), (110.0, 110.0, 5.8)),
-    ((5.7, 12.0, 1.0), (7.9, 11.0, 1.7), (15.0, 15.0, 2.2)),
-    ((7.7, 8.7, 4.2), (4.6, 10.0, 4.3), (15.0, 15.0, 1.6)),
+    ((0.054, 0.16, 0.0017), (0.046, 0.21, 0.0019), (0.35, 0.35, 0.014),
+     (0.2, 0.14, 0.021), (0.16, 0.13, 0.013), (0.21, 0.16, 0.019), (0.21, 0.14, 0.017), (0.16, 0.16, 0.013)),
+    ((19.0, 46.0, 2.7), (16.0, 53.0, 3.3), (5.5, 5.5, 0.14),
+     (37.0, 55.0, 2.4), (33.0, 56.0, 2.0), (33.0, 27.0, 1.8), (34.0, 48.0, 2.0), (38.0, 36.0, 1.6)),
+    ((26.0, 24.0, 0.78), (17.0, 27.0, 0.87), (110.0, 110.0, 5.8),
+     (56.0, 20.0, 4.0), (85.0, 31.0, 6.7), (74.0, 19.0, 5.6), (84.0, 34.0, 6.1), (84.0, 47.0, 6.5)),
+    ((5.7, 12.0, 1.0), (7.9, 11.0, 1.7), (15.0, 15.0, 2.2),
+     (54.0, 23.0, 5.3), (41.0, 24.0, 5.4), (24.0, 13.0, 3.5), (78.0, 38.0, 8.5), (56.0, 45.0, 7.1)),
+    ((7.7, 8.7, 4.2), (4.6, 10.0, 4.3), (15.0, 15.0, 1.6),
+     (210.0, 34.0, 6.3), (230.0, 49.0, 7.0), (76.0, 24.0, 7.1), (380.0, 57.0, 12.0), (210.0, 44.0, 6.4)),
 )
 # Multiplier on the energy network's output weights (eV): gives forces of
 # about 2 eV/A (99th percentile) on the water box and 0.5 eV/A (median) on

@@ -7,11 +7,15 @@ in for them with the same shapes, densities and sizes:
 * water: ``n`` rigid-geometry molecules at 1.0 g/cm^3, oxygens on a jittered
   cubic grid, hydrogens at 0.96 A and 104.5 degrees with a random orientation;
 * fcc: ``k^3`` conventional cells of a lattice constant ``a`` with Gaussian
-  displacements.
+  displacements;
+* high-entropy alloy (the paper's third system type, Sec. 4.1): an fcc random
+  solid solution of five species in equal shares (Co, Cr, Fe, Mn, Ni, the
+  Cantor alloy's elements), lattice constant 3.59 A.
 
 Everything is drawn from ``numpy.random.Generator(PCG64(seed))``.  Cells are
-3x3 arrays whose rows are the lattice vectors (A).  Species indices follow the
-three-element model of :mod:`synth.model`: H=0, O=1, Cu=2.
+3x3 arrays whose rows are the lattice vectors (A).  Species indices: H=0, O=1,
+Cu=2 (the default three-element model of :mod:`synth.model`) and Co=3, Cr=4,
+Fe=5, Mn=6, Ni=7 (models with ``n_elem = 8``).
 """
 
 from __future__ import annotations
@@ -24,9 +28,10 @@ import numpy as np
 SPECIES_H = 0
 SPECIES_O = 1
 SPECIES_CU = 2
+SPECIES_HEA = (3, 4, 5, 6, 7)  # Co, Cr, Fe, Mn, Ni
 
 # atomic masses in amu, indexed by species
-MASS_AMU = np.array([1.008, 15.999, 63.546], dtype=np.float64)
+MASS_AMU = np.array([1.008, 15.999, 63.546, 58.933, 51.996, 55.845, 54.938, 58.693], dtype=np.float64)
 
 # volume per water molecule at 1.0 g/cm^3 (A^3): 18.015 g/mol / (N_A * 1 g/cm^3)
 WATER_VOLUME_A3 = 29.915
@@ -164,6 +169,19 @@ def fcc_box(k: int, a: float = 3.615, seed: int = 0, sigma: float = 0.05, specie
         pos = pos + rng.normal(0.0, sigma, size=pos.shape)
     n = pos.shape[0]
     return Structure(pos, np.full(n, species, dtype=np.int32), np.eye(3) * (k * a), name=f"fcc{k}")
+
+
+def hea_box(k: int, a: float = 3.59, seed: int = 0, sigma: float = 0.05, species=SPECIES_HEA) -> Structure:
+    """fcc random solid solution: ``4 k^3`` atoms, the species in equal shares
+    (as equal as the atom count allows) on a seeded random permutation of the
+    sites, N(0, sigma) displacements."""
+    s = fcc_box(k, a=a, seed=seed, sigma=sigma)
+    rng = np.random.Generator(np.random.PCG64([seed, 1]))
+    n = s.n_atoms
+    kinds = np.asarray(species, dtype=np.int32)
+    labels = np.resize(kinds, n)
+    rng.shuffle(labels)
+    return Structure(s.pos, labels.astype(np.int32), s.cell, name=f"hea{k}")
 
 
 def supercell(s: Structure, reps: tuple[int, int, int]) -> Structure:
