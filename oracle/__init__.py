@@ -53,7 +53,7 @@ def _load():
             i64, i32, dbl, ptr, c_int = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p, ctypes.c_int
             lib.oracle_neighbors.argtypes = [i64, ptr, ptr, dbl, i64, ptr, ptr, ptr, ptr, c_int]
             lib.oracle_neighbors.restype = c_int
-            lib.oracle_energy_forces.argtypes = [c_int] * 7 + [dbl, dbl, ptr, i64, ptr, ptr, ptr, ptr, ptr, ptr, ptr, ptr, c_int]
+            lib.oracle_energy_forces.argtypes = [c_int] * 7 + [dbl, dbl, ptr, i64, ptr, ptr, ptr, ptr, ptr, ptr, ptr, ptr, ptr, c_int]
             lib.oracle_energy_forces.restype = c_int
             lib.oracle_max_threads.argtypes = []
             lib.oracle_max_threads.restype = c_int
@@ -101,7 +101,9 @@ def neighbors(pos, cell, r_cut: float, n_threads: int = 0):
 
 
 def energy_forces(model, pos, species, cell, want_layers: bool = False, n_threads: int = 0):
-    """FP64 energy, forces (N,3), atom energies (N,) [and rho (T,N,F), c (T,N,P)].
+    """FP64 energy, forces (N,3), atom energies (N,), virial (3,3) [and rho (T,N,F), c (T,N,P)].
+
+    The virial is W = -dE/d(strain) (positions and cell strained alike).
 
     ``model`` is a :class:`synth.model.ModelSpec`; its ``T`` is the number of
     message-passing layers.  ``cell=None`` evaluates a free cluster.
@@ -117,13 +119,14 @@ def energy_forces(model, pos, species, cell, want_layers: bool = False, n_thread
     eps = np.zeros(n, np.float64)
     rho = np.zeros((model.T, n, model.n_feat), np.float64) if want_layers else None
     coef = np.zeros((model.T, n, model.n_phi), np.float64) if want_layers else None
+    virial = np.zeros((3, 3), np.float64)
     rc = lib.oracle_energy_forces(
         model.n_elem, model.T, model.n_phi, model.l_max, model.n_orb, model.h1, model.h2,
         float(model.r_c), float(model.alpha), _p(params), n, _p(pos), _p(species), _p(cellp),
-        _p(energy), _p(forces), _p(eps), _p(rho), _p(coef), n_threads,
+        _p(energy), _p(forces), _p(eps), _p(rho), _p(coef), _p(virial), n_threads,
     )
     _check(rc)
-    out = {"energy": float(energy[0]), "forces": forces, "atom_energy": eps}
+    out = {"energy": float(energy[0]), "forces": forces, "atom_energy": eps, "virial": virial}
     if want_layers:
         out["rho"] = rho
         out["coef"] = coef

@@ -433,13 +433,17 @@ static void mlp_backward(const model_t *M, const double *p, int out, const doubl
  * E, F = -dE/dr, per-atom energies and (optionally) every layer's features
  * rho^t [T][n][F] and coefficients c^t [T][n][N_phi] for the model whose flat
  * parameters are `params` (layout of synth/model.py).  cell == NULL means a
- * free (non-periodic) cluster.  Returns OR_E_GEOM on non-finite positions, a
+ * free (non-periodic) cluster.  `virial` (nullable, 3 x 3 row-major) receives
+ * W_ab = -sum over edges e and layers of (dE/dr_e)_a (r_e)_b, minus the
+ * derivative of E with respect to a homogeneous strain eps_ab applied to
+ * positions and cell alike: E depends on positions only through the edge
+ * vectors r_e of Eq. 1.  Returns OR_E_GEOM on non-finite positions, a
  * singular cell, or two atoms closer than 1e-8 A.
  */
 int oracle_energy_forces(int n_elem, int T, int n_phi, int l_max, int n_orb, int h1, int h2, double r_c,
                          double alpha, const float *params, int64_t n, const double *pos, const int32_t *species,
                          const double *cell, double *energy, double *forces, double *atom_energy, double *rho_out,
-                         double *coef_out, int n_threads) {
+                         double *coef_out, double *virial, int n_threads) {
     if (n < 0 || !pos || !species || !energy || (n > 0 && !forces)) return OR_E_ARG;
     if (h1 > 512 || h2 > 512) return OR_E_ARG;
     set_threads(n_threads);
@@ -483,6 +487,8 @@ int oracle_energy_forces(int n_elem, int T, int n_phi, int l_max, int n_orb, int
     double *grad = (double *)calloc(nn * 3, sizeof(double));
     if (!c || !b || !rho || !z1 || !z2 || !eps || !rhobar || !bbar || !cbar || !grad) rc = OR_E_NOMEM;
 
+    if (virial)
+        for (int k = 0; k < 9; ++k) virial[k] = 0.0;
     if (!rc) {
         /* c^0_i = c0[Z_i] */
         for (int64_t i = 0; i < n; ++i)
@@ -586,6 +592,9 @@ int oracle_energy_forces(int n_elem, int T, int n_phi, int l_max, int n_orb, int
                         grad[3 * j + k] += tg[k];
                         grad[3 * i + k] -= tg[k];
                     }
+                    if (virial)
+                        for (int a = 0; a < 3; ++a)
+                            for (int bb = 0; bb < 3; ++bb) virial[3 * a + bb] -= tg[a] * r[bb];
                 }
             }
             /* rhobar^{t-1} = J_{M^{t-1}}^T cbar^t (Eq. 5); c^0 is a constant */

@@ -10,7 +10,7 @@ the reverse pass, the wrong element's network) fails at least one of them:
 * pair-dot identity: sum_a w_a (sum_j u_j A_a(r_j))^2 = sum_jj' u_j u_j' (r_j . r_j')^l,
   so rho^0 of a whole box is recomputed from dot products of neighbour vectors;
 * central finite differences of the oracle energy against its reverse pass
-  (Eqs. 3-5);
+  (Eqs. 3-5), in the positions (forces) and in a homogeneous strain (virial);
 * invariances (translation, rotation of positions and cell, permutation),
   sum F = 0, extensivity of a periodic supercell;
 * isolated atoms and the receptive field T * r_c of Sec. 2.2 / Fig. 2;
@@ -151,6 +151,33 @@ def test_forces_match_central_differences(make):
             fd[a, k] = -(ep - em) / (2 * h)
     assert np.abs(out["forces"]).max() > 1e-3  # the test is not vacuous
     np.testing.assert_allclose(out["forces"], fd, atol=1e-7, rtol=0)
+
+
+@pytest.mark.parametrize(
+    "make",
+    [lambda: water_box(8, seed=2), lambda: fcc_box(2, seed=4, sigma=0.1)],
+    ids=["water24", "fcc32"],
+)
+def test_virial_is_minus_strain_derivative(make):
+    """W_ab = -dE/d eps_ab: central differences of E under the homogeneous strain
+    x -> (I + eps) x applied to every position and every lattice vector; W is
+    symmetric because E is invariant under rotations."""
+    s = make()
+    m = make_model(T=3, seed=5)
+    out = oracle.energy_forces(m, s.pos, s.species, s.cell)
+    h = 1e-5
+    fd = np.zeros((3, 3))
+    for a in range(3):
+        for b in range(3):
+            e = np.zeros((3, 3))
+            e[a, b] = h
+            # row vectors: x' = x (I + eps)^T
+            ep = oracle.energy_forces(m, s.pos @ (np.eye(3) + e).T, s.species, s.cell @ (np.eye(3) + e).T)["energy"]
+            em = oracle.energy_forces(m, s.pos @ (np.eye(3) - e).T, s.species, s.cell @ (np.eye(3) - e).T)["energy"]
+            fd[a, b] = -(ep - em) / (2 * h)
+    assert np.abs(out["virial"]).max() > 1e-3  # not vacuous
+    np.testing.assert_allclose(out["virial"], fd, atol=1e-6, rtol=0)
+    np.testing.assert_allclose(out["virial"], out["virial"].T, atol=1e-9, rtol=0)
 
 
 # ------------------------------------------------------------ invariances ---
