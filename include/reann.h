@@ -217,6 +217,21 @@ int reann_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int 
                         float* atom_energy);
 
 /*
+ * reann_energy_forces plus the virial.  Eq. 1 is the only place positions
+ * enter, through the edge vectors r_e (periodic images included), so
+ *   virial  dev, 3 x 3 FP64 row-major: W_ab = -sum_e (dE/dr_e)_a (r_e)_b
+ *           = -dE/d eps_ab for a homogeneous strain x -> (I + eps) x of the
+ *           positions and the cell (the configurational part of the stress
+ *           times the volume: sigma = -(W + kinetic) / V); summed in FP64
+ *   atom_virial  dev, N x 9 FP32 per-atom share (each directed edge e = (i, j)
+ *           of every layer assigned to its centre i), caller order, or NULL
+ * The first call allocates the per-atom buffer (N x 36 B), later calls do not.
+ * Asynchronous.  Errors: as reann_energy_forces; REANN_E_NOMEM.
+ */
+int reann_energy_forces_virial(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy,
+                               float* forces, float* atom_energy, double* virial, float* atom_virial);
+
+/*
  * Same as reann_energy_forces with HOST buffers: copies pos (host, N x 3
  * FP64) to the device, rebuilds the neighbour list on the device (always if
  * `rebuild` is non-zero, otherwise only when an atom moved more than skin/2

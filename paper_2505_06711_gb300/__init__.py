@@ -121,12 +121,26 @@ class System:
         """Host-buffer evaluation (synchronous): copies in, rebuilds if needed, evaluates, copies out."""
         binding.reann_energy_forces_host(self.pot.ctx, self.nl, pos, self.pot.T, energy, forces, int(rebuild))
 
-    def evaluate(self, pos=None, atom_energy: bool = True) -> None:
-        """Enqueue one energy + force evaluation (results in .energy/.forces/.atom_energy)."""
+    def evaluate(self, pos=None, atom_energy: bool = True, virial: bool = False, atom_virial: bool = False) -> None:
+        """Enqueue one energy + force evaluation (results in .energy/.forces/.atom_energy,
+        with ``virial`` also .virial (3 x 3 FP64, W = -dE/d strain) and, with
+        ``atom_virial``, .atom_virial (N x 9))."""
+        import torch
+
         p = self.pos if pos is None else pos
-        binding.reann_energy_forces(
-            self.pot.ctx, self.nl, p, self.pot.T, self.energy, self.forces, self.atom_energy if atom_energy else None
-        )
+        ae = self.atom_energy if atom_energy else None
+        if not virial:
+            binding.reann_energy_forces(self.pot.ctx, self.nl, p, self.pot.T, self.energy, self.forces, ae)
+            return
+        if getattr(self, "virial", None) is None:
+            self.virial = torch.zeros((3, 3), dtype=torch.float64, device=self.pot.device)
+        av = None
+        if atom_virial:
+            if getattr(self, "atom_virial", None) is None:
+                self.atom_virial = torch.zeros((self.n, 9), dtype=torch.float32, device=self.pot.device)
+            av = self.atom_virial
+        binding.reann_energy_forces_virial(self.pot.ctx, self.nl, p, self.pot.T, self.energy, self.forces,
+                                           self.virial, ae, av)
 
     def md(self, vel, mass, dt_fs: float, n_steps: int, record: bool = True):
         """Run NVE velocity Verlet in place on self.pos / vel; returns (E_pot, E_kin) per step or None."""

@@ -62,6 +62,7 @@ _SIGS = {
     "reann_energy_forces": ([_vp, _vp, _vp, _int, _vp, _vp, _vp], _int),
     "reann_energy_forces_host": ([_vp, _vp, _vp, _int, _vp, _vp, _int], _int),
     "reann_get_layer": ([_vp, _vp, _int, _vp, _vp], _int),
+    "reann_energy_forces_virial": ([_vp, _vp, _vp, _int, _vp, _vp, _vp, _vp, _vp], _int),
     "reann_build_nlist_decomposed": ([_vp, _i64, _vp, _vp, _vp, _dbl, _dbl, _vp, ctypes.POINTER(_vp)], _int),
     "reann_decomp_info": ([_vp, _vp, _vp, _vp, _vp], _int),
     "reann_nlist_rebuild": ([_vp, _vp, _vp], _int),
@@ -245,6 +246,22 @@ def reann_energy_forces(ctx, nl, pos, T: int, energy, forces, atom_energy=None) 
     if atom_energy is not None:
         _dev(atom_energy, torch.float32, (n,), "atom_energy")
     _check(lib().reann_energy_forces(ctx, nl, _ptr(pos), int(T), _ptr(energy), _ptr(forces), _ptr(atom_energy)), ctx)
+
+
+def reann_energy_forces_virial(ctx, nl, pos, T: int, energy, forces, virial, atom_energy=None, atom_virial=None) -> None:
+    import torch
+
+    n = pos.shape[0]
+    _dev(pos, torch.float64, (n, 3), "pos")
+    _dev(energy, torch.float64, (1,), "energy")
+    _dev(forces, torch.float32, (n, 3), "forces")
+    _dev(virial, torch.float64, (3, 3), "virial")
+    if atom_energy is not None:
+        _dev(atom_energy, torch.float32, (n,), "atom_energy")
+    if atom_virial is not None:
+        _dev(atom_virial, torch.float32, (n, 9), "atom_virial")
+    _check(lib().reann_energy_forces_virial(ctx, nl, _ptr(pos), int(T), _ptr(energy), _ptr(forces),
+                                            _ptr(atom_energy), _ptr(virial), _ptr(atom_virial)), ctx)
 
 
 def reann_energy_forces_host(ctx, nl, pos, T: int, energy, forces, rebuild: int = 0) -> None:

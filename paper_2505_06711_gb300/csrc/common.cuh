@@ -178,6 +178,8 @@ struct reann_nlist {
     float* bbar = nullptr;         // (N + g_cap) x 80
     float* cbar = nullptr;         // N x 8
     float* grad = nullptr;         // N x 3
+    float* vir = nullptr;          // N x 9 per-atom virial (allocated on first request)
+    double* vir_partial = nullptr; // virial partial sums
     double* partial = nullptr;     // energy partial sums
     int n_partial = 0;
     reann::NlistScratch w;
@@ -287,7 +289,9 @@ cudaError_t launch_density_fwd(cudaStream_t s, const reann_nlist* nl, const Radi
 cudaError_t launch_bbar(cudaStream_t s, const reann_nlist* nl, const float* W, const float* bck, const float* rhobar,
                         float* bbar);
 cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* coef,
-                               const float* bbar, float* cbar, float* grad, bool want_cbar, int* flags);
+                               const float* bbar, float* cbar, float* grad, bool want_cbar, int* flags,
+                               float* vir = nullptr);
+cudaError_t launch_virial_sum(cudaStream_t s, const reann_nlist* nl, const float* vir, double* partial, double* out);
 cudaError_t launch_energy_sum(cudaStream_t s, const reann_nlist* nl, double* energy);
 cudaError_t launch_scatter_outputs(cudaStream_t s, const reann_nlist* nl, float* forces, float* atom_energy);
 cudaError_t launch_unpermute_rows(cudaStream_t s, const reann_nlist* nl, const float* src, int src_stride, float* dst,

@@ -273,7 +273,10 @@ constexpr int kAdjGroups = 4;  // centre atoms per warp
 constexpr int kGeoStride = 20;
 constexpr int kGroupStride = 8 * kGeoStride + 8;
 
-template <bool WANT_CBAR>
+// WANT_VIR: also W -= (dE/dr_e) r_e^T over the atom's own edges (their
+// bbar_k c_j terms: every directed edge once) into vir (N x 9, accumulated
+// over the layers like grad).
+template <bool WANT_CBAR, bool WANT_VIR>
 __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int stride, Radial R,
                                                                 const int32_t* __restrict__ live,
                                                                 const int32_t* __restrict__ live_cnt,
@@ -281,7 +284,8 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
                                                                 const float4* __restrict__ plo,
                                                                 const float* __restrict__ coef,
                                                                 const float* __restrict__ bbar,
-                                                                float* __restrict__ cbar, float* __restrict__ grad) {
+                                                                float* __restrict__ cbar, float* __restrict__ grad,
+                                                                float* __restrict__ vir) {
     __shared__ __align__(16) float sGeo[kAdjWarps][kAdjGroups * kGroupStride];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, m = lane & 7, grp = lane >> 3;
     const int64_t atom = ((int64_t)blockIdx.x * kAdjWarps + warp) * kAdjGroups + grp;
@@ -309,6 +313,9 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
     const float mu_hi = R.mu_hi[m], mu_lo = R.mu_lo[m], two_alpha = 2.f * R.alpha_hi;
     float* geo = sGeo[warp] + grp * kGroupStride;
     float gx = 0.f, gy = 0.f, gz = 0.f, cb = 0.f;
+    float w[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) w[q] = 0.f;
     for (int e0 = 0; e0 < cmax; e0 += 8) {
         // geometry of edge e0 + m, one edge per lane
         int j = 0;
@@ -377,6 +384,16 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
             gy -= fmaf(sc, y, fmaf(qv, gky, qt * gjy));
             gz -= fmaf(sc, z, fmaf(qv, gkz, qt * gjz));
             if (WANT_CBAR) cb = fmaf(phi, Sj, cb);
+            if (WANT_VIR) {
+                // dE/dr_e of this edge: the bbar_k c_j part
+                const float sa = cj * dphi * Sk * inv_d;
+                const float t3[3] = {fmaf(sa, x, qv * gkx), fmaf(sa, y, qv * gky), fmaf(sa, z, qv * gkz)};
+                const float r3[3] = {x, y, z};
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) w[3 * a + b] = fmaf(-t3[a], r3[b], w[3 * a + b]);
+            }
         };
         gather(0, bjA, cjA);
 #pragma unroll
@@ -394,12 +411,23 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
         gy += __shfl_xor_sync(FULL, gy, o);
         gz += __shfl_xor_sync(FULL, gz, o);
     }
+    if (WANT_VIR) {
+#pragma unroll
+        for (int o = 1; o <= 4; o <<= 1)
+#pragma unroll
+            for (int q = 0; q < 9; ++q) w[q] += __shfl_xor_sync(FULL, w[q], o);
+    }
     if (!valid) return;
     if (m == 0) {
         float* gr = grad + (size_t)atom * 3;
         gr[0] += gx;
         gr[1] += gy;
         gr[2] += gz;
+        if (WANT_VIR) {
+            float* vr = vir + (size_t)atom * 9;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) vr[q] += w[q];
+        }
     }
     if (WANT_CBAR) cbar[(size_t)atom * NPHI + m] = cb;
 }
@@ -469,6 +497,46 @@ __global__ void __launch_bounds__(kSumThreads) k_energy_final(int np, const doub
     if (threadIdx.x == 0) energy[0] = sm[0];
 }
 
+// FP64 sum of the per-atom virials (N x 9): partial sums per 2048 atoms, then one block
+__global__ void __launch_bounds__(kSumThreads) k_virial_partial(int64_t n, const float* __restrict__ vir,
+                                                               double* __restrict__ partial) {
+    __shared__ double sm[kSumThreads];
+    const int64_t base = (int64_t)blockIdx.x * kSumThreads * kSumPer;
+    for (int c = 0; c < 9; ++c) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < kSumPer; ++k) {
+            const int64_t i = base + k * kSumThreads + threadIdx.x;
+            if (i < n) s += (double)vir[9 * i + c];
+        }
+        sm[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = kSumThreads / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[9 * blockIdx.x + c] = sm[0];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kSumThreads) k_virial_final(int np, const double* __restrict__ partial,
+                                                             double* __restrict__ out) {
+    __shared__ double sm[kSumThreads];
+    for (int c = 0; c < 9; ++c) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < np; i += kSumThreads) s += partial[9 * i + c];
+        sm[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = kSumThreads / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[c] = sm[0];
+        __syncthreads();
+    }
+}
+
 __global__ void k_scatter_outputs(int64_t n, const int32_t* __restrict__ perm, const float* __restrict__ grad,
                                   const float* __restrict__ eps, float* __restrict__ forces,
                                   float* __restrict__ atom_energy) {
@@ -524,15 +592,29 @@ cudaError_t launch_bbar(cudaStream_t s, const reann_nlist* nl, const float* W, c
 }
 
 cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* coef,
-                               const float* bbar, float* cbar, float* grad, bool want_cbar, int* flags) {
+                               const float* bbar, float* cbar, float* grad, bool want_cbar, int* flags, float* vir) {
     (void)flags;
     const int64_t per_block = kAdjWarps * kAdjGroups;
-    if (want_cbar)
-        k_density_adj8<true><<<blocks_for(nl->n, per_block), kAdjWarps * 32, 0, s>>>(
-            nl->n, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi, nl->pos_lo, coef, bbar, cbar, grad);
+    const unsigned nb = blocks_for(nl->n, per_block);
+#define REANN_ADJ(C, V)                                                                                              \
+    k_density_adj8<C, V><<<nb, kAdjWarps * 32, 0, s>>>(nl->n, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi,     \
+                                                      nl->pos_lo, coef, bbar, cbar, grad, vir)
+    if (want_cbar && vir)
+        REANN_ADJ(true, true);
+    else if (want_cbar)
+        REANN_ADJ(true, false);
+    else if (vir)
+        REANN_ADJ(false, true);
     else
-        k_density_adj8<false><<<blocks_for(nl->n, per_block), kAdjWarps * 32, 0, s>>>(
-            nl->n, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi, nl->pos_lo, coef, bbar, cbar, grad);
+        REANN_ADJ(false, false);
+#undef REANN_ADJ
+    return cudaGetLastError();
+}
+
+cudaError_t launch_virial_sum(cudaStream_t s, const reann_nlist* nl, const float* vir, double* partial, double* out) {
+    const int np = (int)blocks_for(nl->n, kSumThreads * kSumPer);
+    k_virial_partial<<<np, kSumThreads, 0, s>>>(nl->n, vir, partial);
+    k_virial_final<<<1, kSumThreads, 0, s>>>(np, partial, out);
     return cudaGetLastError();
 }
 

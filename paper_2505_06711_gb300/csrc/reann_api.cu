@@ -725,11 +725,15 @@ const char* kRegionNames[PR_COUNT] = {"nlist_rebuild", "refresh_positions", "liv
                                       "mlp_bwd",       "bbar",              "density_adj",  "scatter_outputs"};
 
 // pos == nullptr: positions already in place (serving pool); seg != nullptr: one FP64
-// energy per segment (structure) into energy[seg.z] instead of one total.
+// energy per segment (structure) into energy[seg.z] instead of one total;
+// virial != nullptr: the 3 x 3 FP64 virial (and, with atom_virial, the per-atom
+// virials in caller order); the buffers must have been sized (ensure_virial).
 int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy, float* forces,
-                      float* atom_energy, const int4* seg = nullptr, int nseg = 0) {
+                      float* atom_energy, const int4* seg = nullptr, int nseg = 0, double* virial = nullptr,
+                      float* atom_virial = nullptr) {
     cudaStream_t s = ctx->stream;
     const int64_t n = nl->n, ne = nl->n + nl->g_cap;
+    float* vir = virial ? nl->vir : nullptr;
     if (pos) {
         ProfScope p(ctx, PR_REFRESH);
         REANN_CUDA_TRY(ctx, launch_refresh_positions(s, nl, pos));
@@ -775,6 +779,7 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
     }
     // reverse: Eqs. 3-5, one vector-Jacobian product per layer
     REANN_CUDA_TRY(ctx, cudaMemsetAsync(nl->grad, 0, sizeof(float) * n * 3, s));
+    if (vir) REANN_CUDA_TRY(ctx, cudaMemsetAsync(vir, 0, sizeof(float) * n * 9, s));
     for (int t = T - 1; t >= 0; --t) {
         const float* coef_t = nl->coef + (size_t)t * ne * NPHI;
         const float* rho_t = nl->rho + (size_t)t * n * NFEAT;
@@ -798,10 +803,22 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
         }
         ProfScope p(ctx, PR_DENSITY_ADJ);
         REANN_CUDA_TRY(ctx, launch_density_adj(s, nl, ctx->radial, coef_t, nl->bbar, nl->cbar, nl->grad, t >= 1,
-                                               ctx->d_flags));
+                                               ctx->d_flags, vir));
     }
     ProfScope p(ctx, PR_OUTPUT);
     REANN_CUDA_TRY(ctx, launch_scatter_outputs(s, nl, forces, atom_energy));
+    if (vir) {
+        REANN_CUDA_TRY(ctx, launch_virial_sum(s, nl, vir, nl->vir_partial, virial));
+        if (atom_virial) REANN_CUDA_TRY(ctx, launch_unpermute_rows(s, nl, vir, 9, atom_virial, 9));
+    }
+    return REANN_OK;
+}
+
+int ensure_virial(reann_ctx* ctx, reann_nlist* nl) {
+    if (nl->vir) return REANN_OK;
+    nl->vir = nl_alloc<float>(nl, (size_t)nl->n * 9);
+    nl->vir_partial = nl_alloc<double>(nl, (size_t)9 * ((nl->n + 2047) / 2048 + 1));
+    if (!nl->vir || !nl->vir_partial) return set_error(ctx, REANN_E_NOMEM, "virial buffers: out of device memory");
     return REANN_OK;
 }
 
@@ -825,6 +842,14 @@ extern "C" int reann_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double
     if (!ctx || !nl || !pos || !energy || !forces) return set_error(ctx, REANN_E_ARG, "null argument");
     if (T != ctx->model.T || T != nl->T) return set_error(ctx, REANN_E_MISMATCH, "T differs from the model");
     return run_energy_forces(ctx, nl, pos, T, energy, forces, atom_energy);
+}
+
+extern "C" int reann_energy_forces_virial(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy,
+                                          float* forces, float* atom_energy, double* virial, float* atom_virial) {
+    if (!ctx || !nl || !pos || !energy || !forces || !virial) return set_error(ctx, REANN_E_ARG, "null argument");
+    if (T != ctx->model.T || T != nl->T) return set_error(ctx, REANN_E_MISMATCH, "T differs from the model");
+    if (int rc = ensure_virial(ctx, nl)) return rc;
+    return run_energy_forces(ctx, nl, pos, T, energy, forces, atom_energy, nullptr, 0, virial, atom_virial);
 }
 
 extern "C" int reann_energy_forces_host(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy,
