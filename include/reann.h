@@ -367,6 +367,20 @@ int reann_ctx_profile_read(reann_ctx* ctx, double* total_ms, int64_t* launches);
 int reann_md_step(reann_ctx* ctx, reann_nlist* nl, double* pos, double* vel, const double* mass, double dt_fs,
                   int n_steps, double* e_pot, double* e_kin);
 
+/*
+ * NVT molecular dynamics (the paper's MD ensemble, Sec. 4.1): as reann_md_step
+ * with one Nose-Hoover thermostat at temperature_k (K) with time constant
+ * tau_fs (fs): friction xi' = (2K - g kB T)/Q, Q = g kB T tau^2, g = 3N - 3,
+ * integrated by a time-reversible splitting (a thermostat half step before
+ * the first and after the second velocity half-kick).  The thermostat state
+ * (xi, eta) belongs to the list and carries over between calls.
+ *   e_bath  dev, n_steps FP64: Q xi^2 / 2 + g kB T eta after each step (eV),
+ *           or NULL; E + K + e_bath is the conserved quantity
+ * Errors: REANN_E_ARG (also for T or tau not > 0), REANN_E_NOMEM, REANN_E_CUDA.
+ */
+int reann_md_step_nvt(reann_ctx* ctx, reann_nlist* nl, double* pos, double* vel, const double* mass, double dt_fs,
+                      int n_steps, double temperature_k, double tau_fs, double* e_pot, double* e_kin, double* e_bath);
+
 /* Steps run by the last reann_md_step call and neighbour-list rebuilds since the
  * first one (host outputs, nullable).  Synchronous. */
 int reann_md_info(reann_ctx* ctx, const reann_nlist* nl, int64_t* steps, int64_t* rebuilds);

@@ -142,16 +142,24 @@ class System:
         binding.reann_energy_forces_virial(self.pot.ctx, self.nl, p, self.pot.T, self.energy, self.forces,
                                            self.virial, ae, av)
 
-    def md(self, vel, mass, dt_fs: float, n_steps: int, record: bool = True):
-        """Run NVE velocity Verlet in place on self.pos / vel; returns (E_pot, E_kin) per step or None."""
+    def md(self, vel, mass, dt_fs: float, n_steps: int, record: bool = True, temperature_k: float | None = None,
+           tau_fs: float = 100.0):
+        """Velocity Verlet in place on self.pos / vel: NVE, or NVT (Nose-Hoover) when
+        ``temperature_k`` is given.  Returns (E_pot, E_kin) per step, with NVT
+        (E_pot, E_kin, E_bath), or None when not recording."""
         import torch
 
-        e_pot = e_kin = None
-        if record:
-            e_pot = torch.zeros(n_steps, dtype=torch.float64, device=self.pot.device)
-            e_kin = torch.zeros(n_steps, dtype=torch.float64, device=self.pot.device)
-        binding.reann_md_step(self.pot.ctx, self.nl, self.pos, vel, mass, dt_fs, n_steps, e_pot, e_kin)
-        return (e_pot, e_kin) if record else None
+        def rec():
+            return torch.zeros(n_steps, dtype=torch.float64, device=self.pot.device) if record else None
+
+        e_pot, e_kin = rec(), rec()
+        if temperature_k is None:
+            binding.reann_md_step(self.pot.ctx, self.nl, self.pos, vel, mass, dt_fs, n_steps, e_pot, e_kin)
+            return (e_pot, e_kin) if record else None
+        e_bath = rec()
+        binding.reann_md_step_nvt(self.pot.ctx, self.nl, self.pos, vel, mass, dt_fs, n_steps, temperature_k, tau_fs,
+                                  e_pot, e_kin, e_bath)
+        return (e_pot, e_kin, e_bath) if record else None
 
     def md_info(self):
         return binding.reann_md_info(self.pot.ctx, self.nl)

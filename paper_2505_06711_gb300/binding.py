@@ -63,6 +63,7 @@ _SIGS = {
     "reann_energy_forces_host": ([_vp, _vp, _vp, _int, _vp, _vp, _int], _int),
     "reann_get_layer": ([_vp, _vp, _int, _vp, _vp], _int),
     "reann_energy_forces_virial": ([_vp, _vp, _vp, _int, _vp, _vp, _vp, _vp, _vp], _int),
+    "reann_md_step_nvt": ([_vp, _vp, _vp, _vp, _vp, _dbl, _int, _dbl, _dbl, _vp, _vp, _vp], _int),
     "reann_build_nlist_decomposed": ([_vp, _i64, _vp, _vp, _vp, _dbl, _dbl, _vp, ctypes.POINTER(_vp)], _int),
     "reann_decomp_info": ([_vp, _vp, _vp, _vp, _vp], _int),
     "reann_nlist_rebuild": ([_vp, _vp, _vp], _int),
@@ -353,6 +354,23 @@ def reann_md_step(ctx, nl, pos, vel, mass, dt_fs: float, n_steps: int, e_pot=Non
                 raise ValueError(f"{name} holds fewer than n_steps entries")
     _check(lib().reann_md_step(ctx, nl, _ptr(pos), _ptr(vel), _ptr(mass), float(dt_fs), int(n_steps), _ptr(e_pot),
                                _ptr(e_kin)), ctx)
+
+
+def reann_md_step_nvt(ctx, nl, pos, vel, mass, dt_fs: float, n_steps: int, temperature_k: float, tau_fs: float,
+                      e_pot=None, e_kin=None, e_bath=None) -> None:
+    import torch
+
+    n = pos.shape[0]
+    _dev(pos, torch.float64, (n, 3), "pos")
+    _dev(vel, torch.float64, (n, 3), "vel")
+    _dev(mass, torch.float64, (n,), "mass")
+    for name, a in (("e_pot", e_pot), ("e_kin", e_kin), ("e_bath", e_bath)):
+        if a is not None:
+            _dev(a, torch.float64, None, name)
+            if a.numel() < n_steps:
+                raise ValueError(f"{name} holds fewer than n_steps entries")
+    _check(lib().reann_md_step_nvt(ctx, nl, _ptr(pos), _ptr(vel), _ptr(mass), float(dt_fs), int(n_steps),
+                                   float(temperature_k), float(tau_fs), _ptr(e_pot), _ptr(e_kin), _ptr(e_bath)), ctx)
 
 
 def reann_md_info(ctx, nl) -> tuple[int, int]:

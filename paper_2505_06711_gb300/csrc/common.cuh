@@ -189,7 +189,7 @@ struct reann_nlist {
     float* d_forces = nullptr;     // N x 3
     // MD state: forces of the current positions, per-step energies, rebuild gate, graph
     float* md_forces = nullptr;    // N x 3 (caller order)
-    double* md_scalars = nullptr;  // [0] E_pot, [1] E_kin
+    double* md_scalars = nullptr;  // [0] E_pot, [1] E_kin, [2] xi, [3] eta, [4] velocity scale
     double* md_partial = nullptr;
     int* md_ints = nullptr;        // [0] rebuild gate, [1] step counter, [2] rebuild count
     bool md_forces_valid = false;
@@ -198,6 +198,7 @@ struct reann_nlist {
     cudaGraphExec_t md_exec = nullptr;
     const void* md_key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     double md_dt = 0.0;
+    double md_kt = 0.0, md_tau = 0.0;  // thermostat of the captured step (tau 0: NVE)
     int md_precision = -1, md_nsteps = -1;
     // spatial decomposition into virtual ranks (reann_build_nlist_decomposed):
     // per rank its local atoms, ghost slots, and ghost slots owned by another rank
@@ -270,12 +271,14 @@ cudaError_t launch_segment_energy(cudaStream_t s, const int4* seg, int nseg, con
 
 // velocity Verlet (md.cu)
 cudaError_t launch_kick(cudaStream_t s, int64_t n, double* vel, const float* forces, const double* mass,
-                        double half_dt);
+                        double half_dt, const double* scale = nullptr);
+cudaError_t launch_scale(cudaStream_t s, int64_t n, double* vel, const double* scale);
+cudaError_t launch_nh_half(cudaStream_t s, double* scalars, double dt, double gkt, double q);
 cudaError_t launch_drift(cudaStream_t s, int64_t n, double* pos, const double* vel, double dt);
 cudaError_t launch_ekin(cudaStream_t s, int64_t n, const double* vel, const double* mass, double* partial,
                         double* out);
-cudaError_t launch_record(cudaStream_t s, int* counter, const double* epot, const double* ekin, double* epot_out,
-                          double* ekin_out, int n_steps, const int* gate, int* rebuilds);
+cudaError_t launch_record(cudaStream_t s, int* counter, const double* scalars, double* epot_out, double* ekin_out,
+                          double* bath_out, double gkt, double q, int n_steps, const int* gate, int* rebuilds);
 const int32_t* ghost_count_ptr(const reann_nlist* nl);
 cudaError_t launch_refresh_positions(cudaStream_t s, const reann_nlist* nl, const double* pos);
 cudaError_t launch_live_edges(cudaStream_t s, const reann_nlist* nl, float rc2, int* flags);

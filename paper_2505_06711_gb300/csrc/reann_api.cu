@@ -890,12 +890,31 @@ extern "C" int reann_energy_forces_host(reann_ctx* ctx, reann_nlist* nl, const d
 namespace {
 
 // enqueue one velocity-Verlet step on ctx->stream (captured into the step graph)
+// Nose-Hoover parameters: kT (eV), Q = g kT tau^2, g = 3N - 3; tau = 0: NVE
+struct Thermo {
+    double kt = 0.0, tau = 0.0, gkt = 0.0, q = 0.0;
+    bool on() const { return tau > 0.0; }
+};
+
+Thermo make_thermo(int64_t n, double temperature_k, double tau_fs) {
+    Thermo th;
+    if (tau_fs > 0.0) {
+        th.kt = 8.617333262e-5 * temperature_k;
+        th.tau = tau_fs;
+        th.gkt = (double)(3 * n - 3) * th.kt;
+        th.q = th.gkt * tau_fs * tau_fs;
+    }
+    return th;
+}
+
 int md_step_body(reann_ctx* ctx, reann_nlist* nl, double* pos, double* vel, const double* mass, double dt,
-                 int n_steps, double* e_pot, double* e_kin) {
+                 int n_steps, double* e_pot, double* e_kin, const Thermo& th, double* e_bath) {
     cudaStream_t s = ctx->stream;
     const int64_t n = nl->n;
     int* gate = nl->md_ints;
-    REANN_CUDA_TRY(ctx, launch_kick(s, n, vel, nl->md_forces, mass, 0.5 * dt));
+    double* sc = nl->md_scalars;
+    if (th.on()) REANN_CUDA_TRY(ctx, launch_nh_half(s, sc, dt, th.gkt, th.q));
+    REANN_CUDA_TRY(ctx, launch_kick(s, n, vel, nl->md_forces, mass, 0.5 * dt, th.on() ? sc + 4 : nullptr));
     REANN_CUDA_TRY(ctx, launch_drift(s, n, pos, vel, dt));
     REANN_CUDA_TRY(ctx, cudaMemsetAsync(gate, 0, sizeof(int), s));
     REANN_CUDA_TRY(ctx, launch_moved(s, nl, pos, gate));
@@ -903,24 +922,29 @@ int md_step_body(reann_ctx* ctx, reann_nlist* nl, double* pos, double* vel, cons
     int rc = run_energy_forces(ctx, nl, pos, nl->T, nl->md_scalars, nl->md_forces, nullptr);
     if (rc) return rc;
     REANN_CUDA_TRY(ctx, launch_kick(s, n, vel, nl->md_forces, mass, 0.5 * dt));
-    REANN_CUDA_TRY(ctx, launch_ekin(s, n, vel, mass, nl->md_partial, nl->md_scalars + 1));
-    REANN_CUDA_TRY(ctx, launch_record(s, nl->md_ints + 1, nl->md_scalars, nl->md_scalars + 1, e_pot, e_kin, n_steps,
-                                      gate, nl->md_ints + 2));
+    REANN_CUDA_TRY(ctx, launch_ekin(s, n, vel, mass, nl->md_partial, sc + 1));
+    if (th.on()) {
+        REANN_CUDA_TRY(ctx, launch_nh_half(s, sc, dt, th.gkt, th.q));
+        REANN_CUDA_TRY(ctx, launch_scale(s, n, vel, sc + 4));
+    }
+    REANN_CUDA_TRY(ctx, launch_record(s, nl->md_ints + 1, sc, e_pot, e_kin, e_bath, th.gkt, th.q, n_steps, gate,
+                                      nl->md_ints + 2));
     return REANN_OK;
 }
 
 int md_run(reann_ctx* ctx, reann_nlist* nl, double* pos, double* vel, const double* mass, double dt, int n_steps,
-           double* e_pot, double* e_kin) {
+           double* e_pot, double* e_kin, const Thermo& th, double* e_bath) {
     cudaStream_t s = ctx->stream;
     const int64_t n = nl->n;
     if (!nl->md_forces) {
         nl->md_forces = nl_alloc<float>(nl, 3 * n);
-        nl->md_scalars = nl_alloc<double>(nl, 2);
+        nl->md_scalars = nl_alloc<double>(nl, 8);
         nl->md_partial = nl_alloc<double>(nl, (n + 2047) / 2048);
         nl->md_ints = nl_alloc<int>(nl, 3);
         if (!nl->md_forces || !nl->md_scalars || !nl->md_partial || !nl->md_ints)
             return set_error(ctx, REANN_E_NOMEM, "MD buffers: out of device memory");
         REANN_CUDA_TRY(ctx, cudaMemsetAsync(nl->md_ints, 0, 3 * sizeof(int), s));
+        REANN_CUDA_TRY(ctx, cudaMemsetAsync(nl->md_scalars, 0, 8 * sizeof(double), s));  // xi = eta = 0
     }
     int* gate = nl->md_ints;
     // forces at the starting positions (rebuilding first if atoms moved beyond skin/2)
@@ -933,16 +957,19 @@ int md_run(reann_ctx* ctx, reann_nlist* nl, double* pos, double* vel, const doub
         nl->md_forces_valid = true;
         nl->md_forces_at = pos;
     }
-    const void* key[6] = {pos, vel, mass, e_pot, e_kin, nullptr};
+    // the thermostat's first half step needs K of the current velocities
+    if (th.on()) REANN_CUDA_TRY(ctx, launch_ekin(s, n, vel, mass, nl->md_partial, nl->md_scalars + 1));
+    const void* key[6] = {pos, vel, mass, e_pot, e_kin, e_bath};
     const bool same = nl->md_exec && std::memcmp(key, nl->md_key, sizeof(key)) == 0 && nl->md_dt == dt &&
-                      nl->md_precision == ctx->precision && nl->md_nsteps == n_steps;
+                      nl->md_precision == ctx->precision && nl->md_nsteps == n_steps && nl->md_kt == th.kt &&
+                      nl->md_tau == th.tau;
     if (!same) {
         if (nl->md_exec) cudaGraphExecDestroy(nl->md_exec);
         if (nl->md_graph) cudaGraphDestroy(nl->md_graph);
         nl->md_exec = nullptr;
         nl->md_graph = nullptr;
         REANN_CUDA_TRY(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        const int rc = md_step_body(ctx, nl, pos, vel, mass, dt, n_steps, e_pot, e_kin);
+        const int rc = md_step_body(ctx, nl, pos, vel, mass, dt, n_steps, e_pot, e_kin, th, e_bath);
         cudaGraph_t g = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(s, &g);
         if (rc || ec != cudaSuccess) {
@@ -955,6 +982,8 @@ int md_run(reann_ctx* ctx, reann_nlist* nl, double* pos, double* vel, const doub
         nl->md_dt = dt;
         nl->md_precision = ctx->precision;
         nl->md_nsteps = n_steps;
+        nl->md_kt = th.kt;
+        nl->md_tau = th.tau;
     }
     REANN_CUDA_TRY(ctx, cudaMemsetAsync(nl->md_ints + 1, 0, sizeof(int), s));
     for (int k = 0; k < n_steps; ++k) REANN_CUDA_TRY(ctx, cudaGraphLaunch(nl->md_exec, s));
@@ -963,8 +992,33 @@ int md_run(reann_ctx* ctx, reann_nlist* nl, double* pos, double* vel, const doub
 
 }  // namespace
 
+namespace {
+
+int md_entry(reann_ctx* ctx, reann_nlist* nl, double* pos, double* vel, const double* mass, double dt_fs, int n_steps,
+             double* e_pot, double* e_kin, const Thermo& th, double* e_bath);
+
+}  // namespace
+
 extern "C" int reann_md_step(reann_ctx* ctx, reann_nlist* nl, double* pos, double* vel, const double* mass,
                              double dt_fs, int n_steps, double* e_pot, double* e_kin) {
+    if (!ctx || !nl) return set_error(ctx, REANN_E_ARG, "bad argument to reann_md_step");
+    return md_entry(ctx, nl, pos, vel, mass, dt_fs, n_steps, e_pot, e_kin, Thermo{}, nullptr);
+}
+
+extern "C" int reann_md_step_nvt(reann_ctx* ctx, reann_nlist* nl, double* pos, double* vel, const double* mass,
+                                 double dt_fs, int n_steps, double temperature_k, double tau_fs, double* e_pot,
+                                 double* e_kin, double* e_bath) {
+    if (!ctx || !nl || !(temperature_k > 0) || !std::isfinite(temperature_k) || !(tau_fs > 0) ||
+        !std::isfinite(tau_fs) || nl->n < 2)
+        return set_error(ctx, REANN_E_ARG, "bad argument to reann_md_step_nvt");
+    return md_entry(ctx, nl, pos, vel, mass, dt_fs, n_steps, e_pot, e_kin, make_thermo(nl->n, temperature_k, tau_fs),
+                    e_bath);
+}
+
+namespace {
+
+int md_entry(reann_ctx* ctx, reann_nlist* nl, double* pos, double* vel, const double* mass, double dt_fs, int n_steps,
+             double* e_pot, double* e_kin, const Thermo& th, double* e_bath) {
     if (!ctx || !nl || !pos || !vel || !mass || !(dt_fs > 0) || !std::isfinite(dt_fs) || n_steps < 0)
         return set_error(ctx, REANN_E_ARG, "bad argument to reann_md_step");
     if (nl->decomposed) return set_error(ctx, REANN_E_ARG, "MD needs device rebuilds: use a single-domain list");
@@ -981,13 +1035,15 @@ extern "C" int reann_md_step(reann_ctx* ctx, reann_nlist* nl, double* pos, doubl
     const bool prof = ctx->prof_on;
     ctx->stream = ctx->md_stream;
     ctx->prof_on = false;
-    const int rc = md_run(ctx, nl, pos, vel, mass, dt_fs, n_steps, e_pot, e_kin);
+    const int rc = md_run(ctx, nl, pos, vel, mass, dt_fs, n_steps, e_pot, e_kin, th, e_bath);
     ctx->stream = user;
     ctx->prof_on = prof;
     REANN_CUDA_TRY(ctx, cudaEventRecord(ctx->md_ev[1], ctx->md_stream));
     REANN_CUDA_TRY(ctx, cudaStreamWaitEvent(user, ctx->md_ev[1], 0));
     return rc;
 }
+
+}  // namespace
 
 extern "C" int reann_md_info(reann_ctx* ctx, const reann_nlist* nl, int64_t* steps, int64_t* rebuilds) {
     if (!ctx || !nl) return REANN_E_ARG;

@@ -88,3 +88,85 @@ def test_nve_conserves_energy_across_device_rebuilds():
                   {k: ref[k] for k in ("energy", "forces")}, s.n_atoms, f_tol=F_TOL_MAX * f_scale)
     fresh.close()
     sy.close()
+
+
+KB = 8.617333262e-5  # eV/K
+
+
+def test_one_nvt_step_is_the_stated_splitting():
+    """One reann_md_step_nvt step against the Nose-Hoover splitting written out
+    here: thermostat half step, half kick, drift, forces, half kick, thermostat
+    half step (xi, eta start at 0)."""
+    import torch
+
+    s, spec, pot, sy, vel, mass = _setup(64, 4)
+    dt, T0, tau = 0.5, 300.0, 20.0
+    n = s.n_atoms
+    gkt = (3 * n - 3) * KB * T0
+    q = gkt * tau * tau
+    m = mass.double()[:, None]
+
+    def ekin(v):
+        return 0.5 * (m * v * v).sum().item() / ACCEL
+
+    def half(K, xi, eta):
+        xi += 0.25 * dt * (2 * K - gkt) / q
+        eta += 0.5 * dt * xi
+        sc = np.exp(-0.5 * dt * xi)
+        K *= sc * sc
+        xi += 0.25 * dt * (2 * K - gkt) / q
+        return K, xi, eta, sc
+
+    x0, v0 = sy.pos.clone(), vel.clone()
+    sy.evaluate()
+    f0 = sy.forces.double().clone()
+    K, xi, eta, sc = half(ekin(v0), 0.0, 0.0)
+    v = sc * v0 + 0.5 * dt * ACCEL * f0 / m
+    x1 = x0 + dt * v
+    sy.evaluate(x1.contiguous())
+    f1 = sy.forces.double().clone()
+    v = v + 0.5 * dt * ACCEL * f1 / m
+    K, xi, eta, sc = half(ekin(v), xi, eta)
+    v = sc * v
+    e_pot, e_kin, e_bath = sy.md(vel, mass, dt, 1, temperature_k=T0, tau_fs=tau)
+    sy.check()
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(sy.pos.cpu().numpy(), x1.cpu().numpy(), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(vel.cpu().numpy(), v.cpu().numpy(), rtol=0, atol=1e-12)
+    assert e_kin[0].item() == pytest.approx(K, rel=1e-12)
+    assert e_bath[0].item() == pytest.approx(0.5 * q * xi * xi + gkt * eta, rel=1e-10, abs=1e-12)
+
+
+def test_nvt_holds_temperature_and_conserves_extended_energy():
+    """4 ps of NVT at 300 K on a 2,048-atom Cu box (the random water model, held
+    at 300 K, lets molecules fall into 0.1 A contacts where 0.5 fs steps no
+    longer resolve the motion; the crystal stays on its lattice).  Measured on
+    GB300: late mean 298.2 K, extended-energy drift -0.096 meV/atom/ps at
+    dt = 1 fs (-0.024 at 0.5 fs: second order in dt)."""
+    import torch
+
+    from synth import fcc_box
+
+    s = fcc_box(8, seed=3)
+    spec = make_model(T=3)
+    pot = potential(spec)
+    sy = pot.system(s.pos, s.species, s.cell, skin=1.0)
+    m = MASS_AMU[s.species]
+    vel = torch.as_tensor(maxwell_boltzmann(m, 300.0, seed=3), device="cuda").contiguous()
+    mass = torch.as_tensor(m, device="cuda").contiguous()
+    n_steps, dt, T0, tau = 4000, 1.0, 300.0, 100.0
+    e_pot, e_kin, e_bath = sy.md(vel, mass, dt, n_steps, temperature_k=T0, tau_fs=tau)
+    sy.check()
+    torch.cuda.synchronize()
+    n = s.n_atoms
+    temp = 2.0 * e_kin.cpu().numpy() / ((3 * n - 3) * KB)
+    h = ((e_pot + e_kin + e_bath) / n).cpu().numpy()
+    t_ps = np.arange(1, n_steps + 1) * dt * 1e-3
+    slope = np.polyfit(t_ps, h, 1)[0]
+    late = temp[n_steps // 2:]
+    print(f"[nvt] T mean(late)={late.mean():.1f} K std={late.std():.1f} K "
+          f"drift={slope * 1e3:.4f} meV/atom/ps fluct={h.std() * 1e3:.4f} meV/atom rebuilds={sy.md_info()[1]}")
+    assert abs(slope) < 5e-4  # |drift| of the conserved quantity < 0.5 meV/atom/ps
+    assert abs(late.mean() - T0) < 0.03 * T0
+    assert e_bath.cpu().numpy()[-1] / n > 0.5  # the bath took up the released potential energy
+    sy.close()
