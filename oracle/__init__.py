@@ -53,7 +53,7 @@ def _load():
             i64, i32, dbl, ptr, c_int = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p, ctypes.c_int
             lib.oracle_neighbors.argtypes = [i64, ptr, ptr, dbl, i64, ptr, ptr, ptr, ptr, c_int]
             lib.oracle_neighbors.restype = c_int
-            lib.oracle_energy_forces.argtypes = [c_int] * 7 + [dbl, dbl, ptr, i64, ptr, ptr, ptr, ptr, ptr, ptr, ptr, ptr, ptr, c_int]
+            lib.oracle_energy_forces.argtypes = [c_int] * 7 + [dbl, dbl, c_int, ptr, i64, ptr, ptr, ptr, ptr, ptr, ptr, ptr, ptr, ptr, c_int]
             lib.oracle_energy_forces.restype = c_int
             lib.oracle_max_threads.argtypes = []
             lib.oracle_max_threads.restype = c_int
@@ -122,7 +122,8 @@ def energy_forces(model, pos, species, cell, want_layers: bool = False, n_thread
     virial = np.zeros((3, 3), np.float64)
     rc = lib.oracle_energy_forces(
         model.n_elem, model.T, model.n_phi, model.l_max, model.n_orb, model.h1, model.h2,
-        float(model.r_c), float(model.alpha), _p(params), n, _p(pos), _p(species), _p(cellp),
+        float(model.r_c), float(model.alpha), int(getattr(model, "pairs", False)), _p(params), n, _p(pos),
+        _p(species), _p(cellp),
         _p(energy), _p(forces), _p(eps), _p(rho), _p(coef), _p(virial), n_threads,
     )
     _check(rc)

@@ -266,6 +266,7 @@ int oracle_neighbors(int64_t n, const double *pos, const double *cell, double r_
 
 typedef struct {
     int n_elem, T, n_phi, l_max, n_orb, h1, h2, n_feat, n_ang;
+    int pairs;            /* 0: Eq. 1's squares; 1: products of orbital pairs k <= k' */
     double r_c, alpha;
     int lx[MAX_ANG], ly[MAX_ANG], lz[MAX_ANG], l_of[MAX_ANG];
     double wmul[MAX_ANG]; /* l! / (lx! ly! lz!) */
@@ -282,10 +283,10 @@ static double factorial(int k) {
 }
 
 static int model_init(model_t *M, int n_elem, int T, int n_phi, int l_max, int n_orb, int h1, int h2, double r_c,
-                      double alpha, const float *params) {
+                      double alpha, int pairs, const float *params) {
     memset(M, 0, sizeof(*M));
-    if (n_elem < 1 || T < 1 || n_phi < 2 || l_max < 0 || l_max > 6 || n_orb < 1 || h1 < 1 || h2 < 1 || !(r_c > 0) ||
-        !(alpha > 0) || !params)
+    if (n_elem < 1 || T < 1 || n_phi < 2 || l_max < 0 || l_max > 6 || n_orb < 1 || n_orb > 64 || h1 < 1 || h2 < 1 ||
+        !(r_c > 0) || !(alpha > 0) || !params || (pairs != 0 && pairs != 1))
         return OR_E_ARG;
     M->n_elem = n_elem;
     M->T = T;
@@ -296,7 +297,10 @@ static int model_init(model_t *M, int n_elem, int T, int n_phi, int l_max, int n
     M->h2 = h2;
     M->r_c = r_c;
     M->alpha = alpha;
-    M->n_feat = (l_max + 1) * n_orb;
+    M->pairs = pairs;
+    /* one feature per (l, orbital) for Eq. 1's squares; per (l, orbital pair k <= k') for the
+       pair products, (L+1) n_orb (n_orb+1)/2 features (the count Sec. 2.1 states) */
+    M->n_feat = (l_max + 1) * (pairs ? n_orb * (n_orb + 1) / 2 : n_orb);
     int a = 0;
     for (int l = 0; l <= l_max; ++l)
         for (int lx = l; lx >= 0; --lx)
@@ -432,7 +436,10 @@ static void mlp_backward(const model_t *M, const double *p, int out, const doubl
 /*
  * E, F = -dE/dr, per-atom energies and (optionally) every layer's features
  * rho^t [T][n][F] and coefficients c^t [T][n][N_phi] for the model whose flat
- * parameters are `params` (layout of synth/model.py).  cell == NULL means a
+ * parameters are `params` (layout of synth/model.py).  feature_pairs selects
+ * the features: 0 for Eq. 1 (the squares of the contracted orbitals, F =
+ * (L+1) n_orb), 1 for the products of orbital pairs k <= k' summed the same
+ * way (F = (L+1) n_orb (n_orb+1)/2, the feature count Sec. 2.1 states).  cell == NULL means a
  * free (non-periodic) cluster.  `virial` (nullable, 3 x 3 row-major) receives
  * W_ab = -sum over edges e and layers of (dE/dr_e)_a (r_e)_b, minus the
  * derivative of E with respect to a homogeneous strain eps_ab applied to
@@ -441,14 +448,14 @@ static void mlp_backward(const model_t *M, const double *p, int out, const doubl
  * singular cell, or two atoms closer than 1e-8 A.
  */
 int oracle_energy_forces(int n_elem, int T, int n_phi, int l_max, int n_orb, int h1, int h2, double r_c,
-                         double alpha, const float *params, int64_t n, const double *pos, const int32_t *species,
-                         const double *cell, double *energy, double *forces, double *atom_energy, double *rho_out,
-                         double *coef_out, double *virial, int n_threads) {
+                         double alpha, int feature_pairs, const float *params, int64_t n, const double *pos,
+                         const int32_t *species, const double *cell, double *energy, double *forces,
+                         double *atom_energy, double *rho_out, double *coef_out, double *virial, int n_threads) {
     if (n < 0 || !pos || !species || !energy || (n > 0 && !forces)) return OR_E_ARG;
     if (h1 > 512 || h2 > 512) return OR_E_ARG;
     set_threads(n_threads);
     model_t M;
-    int rc = model_init(&M, n_elem, T, n_phi, l_max, n_orb, h1, h2, r_c, alpha, params);
+    int rc = model_init(&M, n_elem, T, n_phi, l_max, n_orb, h1, h2, r_c, alpha, feature_pairs, params);
     if (rc) return rc;
     for (int64_t i = 0; i < n; ++i)
         if (species[i] < 0 || species[i] >= n_elem) {
@@ -514,10 +521,18 @@ int oracle_energy_forces(int n_elem, int T, int n_phi, int l_max, int n_orb, int
                 double *ri = rt + (size_t)i * F;
                 for (int a = 0; a < A; ++a) {
                     int l = M.l_of[a];
+                    double g[64];
                     for (int k = 0; k < K; ++k) {
-                        double g = 0.0;
-                        for (int m = 0; m < P; ++m) g += bi[a * P + m] * Wt[((size_t)l * P + m) * K + k];
-                        ri[l * K + k] += M.wmul[a] * g * g;
+                        g[k] = 0.0;
+                        for (int m = 0; m < P; ++m) g[k] += bi[a * P + m] * Wt[((size_t)l * P + m) * K + k];
+                    }
+                    if (!M.pairs) {
+                        for (int k = 0; k < K; ++k) ri[l * K + k] += M.wmul[a] * g[k] * g[k];
+                    } else {
+                        const int KP = K * (K + 1) / 2;
+                        int q = 0;
+                        for (int k = 0; k < K; ++k)
+                            for (int k2 = k; k2 < K; ++k2, ++q) ri[l * KP + q] += M.wmul[a] * g[k] * g[k2];
                     }
                 }
                 int out = (t == T - 1) ? 1 : P;
@@ -558,11 +573,29 @@ int oracle_energy_forces(int n_elem, int T, int n_phi, int l_max, int n_orb, int
                 double *bbi = bbar + (size_t)i * A * P;
                 for (int a = 0; a < A; ++a) {
                     int l = M.l_of[a];
+                    double g[64];
+                    for (int k = 0; k < K; ++k) {
+                        g[k] = 0.0;
+                        for (int m = 0; m < P; ++m) g[k] += bi[a * P + m] * Wt[((size_t)l * P + m) * K + k];
+                    }
                     for (int m = 0; m < P; ++m) bbi[a * P + m] = 0.0;
                     for (int k = 0; k < K; ++k) {
-                        double g = 0.0;
-                        for (int m = 0; m < P; ++m) g += bi[a * P + m] * Wt[((size_t)l * P + m) * K + k];
-                        double gbar = 2.0 * M.wmul[a] * g * rhobar[(size_t)i * F + l * K + k];
+                        double gbar;
+                        if (!M.pairs) {
+                            gbar = 2.0 * M.wmul[a] * g[k] * rhobar[(size_t)i * F + l * K + k];
+                        } else {
+                            /* d rho_(p,q) / d g_k = w_a (g_q [p = k] + g_p [q = k]) */
+                            const int KP = K * (K + 1) / 2;
+                            gbar = 0.0;
+                            int q = 0;
+                            for (int k1 = 0; k1 < K; ++k1)
+                                for (int k2 = k1; k2 < K; ++k2, ++q) {
+                                    const double rb = rhobar[(size_t)i * F + l * KP + q];
+                                    if (k1 == k) gbar += rb * g[k2];
+                                    if (k2 == k) gbar += rb * g[k1];
+                                }
+                            gbar *= M.wmul[a];
+                        }
                         for (int m = 0; m < P; ++m) bbi[a * P + m] += gbar * Wt[((size_t)l * P + m) * K + k];
                     }
                 }

@@ -68,6 +68,16 @@ FEATURE_SCALE = (
     ((7.7, 8.7, 4.2), (4.6, 10.0, 4.3), (15.0, 15.0, 1.6),
      (210.0, 34.0, 6.3), (230.0, 49.0, 7.0), (76.0, 24.0, 7.1), (380.0, 57.0, 12.0), (210.0, 44.0, 6.4)),
 )
+# The same for the orbital-pair-product features (8 orbitals, 36 pairs per l,
+# elements H, O, Cu), calibrated the same way, layer by layer, on the
+# 2,048-molecule water box and the 4,000-atom Cu box (seed 0).
+FEATURE_SCALE_PAIRS = (
+    ((0.036, 0.11, 0.0025), (0.041, 0.14, 0.0028), (0.17, 0.17, 0.011)),
+    ((8.3, 18.0, 1.4), (9.5, 18.0, 1.4), (21.0, 21.0, 0.66)),
+    ((28.0, 65.0, 0.92), (53.0, 87.0, 1.2), (4.0, 4.0, 0.36)),
+    ((12.0, 19.0, 0.78), (17.0, 24.0, 1.2), (58.0, 58.0, 1.3)),
+    ((24.0, 12.0, 0.62), (58.0, 18.0, 1.0), (40.0, 40.0, 14.0)),
+)
 # Multiplier on the energy network's output weights (eV): gives forces of
 # about 2 eV/A (99th percentile) on the water box and 0.5 eV/A (median) on
 # the Cu box at T = 3.
@@ -86,18 +96,25 @@ class ModelSpec:
     r_c: float
     alpha: float
     params: np.ndarray  # float32 flat
+    pairs: bool = False  # features: Eq. 1's squares (False) or orbital-pair products (True)
 
     @property
     def n_feat(self) -> int:
-        return (self.l_max + 1) * self.n_orb
+        return n_features(self.l_max, self.n_orb, self.pairs)
 
     def out_dim(self, t: int) -> int:
         return 1 if t == self.T - 1 else self.n_phi
 
 
-def param_layout(n_elem: int, T: int, n_phi: int, l_max: int, n_orb: int, h1: int, h2: int) -> dict:
+def n_features(l_max: int, n_orb: int, pairs: bool = False) -> int:
+    """(L+1) n_orb squares (Eq. 1), or (L+1) n_orb (n_orb+1)/2 orbital-pair products."""
+    return (l_max + 1) * (n_orb * (n_orb + 1) // 2 if pairs else n_orb)
+
+
+def param_layout(n_elem: int, T: int, n_phi: int, l_max: int, n_orb: int, h1: int, h2: int,
+                 pairs: bool = False) -> dict:
     """Offsets (in floats) of every block of the flat parameter vector."""
-    f = (l_max + 1) * n_orb
+    f = n_features(l_max, n_orb, pairs)
     off = 0
     lay: dict = {"c0": (off, (n_elem, n_phi))}
     off += n_elem * n_phi
@@ -138,15 +155,24 @@ def make_model(
     alpha: float = 0.5,
     feature_scale: tuple | None = None,
     energy_scale: float | None = None,
+    pairs: bool = False,
 ) -> ModelSpec:
-    """Draw a seeded parameter set (see module docstring for the layout)."""
+    """Draw a seeded parameter set (see module docstring for the layout).
+
+    ``pairs=True`` selects the orbital-pair-product features (with the default
+    ``n_orb`` then 8, the feature count N_phi (N_phi+1) (L+1)/2 = 108 that
+    Sec. 2.1 states) and their own input scales.
+    """
     if T < 1:
         raise ValueError("T must be >= 1")
-    fs = FEATURE_SCALE if feature_scale is None else feature_scale
+    if pairs and n_orb == 16:
+        n_orb = 8
+    fs = (FEATURE_SCALE_PAIRS if pairs else FEATURE_SCALE) if feature_scale is None else feature_scale
     if any(len(row) < l_max + 1 for per_t in fs for row in per_t):
         raise ValueError("feature_scale needs one entry per l")
     es = ENERGY_SCALE if energy_scale is None else energy_scale
-    lay = param_layout(n_elem, T, n_phi, l_max, n_orb, h1, h2)
+    lay = param_layout(n_elem, T, n_phi, l_max, n_orb, h1, h2, pairs)
+    per_l = n_orb * (n_orb + 1) // 2 if pairs else n_orb  # features per angular momentum
 
     def stream(*key):
         # an independent substream per block, so layer t's draws do not depend on T
@@ -160,12 +186,12 @@ def make_model(
 
     put("c0", stream(0).normal(0.0, 1.0, size=(n_elem, n_phi)))
     put("W", np.stack([np.stack([_xavier(stream(1, t, l), n_phi, n_orb) for l in range(l_max + 1)]) for t in range(T)]))
-    f = (l_max + 1) * n_orb
+    f = (l_max + 1) * per_l
     for t in range(T):
         out = 1 if t == T - 1 else n_phi
         for e in range(n_elem):
             row = np.asarray(fs[min(t, len(fs) - 1)][min(e, len(fs[0]) - 1)][: l_max + 1], dtype=np.float64)
-            put((t, e, "W1"), _xavier(stream(2, t, e), f, h1) * np.repeat(row, n_orb)[:, None])
+            put((t, e, "W1"), _xavier(stream(2, t, e), f, h1) * np.repeat(row, per_l)[:, None])
             put((t, e, "b1"), np.zeros(h1))
             put((t, e, "W2"), _xavier(stream(3, t, e), h1, h2))
             put((t, e, "b2"), np.zeros(h2))
@@ -176,4 +202,4 @@ def make_model(
                 w3 = np.abs(w3) * es
             put((t, e, "W3"), w3)
             put((t, e, "b3"), np.zeros(out))
-    return ModelSpec(n_elem, T, n_phi, l_max, n_orb, h1, h2, float(r_c), float(alpha), p.astype(np.float32))
+    return ModelSpec(n_elem, T, n_phi, l_max, n_orb, h1, h2, float(r_c), float(alpha), p.astype(np.float32), pairs)
