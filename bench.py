@@ -80,6 +80,7 @@ def parse():
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-decomp", action="store_true")
     p.add_argument("--no-hea", action="store_true")
+    p.add_argument("--no-pairs", action="store_true")
     p.add_argument("--serve-requests", type=int, default=10000)
     return p.parse_args()
 
@@ -124,6 +125,40 @@ def run_hea(args, steps: int = 10):
         sy.close()
     pot.close()
     return out
+
+
+def run_pairs(args, steps: int = 50):
+    """The orbital-pair-product feature variant (108 features over 8 orbitals, the count Sec. 2.1
+    states) on the same 24,576-atom water box and step (rebuild + energy/forces), FP32 networks."""
+    import torch
+
+    from paper_2505_06711_gb300 import Potential, binding
+    from synth import make_model, water_box
+
+    s = water_box(8192, seed=0)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    pot = Potential(make_model(T=T_LAYERS, pairs=True))
+    sy = pot.system(s.pos, s.species, s.cell, skin=SKIN)
+
+    def step():
+        binding.reann_nlist_rebuild(pot.ctx, sy.nl, sy.pos)
+        binding.reann_energy_forces(pot.ctx, sy.nl, sy.pos, T_LAYERS, sy.energy, sy.forces, None)
+
+    for _ in range(5):
+        step()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record()
+        step()
+        b.record()
+    torch.cuda.synchronize()
+    binding.reann_ctx_check(pot.ctx)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    sy.close()
+    pot.close()
+    return {"workload": f"water box 8192 H2O ({s.n_atoms} atoms), T = {T_LAYERS}, 108 pair features, FP32",
+            "ms_per_step": ms, "atom_evals_per_s": s.n_atoms / (ms * 1e-3)}
 
 
 def run_decomp(args, steps: int = 100):
@@ -648,6 +683,7 @@ def run_ours(args):
     serve = None if args.no_serve or ws > 1 else run_serve(args)
     decomp = None if args.no_decomp else run_decomp(args)
     hea = None if args.no_hea else run_hea(args)
+    pairs = None if args.no_pairs else run_pairs(args)
 
     if rank == 0:
         line = base_line(args, ws, value, ms, "f32")
@@ -657,6 +693,7 @@ def run_ours(args):
         line["serve"] = serve
         line["decomposition"] = decomp
         line["hea"] = hea
+        line["pair_features"] = pairs
         line["e2e"] = e2e
         line["roofline"] = roof
         line["gpu_launches"] = launches_per_step(T_LAYERS) * args.steps

@@ -82,6 +82,18 @@ typedef struct reann_nlist reann_nlist;
  */
 int reann_model_create(int n_elem, int T, int n_phi, int l_max, int n_orb, int h1, int h2, double r_c, double alpha,
                        const float* params, int64_t n_params, reann_model** out);
+
+/*
+ * As reann_model_create, with the choice of features:
+ *   feature_pairs = 0  Eq. 1: rho_{l,k} = sum_{a in l} w_a g_{a,k}^2, n_orb = 16, F = 48
+ *   feature_pairs = 1  orbital-pair products rho_{l,(k,k')} = sum_{a in l} w_a g_{a,k} g_{a,k'}
+ *                      for k <= k', n_orb = 8, F = (l_max+1) n_orb (n_orb+1)/2 = 108 (the
+ *                      feature count Sec. 2.1 states), features ordered f = l 36 + p with p
+ *                      enumerating (k, k') row-major; FP32 networks only
+ * and the same parameter layout with these F and n_orb.  Errors: REANN_E_ARG.
+ */
+int reann_model_create_ex(int n_elem, int T, int n_phi, int l_max, int n_orb, int h1, int h2, double r_c,
+                          double alpha, int feature_pairs, const float* params, int64_t n_params, reann_model** out);
 void reann_model_free(reann_model* model);
 
 /* -------------------------------------------------------------- context --- */
@@ -387,7 +399,8 @@ int reann_md_info(reann_ctx* ctx, const reann_nlist* nl, int64_t* steps, int64_t
 
 /*
  * Per-layer intermediates of the last evaluation of `nl`, in caller order
- * (inspection and testing): rho (dev, N x F FP32) and c (dev, N x N_phi FP32)
+ * (inspection and testing): rho (dev, N x F FP32, F the model's feature count)
+ * and c (dev, N x N_phi FP32)
  * of layer `layer` in [0, T).  Either output may be NULL.  Asynchronous.
  */
 int reann_get_layer(reann_ctx* ctx, const reann_nlist* nl, int layer, float* rho, float* coef);

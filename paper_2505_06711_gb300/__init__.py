@@ -167,7 +167,7 @@ class System:
     def layer(self, t: int):
         import torch
 
-        rho = torch.zeros((self.n, 48), dtype=torch.float32, device=self.pot.device)
+        rho = torch.zeros((self.n, self.pot.spec.n_feat), dtype=torch.float32, device=self.pot.device)
         coef = torch.zeros((self.n, 8), dtype=torch.float32, device=self.pot.device)
         binding.reann_get_layer(self.pot.ctx, self.nl, t, rho, coef)
         return rho, coef

@@ -49,6 +49,7 @@ _vp, _i64, _i32, _int, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, c
 
 _SIGS = {
     "reann_model_create": ([_int] * 7 + [_dbl, _dbl, _vp, _i64, ctypes.POINTER(_vp)], _int),
+    "reann_model_create_ex": ([_int] * 7 + [_dbl, _dbl, _int, _vp, _i64, ctypes.POINTER(_vp)], _int),
     "reann_model_free": ([_vp], None),
     "reann_ctx_create": ([_vp, _vp, ctypes.POINTER(_vp)], _int),
     "reann_ctx_free": ([_vp], None),
@@ -133,12 +134,28 @@ def _check(rc, ctx=None):
 
 # ------------------------------------------------------------------ model --
 def reann_model_create(spec) -> ctypes.c_void_p:
-    """``spec`` is a :class:`synth.model.ModelSpec` (or any object with its fields)."""
+    """``spec`` is a :class:`synth.model.ModelSpec` (or any object with its fields);
+    a pair-feature spec (``spec.pairs``) goes through reann_model_create_ex."""
+    if getattr(spec, "pairs", False):
+        return reann_model_create_ex(spec, 1)
     params = np.ascontiguousarray(spec.params, dtype=np.float32)
     out = _vp()
     rc = lib().reann_model_create(
         spec.n_elem, spec.T, spec.n_phi, spec.l_max, spec.n_orb, spec.h1, spec.h2,
         float(spec.r_c), float(spec.alpha), _ptr(params), params.size, ctypes.byref(out),
+    )
+    _check(rc)
+    return out
+
+
+def reann_model_create_ex(spec, feature_pairs: int | None = None) -> ctypes.c_void_p:
+    """As reann_model_create with the feature choice (default: ``spec.pairs``)."""
+    fp = int(getattr(spec, "pairs", False)) if feature_pairs is None else int(feature_pairs)
+    params = np.ascontiguousarray(spec.params, dtype=np.float32)
+    out = _vp()
+    rc = lib().reann_model_create_ex(
+        spec.n_elem, spec.T, spec.n_phi, spec.l_max, spec.n_orb, spec.h1, spec.h2,
+        float(spec.r_c), float(spec.alpha), fp, _ptr(params), params.size, ctypes.byref(out),
     )
     _check(rc)
     return out

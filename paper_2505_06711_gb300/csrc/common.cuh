@@ -19,6 +19,9 @@ constexpr int NANG = 10;  // angular terms for L = 2
 constexpr int LMAX = 2;
 constexpr int NORB = 16;
 constexpr int NFEAT = (LMAX + 1) * NORB;  // 48
+// orbital-pair-product features: 8 orbitals, (L+1) 8 (8+1)/2 = 108 features
+constexpr int NORB_P = 8;
+constexpr int NFEAT_P = (LMAX + 1) * NORB_P * (NORB_P + 1) / 2;
 constexpr int NB = NANG * NPHI;           // 80 per-atom density partials b_{a,m}
 constexpr int H1 = 64;
 constexpr int H2 = 64;
@@ -89,6 +92,9 @@ struct CellGeom {
 struct Model {
     int n_elem, T;
     double r_c, alpha;
+    bool pairs = false;  // orbital-pair-product features instead of Eq. 1's squares
+    int n_orb() const { return pairs ? NORB_P : NORB; }
+    int n_feat() const { return pairs ? NFEAT_P : NFEAT; }
     std::vector<float> params;  // host copy, flat layout of reann.h
 };
 
@@ -149,6 +155,7 @@ struct reann_nlist {
     int stride = 0;                   // neighbour row capacity
     int max_count = 0;                // longest row found by the first build
     int n_elem = 0, T = 0;
+    int n_feat = reann::NFEAT;        // features per atom of the model the buffers were sized for
     double r_c = 0, skin = 0;
     reann::CellGeom geom{};
     int elem_start[reann::MAX_ELEM + 1] = {0};
@@ -288,12 +295,13 @@ int export_nlist(reann_ctx* ctx, const reann_nlist* nl, int64_t cap, int32_t* i,
 cudaError_t launch_init_coef(cudaStream_t s, const reann_nlist* nl, const float* c0);
 cudaError_t launch_gather_ghost_rows(cudaStream_t s, const reann_nlist* nl, float* base, int width);
 cudaError_t launch_density_fwd(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* W, const float* coef,
-                               float* rho, float* bck);
+                               float* rho, float* bck, bool pairs = false);
 cudaError_t launch_bbar(cudaStream_t s, const reann_nlist* nl, const float* W, const float* bck, const float* rhobar,
-                        float* bbar);
+                        float* bbar, bool pairs = false);
 cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* coef,
                                const float* bbar, float* cbar, float* grad, bool want_cbar, int* flags,
                                float* vir = nullptr);
+cudaError_t upload_pair_table();
 cudaError_t launch_virial_sum(cudaStream_t s, const reann_nlist* nl, const float* vir, double* partial, double* out);
 cudaError_t launch_energy_sum(cudaStream_t s, const reann_nlist* nl, double* energy);
 cudaError_t launch_scatter_outputs(cudaStream_t s, const reann_nlist* nl, float* forces, float* atom_energy);
@@ -302,7 +310,7 @@ cudaError_t launch_unpermute_rows(cudaStream_t s, const reann_nlist* nl, const f
 
 // atomic networks, FP32 SIMT (mlp_fp32.cu)
 cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
-                               const float* rho, float* out, int out_stride);
+                               const float* rho, float* out, int out_stride, bool pairs = false);
 // atomic networks, BF16 on tcgen05 tensor cores (mlp_tc.cu)
 cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
                               bool split, const float* rho, float* out, int out_stride, int* flags);
@@ -310,6 +318,6 @@ cudaError_t launch_mlp_bwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTab
                               bool split, const float* rho, const float* ybar, float* rhobar, int* flags);
 
 cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
-                               const float* rho, const float* ybar, float* rhobar);
+                               const float* rho, const float* ybar, float* rhobar, bool pairs = false);
 
 }  // namespace reann

@@ -108,7 +108,15 @@ __device__ __forceinline__ void monomials(float x, float y, float z, float A[NAN
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 
+// Orbital pair (k, k'), k <= k', of pair feature p = 0..35 (row-major over k)
+__constant__ unsigned char c_pair_k[NORB_P * (NORB_P + 1) / 2];
+__constant__ unsigned char c_pair_k2[NORB_P * (NORB_P + 1) / 2];
+
 // ------------------------------------------------------------- forward ---
+// PAIRS = false: Eq. 1, rho_{l,k} = sum_{a in l} w_a g_{a,k}^2 over 16 orbitals.
+// PAIRS = true: the orbital-pair products rho_{l,(k,k')} = sum_{a in l} w_a g_{a,k} g_{a,k'},
+// k <= k' over 8 orbitals (108 features).
+template <bool PAIRS>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_density_fwd(int64_t n, int stride, Radial R,
                                                             const int32_t* __restrict__ live,
                                                             const int32_t* __restrict__ live_cnt,
@@ -117,9 +125,10 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_density_fwd(int64_t n, int s
                                                             const float* __restrict__ coef,
                                                             const float* __restrict__ Wt, float* __restrict__ rho,
                                                             float* __restrict__ bck) {
-    __shared__ __align__(16) float sW[(LMAX + 1) * NPHI * NORB];
+    constexpr int KO = PAIRS ? NORB_P : NORB;
+    __shared__ __align__(16) float sW[(LMAX + 1) * NPHI * KO];
     __shared__ __align__(16) float sB[kWarps][kAtomsPerWarp][kBStride];
-    for (int i = threadIdx.x; i < (LMAX + 1) * NPHI * NORB; i += blockDim.x) sW[i] = Wt[i];
+    for (int i = threadIdx.x; i < (LMAX + 1) * NPHI * KO; i += blockDim.x) sW[i] = Wt[i];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, q = lane & 3, slot = lane >> 2;
     const int64_t atom = ((int64_t)blockIdx.x * kWarps + warp) * kAtomsPerWarp + slot;
@@ -180,6 +189,41 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_density_fwd(int64_t n, int s
         if (valid) *reinterpret_cast<float4*>(bck + (size_t)atom * NB + 20 * q + v) = w4;
     }
     __syncwarp();
+    if constexpr (PAIRS) {
+        // g_{a,k} = sum_m b_{a,m} W_{l,m,k}: lane q the orbitals 2q, 2q+1 of every a,
+        // into the b row's place (after all four lanes have read it); then lane q
+        // the 27 features 27q .. 27q+26
+        float g[NANG][2];
+#pragma unroll
+        for (int a = 0; a < NANG; ++a) {
+            const int l = ang_l(a);
+            const float4 b0 = ld4(sb + a * NPHI), b1 = ld4(sb + a * NPHI + 4);
+            const float bm[NPHI] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            g[a][0] = g[a][1] = 0.f;
+#pragma unroll
+            for (int m = 0; m < NPHI; ++m) {
+                const float2 w = *reinterpret_cast<const float2*>(sW + (l * NPHI + m) * KO + 2 * q);
+                g[a][0] = fmaf(bm[m], w.x, g[a][0]);
+                g[a][1] = fmaf(bm[m], w.y, g[a][1]);
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int a = 0; a < NANG; ++a)
+            *reinterpret_cast<float2*>(sb + a * NORB_P + 2 * q) = make_float2(g[a][0], g[a][1]);
+        __syncwarp();
+        if (!valid) return;
+        constexpr int KP = NORB_P * (NORB_P + 1) / 2;
+        for (int f = 27 * q; f < 27 * q + 27; ++f) {
+            const int l = f / KP, p = f - l * KP;
+            const int k = c_pair_k[p], k2 = c_pair_k2[p];
+            const int a0 = l == 0 ? 0 : (l == 1 ? 1 : 4), a1 = l == 0 ? 1 : (l == 1 ? 4 : NANG);
+            float acc_f = 0.f;
+            for (int a = a0; a < a1; ++a) acc_f = fmaf(ang_w(a) * sb[a * NORB_P + k], sb[a * NORB_P + k2], acc_f);
+            rho[(size_t)atom * NFEAT_P + f] = acc_f;
+        }
+        return;
+    }
     if (!valid) return;
     // contraction over m and the squared multinomial sum; lane q owns orbitals 4q..4q+3
     float racc[LMAX + 1][4];
@@ -212,16 +256,58 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_density_fwd(int64_t n, int s
 }
 
 // -------------------------------------------------------------- bbar -----
-// bbar_{a,m} = sum_k 2 w_a g_{a,k} rhobar_{l(a),k} W_{l(a),m,k}, g recomputed from the b checkpoint.
+// bbar_{a,m} = sum_k gbar_{a,k} W_{l(a),m,k}, g recomputed from the b checkpoint, with
+//   squares:  gbar_{a,k} = 2 w_a g_{a,k} rhobar_{l,k}
+//   pairs:    gbar_{a,k} = w_a sum_k' R_{kk'} g_{a,k'},  R_{kk'} = rhobar_{l,(min,max)} (x 2 on the diagonal)
+template <bool PAIRS>
 __global__ void __launch_bounds__(256) k_bbar(int64_t n, const float* __restrict__ Wt, const float* __restrict__ bck,
                                               const float* __restrict__ rhobar, float* __restrict__ bbar) {
-    __shared__ __align__(16) float sW[(LMAX + 1) * NPHI * NORB];
-    for (int i = threadIdx.x; i < (LMAX + 1) * NPHI * NORB; i += blockDim.x) sW[i] = Wt[i];
+    constexpr int KO = PAIRS ? NORB_P : NORB;
+    __shared__ __align__(16) float sW[(LMAX + 1) * NPHI * KO];
+    for (int i = threadIdx.x; i < (LMAX + 1) * NPHI * KO; i += blockDim.x) sW[i] = Wt[i];
     __syncthreads();
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t atom = tid >> 2;
     const int q = tid & 3;
     if (atom >= n) return;
+    if constexpr (PAIRS) {
+        constexpr int KP = NORB_P * (NORB_P + 1) / 2;
+        for (int a = q; a < NANG; a += 4) {
+            const int l = ang_l(a);
+            const float4 b0 = ldg4(bck + (size_t)atom * NB + a * NPHI), b1 = ldg4(bck + (size_t)atom * NB + a * NPHI + 4);
+            const float bm[NPHI] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            float g[NORB_P], gb[NORB_P];
+#pragma unroll
+            for (int k = 0; k < NORB_P; ++k) {
+                g[k] = 0.f;
+                gb[k] = 0.f;
+#pragma unroll
+                for (int m = 0; m < NPHI; ++m) g[k] = fmaf(bm[m], sW[(l * NPHI + m) * KO + k], g[k]);
+            }
+            const float* rb = rhobar + (size_t)atom * NFEAT_P + l * KP;
+            int p = 0;
+#pragma unroll
+            for (int k = 0; k < NORB_P; ++k)
+#pragma unroll
+                for (int k2 = k; k2 < NORB_P; ++k2, ++p) {
+                    const float r = __ldg(rb + p);
+                    gb[k] = fmaf(r, g[k2], gb[k]);
+                    gb[k2] = fmaf(r, g[k], gb[k2]);
+                }
+            const float wa = ang_w(a);
+            float out[NPHI];
+#pragma unroll
+            for (int m = 0; m < NPHI; ++m) {
+                out[m] = 0.f;
+#pragma unroll
+                for (int k = 0; k < NORB_P; ++k) out[m] = fmaf(wa * gb[k], sW[(l * NPHI + m) * KO + k], out[m]);
+            }
+            float* dst = bbar + (size_t)atom * NB + a * NPHI;
+            *reinterpret_cast<float4*>(dst) = make_float4(out[0], out[1], out[2], out[3]);
+            *reinterpret_cast<float4*>(dst + 4) = make_float4(out[4], out[5], out[6], out[7]);
+        }
+        return;
+    }
     for (int a = q; a < NANG; a += 4) {
         const int l = ang_l(a);
         const float4 b0 = ldg4(bck + (size_t)atom * NB + a * NPHI), b1 = ldg4(bck + (size_t)atom * NB + a * NPHI + 4);
@@ -578,17 +664,38 @@ cudaError_t launch_gather_ghost_rows(cudaStream_t s, const reann_nlist* nl, floa
 }
 
 cudaError_t launch_density_fwd(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* W, const float* coef,
-                               float* rho, float* bck) {
+                               float* rho, float* bck, bool pairs) {
     const int64_t per_block = kWarps * kAtomsPerWarp;
-    k_density_fwd<<<blocks_for(nl->n, per_block), kWarps * 32, 0, s>>>(nl->n, nl->stride, r, nl->live, nl->live_cnt,
-                                                                        nl->pos_hi, nl->pos_lo, coef, W, rho, bck);
+    const unsigned nb = blocks_for(nl->n, per_block);
+    if (pairs)
+        k_density_fwd<true><<<nb, kWarps * 32, 0, s>>>(nl->n, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi,
+                                                       nl->pos_lo, coef, W, rho, bck);
+    else
+        k_density_fwd<false><<<nb, kWarps * 32, 0, s>>>(nl->n, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi,
+                                                        nl->pos_lo, coef, W, rho, bck);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bbar(cudaStream_t s, const reann_nlist* nl, const float* W, const float* bck, const float* rhobar,
-                        float* bbar) {
-    k_bbar<<<blocks_for(nl->n * 4, 256), 256, 0, s>>>(nl->n, W, bck, rhobar, bbar);
+                        float* bbar, bool pairs) {
+    if (pairs)
+        k_bbar<true><<<blocks_for(nl->n * 4, 256), 256, 0, s>>>(nl->n, W, bck, rhobar, bbar);
+    else
+        k_bbar<false><<<blocks_for(nl->n * 4, 256), 256, 0, s>>>(nl->n, W, bck, rhobar, bbar);
     return cudaGetLastError();
+}
+
+cudaError_t upload_pair_table() {
+    unsigned char k1[NORB_P * (NORB_P + 1) / 2], k2[NORB_P * (NORB_P + 1) / 2];
+    int p = 0;
+    for (int a = 0; a < NORB_P; ++a)
+        for (int b = a; b < NORB_P; ++b, ++p) {
+            k1[p] = (unsigned char)a;
+            k2[p] = (unsigned char)b;
+        }
+    cudaError_t e = cudaMemcpyToSymbol(c_pair_k, k1, sizeof(k1));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_pair_k2, k2, sizeof(k2));
+    return e;
 }
 
 cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* coef,

@@ -24,8 +24,13 @@ namespace {
 
 constexpr int kT = 256;       // threads per block
 constexpr int kR = MLP_TILE;  // 64 rows per tile
-constexpr int LDX = NFEAT + 4;  // 52
 constexpr int LDH = H1 + 4;     // 68
+// input rows of FIN features are held with stride FIN + 4 (52 or 112) in the
+// buffer that later holds h1 (stride LDH)
+template <int FIN>
+__host__ __device__ constexpr int ldx() { return FIN + 4; }
+template <int FIN>
+__host__ __device__ constexpr int abuf() { return kR * (ldx<FIN>() > LDH ? ldx<FIN>() : LDH); }
 
 struct NetsOfLayer {
     NetDev e[MAX_ELEM];
@@ -67,13 +72,14 @@ __device__ __forceinline__ void mma_4x4(const float* A, const float* B, int ty, 
     }
 }
 
+template <int FIN>
 __device__ __forceinline__ void load_rows(float* sX, const float* src, int row0, int nrows, int tid) {
-    // 64 rows x 48 floats -> sX[r][LDX]
-    for (int t = tid; t < kR * (NFEAT / 4); t += kT) {
-        const int r = t / (NFEAT / 4), c = t % (NFEAT / 4);
+    // 64 rows x FIN floats -> sX[r][FIN + 4]
+    for (int t = tid; t < kR * (FIN / 4); t += kT) {
+        const int r = t / (FIN / 4), c = t % (FIN / 4);
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (r < nrows) v = *reinterpret_cast<const float4*>(src + (size_t)(row0 + r) * NFEAT + 4 * c);
-        *reinterpret_cast<float4*>(sX + r * LDX + 4 * c) = v;
+        if (r < nrows) v = *reinterpret_cast<const float4*>(src + (size_t)(row0 + r) * FIN + 4 * c);
+        *reinterpret_cast<float4*>(sX + r * ldx<FIN>() + 4 * c) = v;
     }
 }
 
@@ -114,29 +120,29 @@ __device__ __forceinline__ int w3_row(int k) {
 // Shared memory: weights (31 KB) and one 64 x 68 activation buffer that holds
 // the input rows, then h1; h2 stays in registers and the output layer is a
 // half-warp reduction, so four blocks fit on an SM.
-template <int OUT>
+template <int OUT, int FIN>
 __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __restrict__ tiles,
                                                const float* __restrict__ rho, float* __restrict__ out,
                                                int out_stride) {
     extern __shared__ __align__(16) float sm[];
-    float* sW1 = sm;                 // 48 x 64
-    float* sW2 = sW1 + NFEAT * H1;   // 64 x 64
+    float* sW1 = sm;                 // FIN x 64
+    float* sW2 = sW1 + FIN * H1;     // 64 x 64
     float* sW3 = sW2 + H1 * H2;      // 64 x OUT (8 reserved), rows permuted (w3_row)
     float* sb1 = sW3 + H2 * 8;       // 64
     float* sb2 = sb1 + H1;           // 64
     float* sb3 = sb2 + H2;           // 8
-    float* sA = sb3 + 8;             // 64 x 68: input rows (stride LDX), then h1 (stride LDH)
+    float* sA = sb3 + 8;             // input rows (stride FIN + 4), then h1 (stride LDH)
     const int tid = threadIdx.x;
     const Tile tl = tiles[blockIdx.x];
     if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list
     const NetDev& w = nets.e[tl.elem];
-    copy_f4(sW1, w.W1, NFEAT * H1, tid);
+    copy_f4(sW1, w.W1, FIN * H1, tid);
     copy_f4(sW2, w.W2, H1 * H2, tid);
     for (int i = tid; i < H2 * OUT; i += kT) sW3[w3_row<OUT>(i / OUT) * OUT + i % OUT] = w.W3[i];
     for (int i = tid; i < H1; i += kT) sb1[i] = w.b1[i];
     for (int i = tid; i < H2; i += kT) sb2[i] = w.b2[i];
     if (tid < OUT) sb3[tid] = w.b3[tid];
-    load_rows(sA, rho, tl.row0, tl.nrows, tid);
+    load_rows<FIN>(sA, rho, tl.row0, tl.nrows, tid);
     __syncthreads();
     const int ty = tid >> 4, tx = tid & 15;
     float acc[4][4];
@@ -145,7 +151,7 @@ __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = sb1[4 * tx + j];
-    mma_4x4<NFEAT, LDX, H1>(sA, sW1, ty, tx, acc);
+    mma_4x4<FIN, ldx<FIN>(), H1>(sA, sW1, ty, tx, acc);
     __syncthreads();  // every thread is done reading the input rows
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -201,24 +207,24 @@ __device__ __forceinline__ void cp_async16(float* dst, const float* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 
-template <int OUT>
+template <int OUT, int FIN>
 __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __restrict__ tiles,
                                                const float* __restrict__ rho, const float* __restrict__ ybar,
                                                float* __restrict__ rhobar) {
     extern __shared__ __align__(16) float sm[];
-    float* sW1 = sm;                  // 48 x 64, later W1^T 64 x 48
-    float* sW2 = sW1 + NFEAT * H1;    // 64 x 64, later W2^T
+    float* sW1 = sm;                  // FIN x 64, later W1^T 64 x FIN
+    float* sW2 = sW1 + FIN * H1;      // 64 x 64, later W2^T
     float* sW3t = sW2 + H1 * H2;      // OUT x 64 (8 rows reserved)
     float* sb1 = sW3t + 8 * H2;       // 64
     float* sb2 = sb1 + H1;            // 64
     float* sY = sb2 + H2;             // 64 x 8
-    float* sG = sY + kR * 8;          // 64 x 68: input rows, h1, z2bar, z1bar
-    float* sZ1 = sG + kR * LDH;       // 64 x 68: z1
+    float* sG = sY + kR * 8;          // input rows (stride FIN + 4), h1, z2bar, z1bar (stride LDH)
+    float* sZ1 = sG + abuf<FIN>();    // 64 x 68: z1
     const int tid = threadIdx.x;
     const Tile tl = tiles[blockIdx.x];
     if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list
     const NetDev& w = nets.e[tl.elem];
-    copy_f4(sW1, w.W1, NFEAT * H1, tid);
+    copy_f4(sW1, w.W1, FIN * H1, tid);
     copy_f4(sW2, w.W2, H1 * H2, tid);
     for (int i = tid; i < OUT * H2; i += kT) sW3t[i] = w.W3t[i];
     for (int i = tid; i < H1; i += kT) sb1[i] = w.b1[i];
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
         const int r = i / OUT, o = i % OUT;
         sY[r * 8 + o] = (OUT == 1) ? 1.f : (r < tl.nrows ? ybar[(size_t)(tl.row0 + r) * OUT + o] : 0.f);
     }
-    load_rows(sG, rho, tl.row0, tl.nrows, tid);
+    load_rows<FIN>(sG, rho, tl.row0, tl.nrows, tid);
     __syncthreads();
     const int ty = tid >> 4, tx = tid & 15;
     float acc[4][4];
@@ -236,7 +242,7 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = sb1[4 * tx + j];
-    mma_4x4<NFEAT, LDX, H1>(sG, sW1, ty, tx, acc);
+    mma_4x4<FIN, ldx<FIN>(), H1>(sG, sW1, ty, tx, acc);
     __syncthreads();  // every thread is done reading the input rows
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -259,7 +265,7 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
     __syncthreads();  // everyone is done reading h1, W1 and W2
     // bring in the transposes while z2bar is computed
     for (int i = tid; i < H1 * H2 / 4; i += kT) cp_async16(sW2 + 4 * i, w.W2t + 4 * i);
-    for (int i = tid; i < H1 * NFEAT / 4; i += kT) cp_async16(sW1 + 4 * i, w.W1t + 4 * i);
+    for (int i = tid; i < H1 * FIN / 4; i += kT) cp_async16(sW1 + 4 * i, w.W1t + 4 * i);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     // z2bar = (ybar W3^T) * dsilu(z2) -> sG
 #pragma unroll
@@ -293,25 +299,29 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
             acc[i][0] * dsilu(z1.x), acc[i][1] * dsilu(z1.y), acc[i][2] * dsilu(z1.z), acc[i][3] * dsilu(z1.w));
     }
     __syncthreads();
-    // rhobar = z1bar W1^T  (64 x 48): 12 column groups of 4
-    if (tx < NFEAT / 4) {
+    // rhobar = z1bar W1^T  (64 x FIN): FIN / 4 column groups of 4 over the 16 tx
+    for (int cg = tx; cg < FIN / 4; cg += 16) {
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-        mma_4x4<H1, LDH, NFEAT>(sG, sW1, ty, tx, acc);
+        mma_4x4<H1, LDH, FIN>(sG, sW1, ty, cg, acc);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int r = 4 * ty + i;
             if (r < tl.nrows)
-                *reinterpret_cast<float4*>(rhobar + (size_t)(tl.row0 + r) * NFEAT + 4 * tx) =
+                *reinterpret_cast<float4*>(rhobar + (size_t)(tl.row0 + r) * FIN + 4 * cg) =
                     make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
         }
     }
 }
 
-constexpr size_t fwd_smem() { return sizeof(float) * (NFEAT * H1 + H1 * H2 + H2 * 8 + H1 + H2 + 8 + kR * LDH); }
-constexpr size_t bwd_smem() { return sizeof(float) * (NFEAT * H1 + H1 * H2 + 8 * H2 + H1 + H2 + kR * 8 + 2 * kR * LDH); }
+template <int FIN>
+constexpr size_t fwd_smem() { return sizeof(float) * (FIN * H1 + H1 * H2 + H2 * 8 + H1 + H2 + 8 + abuf<FIN>()); }
+template <int FIN>
+constexpr size_t bwd_smem() {
+    return sizeof(float) * (FIN * H1 + H1 * H2 + 8 * H2 + H1 + H2 + kR * 8 + abuf<FIN>() + kR * LDH);
+}
 
 void ensure_attrs() {
     // once per device, safe under concurrent first calls
@@ -321,10 +331,16 @@ void ensure_attrs() {
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(mu);
     if (dev < 64 && ((done >> dev) & 1)) return;
-    cudaFuncSetAttribute(k_mlp_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
-    cudaFuncSetAttribute(k_mlp_fwd<NPHI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem());
-    cudaFuncSetAttribute(k_mlp_bwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem());
-    cudaFuncSetAttribute(k_mlp_bwd<NPHI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem());
+    cudaFuncSetAttribute(k_mlp_fwd<1, NFEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<NFEAT>());
+    cudaFuncSetAttribute(k_mlp_fwd<NPHI, NFEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<NFEAT>());
+    cudaFuncSetAttribute(k_mlp_bwd<1, NFEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<NFEAT>());
+    cudaFuncSetAttribute(k_mlp_bwd<NPHI, NFEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<NFEAT>());
+    cudaFuncSetAttribute(k_mlp_fwd<1, NFEAT_P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<NFEAT_P>());
+    cudaFuncSetAttribute(k_mlp_fwd<NPHI, NFEAT_P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fwd_smem<NFEAT_P>());
+    cudaFuncSetAttribute(k_mlp_bwd<1, NFEAT_P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<NFEAT_P>());
+    cudaFuncSetAttribute(k_mlp_bwd<NPHI, NFEAT_P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bwd_smem<NFEAT_P>());
     if (dev < 64) done |= (uint64_t)1 << dev;
 }
 
@@ -337,28 +353,42 @@ NetsOfLayer layer_nets(const NetTable& t, int layer) {
 }  // namespace
 
 cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
-                               const float* rho, float* out, int out_stride) {
+                               const float* rho, float* out, int out_stride, bool pairs) {
     const int nt = (int)nl->tiles_h.size();
     if (nt == 0) return cudaSuccess;
     ensure_attrs();
     const NetsOfLayer ln = layer_nets(nets, t);
-    if (energy)
-        k_mlp_fwd<1><<<nt, kT, fwd_smem(), s>>>(ln, nl->tiles, rho, out, out_stride);
-    else
-        k_mlp_fwd<NPHI><<<nt, kT, fwd_smem(), s>>>(ln, nl->tiles, rho, out, out_stride);
+    if (pairs) {
+        if (energy)
+            k_mlp_fwd<1, NFEAT_P><<<nt, kT, fwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, out, out_stride);
+        else
+            k_mlp_fwd<NPHI, NFEAT_P><<<nt, kT, fwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, out, out_stride);
+    } else {
+        if (energy)
+            k_mlp_fwd<1, NFEAT><<<nt, kT, fwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, out, out_stride);
+        else
+            k_mlp_fwd<NPHI, NFEAT><<<nt, kT, fwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, out, out_stride);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
-                               const float* rho, const float* ybar, float* rhobar) {
+                               const float* rho, const float* ybar, float* rhobar, bool pairs) {
     const int nt = (int)nl->tiles_h.size();
     if (nt == 0) return cudaSuccess;
     ensure_attrs();
     const NetsOfLayer ln = layer_nets(nets, t);
-    if (energy)
-        k_mlp_bwd<1><<<nt, kT, bwd_smem(), s>>>(ln, nl->tiles, rho, ybar, rhobar);
-    else
-        k_mlp_bwd<NPHI><<<nt, kT, bwd_smem(), s>>>(ln, nl->tiles, rho, ybar, rhobar);
+    if (pairs) {
+        if (energy)
+            k_mlp_bwd<1, NFEAT_P><<<nt, kT, bwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, ybar, rhobar);
+        else
+            k_mlp_bwd<NPHI, NFEAT_P><<<nt, kT, bwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, ybar, rhobar);
+    } else {
+        if (energy)
+            k_mlp_bwd<1, NFEAT><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar);
+        else
+            k_mlp_bwd<NPHI, NFEAT><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar);
+    }
     return cudaGetLastError();
 }
 

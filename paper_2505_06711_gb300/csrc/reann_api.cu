@@ -30,11 +30,12 @@ int set_error(reann_ctx* ctx, int code, const std::string& msg) {
 
 namespace {
 
-constexpr int64_t expected_params(int n_elem, int T) {
-    int64_t n = (int64_t)n_elem * NPHI + (int64_t)T * (LMAX + 1) * NPHI * NORB;
+constexpr int64_t expected_params(int n_elem, int T, bool pairs = false) {
+    const int ko = pairs ? NORB_P : NORB, nf = pairs ? NFEAT_P : NFEAT;
+    int64_t n = (int64_t)n_elem * NPHI + (int64_t)T * (LMAX + 1) * NPHI * ko;
     for (int t = 0; t < T; ++t) {
         const int out = (t == T - 1) ? 1 : NPHI;
-        n += (int64_t)n_elem * (NFEAT * H1 + H1 + H1 * H2 + H2 + H2 * out + out);
+        n += (int64_t)n_elem * (nf * H1 + H1 + H1 * H2 + H2 + H2 * out + out);
     }
     return n;
 }
@@ -104,10 +105,11 @@ int alloc_eval_buffers(reann_ctx* ctx, reann_nlist* nl, const std::vector<std::a
     nl->pos_hi = nl_alloc<float4>(nl, ne);
     nl->pos_lo = nl_alloc<float4>(nl, ne);
     nl->coef = nl_alloc<float>(nl, (size_t)T * ne * NPHI);
-    nl->rho = nl_alloc<float>(nl, (size_t)T * n * NFEAT);
+    nl->n_feat = ctx->model.n_feat();
+    nl->rho = nl_alloc<float>(nl, (size_t)T * n * nl->n_feat);
     nl->bck = nl_alloc<float>(nl, (size_t)T * n * NB);
     nl->eps = nl_alloc<float>(nl, n);
-    nl->rhobar = nl_alloc<float>(nl, (size_t)n * NFEAT);
+    nl->rhobar = nl_alloc<float>(nl, (size_t)n * nl->n_feat);
     nl->bbar = nl_alloc<float>(nl, (size_t)ne * NB);
     nl->cbar = nl_alloc<float>(nl, (size_t)n * NPHI);
     nl->grad = nl_alloc<float>(nl, (size_t)n * 3);
@@ -199,15 +201,17 @@ void push_block(std::vector<float>& dst, const float* src, size_t count) {
 
 // ===================================================================== ABI ==
 
-extern "C" int reann_model_create(int n_elem, int T, int n_phi, int l_max, int n_orb, int h1, int h2, double r_c,
-                                  double alpha, const float* params, int64_t n_params, reann_model** out) {
-    if (!out || !params) return REANN_E_ARG;
+extern "C" int reann_model_create_ex(int n_elem, int T, int n_phi, int l_max, int n_orb, int h1, int h2, double r_c,
+                                     double alpha, int feature_pairs, const float* params, int64_t n_params,
+                                     reann_model** out) {
+    if (!out || !params || (feature_pairs != 0 && feature_pairs != 1)) return REANN_E_ARG;
     *out = nullptr;
-    if (n_elem < 1 || n_elem > MAX_ELEM || T < 1 || T > 8 || n_phi != NPHI || l_max != LMAX || n_orb != NORB ||
-        h1 != H1 || h2 != H2 || !(r_c > 0) || !(alpha > 0) || !std::isfinite(r_c) || !std::isfinite(alpha) ||
-        alpha * r_c * r_c > 80.0)
+    const bool pairs = feature_pairs == 1;
+    if (n_elem < 1 || n_elem > MAX_ELEM || T < 1 || T > 8 || n_phi != NPHI || l_max != LMAX ||
+        n_orb != (pairs ? NORB_P : NORB) || h1 != H1 || h2 != H2 || !(r_c > 0) || !(alpha > 0) ||
+        !std::isfinite(r_c) || !std::isfinite(alpha) || alpha * r_c * r_c > 80.0)
         return REANN_E_ARG;
-    if (n_params != expected_params(n_elem, T)) return REANN_E_ARG;
+    if (n_params != expected_params(n_elem, T, pairs)) return REANN_E_ARG;
     for (int64_t i = 0; i < n_params; ++i)
         if (!std::isfinite(params[i])) return REANN_E_ARG;
     reann_model* m = new (std::nothrow) reann_model;
@@ -216,9 +220,15 @@ extern "C" int reann_model_create(int n_elem, int T, int n_phi, int l_max, int n
     m->m.T = T;
     m->m.r_c = r_c;
     m->m.alpha = alpha;
+    m->m.pairs = pairs;
     m->m.params.assign(params, params + n_params);
     *out = m;
     return REANN_OK;
+}
+
+extern "C" int reann_model_create(int n_elem, int T, int n_phi, int l_max, int n_orb, int h1, int h2, double r_c,
+                                  double alpha, const float* params, int64_t n_params, reann_model** out) {
+    return reann_model_create_ex(n_elem, T, n_phi, l_max, n_orb, h1, h2, r_c, alpha, 0, params, n_params, out);
 }
 
 extern "C" void reann_model_free(reann_model* model) { delete model; }
@@ -260,8 +270,9 @@ extern "C" int reann_ctx_create(const reann_model* model, void* cuda_stream, rea
     push_block(img, p, (size_t)M.n_elem * NPHI);
     p += M.n_elem * NPHI;
     off_W[0] = img.size();
-    push_block(img, p, (size_t)M.T * (LMAX + 1) * NPHI * NORB);
-    p += M.T * (LMAX + 1) * NPHI * NORB;
+    const int KO = M.n_orb(), NF = M.n_feat();
+    push_block(img, p, (size_t)M.T * (LMAX + 1) * NPHI * KO);
+    p += M.T * (LMAX + 1) * NPHI * KO;
     struct Off {
         size_t W1, b1, W2, b2, W3, b3, W1t, W2t, W3t;
     };
@@ -272,22 +283,22 @@ extern "C" int reann_ctx_create(const reann_model* model, void* cuda_stream, rea
         for (int e = 0; e < M.n_elem; ++e) {
             Off& o = offs[(size_t)t * M.n_elem + e];
             const float* W1 = p;
-            const float* b1 = W1 + NFEAT * H1;
+            const float* b1 = W1 + NF * H1;
             const float* W2 = b1 + H1;
             const float* b2 = W2 + H1 * H2;
             const float* W3 = b2 + H2;
             const float* b3 = W3 + H2 * outd;
             p = b3 + outd;
-            o.W1 = img.size(); push_block(img, W1, NFEAT * H1);
+            o.W1 = img.size(); push_block(img, W1, NF * H1);
             o.b1 = img.size(); push_block(img, b1, H1);
             o.W2 = img.size(); push_block(img, W2, H1 * H2);
             o.b2 = img.size(); push_block(img, b2, H2);
             o.W3 = img.size(); push_block(img, W3, H2 * outd);
             o.b3 = img.size(); push_block(img, b3, outd);
             std::vector<float> tr;
-            tr.resize(H1 * NFEAT);
-            for (int f = 0; f < NFEAT; ++f)
-                for (int q = 0; q < H1; ++q) tr[q * NFEAT + f] = W1[f * H1 + q];
+            tr.resize(H1 * NF);
+            for (int f = 0; f < NF; ++f)
+                for (int q = 0; q < H1; ++q) tr[q * NF + f] = W1[f * H1 + q];
             o.W1t = img.size(); push_block(img, tr.data(), tr.size());
             tr.assign(H2 * H1, 0.f);
             for (int u = 0; u < H1; ++u)
@@ -297,7 +308,9 @@ extern "C" int reann_ctx_create(const reann_model* model, void* cuda_stream, rea
             for (int u = 0; u < H2; ++u)
                 for (int q = 0; q < outd; ++q) tr[q * H2 + u] = W3[u * outd + q];
             o.W3t = img.size(); push_block(img, tr.data(), tr.size());
-            // BF16 images for the tensor-core networks (B operands are N x K, K-major)
+            // BF16 images for the tensor-core networks (B operands are N x K, K-major),
+            // built for the 48-feature networks only
+            if (M.pairs) continue;
             std::vector<float> w1t(H1 * NFEAT), w2t(H2 * H1);
             for (int f = 0; f < NFEAT; ++f)
                 for (int q = 0; q < H1; ++q) w1t[q * NFEAT + f] = W1[f * H1 + q];
@@ -315,6 +328,7 @@ extern "C" int reann_ctx_create(const reann_model* model, void* cuda_stream, rea
             }
         }
     }
+    if (tcimg.empty()) tcimg.resize(1);
     if (cudaMalloc(&ctx->d_bf16, tcimg.size() * sizeof(uint16_t)) != cudaSuccess) return fail(REANN_E_NOMEM);
     if (cudaMemcpy(ctx->d_bf16, tcimg.data(), tcimg.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) !=
         cudaSuccess)
@@ -330,9 +344,11 @@ extern "C" int reann_ctx_create(const reann_model* model, void* cuda_stream, rea
             const Off& o = offs[(size_t)t * M.n_elem + e];
             ctx->nets.net[t][e] = NetDev{base + o.W1, base + o.b1, base + o.W2, base + o.b2, base + o.W3,
                                          base + o.b3, base + o.W1t, base + o.W2t, base + o.W3t};
-            const uint8_t* ib = static_cast<const uint8_t*>(ctx->d_bf16) + ((size_t)t * M.n_elem + e) * 4 * 16384;
+            const uint8_t* ib =
+                static_cast<const uint8_t*>(ctx->d_bf16) + (M.pairs ? 0 : ((size_t)t * M.n_elem + e) * 4 * 16384);
             ctx->tc.img[t][e] = TcImg{ib, base + o.b1, base + o.b2, base + o.b3};
         }
+    if (M.pairs && upload_pair_table() != cudaSuccess) return fail(REANN_E_CUDA);
     if (cudaMalloc(&ctx->d_flags, sizeof(int) * NFLAGS) != cudaSuccess) return fail(REANN_E_NOMEM);
     if (cudaMemset(ctx->d_flags, 0, sizeof(int) * NFLAGS) != cudaSuccess) return fail(REANN_E_CUDA);
     if (cudaMallocHost(&ctx->h_flags, sizeof(int) * NFLAGS) != cudaSuccess) return fail(REANN_E_NOMEM);
@@ -365,6 +381,8 @@ extern "C" int reann_ctx_set_mlp_precision(reann_ctx* ctx, int precision) {
     if (!ctx) return REANN_E_ARG;
     if (precision != REANN_MLP_FP32 && precision != REANN_MLP_BF16 && precision != REANN_MLP_BF16X3)
         return set_error(ctx, REANN_E_ARG, "unsupported network precision");
+    if (precision != REANN_MLP_FP32 && ctx->model.pairs)
+        return set_error(ctx, REANN_E_ARG, "tensor-core networks are built for the 48-feature models only");
     ctx->precision = precision;
     return REANN_OK;
 }
@@ -746,11 +764,13 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
         ProfScope p(ctx, PR_INIT);
         REANN_CUDA_TRY(ctx, launch_init_coef(s, nl, ctx->d_c0));
     }
-    const size_t lw = (size_t)(LMAX + 1) * NPHI * NORB;
+    const bool pairs = ctx->model.pairs;
+    const size_t lw = (size_t)(LMAX + 1) * NPHI * ctx->model.n_orb();
+    const int64_t nf = nl->n_feat;
     // forward: Eq. 1 then Eq. 2, re-using the same list in every layer (Sec. 2.2)
     for (int t = 0; t < T; ++t) {
         float* coef_t = nl->coef + (size_t)t * ne * NPHI;
-        float* rho_t = nl->rho + (size_t)t * n * NFEAT;
+        float* rho_t = nl->rho + (size_t)t * n * nf;
         float* bck_t = nl->bck + (size_t)t * n * NB;
         if (t > 0) {
             ProfScope p(ctx, PR_GATHER);  // ghost slots receive their owners' coefficients (Fig. 4a)
@@ -758,7 +778,7 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
         }
         {
             ProfScope p(ctx, PR_DENSITY_FWD);
-            REANN_CUDA_TRY(ctx, launch_density_fwd(s, nl, ctx->radial, ctx->d_W + t * lw, coef_t, rho_t, bck_t));
+            REANN_CUDA_TRY(ctx, launch_density_fwd(s, nl, ctx->radial, ctx->d_W + t * lw, coef_t, rho_t, bck_t, pairs));
         }
         ProfScope p(ctx, PR_MLP_FWD);
         const bool energy_net = t == T - 1;
@@ -768,7 +788,7 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
             REANN_CUDA_TRY(ctx, launch_mlp_fwd_tc(s, nl, ctx->tc, t, energy_net, ctx->precision == REANN_MLP_BF16X3,
                                                   rho_t, out, out_stride, ctx->d_flags));
         else
-            REANN_CUDA_TRY(ctx, launch_mlp_fwd_f32(s, nl, ctx->nets, t, energy_net, rho_t, out, out_stride));
+            REANN_CUDA_TRY(ctx, launch_mlp_fwd_f32(s, nl, ctx->nets, t, energy_net, rho_t, out, out_stride, pairs));
     }
     {
         ProfScope p(ctx, PR_ENERGY);
@@ -782,7 +802,7 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
     if (vir) REANN_CUDA_TRY(ctx, cudaMemsetAsync(vir, 0, sizeof(float) * n * 9, s));
     for (int t = T - 1; t >= 0; --t) {
         const float* coef_t = nl->coef + (size_t)t * ne * NPHI;
-        const float* rho_t = nl->rho + (size_t)t * n * NFEAT;
+        const float* rho_t = nl->rho + (size_t)t * n * nf;
         const float* bck_t = nl->bck + (size_t)t * n * NB;
         {
             ProfScope p(ctx, PR_MLP_BWD);
@@ -791,11 +811,12 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
                                                       ctx->precision == REANN_MLP_BF16X3, rho_t, nl->cbar, nl->rhobar,
                                                       ctx->d_flags));
             else
-                REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, rho_t, nl->cbar, nl->rhobar));
+                REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, rho_t, nl->cbar, nl->rhobar,
+                                                       pairs));
         }
         {
             ProfScope p(ctx, PR_BBAR);
-            REANN_CUDA_TRY(ctx, launch_bbar(s, nl, ctx->d_W + t * lw, bck_t, nl->rhobar, nl->bbar));
+            REANN_CUDA_TRY(ctx, launch_bbar(s, nl, ctx->d_W + t * lw, bck_t, nl->rhobar, nl->bbar, pairs));
         }
         {
             ProfScope p(ctx, PR_GATHER);  // ghost slots receive their owners' adjoints (vector-Jacobian product)
@@ -1088,7 +1109,8 @@ extern "C" int reann_get_layer(reann_ctx* ctx, const reann_nlist* nl, int layer,
     if (!ctx || !nl || layer < 0 || layer >= nl->T) return set_error(ctx, REANN_E_ARG, "bad layer");
     const int64_t n = nl->n, ne = nl->n + nl->g_cap;
     if (rho)
-        REANN_CUDA_TRY(ctx, launch_unpermute_rows(ctx->stream, nl, nl->rho + (size_t)layer * n * NFEAT, NFEAT, rho, NFEAT));
+        REANN_CUDA_TRY(ctx, launch_unpermute_rows(ctx->stream, nl, nl->rho + (size_t)layer * n * nl->n_feat, nl->n_feat,
+                                                  rho, nl->n_feat));
     if (coef)
         REANN_CUDA_TRY(ctx, launch_unpermute_rows(ctx->stream, nl, nl->coef + (size_t)layer * ne * NPHI, NPHI, coef, NPHI));
     return REANN_OK;

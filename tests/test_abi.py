@@ -73,6 +73,22 @@ def test_model_create_validates_on_host(libpath):
         binding.reann_model_create(spec3)
 
 
+def test_pair_feature_model_validates_on_host(libpath):
+    from paper_2505_06711_gb300 import binding
+    from synth import make_model
+
+    spec = make_model(T=3, pairs=True)
+    assert spec.n_orb == 8 and spec.n_feat == 108
+    m = binding.reann_model_create(spec)  # dispatches to reann_model_create_ex
+    binding.reann_model_free(m)
+    with pytest.raises(binding.ReannError):
+        binding.reann_model_create_ex(spec, 0)  # a pair parameter vector read as Eq. 1's layout
+    with pytest.raises(binding.ReannError):
+        binding.reann_model_create_ex(make_model(T=3), 1)  # n_orb 16 with pair features
+    with pytest.raises(binding.ReannError):
+        binding.reann_model_create_ex(spec, 2)
+
+
 def test_ctx_without_device_fails_cleanly(libpath):
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
