@@ -30,6 +30,11 @@ constexpr int MLP_TILE = 64;  // rows per FP32 network tile
 
 // Internal angular order: 1, x, y, z, xx, yy, zz, xy, xz, yz.
 // l(a), multinomial weight l!/(lx! ly! lz!) and parity (-1)^l.
+#ifdef __CUDACC__
+__device__ __forceinline__ int ang_l(int a) { return a == 0 ? 0 : (a < 4 ? 1 : 2); }
+__device__ __forceinline__ float ang_w(int a) { return a >= 7 ? 2.f : 1.f; }
+__device__ __forceinline__ float ang_sign(int a) { return (a >= 1 && a <= 3) ? -1.f : 1.f; }
+#endif
 
 // Device-side error flags (ctx->d_flags)
 enum Flag {
@@ -318,6 +323,7 @@ cudaError_t launch_mlp_bwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTab
                               bool split, const float* rho, const float* ybar, float* rhobar, int* flags);
 
 cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
-                               const float* rho, const float* ybar, float* rhobar, bool pairs = false);
+                               const float* rho, const float* ybar, float* rhobar, bool pairs = false,
+                               const float* Wt = nullptr, const float* bck = nullptr, float* bbar = nullptr);
 
 }  // namespace reann

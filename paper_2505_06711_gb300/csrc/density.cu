@@ -32,9 +32,6 @@ constexpr int kWarps = 8;          // warps per block
 constexpr int kAtomsPerWarp = 8;   // quads per warp
 constexpr int kBStride = 84;       // padded per-atom row in shared memory (16 B aligned)
 
-__device__ __forceinline__ int ang_l(int a) { return a == 0 ? 0 : (a < 4 ? 1 : 2); }
-__device__ __forceinline__ float ang_w(int a) { return a >= 7 ? 2.f : 1.f; }
-__device__ __forceinline__ float ang_sign(int a) { return (a >= 1 && a <= 3) ? -1.f : 1.f; }
 
 struct Edge {
     float x, y, z, d;

@@ -207,10 +207,15 @@ __device__ __forceinline__ void cp_async16(float* dst, const float* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 
-template <int OUT, int FIN>
+// BBAR (Eq. 1's squares only): instead of writing rhobar, go on to the density
+// adjoint's first step for the tile's rows, bbar_{a,m} = sum_k 2 w_a g_{a,k}
+// rhobar_{l,k} W_{l,m,k} with g = b W recomputed from the b checkpoint (bck), and
+// write bbar (the separate bbar kernel's work, without the rhobar round trip).
+template <int OUT, int FIN, bool BBAR>
 __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __restrict__ tiles,
                                                const float* __restrict__ rho, const float* __restrict__ ybar,
-                                               float* __restrict__ rhobar) {
+                                               float* __restrict__ rhobar, const float* __restrict__ Wt,
+                                               const float* __restrict__ bck, float* __restrict__ bbar) {
     extern __shared__ __align__(16) float sm[];
     float* sW1 = sm;                  // FIN x 64, later W1^T 64 x FIN
     float* sW2 = sW1 + FIN * H1;      // 64 x 64, later W2^T
@@ -219,7 +224,8 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
     float* sb2 = sb1 + H1;            // 64
     float* sY = sb2 + H2;             // 64 x 8
     float* sG = sY + kR * 8;          // input rows (stride FIN + 4), h1, z2bar, z1bar (stride LDH)
-    float* sZ1 = sG + abuf<FIN>();    // 64 x 68: z1
+    float* sZ1 = sG + abuf<FIN>();    // 64 x 68: z1, then rhobar (BBAR)
+    float* sWc = sZ1 + kR * LDH;      // (L+1) x N_phi x N_orb contraction W^t (BBAR)
     const int tid = threadIdx.x;
     const Tile tl = tiles[blockIdx.x];
     if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list
@@ -229,6 +235,8 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
     for (int i = tid; i < OUT * H2; i += kT) sW3t[i] = w.W3t[i];
     for (int i = tid; i < H1; i += kT) sb1[i] = w.b1[i];
     for (int i = tid; i < H2; i += kT) sb2[i] = w.b2[i];
+    if (BBAR)
+        for (int i = tid; i < (LMAX + 1) * NPHI * NORB; i += kT) sWc[i] = Wt[i];
     for (int i = tid; i < kR * OUT; i += kT) {
         const int r = i / OUT, o = i % OUT;
         sY[r * 8 + o] = (OUT == 1) ? 1.f : (r < tl.nrows ? ybar[(size_t)(tl.row0 + r) * OUT + o] : 0.f);
@@ -309,10 +317,42 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int r = 4 * ty + i;
-            if (r < tl.nrows)
+            if (BBAR) {
+                *reinterpret_cast<float4*>(sZ1 + r * LDH + 4 * cg) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            } else if (r < tl.nrows) {
                 *reinterpret_cast<float4*>(rhobar + (size_t)(tl.row0 + r) * FIN + 4 * cg) =
                     make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            }
         }
+    }
+    if (!BBAR) return;
+    __syncthreads();
+    // four threads per row, angular terms a = q, q + 4, q + 8
+    const int r = tid >> 2, q = tid & 3;
+    if (r >= tl.nrows) return;
+    const size_t row = (size_t)(tl.row0 + r);
+    const float* rb = sZ1 + r * LDH;
+    for (int a = q; a < NANG; a += 4) {
+        const int l = ang_l(a);
+        const float4 b0 = __ldg(reinterpret_cast<const float4*>(bck + row * NB + a * NPHI));
+        const float4 b1 = __ldg(reinterpret_cast<const float4*>(bck + row * NB + a * NPHI + 4));
+        const float bm[NPHI] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        float o[NPHI];
+#pragma unroll
+        for (int m = 0; m < NPHI; ++m) o[m] = 0.f;
+        const float two_w = 2.f * ang_w(a);
+#pragma unroll 4
+        for (int k = 0; k < NORB; ++k) {
+            float g = 0.f;
+#pragma unroll
+            for (int m = 0; m < NPHI; ++m) g = fmaf(bm[m], sWc[(l * NPHI + m) * NORB + k], g);
+            const float gb = two_w * g * rb[l * NORB + k];
+#pragma unroll
+            for (int m = 0; m < NPHI; ++m) o[m] = fmaf(gb, sWc[(l * NPHI + m) * NORB + k], o[m]);
+        }
+        float* dst = bbar + row * NB + a * NPHI;
+        *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<float4*>(dst + 4) = make_float4(o[4], o[5], o[6], o[7]);
     }
 }
 
@@ -320,7 +360,8 @@ template <int FIN>
 constexpr size_t fwd_smem() { return sizeof(float) * (FIN * H1 + H1 * H2 + H2 * 8 + H1 + H2 + 8 + abuf<FIN>()); }
 template <int FIN>
 constexpr size_t bwd_smem() {
-    return sizeof(float) * (FIN * H1 + H1 * H2 + 8 * H2 + H1 + H2 + kR * 8 + abuf<FIN>() + kR * LDH);
+    return sizeof(float) * (FIN * H1 + H1 * H2 + 8 * H2 + H1 + H2 + kR * 8 + abuf<FIN>() + kR * LDH +
+                            (LMAX + 1) * NPHI * NORB);
 }
 
 void ensure_attrs() {
@@ -333,13 +374,18 @@ void ensure_attrs() {
     if (dev < 64 && ((done >> dev) & 1)) return;
     cudaFuncSetAttribute(k_mlp_fwd<1, NFEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<NFEAT>());
     cudaFuncSetAttribute(k_mlp_fwd<NPHI, NFEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<NFEAT>());
-    cudaFuncSetAttribute(k_mlp_bwd<1, NFEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<NFEAT>());
-    cudaFuncSetAttribute(k_mlp_bwd<NPHI, NFEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<NFEAT>());
+    cudaFuncSetAttribute(k_mlp_bwd<1, NFEAT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<NFEAT>());
+    cudaFuncSetAttribute(k_mlp_bwd<NPHI, NFEAT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bwd_smem<NFEAT>());
+    cudaFuncSetAttribute(k_mlp_bwd<1, NFEAT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<NFEAT>());
+    cudaFuncSetAttribute(k_mlp_bwd<NPHI, NFEAT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bwd_smem<NFEAT>());
     cudaFuncSetAttribute(k_mlp_fwd<1, NFEAT_P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<NFEAT_P>());
     cudaFuncSetAttribute(k_mlp_fwd<NPHI, NFEAT_P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)fwd_smem<NFEAT_P>());
-    cudaFuncSetAttribute(k_mlp_bwd<1, NFEAT_P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<NFEAT_P>());
-    cudaFuncSetAttribute(k_mlp_bwd<NPHI, NFEAT_P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_mlp_bwd<1, NFEAT_P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bwd_smem<NFEAT_P>());
+    cudaFuncSetAttribute(k_mlp_bwd<NPHI, NFEAT_P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)bwd_smem<NFEAT_P>());
     if (dev < 64) done |= (uint64_t)1 << dev;
 }
@@ -373,21 +419,33 @@ cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetT
 }
 
 cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
-                               const float* rho, const float* ybar, float* rhobar, bool pairs) {
+                               const float* rho, const float* ybar, float* rhobar, bool pairs, const float* Wt,
+                               const float* bck, float* bbar) {
     const int nt = (int)nl->tiles_h.size();
     if (nt == 0) return cudaSuccess;
     ensure_attrs();
     const NetsOfLayer ln = layer_nets(nets, t);
     if (pairs) {
         if (energy)
-            k_mlp_bwd<1, NFEAT_P><<<nt, kT, bwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, ybar, rhobar);
+            k_mlp_bwd<1, NFEAT_P, false><<<nt, kT, bwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, ybar, rhobar, nullptr,
+                                                                           nullptr, nullptr);
         else
-            k_mlp_bwd<NPHI, NFEAT_P><<<nt, kT, bwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, ybar, rhobar);
+            k_mlp_bwd<NPHI, NFEAT_P, false><<<nt, kT, bwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, ybar, rhobar,
+                                                                              nullptr, nullptr, nullptr);
+    } else if (bbar) {
+        if (energy)
+            k_mlp_bwd<1, NFEAT, true><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar, Wt, bck,
+                                                                       bbar);
+        else
+            k_mlp_bwd<NPHI, NFEAT, true><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar, Wt,
+                                                                          bck, bbar);
     } else {
         if (energy)
-            k_mlp_bwd<1, NFEAT><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar);
+            k_mlp_bwd<1, NFEAT, false><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar, nullptr,
+                                                                        nullptr, nullptr);
         else
-            k_mlp_bwd<NPHI, NFEAT><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar);
+            k_mlp_bwd<NPHI, NFEAT, false><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar,
+                                                                           nullptr, nullptr, nullptr);
     }
     return cudaGetLastError();
 }

@@ -810,11 +810,14 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
                 REANN_CUDA_TRY(ctx, launch_mlp_bwd_tc(s, nl, ctx->tc, t, t == T - 1,
                                                       ctx->precision == REANN_MLP_BF16X3, rho_t, nl->cbar, nl->rhobar,
                                                       ctx->d_flags));
+            else if (!pairs)  // the FP32 backward networks also take the bbar step (fused)
+                REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, rho_t, nl->cbar, nl->rhobar,
+                                                       false, ctx->d_W + t * lw, bck_t, nl->bbar));
             else
                 REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, rho_t, nl->cbar, nl->rhobar,
-                                                       pairs));
+                                                       true));
         }
-        {
+        if (ctx->precision != REANN_MLP_FP32 || pairs) {
             ProfScope p(ctx, PR_BBAR);
             REANN_CUDA_TRY(ctx, launch_bbar(s, nl, ctx->d_W + t * lw, bck_t, nl->rhobar, nl->bbar, pairs));
         }
