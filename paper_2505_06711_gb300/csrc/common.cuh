@@ -48,6 +48,14 @@ enum Flag {
     NFLAGS = 8
 };
 
+// Ghost slots filled by their owners: ghost slot g (row base + g) copies owned
+// row i for g in [goff[i], goff[i+1]) (the single-domain list enumerates each
+// atom's images contiguously), g < gcap.  goff == nullptr: the caller gathers.
+struct GhostOut {
+    const int32_t* goff = nullptr;
+    int64_t base = 0, gcap = 0;
+};
+
 // Named regions of the optional per-kernel event profile (reann_ctx_profile).
 enum ProfRegion {
     PR_REBUILD = 0,
@@ -215,6 +223,7 @@ struct reann_nlist {
     // spatial decomposition into virtual ranks (reann_build_nlist_decomposed):
     // per rank its local atoms, ghost slots, and ghost slots owned by another rank
     bool decomposed = false;
+    bool ghosts_by_owner = false;  // ghost slots of owned row i are [goff[i], goff[i+1]) (single-domain build)
     int rank_grid[3] = {1, 1, 1};
     std::vector<int64_t> rank_local, rank_ghost, rank_remote;
     std::vector<void*> allocs;
@@ -302,7 +311,7 @@ cudaError_t launch_gather_ghost_rows(cudaStream_t s, const reann_nlist* nl, floa
 cudaError_t launch_density_fwd(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* W, const float* coef,
                                float* rho, float* bck, bool pairs = false);
 cudaError_t launch_bbar(cudaStream_t s, const reann_nlist* nl, const float* W, const float* bck, const float* rhobar,
-                        float* bbar, bool pairs = false);
+                        float* bbar, bool pairs = false, GhostOut gh = {});
 cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* coef,
                                const float* bbar, float* cbar, float* grad, bool want_cbar, int* flags,
                                float* vir = nullptr);
@@ -315,15 +324,15 @@ cudaError_t launch_unpermute_rows(cudaStream_t s, const reann_nlist* nl, const f
 
 // atomic networks, FP32 SIMT (mlp_fp32.cu)
 cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
-                               const float* rho, float* out, int out_stride, bool pairs = false);
+                               const float* rho, float* out, int out_stride, bool pairs = false, GhostOut gh = {});
 // atomic networks, BF16 on tcgen05 tensor cores (mlp_tc.cu)
 cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
-                              bool split, const float* rho, float* out, int out_stride, int* flags);
+                              bool split, const float* rho, float* out, int out_stride, int* flags, GhostOut gh = {});
 cudaError_t launch_mlp_bwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
                               bool split, const float* rho, const float* ybar, float* rhobar, int* flags);
 
 cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
                                const float* rho, const float* ybar, float* rhobar, bool pairs = false,
-                               const float* Wt = nullptr, const float* bck = nullptr, float* bbar = nullptr);
+                               const float* Wt = nullptr, const float* bck = nullptr, float* bbar = nullptr, GhostOut gh = {});
 
 }  // namespace reann

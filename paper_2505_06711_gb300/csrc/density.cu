@@ -256,9 +256,24 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_density_fwd(int64_t n, int s
 // bbar_{a,m} = sum_k gbar_{a,k} W_{l(a),m,k}, g recomputed from the b checkpoint, with
 //   squares:  gbar_{a,k} = 2 w_a g_{a,k} rhobar_{l,k}
 //   pairs:    gbar_{a,k} = w_a sum_k' R_{kk'} g_{a,k'},  R_{kk'} = rhobar_{l,(min,max)} (x 2 on the diagonal)
+__device__ __forceinline__ void store_bbar(float* __restrict__ bbar, int64_t atom, int a, const float out[NPHI],
+                                           const GhostOut& gh) {
+    const float4 o0 = make_float4(out[0], out[1], out[2], out[3]), o1 = make_float4(out[4], out[5], out[6], out[7]);
+    float* dst = bbar + (size_t)atom * NB + a * NPHI;
+    *reinterpret_cast<float4*>(dst) = o0;
+    *reinterpret_cast<float4*>(dst + 4) = o1;
+    if (gh.goff)  // the atom's ghost images carry its bbar
+        for (int64_t g = gh.goff[atom]; g < gh.goff[atom + 1] && g < gh.gcap; ++g) {
+            float* gd = bbar + (size_t)(gh.base + g) * NB + a * NPHI;
+            *reinterpret_cast<float4*>(gd) = o0;
+            *reinterpret_cast<float4*>(gd + 4) = o1;
+        }
+}
+
 template <bool PAIRS>
 __global__ void __launch_bounds__(256) k_bbar(int64_t n, const float* __restrict__ Wt, const float* __restrict__ bck,
-                                              const float* __restrict__ rhobar, float* __restrict__ bbar) {
+                                              const float* __restrict__ rhobar, float* __restrict__ bbar,
+                                              GhostOut gh) {
     constexpr int KO = PAIRS ? NORB_P : NORB;
     __shared__ __align__(16) float sW[(LMAX + 1) * NPHI * KO];
     for (int i = threadIdx.x; i < (LMAX + 1) * NPHI * KO; i += blockDim.x) sW[i] = Wt[i];
@@ -299,9 +314,7 @@ __global__ void __launch_bounds__(256) k_bbar(int64_t n, const float* __restrict
 #pragma unroll
                 for (int k = 0; k < NORB_P; ++k) out[m] = fmaf(wa * gb[k], sW[(l * NPHI + m) * KO + k], out[m]);
             }
-            float* dst = bbar + (size_t)atom * NB + a * NPHI;
-            *reinterpret_cast<float4*>(dst) = make_float4(out[0], out[1], out[2], out[3]);
-            *reinterpret_cast<float4*>(dst + 4) = make_float4(out[4], out[5], out[6], out[7]);
+            store_bbar(bbar, atom, a, out, gh);
         }
         return;
     }
@@ -332,9 +345,7 @@ __global__ void __launch_bounds__(256) k_bbar(int64_t n, const float* __restrict
                 out[m] = fmaf(gb[0], w.x, fmaf(gb[1], w.y, fmaf(gb[2], w.z, fmaf(gb[3], w.w, out[m]))));
             }
         }
-        float* dst = bbar + (size_t)atom * NB + a * NPHI;
-        *reinterpret_cast<float4*>(dst) = make_float4(out[0], out[1], out[2], out[3]);
-        *reinterpret_cast<float4*>(dst + 4) = make_float4(out[4], out[5], out[6], out[7]);
+        store_bbar(bbar, atom, a, out, gh);
     }
 }
 
@@ -674,11 +685,11 @@ cudaError_t launch_density_fwd(cudaStream_t s, const reann_nlist* nl, const Radi
 }
 
 cudaError_t launch_bbar(cudaStream_t s, const reann_nlist* nl, const float* W, const float* bck, const float* rhobar,
-                        float* bbar, bool pairs) {
+                        float* bbar, bool pairs, GhostOut gh) {
     if (pairs)
-        k_bbar<true><<<blocks_for(nl->n * 4, 256), 256, 0, s>>>(nl->n, W, bck, rhobar, bbar);
+        k_bbar<true><<<blocks_for(nl->n * 4, 256), 256, 0, s>>>(nl->n, W, bck, rhobar, bbar, gh);
     else
-        k_bbar<false><<<blocks_for(nl->n * 4, 256), 256, 0, s>>>(nl->n, W, bck, rhobar, bbar);
+        k_bbar<false><<<blocks_for(nl->n * 4, 256), 256, 0, s>>>(nl->n, W, bck, rhobar, bbar, gh);
     return cudaGetLastError();
 }
 

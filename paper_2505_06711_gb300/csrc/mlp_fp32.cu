@@ -123,7 +123,7 @@ __device__ __forceinline__ int w3_row(int k) {
 template <int OUT, int FIN>
 __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __restrict__ tiles,
                                                const float* __restrict__ rho, float* __restrict__ out,
-                                               int out_stride) {
+                                               int out_stride, GhostOut gh) {
     extern __shared__ __align__(16) float sm[];
     float* sW1 = sm;                 // FIN x 64
     float* sW2 = sW1 + FIN * H1;     // 64 x 64
@@ -189,9 +189,17 @@ __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __
     } else {
         const int r = 4 * ty + (tx >> 2), o = 2 * (tx & 3);
         if (r < tl.nrows) {
-            float* dst = out + (size_t)(tl.row0 + r) * out_stride + o;
-            dst[0] = v[0] + sb3[o];
-            dst[1] = v[1] + sb3[o + 1];
+            const int64_t i = tl.row0 + r;
+            const float y0 = v[0] + sb3[o], y1 = v[1] + sb3[o + 1];
+            float* dst = out + (size_t)i * out_stride + o;
+            dst[0] = y0;
+            dst[1] = y1;
+            if (gh.goff)  // the row's ghost images get the same coefficients (Fig. 4a)
+                for (int64_t g = gh.goff[i]; g < gh.goff[i + 1] && g < gh.gcap; ++g) {
+                    float* gd = out + (size_t)(gh.base + g) * out_stride + o;
+                    gd[0] = y0;
+                    gd[1] = y1;
+                }
         }
     }
 }
@@ -215,7 +223,7 @@ template <int OUT, int FIN, bool BBAR>
 __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __restrict__ tiles,
                                                const float* __restrict__ rho, const float* __restrict__ ybar,
                                                float* __restrict__ rhobar, const float* __restrict__ Wt,
-                                               const float* __restrict__ bck, float* __restrict__ bbar) {
+                                               const float* __restrict__ bck, float* __restrict__ bbar, GhostOut gh) {
     extern __shared__ __align__(16) float sm[];
     float* sW1 = sm;                  // FIN x 64, later W1^T 64 x FIN
     float* sW2 = sW1 + FIN * H1;      // 64 x 64, later W2^T
@@ -350,9 +358,16 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
 #pragma unroll
             for (int m = 0; m < NPHI; ++m) o[m] = fmaf(gb, sWc[(l * NPHI + m) * NORB + k], o[m]);
         }
+        const float4 o0 = make_float4(o[0], o[1], o[2], o[3]), o1 = make_float4(o[4], o[5], o[6], o[7]);
         float* dst = bbar + row * NB + a * NPHI;
-        *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
-        *reinterpret_cast<float4*>(dst + 4) = make_float4(o[4], o[5], o[6], o[7]);
+        *reinterpret_cast<float4*>(dst) = o0;
+        *reinterpret_cast<float4*>(dst + 4) = o1;
+        if (gh.goff)  // the row's ghost images carry its bbar (reverse exchange)
+            for (int64_t g = gh.goff[row]; g < gh.goff[row + 1] && g < gh.gcap; ++g) {
+                float* gd = bbar + (size_t)(gh.base + g) * NB + a * NPHI;
+                *reinterpret_cast<float4*>(gd) = o0;
+                *reinterpret_cast<float4*>(gd + 4) = o1;
+            }
     }
 }
 
@@ -399,28 +414,28 @@ NetsOfLayer layer_nets(const NetTable& t, int layer) {
 }  // namespace
 
 cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
-                               const float* rho, float* out, int out_stride, bool pairs) {
+                               const float* rho, float* out, int out_stride, bool pairs, GhostOut gh) {
     const int nt = (int)nl->tiles_h.size();
     if (nt == 0) return cudaSuccess;
     ensure_attrs();
     const NetsOfLayer ln = layer_nets(nets, t);
     if (pairs) {
         if (energy)
-            k_mlp_fwd<1, NFEAT_P><<<nt, kT, fwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, out, out_stride);
+            k_mlp_fwd<1, NFEAT_P><<<nt, kT, fwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, out, out_stride, gh);
         else
-            k_mlp_fwd<NPHI, NFEAT_P><<<nt, kT, fwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, out, out_stride);
+            k_mlp_fwd<NPHI, NFEAT_P><<<nt, kT, fwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, out, out_stride, gh);
     } else {
         if (energy)
-            k_mlp_fwd<1, NFEAT><<<nt, kT, fwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, out, out_stride);
+            k_mlp_fwd<1, NFEAT><<<nt, kT, fwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, out, out_stride, gh);
         else
-            k_mlp_fwd<NPHI, NFEAT><<<nt, kT, fwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, out, out_stride);
+            k_mlp_fwd<NPHI, NFEAT><<<nt, kT, fwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, out, out_stride, gh);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
                                const float* rho, const float* ybar, float* rhobar, bool pairs, const float* Wt,
-                               const float* bck, float* bbar) {
+                               const float* bck, float* bbar, GhostOut gh) {
     const int nt = (int)nl->tiles_h.size();
     if (nt == 0) return cudaSuccess;
     ensure_attrs();
@@ -428,24 +443,24 @@ cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetT
     if (pairs) {
         if (energy)
             k_mlp_bwd<1, NFEAT_P, false><<<nt, kT, bwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, ybar, rhobar, nullptr,
-                                                                           nullptr, nullptr);
+                                                                           nullptr, nullptr, GhostOut{});
         else
             k_mlp_bwd<NPHI, NFEAT_P, false><<<nt, kT, bwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, ybar, rhobar,
-                                                                              nullptr, nullptr, nullptr);
+                                                                              nullptr, nullptr, nullptr, GhostOut{});
     } else if (bbar) {
         if (energy)
             k_mlp_bwd<1, NFEAT, true><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar, Wt, bck,
-                                                                       bbar);
+                                                                       bbar, gh);
         else
             k_mlp_bwd<NPHI, NFEAT, true><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar, Wt,
-                                                                          bck, bbar);
+                                                                          bck, bbar, gh);
     } else {
         if (energy)
             k_mlp_bwd<1, NFEAT, false><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar, nullptr,
-                                                                        nullptr, nullptr);
+                                                                        nullptr, nullptr, GhostOut{});
         else
             k_mlp_bwd<NPHI, NFEAT, false><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar,
-                                                                           nullptr, nullptr, nullptr);
+                                                                           nullptr, nullptr, nullptr, GhostOut{});
     }
     return cudaGetLastError();
 }

@@ -319,7 +319,7 @@ __device__ __forceinline__ void dsilu_to_tile(uint32_t tmem, int warp, int cg, i
 template <int OUT, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_fwd(TcLayer nets, const Tile* __restrict__ tiles,
                                                            const float* __restrict__ rho, float* __restrict__ out,
-                                                           int out_stride, int* __restrict__ flags) {
+                                                           int out_stride, int* __restrict__ flags, GhostOut gh) {
     using L = FwdSmem<SPLIT>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::BAR);  // [0] weights, [1] MMA
@@ -376,9 +376,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_fwd(TcLayer nets, const 
         float v[16];
         tmem_ld16(lane_addr(tmem, warp, 128), v);
         if (r < tl.nrows) {
-            float* o = out + (size_t)(tl.row0 + r) * out_stride;
+            const int64_t row = tl.row0 + r;
+            float* o = out + (size_t)row * out_stride;
 #pragma unroll
             for (int i = 0; i < OUT; ++i) o[i] = v[i] + w.b3[i];
+            if (OUT > 1 && gh.goff)  // the row's ghost images get the same coefficients
+                for (int64_t g = gh.goff[row]; g < gh.goff[row + 1] && g < gh.gcap; ++g) {
+                    float* go = out + (size_t)(gh.base + g) * out_stride;
+#pragma unroll
+                    for (int i = 0; i < OUT; ++i) go[i] = v[i] + w.b3[i];
+                }
         }
     }
     teardown(tmem);
@@ -519,8 +526,8 @@ void ensure_tc_attrs() {
 
 template <int OUT, bool SPLIT>
 void fwd_launch(cudaStream_t s, int nt, const TcLayer& l, const Tile* tiles, const float* rho, float* out,
-                int out_stride, int* flags) {
-    k_mlp_tc_fwd<OUT, SPLIT><<<nt, kThreads, FwdSmem<SPLIT>::REQUEST, s>>>(l, tiles, rho, out, out_stride, flags);
+                int out_stride, int* flags, GhostOut gh) {
+    k_mlp_tc_fwd<OUT, SPLIT><<<nt, kThreads, FwdSmem<SPLIT>::REQUEST, s>>>(l, tiles, rho, out, out_stride, flags, gh);
 }
 
 template <int OUT, bool SPLIT>
@@ -532,16 +539,16 @@ void bwd_launch(cudaStream_t s, int nt, const TcLayer& l, const Tile* tiles, con
 }  // namespace
 
 cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
-                              bool split, const float* rho, float* out, int out_stride, int* flags) {
+                              bool split, const float* rho, float* out, int out_stride, int* flags, GhostOut gh) {
     const int nt = (int)nl->tiles128_h.size();
     if (nt == 0) return cudaSuccess;
     ensure_tc_attrs();
     const TcLayer l = layer_of(nets, t);
     if (energy)
-        (split ? fwd_launch<1, true> : fwd_launch<1, false>)(s, nt, l, nl->tiles128, rho, out, out_stride, flags);
+        (split ? fwd_launch<1, true> : fwd_launch<1, false>)(s, nt, l, nl->tiles128, rho, out, out_stride, flags, gh);
     else
         (split ? fwd_launch<NPHI, true> : fwd_launch<NPHI, false>)(s, nt, l, nl->tiles128, rho, out, out_stride,
-                                                                    flags);
+                                                                    flags, gh);
     return cudaGetLastError();
 }
 

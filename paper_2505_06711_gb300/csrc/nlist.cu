@@ -625,6 +625,7 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
     if (ctx->h_flags[FLAG_GEOM]) return set_error(ctx, REANN_E_GEOM, "non-finite atom position");
     for (int e = 0; e <= nl->n_elem; ++e) nl->elem_start[e] = es[e];
     nl->g = G;
+    nl->ghosts_by_owner = true;  // k_ghosts enumerates each atom's images contiguously at goff[i]
     // capacity with headroom so that rebuilds after atom motion fit
     nl->g_cap = G + G / 4 + 64;
     const int64_t next = n + nl->g_cap;

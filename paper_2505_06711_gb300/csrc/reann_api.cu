@@ -767,12 +767,14 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
     const bool pairs = ctx->model.pairs;
     const size_t lw = (size_t)(LMAX + 1) * NPHI * ctx->model.n_orb();
     const int64_t nf = nl->n_feat;
+    // single-domain lists: owners write their ghost rows (no gather launches); otherwise gather
+    const GhostOut gh = nl->ghosts_by_owner ? GhostOut{nl->w.goff, n, nl->g_cap} : GhostOut{};
     // forward: Eq. 1 then Eq. 2, re-using the same list in every layer (Sec. 2.2)
     for (int t = 0; t < T; ++t) {
         float* coef_t = nl->coef + (size_t)t * ne * NPHI;
         float* rho_t = nl->rho + (size_t)t * n * nf;
         float* bck_t = nl->bck + (size_t)t * n * NB;
-        if (t > 0) {
+        if (t > 0 && !gh.goff) {
             ProfScope p(ctx, PR_GATHER);  // ghost slots receive their owners' coefficients (Fig. 4a)
             REANN_CUDA_TRY(ctx, launch_gather_ghost_rows(s, nl, coef_t, NPHI));
         }
@@ -786,9 +788,9 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
         const int out_stride = energy_net ? 1 : NPHI;
         if (ctx->precision != REANN_MLP_FP32)
             REANN_CUDA_TRY(ctx, launch_mlp_fwd_tc(s, nl, ctx->tc, t, energy_net, ctx->precision == REANN_MLP_BF16X3,
-                                                  rho_t, out, out_stride, ctx->d_flags));
+                                                  rho_t, out, out_stride, ctx->d_flags, gh));
         else
-            REANN_CUDA_TRY(ctx, launch_mlp_fwd_f32(s, nl, ctx->nets, t, energy_net, rho_t, out, out_stride, pairs));
+            REANN_CUDA_TRY(ctx, launch_mlp_fwd_f32(s, nl, ctx->nets, t, energy_net, rho_t, out, out_stride, pairs, gh));
     }
     {
         ProfScope p(ctx, PR_ENERGY);
@@ -812,16 +814,16 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
                                                       ctx->d_flags));
             else if (!pairs)  // the FP32 backward networks also take the bbar step (fused)
                 REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, rho_t, nl->cbar, nl->rhobar,
-                                                       false, ctx->d_W + t * lw, bck_t, nl->bbar));
+                                                       false, ctx->d_W + t * lw, bck_t, nl->bbar, gh));
             else
                 REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, rho_t, nl->cbar, nl->rhobar,
                                                        true));
         }
         if (ctx->precision != REANN_MLP_FP32 || pairs) {
             ProfScope p(ctx, PR_BBAR);
-            REANN_CUDA_TRY(ctx, launch_bbar(s, nl, ctx->d_W + t * lw, bck_t, nl->rhobar, nl->bbar, pairs));
+            REANN_CUDA_TRY(ctx, launch_bbar(s, nl, ctx->d_W + t * lw, bck_t, nl->rhobar, nl->bbar, pairs, gh));
         }
-        {
+        if (!gh.goff) {
             ProfScope p(ctx, PR_GATHER);  // ghost slots receive their owners' adjoints (vector-Jacobian product)
             REANN_CUDA_TRY(ctx, launch_gather_ghost_rows(s, nl, nl->bbar, NB));
         }
