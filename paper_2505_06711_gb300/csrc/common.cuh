@@ -80,6 +80,7 @@ enum ProfRegion {
 // atomic energy by the same amount).
 struct Radial {
     float rc, rc2;
+    float inv_rc_hi, inv_rc_lo;  // 1 / r_c as a float pair
     float alpha_hi, alpha_lo;  // alpha
     float tad_hi, tad_lo;      // 2 alpha Delta, Delta = r_c / (N_phi - 1)
     float mu_hi[NPHI], mu_lo[NPHI];      // Gaussian centres m Delta

@@ -75,18 +75,20 @@ __device__ __forceinline__ void gaussians(const Radial& R, float d, float gs[NPH
     }
 }
 
-// f_c(d) = (cos(pi d/r_c)/2 + 1/2)^2 evaluated as cos^4(pi x / 2), x = d / r_c by
-// an IEEE division (no rounded 1/r_c or pi constant: near r_c the cutoff's
-// logarithmic derivative is large, so a rounded constant would bias every atom),
-// and without the cancellation of 1/2 + cos/2 near d = r_c.
-// dfc = -(2 pi / r_c) cos^3 sin (half angle).
+// f_c(d) = (cos(pi d/r_c)/2 + 1/2)^2 evaluated as cos^4(pi x / 2), x = d / r_c
+// taken with 1/r_c as a float pair (d inv_hi + d inv_lo: within an ulp of the
+// correctly rounded quotient and without the one-sided error of a rounded 1/r_c,
+// which near r_c, where the cutoff's logarithmic derivative is large, would
+// bias every atom), no rounded pi constant, and no cancellation of 1/2 + cos/2
+// near d = r_c.  dfc = -(2 pi / r_c) cos^3 sin (half angle).
 __device__ __forceinline__ void cutoff(const Radial& R, float d, float& fc, float& dfc) {
     float s, c;
-    const float x = __fdiv_rn(d, R.rc);
+    const float x = fmaf(d, R.inv_rc_hi, d * R.inv_rc_lo);
     sincospif(0.5f * x, &s, &c);
     const float c2 = c * c;
     fc = c2 * c2;
-    dfc = __fdiv_rn(-6.28318530717959f * c2 * c * s, R.rc);
+    const float u = -6.28318530717959f * c2 * c * s;
+    dfc = fmaf(u, R.inv_rc_hi, u * R.inv_rc_lo);
 }
 
 __device__ __forceinline__ void monomials(float x, float y, float z, float A[NANG]) {

@@ -255,6 +255,7 @@ extern "C" int reann_ctx_create(const reann_model* model, void* cuda_stream, rea
     };
     R.rc = (float)M.r_c;
     R.rc2 = (float)(M.r_c * M.r_c);
+    split(1.0 / M.r_c, R.inv_rc_hi, R.inv_rc_lo);
     split(M.alpha, R.alpha_hi, R.alpha_lo);
     const double delta = M.r_c / (NPHI - 1);
     split(2.0 * M.alpha * delta, R.tad_hi, R.tad_lo);
