@@ -463,8 +463,11 @@ def region_flops(region: str, n_atoms: int, n_live: int, T: int, launches: int) 
 
 
 def launches_per_step(T: int) -> int:
-    """Library kernels per step: rebuild 15, evaluation 3 + (3T - 1) + 2 + 4T + 1."""
-    return 15 + 3 + (3 * T - 1) + 2 + 4 * T + 1
+    """Library kernels per step (FP32 networks, single-domain list): rebuild 13
+    (wrap, 2 x 4 sort kernels, gather, scan, ghosts + extended keys, search),
+    evaluation 3 (refresh, live edges, c0) + 2T forward (density, network) + 2
+    (energy) + 2T reverse (network with bbar, density adjoint) + 1 (outputs)."""
+    return 13 + 3 + 2 * T + 2 + 2 * T + 1
 
 
 def cpu_baseline(structure, spec):

@@ -12,7 +12,7 @@
 //   2. counting sort by key -> internal order (element-major so the atomic
 //      networks see contiguous per-element tiles, spatially sorted inside an
 //      element so neighbour gathers stay local);
-//   3. enumerate ghost images (count, scan, fill);
+//   3. enumerate ghost images (count while gathering, scan, fill while keying);
 //   4. bin owned + ghost slots into an extended cell grid (counting sort);
 //   5. warp per owned atom: scan the stencil bins, FP32 pre-test with a
 //      margin, FP64 exact test for pairs near r_c + skin, ballot-compacted
@@ -65,11 +65,15 @@ __device__ __forceinline__ int64_t ghosts_in_use(const int32_t* g_count, int64_t
 // 1. wrap + key (caller order)
 __global__ void k_wrap_key(const int* __restrict__ gate, int64_t n, const double* __restrict__ pos, const int32_t* __restrict__ species, int n_elem,
                            CellGeom g, double* __restrict__ xw, double* __restrict__ fw, int32_t* __restrict__ mw,
-                           int32_t* __restrict__ key, int* __restrict__ flags) {
+                           int32_t* __restrict__ key, int* __restrict__ flags, double* __restrict__ ref) {
     if (gate && *gate == 0) return;  // rebuild not needed this step
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double x[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    // the positions of this build, for the moved-by-more-than-skin/2 test
+    ref[3 * i] = x[0];
+    ref[3 * i + 1] = x[1];
+    ref[3 * i + 2] = x[2];
     int sp = species[i];
     bool bad = !(isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]));
     if (sp < 0 || sp >= n_elem) {
@@ -219,28 +223,8 @@ __global__ void k_bucket_rank(const int* __restrict__ gate, int64_t n, const int
     }
 }
 
-// 2. gather per-atom arrays into internal order
-__global__ void k_gather_internal(const int* __restrict__ gate, int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ xw_c,
-                                  const double* __restrict__ fw_c, const int32_t* __restrict__ mw_c,
-                                  const int32_t* __restrict__ sp_c, double* __restrict__ xw, double* __restrict__ fw,
-                                  int32_t* __restrict__ mw, int32_t* __restrict__ sp) {
-    if (gate && *gate == 0) return;  // rebuild not needed this step
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int c = perm[i];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        xw[3 * i + k] = xw_c[3 * (int64_t)c + k];
-        fw[3 * i + k] = fw_c[3 * (int64_t)c + k];
-        mw[3 * i + k] = mw_c[3 * (int64_t)c + k];
-    }
-    sp[i] = sp_c[c];
-}
-
-// 3. ghost images: fractional coordinate within (-reach, 1 + reach) on every axis.
-// The admissible shifts of one axis form an interval (the test is monotone in
-// the shift), so each axis is tested once per shift and only the admissible
-// box is enumerated, in the order a, b, c.
+// admissible image shifts of one axis: those keeping f + a within (-reach, 1 + reach),
+// an interval because the test is monotone in a
 __device__ __forceinline__ void halo_interval(const CellGeom& g, int k, double f, int& lo, int& hi) {
     lo = 1;
     hi = 0;
@@ -253,58 +237,39 @@ __device__ __forceinline__ void halo_interval(const CellGeom& g, int k, double f
     }
 }
 
-template <bool FILL>
-__global__ void k_ghosts(const int* __restrict__ gate, int64_t n, CellGeom g, const double* __restrict__ fw, const int32_t* __restrict__ goff,
-                         int32_t* __restrict__ gcnt, int32_t* __restrict__ owner, int32_t* __restrict__ shift,
-                         int64_t g_cap, int* __restrict__ flags) {
+// 2. gather per-atom arrays into internal order
+// (also each atom's number of ghost images: the product of its per-axis intervals
+// minus the zero shift, which wrapped coordinates in [0, 1) always admit)
+__global__ void k_gather_internal(const int* __restrict__ gate, int64_t n, CellGeom g, const int32_t* __restrict__ perm,
+                                  const double* __restrict__ xw_c, const double* __restrict__ fw_c,
+                                  const int32_t* __restrict__ mw_c, const int32_t* __restrict__ sp_c,
+                                  double* __restrict__ xw, double* __restrict__ fw, int32_t* __restrict__ mw,
+                                  int32_t* __restrict__ sp, int32_t* __restrict__ gcnt) {
     if (gate && *gate == 0) return;  // rebuild not needed this step
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int lo[3], hi[3];
+    int c = perm[i];
+    int cnt = 1;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) halo_interval(g, k, fw[3 * i + k], lo[k], hi[k]);
-    if (!FILL) {
-        // the zero shift always lies in the interval (wrapped coordinates are in [0, 1))
-        gcnt[i] = (hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1) - 1;
-        return;
+    for (int k = 0; k < 3; ++k) {
+        xw[3 * i + k] = xw_c[3 * (int64_t)c + k];
+        const double f = fw_c[3 * (int64_t)c + k];
+        fw[3 * i + k] = f;
+        mw[3 * i + k] = mw_c[3 * (int64_t)c + k];
+        int lo, hi;
+        halo_interval(g, k, f, lo, hi);
+        cnt *= hi - lo + 1;
     }
-    int cnt = 0;
-    const int64_t o = goff[i];
-    for (int a = lo[0]; a <= hi[0]; ++a)
-        for (int b = lo[1]; b <= hi[1]; ++b)
-            for (int c = lo[2]; c <= hi[2]; ++c) {
-                if (a == 0 && b == 0 && c == 0) continue;
-                const int64_t q = o + cnt;
-                if (q < g_cap) {
-                    owner[q] = (int32_t)i;
-                    shift[q] = pack_shift(a, b, c);
-                } else {
-                    atomicOr(&flags[FLAG_GHOST_OVERFLOW], 1);
-                }
-                ++cnt;
-            }
+    sp[i] = sp_c[c];
+    gcnt[i] = cnt - 1;
 }
 
-// 4. extended binning of owned + ghost slots (unused ghost capacity sorts last)
-__global__ void k_ext_key(const int* __restrict__ gate, int64_t n, const int32_t* __restrict__ g_count, int64_t g_cap, CellGeom g,
-                          const double* __restrict__ xw, const double* __restrict__ fw,
-                          const int32_t* __restrict__ owner, const int32_t* __restrict__ shift,
-                          int32_t* __restrict__ key, float4* __restrict__ p32, int32_t dead_key) {
-    if (gate && *gate == 0) return;  // rebuild not needed this step
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n + g_cap) return;
-    const int64_t G = ghosts_in_use(g_count, g_cap);
-    if (s >= n + G) {
-        key[s] = dead_key;
-        p32[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
-    }
-    int64_t o = s;
-    int a = 0, b = 0, c = 0;
-    if (s >= n) {
-        o = owner[s - n];
-        unpack_shift(shift[s - n], a, b, c);
-    }
+// 3-4. ghost images (fractional coordinate within (-reach, 1 + reach) on every
+// axis) and the extended binning of owned + ghost slots.
+// Extended key and FP32 position of slot (owner o, image shift (a, b, c)):
+__device__ __forceinline__ void ext_slot(const CellGeom& g, const double* __restrict__ xw, const double* __restrict__ fw,
+                                         int64_t o, int a, int b, int c, int32_t* __restrict__ key,
+                                         float4* __restrict__ p32, int64_t s) {
     double f[3] = {fw[3 * o] + a, fw[3 * o + 1] + b, fw[3 * o + 2] + c};
     int bx[3];
 #pragma unroll
@@ -313,6 +278,44 @@ __global__ void k_ext_key(const int* __restrict__ gate, int64_t n, const int32_t
     double sv[3];
     shift_vec(g, a, b, c, sv);
     p32[s] = make_float4((float)(xw[3 * o] + sv[0]), (float)(xw[3 * o + 1] + sv[1]), (float)(xw[3 * o + 2] + sv[2]), 0.f);
+}
+
+// 3-4. ghost images and the extended binning, one thread per slot of [0, n + g_cap):
+// owned slot i keys itself and fills its images' slots [goff[i], goff[i+1])
+// (owner, shift, key, FP32 position) in the order a, b, c of the per-axis
+// intervals; unused ghost capacity sorts last.
+__global__ void k_ghosts_ext(const int* __restrict__ gate, int64_t n, CellGeom g, const double* __restrict__ xw,
+                             const double* __restrict__ fw, const int32_t* __restrict__ goff, int64_t g_cap,
+                             int32_t* __restrict__ owner, int32_t* __restrict__ shift, int32_t* __restrict__ key,
+                             float4* __restrict__ p32, int32_t dead_key, int* __restrict__ flags) {
+    if (gate && *gate == 0) return;  // rebuild not needed this step
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n + g_cap) return;
+    if (s >= n) {
+        if (s >= n + ghosts_in_use(goff + n, g_cap)) {
+            key[s] = dead_key;
+            p32[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        return;  // slots in use are written by their owners
+    }
+    ext_slot(g, xw, fw, s, 0, 0, 0, key, p32, s);
+    int lo[3], hi[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) halo_interval(g, k, fw[3 * s + k], lo[k], hi[k]);
+    int64_t q = goff[s];
+    for (int a = lo[0]; a <= hi[0]; ++a)
+        for (int b = lo[1]; b <= hi[1]; ++b)
+            for (int c = lo[2]; c <= hi[2]; ++c) {
+                if (a == 0 && b == 0 && c == 0) continue;
+                if (q < g_cap) {
+                    owner[q] = (int32_t)s;
+                    shift[q] = pack_shift(a, b, c);
+                    ext_slot(g, xw, fw, s, a, b, c, key, p32, n + q);
+                } else {
+                    atomicOr(&flags[FLAG_GHOST_OVERFLOW], 1);
+                }
+                ++q;
+            }
 }
 
 // 5. neighbour search: one warp per owned atom.  For each (x, y) column of the
@@ -492,12 +495,6 @@ __global__ void k_moved(int64_t n, const double* __restrict__ pos, const double*
     if (!(dx * dx + dy * dy + dz * dz <= thr2)) atomicOr(moved, 1);
 }
 
-__global__ void k_copy_ref(const int* __restrict__ gate, int64_t n3, const double* __restrict__ pos,
-                           double* __restrict__ ref) {
-    if (gate && *gate == 0) return;  // rebuild not needed this step
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n3) ref[i] = pos[i];
-}
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -552,13 +549,11 @@ static cudaError_t stage_sort_and_count(cudaStream_t s, reann_nlist* nl, const d
                                         const int* gate) {
     const int64_t n = nl->n;
     NlistScratch& w = nl->w;
-    k_copy_ref<<<blocks_for(3 * n, 256), 256, 0, s>>>(gate, 3 * n, pos, nl->pos_ref);
     k_wrap_key<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, pos, w.species_c, nl->n_elem, nl->geom, w.xw_c, w.fw_c, w.mw_c,
-                                                  w.key, flags);
+                                                  w.key, flags, nl->pos_ref);
     counting_sort(s, gate, n, owned_keys(nl), w.key, w.counts, w.start, w.scat, nl->perm, owned_keys(nl));
-    k_gather_internal<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, nl->perm, w.xw_c, w.fw_c, w.mw_c, w.species_c, w.xw, w.fw,
-                                                         nl->wrapm, nl->species);
-    k_ghosts<false><<<blocks_for(n, 256), 256, 0, s>>>(gate, n, nl->geom, w.fw, nullptr, w.gcnt, nullptr, nullptr, 0, flags);
+    k_gather_internal<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, nl->geom, nl->perm, w.xw_c, w.fw_c, w.mw_c, w.species_c,
+                                                         w.xw, w.fw, nl->wrapm, nl->species, w.gcnt);
     k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(gate, n, w.gcnt, w.goff);
     return cudaGetLastError();
 }
@@ -567,11 +562,9 @@ static cudaError_t stage_sort_and_count(cudaStream_t s, reann_nlist* nl, const d
 static cudaError_t stage_ghosts_and_bins(cudaStream_t s, reann_nlist* nl, int* flags, const int* gate) {
     const int64_t n = nl->n, next = n + nl->g_cap;
     NlistScratch& w = nl->w;
-    k_ghosts<true><<<blocks_for(n, 256), 256, 0, s>>>(gate, n, nl->geom, w.fw, w.goff, nullptr, nl->g_owner, nl->g_shift,
-                                                      nl->g_cap, flags);
     const int64_t nx = ext_bins(nl);
-    k_ext_key<<<blocks_for(next, 256), 256, 0, s>>>(gate, n, w.goff + n, nl->g_cap, nl->geom, w.xw, w.fw, nl->g_owner,
-                                                    nl->g_shift, w.ekey, w.p32, (int32_t)nx);
+    k_ghosts_ext<<<blocks_for(next, 256), 256, 0, s>>>(gate, n, nl->geom, w.xw, w.fw, w.goff, nl->g_cap, nl->g_owner,
+                                                       nl->g_shift, w.ekey, w.p32, (int32_t)nx, flags);
     counting_sort(s, gate, next, nx + 1, w.ekey, w.ecounts, w.estart, w.escat, w.eorder, nx, w.p32, w.p32s);
     return cudaGetLastError();
 }
