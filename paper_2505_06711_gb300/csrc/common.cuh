@@ -23,6 +23,13 @@ constexpr int NFEAT = (LMAX + 1) * NORB;  // 48
 constexpr int NORB_P = 8;
 constexpr int NFEAT_P = (LMAX + 1) * NORB_P * (NORB_P + 1) / 2;
 constexpr int NB = NANG * NPHI;           // 80 per-atom density partials b_{a,m}
+// Adjoint record of an atom (the reverse pass's per-atom row): 3 lines of
+// 128 B, line v / 4 holding value v of channel m at float 4 m + v % 4, with
+// values v = 0..9 the adjoint bbar_{a = v, m}, v = 10 the coefficient c_m of
+// the layer and v = 11 zero.  Channel m's 12 values are then 3 aligned float4s,
+// one per line, so the 8 lanes of an atom read one full line per load.
+constexpr int NREC = 3 * 4 * NPHI;  // 96 floats
+__host__ __device__ constexpr int rec_at(int v, int m) { return (v >> 2) * (4 * NPHI) + 4 * m + (v & 3); }
 constexpr int H1 = 64;
 constexpr int H2 = 64;
 constexpr int MAX_ELEM = 8;
@@ -55,6 +62,46 @@ struct GhostOut {
     const int32_t* goff = nullptr;
     int64_t base = 0, gcap = 0;
 };
+
+#ifdef __CUDACC__
+// Staging of a tile's records in shared memory: row stride 100 floats, so that
+// the 4 threads of a row writing value v of channel m (8 rows per warp) hit 32
+// distinct banks, and every row starts on a 16 B boundary.
+constexpr int kRecLd = NREC + 4;
+__device__ __forceinline__ void stage_rec(float* __restrict__ sRec, int r, int v, const float val[NPHI]) {
+#pragma unroll
+    for (int m = 0; m < NPHI; ++m) sRec[r * kRecLd + rec_at(v, m)] = val[m];
+}
+// Copies the staged records of rows row0 .. row0 + nrows - 1 to global memory
+// with float4 stores (whole 128 B lines), and to the rows' ghost images when
+// gh.goff is set.
+__device__ __forceinline__ void flush_rec(const float* __restrict__ sRec, int nrows, int64_t row0,
+                                          float* __restrict__ rec, const GhostOut& gh, int tid, int nthreads) {
+    constexpr int W4 = NREC / 4;
+    for (int i = tid; i < nrows * W4; i += nthreads) {
+        const int r = i / W4, c = i - r * W4;
+        const float4 x = *reinterpret_cast<const float4*>(sRec + r * kRecLd + 4 * c);
+        const int64_t row = row0 + r;
+        reinterpret_cast<float4*>(rec + (size_t)row * NREC)[c] = x;
+        if (gh.goff)
+            for (int64_t g = gh.goff[row]; g < gh.goff[row + 1] && g < gh.gcap; ++g)
+                reinterpret_cast<float4*>(rec + (size_t)(gh.base + g) * NREC)[c] = x;
+    }
+}
+
+// Values 10 and 11 of the record: the layer's coefficients c_m of `row`, and zero.
+__device__ __forceinline__ void rec_tail(const float* __restrict__ coef, int64_t row, int v, float val[NPHI]) {
+    if (v == NANG) {
+        const float4 c0 = __ldg(reinterpret_cast<const float4*>(coef + (size_t)row * NPHI));
+        const float4 c1 = __ldg(reinterpret_cast<const float4*>(coef + (size_t)row * NPHI + 4));
+        val[0] = c0.x, val[1] = c0.y, val[2] = c0.z, val[3] = c0.w;
+        val[4] = c1.x, val[5] = c1.y, val[6] = c1.z, val[7] = c1.w;
+    } else {
+#pragma unroll
+        for (int m = 0; m < NPHI; ++m) val[m] = 0.f;
+    }
+}
+#endif
 
 // Named regions of the optional per-kernel event profile (reann_ctx_profile).
 enum ProfRegion {
@@ -196,7 +243,7 @@ struct reann_nlist {
     float* bck = nullptr;          // T x N x 80
     float* eps = nullptr;          // N
     float* rhobar = nullptr;       // N x 48
-    float* bbar = nullptr;         // (N + g_cap) x 80
+    float* bbar = nullptr;         // (N + g_cap) x 96 adjoint records (bbar, c)
     float* cbar = nullptr;         // N x 8
     float* grad = nullptr;         // N x 3
     float* vir = nullptr;          // N x 9 per-atom virial (allocated on first request)
@@ -312,10 +359,9 @@ cudaError_t launch_gather_ghost_rows(cudaStream_t s, const reann_nlist* nl, floa
 cudaError_t launch_density_fwd(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* W, const float* coef,
                                float* rho, float* bck, bool pairs = false);
 cudaError_t launch_bbar(cudaStream_t s, const reann_nlist* nl, const float* W, const float* bck, const float* rhobar,
-                        float* bbar, bool pairs = false, GhostOut gh = {});
-cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* coef,
-                               const float* bbar, float* cbar, float* grad, bool want_cbar, int* flags,
-                               float* vir = nullptr);
+                        const float* coef, float* rec, bool pairs = false, GhostOut gh = {});
+cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* rec, float* cbar,
+                               float* grad, bool want_cbar, int* flags, float* vir = nullptr);
 cudaError_t upload_pair_table();
 cudaError_t launch_virial_sum(cudaStream_t s, const reann_nlist* nl, const float* vir, double* partial, double* out);
 cudaError_t launch_energy_sum(cudaStream_t s, const reann_nlist* nl, double* energy);
@@ -334,6 +380,7 @@ cudaError_t launch_mlp_bwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTab
 
 cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
                                const float* rho, const float* ybar, float* rhobar, bool pairs = false,
-                               const float* Wt = nullptr, const float* bck = nullptr, float* bbar = nullptr, GhostOut gh = {});
+                               const float* Wt = nullptr, const float* bck = nullptr, const float* coef = nullptr,
+                               float* rec = nullptr, GhostOut gh = {});
 
 }  // namespace reann

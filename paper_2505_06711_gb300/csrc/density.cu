@@ -111,6 +111,14 @@ __device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpre
 __constant__ unsigned char c_pair_k[NORB_P * (NORB_P + 1) / 2];
 __constant__ unsigned char c_pair_k2[NORB_P * (NORB_P + 1) / 2];
 
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 // ------------------------------------------------------------- forward ---
 // PAIRS = false: Eq. 1, rho_{l,k} = sum_{a in l} w_a g_{a,k}^2 over 16 orbitals.
 // PAIRS = true: the orbital-pair products rho_{l,(k,k')} = sum_{a in l} w_a g_{a,k} g_{a,k'},
@@ -126,7 +134,12 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_density_fwd(int64_t n, int s
                                                             float* __restrict__ bck) {
     constexpr int KO = PAIRS ? NORB_P : NORB;
     __shared__ __align__(16) float sW[(LMAX + 1) * NPHI * KO];
-    __shared__ __align__(16) float sB[kWarps][kAtomsPerWarp][kBStride];
+    // During the edge loop: two stages of a lane's next neighbours (hi, lo position
+    // and c of j), [stage][part][thread] float4; afterwards the b rows of the atoms.
+    constexpr int kStage = 2 * 4 * kWarps * 32 * 4;
+    static_assert(kStage >= kWarps * kAtomsPerWarp * kBStride, "b rows must fit in the staging area");
+    __shared__ __align__(16) float sU[kStage];
+    float4* stg = reinterpret_cast<float4*>(sU);
     for (int i = threadIdx.x; i < (LMAX + 1) * NPHI * KO; i += blockDim.x) sW[i] = Wt[i];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, q = lane & 3, slot = lane >> 2;
@@ -140,9 +153,28 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_density_fwd(int64_t n, int s
         const float4 hi_i = phi_hi[atom], lo_i = plo[atom];
         const int cnt = live_cnt[atom];
         const int32_t* row = live + (size_t)atom * stride;
+        constexpr int kT = kWarps * 32;
+        auto stage = [&](int st, int j) {
+            float4* d = stg + st * 4 * kT + threadIdx.x;
+            cp_async16(d, phi_hi + j);
+            cp_async16(d + kT, plo + j);
+            cp_async16(d + 2 * kT, coef + (size_t)j * NPHI);
+            cp_async16(d + 3 * kT, coef + (size_t)j * NPHI + 4);
+        };
+        // the lane's edges e = q, q + 4, ...: edge e + 4 is copied while edge e is
+        // computed, and the index of edge e + 8 is loaded
+        if (q < cnt) stage(0, row[q]);
+        cp_async_commit();
+        int j_nx = q + 4 < cnt ? row[q + 4] : 0;
+        int st = 0;
         for (int e = q; e < cnt; e += 4) {
-            const int j = row[e];
-            const float4 hj = phi_hi[j], lj = plo[j];
+            if (e + 4 < cnt) stage(st ^ 1, j_nx);
+            cp_async_commit();
+            j_nx = e + 8 < cnt ? row[e + 8] : 0;
+            cp_async_wait_prior();  // edge e's stage has landed
+            const float4* src = stg + st * 4 * kT + threadIdx.x;
+            const float4 hj = src[0], lj = src[kT], c0 = src[2 * kT], c1 = src[3 * kT];
+            st ^= 1;
             const float x = (hj.x - hi_i.x) + (lj.x - lo_i.x);
             const float y = (hj.y - hi_i.y) + (lj.y - lo_i.y);
             const float z = (hj.z - hi_i.z) + (lj.z - lo_i.z);
@@ -150,7 +182,6 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_density_fwd(int64_t n, int s
             float gs[NPHI], fc, dfc;
             gaussians(R, d, gs);
             cutoff(R, d, fc, dfc);
-            const float4 c0 = ldg4(coef + (size_t)j * NPHI), c1 = ldg4(coef + (size_t)j * NPHI + 4);
             const float cj[NPHI] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
             float tm[NPHI];
 #pragma unroll
@@ -163,6 +194,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_density_fwd(int64_t n, int s
                 for (int m = 0; m < NPHI; ++m) acc[a * NPHI + m] = fmaf(tm[m], A[a], acc[a * NPHI + m]);
         }
     }
+    cp_async_wait_all();
+    __syncthreads();  // the staging area becomes the b rows
     // butterfly reduce-scatter over the quad: lane q keeps b[20q, 20q+20)
     float r1[NB / 2];
     const bool hi_half = (q >> 1) & 1;
@@ -180,7 +213,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_density_fwd(int64_t n, int s
         const float keep = odd ? r1[NB / 4 + v] : r1[v];
         r2[v] = keep + __shfl_xor_sync(FULL, send, 1);
     }
-    float* sb = sB[warp][slot];
+    float* sb = sU + (warp * kAtomsPerWarp + slot) * kBStride;
 #pragma unroll
     for (int v = 0; v < NB / 4; v += 4) {
         const float4 w4 = make_float4(r2[v], r2[v + 1], r2[v + 2], r2[v + 3]);
@@ -258,38 +291,36 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_density_fwd(int64_t n, int s
 // bbar_{a,m} = sum_k gbar_{a,k} W_{l(a),m,k}, g recomputed from the b checkpoint, with
 //   squares:  gbar_{a,k} = 2 w_a g_{a,k} rhobar_{l,k}
 //   pairs:    gbar_{a,k} = w_a sum_k' R_{kk'} g_{a,k'},  R_{kk'} = rhobar_{l,(min,max)} (x 2 on the diagonal)
-__device__ __forceinline__ void store_bbar(float* __restrict__ bbar, int64_t atom, int a, const float out[NPHI],
-                                           const GhostOut& gh) {
-    const float4 o0 = make_float4(out[0], out[1], out[2], out[3]), o1 = make_float4(out[4], out[5], out[6], out[7]);
-    float* dst = bbar + (size_t)atom * NB + a * NPHI;
-    *reinterpret_cast<float4*>(dst) = o0;
-    *reinterpret_cast<float4*>(dst + 4) = o1;
-    if (gh.goff)  // the atom's ghost images carry its bbar
-        for (int64_t g = gh.goff[atom]; g < gh.goff[atom + 1] && g < gh.gcap; ++g) {
-            float* gd = bbar + (size_t)(gh.base + g) * NB + a * NPHI;
-            *reinterpret_cast<float4*>(gd) = o0;
-            *reinterpret_cast<float4*>(gd + 4) = o1;
-        }
-}
-
+// written into the atom's adjoint record with the layer's c (values 10, 11 of
+// the record); 4 threads per atom take values q, q + 4, q + 8.  The block's 64
+// records are staged in shared memory and stored as whole lines.
 template <bool PAIRS>
 __global__ void __launch_bounds__(256) k_bbar(int64_t n, const float* __restrict__ Wt, const float* __restrict__ bck,
-                                              const float* __restrict__ rhobar, float* __restrict__ bbar,
-                                              GhostOut gh) {
+                                              const float* __restrict__ rhobar, const float* __restrict__ coef,
+                                              float* __restrict__ rec, GhostOut gh) {
     constexpr int KO = PAIRS ? NORB_P : NORB;
     __shared__ __align__(16) float sW[(LMAX + 1) * NPHI * KO];
+    __shared__ __align__(16) float sRec[64 * kRecLd];
     for (int i = threadIdx.x; i < (LMAX + 1) * NPHI * KO; i += blockDim.x) sW[i] = Wt[i];
     __syncthreads();
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t atom = tid >> 2;
-    const int q = tid & 3;
-    if (atom >= n) return;
-    if constexpr (PAIRS) {
-        constexpr int KP = NORB_P * (NORB_P + 1) / 2;
-        for (int a = q; a < NANG; a += 4) {
-            const int l = ang_l(a);
-            const float4 b0 = ldg4(bck + (size_t)atom * NB + a * NPHI), b1 = ldg4(bck + (size_t)atom * NB + a * NPHI + 4);
-            const float bm[NPHI] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    const int64_t atom0 = (int64_t)blockIdx.x * 64;
+    const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
+    const int64_t atom = atom0 + r;
+    const int nrows = n - atom0 < 64 ? (int)(n - atom0) : 64;
+    for (int v = q; v < NREC / NPHI && r < nrows; v += 4) {
+        float out[NPHI];
+        if (v >= NANG) {
+            rec_tail(coef, atom, v, out);
+            stage_rec(sRec, r, v, out);
+            continue;
+        }
+        const int a = v, l = ang_l(a);
+        const float4 b0 = ldg4(bck + (size_t)atom * NB + a * NPHI), b1 = ldg4(bck + (size_t)atom * NB + a * NPHI + 4);
+        const float bm[NPHI] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int m = 0; m < NPHI; ++m) out[m] = 0.f;
+        if constexpr (PAIRS) {
+            constexpr int KP = NORB_P * (NORB_P + 1) / 2;
             float g[NORB_P], gb[NORB_P];
 #pragma unroll
             for (int k = 0; k < NORB_P; ++k) {
@@ -304,62 +335,54 @@ __global__ void __launch_bounds__(256) k_bbar(int64_t n, const float* __restrict
             for (int k = 0; k < NORB_P; ++k)
 #pragma unroll
                 for (int k2 = k; k2 < NORB_P; ++k2, ++p) {
-                    const float r = __ldg(rb + p);
-                    gb[k] = fmaf(r, g[k2], gb[k]);
-                    gb[k2] = fmaf(r, g[k], gb[k2]);
+                    const float rv = __ldg(rb + p);
+                    gb[k] = fmaf(rv, g[k2], gb[k]);
+                    gb[k2] = fmaf(rv, g[k], gb[k2]);
                 }
             const float wa = ang_w(a);
-            float out[NPHI];
 #pragma unroll
-            for (int m = 0; m < NPHI; ++m) {
-                out[m] = 0.f;
+            for (int m = 0; m < NPHI; ++m)
 #pragma unroll
                 for (int k = 0; k < NORB_P; ++k) out[m] = fmaf(wa * gb[k], sW[(l * NPHI + m) * KO + k], out[m]);
-            }
-            store_bbar(bbar, atom, a, out, gh);
-        }
-        return;
-    }
-    for (int a = q; a < NANG; a += 4) {
-        const int l = ang_l(a);
-        const float4 b0 = ldg4(bck + (size_t)atom * NB + a * NPHI), b1 = ldg4(bck + (size_t)atom * NB + a * NPHI + 4);
-        const float bm[NPHI] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-        float out[NPHI];
+        } else {
+            const float two_w = 2.f * ang_w(a);
 #pragma unroll
-        for (int m = 0; m < NPHI; ++m) out[m] = 0.f;
-        const float two_w = 2.f * ang_w(a);
+            for (int k4 = 0; k4 < NORB; k4 += 4) {
+                float g[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int k4 = 0; k4 < NORB; k4 += 4) {
-            float g[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int m = 0; m < NPHI; ++m) {
+                    const float4 w = ld4(sW + (l * NPHI + m) * NORB + k4);
+                    g[0] = fmaf(bm[m], w.x, g[0]);
+                    g[1] = fmaf(bm[m], w.y, g[1]);
+                    g[2] = fmaf(bm[m], w.z, g[2]);
+                    g[3] = fmaf(bm[m], w.w, g[3]);
+                }
+                const float4 rb = ldg4(rhobar + (size_t)atom * NFEAT + l * NORB + k4);
+                const float gb[4] = {two_w * g[0] * rb.x, two_w * g[1] * rb.y, two_w * g[2] * rb.z, two_w * g[3] * rb.w};
 #pragma unroll
-            for (int m = 0; m < NPHI; ++m) {
-                const float4 w = ld4(sW + (l * NPHI + m) * NORB + k4);
-                g[0] = fmaf(bm[m], w.x, g[0]);
-                g[1] = fmaf(bm[m], w.y, g[1]);
-                g[2] = fmaf(bm[m], w.z, g[2]);
-                g[3] = fmaf(bm[m], w.w, g[3]);
-            }
-            const float4 rb = ldg4(rhobar + (size_t)atom * NFEAT + l * NORB + k4);
-            const float gb[4] = {two_w * g[0] * rb.x, two_w * g[1] * rb.y, two_w * g[2] * rb.z, two_w * g[3] * rb.w};
-#pragma unroll
-            for (int m = 0; m < NPHI; ++m) {
-                const float4 w = ld4(sW + (l * NPHI + m) * NORB + k4);
-                out[m] = fmaf(gb[0], w.x, fmaf(gb[1], w.y, fmaf(gb[2], w.z, fmaf(gb[3], w.w, out[m]))));
+                for (int m = 0; m < NPHI; ++m) {
+                    const float4 w = ld4(sW + (l * NPHI + m) * NORB + k4);
+                    out[m] = fmaf(gb[0], w.x, fmaf(gb[1], w.y, fmaf(gb[2], w.z, fmaf(gb[3], w.w, out[m]))));
+                }
             }
         }
-        store_bbar(bbar, atom, a, out, gh);
+        stage_rec(sRec, r, v, out);
     }
+    __syncthreads();
+    flush_rec(sRec, nrows, atom0, rec, gh, threadIdx.x, blockDim.x);
 }
 
 // ---------------------------------------------------------- adjoint ------
+
 // Reverse pass (header formulas), laid out for coalesced gathers: 8
 // lanes per centre atom k (4 atoms per warp), lane m owning radial channel m.
 // Per batch of 8 live edges each lane first computes the geometry of one edge
 // (d, f_c, f_c', the 8 Gaussians) into shared memory; then every lane walks the
-// 8 edges and, for its channel m, gathers bbar_{j,a,m} (a = 0..9: per load the
-// 8 lanes read one contiguous 32 B sector of row j) and c_{j,m}, and
-// accumulates its share of dE/dr_k; cbar_{k,m} is lane m's own sum.  The
-// force is reduced over the 8 lanes once per atom.
+// 8 edges and, for its channel m, gathers bbar_{j,a,m} (a = 0..9) and c_{j,m}
+// from j's adjoint record (3 float4 loads per lane; per load the 8 lanes read
+// one full 128 B line of the record), and accumulates its share of dE/dr_k;
+// cbar_{k,m} is lane m's own sum.  The force is reduced over the 8 lanes once
+// per atom.
 constexpr int kAdjWarps = 8;
 constexpr int kAdjGroups = 4;  // centre atoms per warp
 // Edge record in shared memory: x y z 1/d | d fc fc' - | g_0..g_7 (16 floats).
@@ -378,46 +401,75 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
                                                                 const int32_t* __restrict__ live_cnt,
                                                                 const float4* __restrict__ phi_hi,
                                                                 const float4* __restrict__ plo,
-                                                                const float* __restrict__ coef,
-                                                                const float* __restrict__ bbar,
+                                                                const float* __restrict__ rec,
                                                                 float* __restrict__ cbar, float* __restrict__ grad,
                                                                 float* __restrict__ vir) {
     __shared__ __align__(16) float sGeo[kAdjWarps][kAdjGroups * kGroupStride];
+    __shared__ __align__(16) float4 sPos[2][kAdjWarps * 32];  // a lane's next edge: hi, lo position of j
+    __shared__ __align__(16) float4 sCen[kAdjWarps * kAdjGroups][2];  // hi, lo position of the centre atom
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, m = lane & 7, grp = lane >> 3;
     const int64_t atom = ((int64_t)blockIdx.x * kAdjWarps + warp) * kAdjGroups + grp;
     const bool valid = atom < n;
-    float bk[NANG];
-    float ck = 0.f;
-    int cnt = 0;
-    float4 hi_i = make_float4(0.f, 0.f, 0.f, 0.f), lo_i = hi_i;
-    const int32_t* row = live;
-    if (valid) {
+    // the 12 values of channel m in an atom's record: bbar_{0..9,m}, c_m, 0
+    auto load_rec = [&](int64_t r, float* v) {
+        const float* p = rec + (size_t)r * NREC + 4 * m;
 #pragma unroll
-        for (int a = 0; a < NANG; ++a) bk[a] = __ldg(bbar + (size_t)atom * NB + a * NPHI + m);
-        ck = __ldg(coef + (size_t)atom * NPHI + m);
+        for (int line = 0; line < 3; ++line) {
+            const float4 x = ldg4(p + line * 4 * NPHI);
+            v[4 * line] = x.x, v[4 * line + 1] = x.y, v[4 * line + 2] = x.z, v[4 * line + 3] = x.w;
+        }
+    };
+    float bk[12];
+    int cnt = 0;
+    const int32_t* row = live;
+    float4* cen = sCen[warp * kAdjGroups + grp];
+    if (valid) {
+        load_rec(atom, bk);
         cnt = live_cnt[atom];
-        hi_i = phi_hi[atom];
-        lo_i = plo[atom];
+        if (m < 2) cen[m] = (m == 0 ? phi_hi : plo)[atom];
         row = live + (size_t)atom * stride;
     } else {
 #pragma unroll
-        for (int a = 0; a < NANG; ++a) bk[a] = 0.f;
+        for (int a = 0; a < 12; ++a) bk[a] = 0.f;
     }
+    const float ck = bk[NANG];
     int cmax = cnt;
     cmax = max(cmax, __shfl_xor_sync(FULL, cmax, 8));
     cmax = max(cmax, __shfl_xor_sync(FULL, cmax, 16));
+    __syncwarp();  // the centre positions are visible to the group
     const float mu_hi = R.mu_hi[m], mu_lo = R.mu_lo[m], two_alpha = 2.f * R.alpha_hi;
     float* geo = sGeo[warp] + grp * kGroupStride;
+    float4* my_hi = &sPos[0][threadIdx.x];
+    float4* my_lo = &sPos[1][threadIdx.x];
     float gx = 0.f, gy = 0.f, gz = 0.f, cb = 0.f;
     float w[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) w[q] = 0.f;
+    // Pipeline across batches of 8 edges: while batch b is computed, the
+    // positions of batch b + 1 are copied into shared memory (cp.async), the
+    // indices of batch b + 2 are loaded, and the record of batch b + 1's first
+    // edge is gathered during b's last edge.
+    int j_cur = 0;
+    if (m < cnt) {
+        j_cur = row[m];
+        cp_async16(my_hi, phi_hi + j_cur);
+        cp_async16(my_lo, plo + j_cur);
+    }
+    cp_async_commit();
+    int j_nx = 8 + m < cnt ? row[8 + m] : 0;
+    float bjA[12], bjB[12];
+#pragma unroll
+    for (int a = 0; a < 12; ++a) bjA[a] = bjB[a] = 0.f;
+    {
+        const int js = __shfl_sync(FULL, j_cur, lane & ~7);
+        if (cnt > 0) load_rec(js, bjA);
+    }
     for (int e0 = 0; e0 < cmax; e0 += 8) {
-        // geometry of edge e0 + m, one edge per lane
-        int j = 0;
-        if (e0 + m < cnt) {
-            j = row[e0 + m];
-            const float4 hj = phi_hi[j], lj = plo[j];
+        const int ns = cnt - e0;
+        // geometry of edge e0 + m, one edge per lane, from the staged positions
+        cp_async_wait_all();
+        if (m < ns) {
+            const float4 hj = *my_hi, lj = *my_lo, hi_i = cen[0], lo_i = cen[1];
             const float x = (hj.x - hi_i.x) + (lj.x - lo_i.x);
             const float y = (hj.y - hi_i.y) + (lj.y - lo_i.y);
             const float z = (hj.z - hi_i.z) + (lj.z - lo_i.z);
@@ -427,27 +479,27 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
             cutoff(R, d, fc, dfc);
             float* g = geo + m * kGeoStride;
             *reinterpret_cast<float4*>(g) = make_float4(x, y, z, 1.f / d);
-            *reinterpret_cast<float4*>(g + 4) = make_float4(d, fc, dfc, 0.f);
+            *reinterpret_cast<float4*>(g + 4) = make_float4(d, fc, dfc, __int_as_float(j_cur));
             *reinterpret_cast<float4*>(g + 8) = make_float4(gs[0], gs[1], gs[2], gs[3]);
             *reinterpret_cast<float4*>(g + 12) = make_float4(gs[4], gs[5], gs[6], gs[7]);
         }
         __syncwarp();
-        const int ns = cnt - e0;
+        // this lane's slot has been read (its values are used above): stage the next batch
+        if (8 + m < ns) {
+            cp_async16(my_hi, phi_hi + j_nx);
+            cp_async16(my_lo, plo + j_nx);
+        }
+        cp_async_commit();
+        const int j_first_nx = __shfl_sync(FULL, j_nx, lane & ~7);
+        const int j_nx2 = 16 + m < ns ? row[e0 + 16 + m] : 0;
         // software pipeline over the batch: the gathers of edge s + 1 (register set
         // B, or A) are in flight while edge s (set A, or B) is computed
-        float bjA[NANG], bjB[NANG], cjA = 0.f, cjB = 0.f;
-#pragma unroll
-        for (int a = 0; a < NANG; ++a) bjA[a] = bjB[a] = 0.f;
-        auto gather = [&](int s, float* bj, float& cj) {
-            const int js = __shfl_sync(FULL, j, (lane & ~7) | s);
-            if (s < ns) {
-#pragma unroll
-                for (int a = 0; a < NANG; ++a) bj[a] = __ldg(bbar + (size_t)js * NB + m + a * NPHI);
-                cj = __ldg(coef + (size_t)js * NPHI + m);
-            }
+        auto gather = [&](int s, float* bj) {
+            if (s < ns) load_rec(__float_as_int(geo[s * kGeoStride + 7]), bj);
         };
-        auto edge = [&](int s, const float* bj, float cj) {
+        auto edge = [&](int s, const float* bj) {
             if (s >= ns) return;
+            const float cj = bj[NANG];
             const float* g = geo + s * kGeoStride;
             const float4 g0 = *reinterpret_cast<const float4*>(g);
             const float4 g1 = *reinterpret_cast<const float4*>(g + 4);
@@ -491,15 +543,19 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
                     for (int b = 0; b < 3; ++b) w[3 * a + b] = fmaf(-t3[a], r3[b], w[3 * a + b]);
             }
         };
-        gather(0, bjA, cjA);
 #pragma unroll
         for (int s = 0; s < 8; s += 2) {
-            gather(s + 1, bjB, cjB);
-            edge(s, bjA, cjA);
-            if (s + 2 < 8) gather(s + 2, bjA, cjA);
-            edge(s + 1, bjB, cjB);
+            gather(s + 1, bjB);
+            edge(s, bjA);
+            if (s + 2 < 8)
+                gather(s + 2, bjA);
+            else if (8 < ns)
+                load_rec(j_first_nx, bjA);  // the next batch's first edge
+            edge(s + 1, bjB);
         }
         __syncwarp();
+        j_cur = j_nx;
+        j_nx = j_nx2;
     }
 #pragma unroll
     for (int o = 1; o <= 4; o <<= 1) {
@@ -687,11 +743,11 @@ cudaError_t launch_density_fwd(cudaStream_t s, const reann_nlist* nl, const Radi
 }
 
 cudaError_t launch_bbar(cudaStream_t s, const reann_nlist* nl, const float* W, const float* bck, const float* rhobar,
-                        float* bbar, bool pairs, GhostOut gh) {
+                        const float* coef, float* rec, bool pairs, GhostOut gh) {
     if (pairs)
-        k_bbar<true><<<blocks_for(nl->n * 4, 256), 256, 0, s>>>(nl->n, W, bck, rhobar, bbar, gh);
+        k_bbar<true><<<blocks_for(nl->n * 4, 256), 256, 0, s>>>(nl->n, W, bck, rhobar, coef, rec, gh);
     else
-        k_bbar<false><<<blocks_for(nl->n * 4, 256), 256, 0, s>>>(nl->n, W, bck, rhobar, bbar, gh);
+        k_bbar<false><<<blocks_for(nl->n * 4, 256), 256, 0, s>>>(nl->n, W, bck, rhobar, coef, rec, gh);
     return cudaGetLastError();
 }
 
@@ -708,14 +764,14 @@ cudaError_t upload_pair_table() {
     return e;
 }
 
-cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* coef,
-                               const float* bbar, float* cbar, float* grad, bool want_cbar, int* flags, float* vir) {
+cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* rec, float* cbar,
+                               float* grad, bool want_cbar, int* flags, float* vir) {
     (void)flags;
     const int64_t per_block = kAdjWarps * kAdjGroups;
     const unsigned nb = blocks_for(nl->n, per_block);
 #define REANN_ADJ(C, V)                                                                                              \
     k_density_adj8<C, V><<<nb, kAdjWarps * 32, 0, s>>>(nl->n, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi,     \
-                                                      nl->pos_lo, coef, bbar, cbar, grad, vir)
+                                                      nl->pos_lo, rec, cbar, grad, vir)
     if (want_cbar && vir)
         REANN_ADJ(true, true);
     else if (want_cbar)

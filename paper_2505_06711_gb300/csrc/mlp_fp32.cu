@@ -218,12 +218,14 @@ __device__ __forceinline__ void cp_async16(float* dst, const float* src) {
 // BBAR (Eq. 1's squares only): instead of writing rhobar, go on to the density
 // adjoint's first step for the tile's rows, bbar_{a,m} = sum_k 2 w_a g_{a,k}
 // rhobar_{l,k} W_{l,m,k} with g = b W recomputed from the b checkpoint (bck), and
-// write bbar (the separate bbar kernel's work, without the rhobar round trip).
+// write the rows' adjoint records, bbar with the layer's c (the separate bbar
+// kernel's work, without the rhobar round trip).
 template <int OUT, int FIN, bool BBAR>
 __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __restrict__ tiles,
                                                const float* __restrict__ rho, const float* __restrict__ ybar,
                                                float* __restrict__ rhobar, const float* __restrict__ Wt,
-                                               const float* __restrict__ bck, float* __restrict__ bbar, GhostOut gh) {
+                                               const float* __restrict__ bck, const float* __restrict__ coef,
+                                               float* __restrict__ rec, GhostOut gh) {
     extern __shared__ __align__(16) float sm[];
     float* sW1 = sm;                  // FIN x 64, later W1^T 64 x FIN
     float* sW2 = sW1 + FIN * H1;      // 64 x 64, later W2^T
@@ -335,17 +337,23 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
     }
     if (!BBAR) return;
     __syncthreads();
-    // four threads per row, angular terms a = q, q + 4, q + 8
+    // four threads per row, record values v = q, q + 4, q + 8 (angular terms, then c and 0),
+    // staged in shared memory (W1^T, W2^T are no longer needed) and stored as whole lines
+    float* sRec = sW1;
     const int r = tid >> 2, q = tid & 3;
-    if (r >= tl.nrows) return;
     const size_t row = (size_t)(tl.row0 + r);
     const float* rb = sZ1 + r * LDH;
-    for (int a = q; a < NANG; a += 4) {
-        const int l = ang_l(a);
+    for (int v = q; v < NREC / NPHI && r < tl.nrows; v += 4) {
+        float o[NPHI];
+        if (v >= NANG) {
+            rec_tail(coef, row, v, o);
+            stage_rec(sRec, r, v, o);
+            continue;
+        }
+        const int a = v, l = ang_l(a);
         const float4 b0 = __ldg(reinterpret_cast<const float4*>(bck + row * NB + a * NPHI));
         const float4 b1 = __ldg(reinterpret_cast<const float4*>(bck + row * NB + a * NPHI + 4));
         const float bm[NPHI] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-        float o[NPHI];
 #pragma unroll
         for (int m = 0; m < NPHI; ++m) o[m] = 0.f;
         const float two_w = 2.f * ang_w(a);
@@ -358,18 +366,13 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
 #pragma unroll
             for (int m = 0; m < NPHI; ++m) o[m] = fmaf(gb, sWc[(l * NPHI + m) * NORB + k], o[m]);
         }
-        const float4 o0 = make_float4(o[0], o[1], o[2], o[3]), o1 = make_float4(o[4], o[5], o[6], o[7]);
-        float* dst = bbar + row * NB + a * NPHI;
-        *reinterpret_cast<float4*>(dst) = o0;
-        *reinterpret_cast<float4*>(dst + 4) = o1;
-        if (gh.goff)  // the row's ghost images carry its bbar (reverse exchange)
-            for (int64_t g = gh.goff[row]; g < gh.goff[row + 1] && g < gh.gcap; ++g) {
-                float* gd = bbar + (size_t)(gh.base + g) * NB + a * NPHI;
-                *reinterpret_cast<float4*>(gd) = o0;
-                *reinterpret_cast<float4*>(gd + 4) = o1;
-            }
+        stage_rec(sRec, r, v, o);
     }
+    __syncthreads();
+    flush_rec(sRec, tl.nrows, tl.row0, rec, gh, tid, kT);  // ghost images get the rows' records too (reverse exchange)
 }
+
+static_assert(NFEAT * H1 + H1 * H2 >= kR * kRecLd, "record staging must fit in the W1, W2 region");
 
 template <int FIN>
 constexpr size_t fwd_smem() { return sizeof(float) * (FIN * H1 + H1 * H2 + H2 * 8 + H1 + H2 + 8 + abuf<FIN>()); }
@@ -435,7 +438,7 @@ cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetT
 
 cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
                                const float* rho, const float* ybar, float* rhobar, bool pairs, const float* Wt,
-                               const float* bck, float* bbar, GhostOut gh) {
+                               const float* bck, const float* coef, float* rec, GhostOut gh) {
     const int nt = (int)nl->tiles_h.size();
     if (nt == 0) return cudaSuccess;
     ensure_attrs();
@@ -443,24 +446,24 @@ cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetT
     if (pairs) {
         if (energy)
             k_mlp_bwd<1, NFEAT_P, false><<<nt, kT, bwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, ybar, rhobar, nullptr,
-                                                                           nullptr, nullptr, GhostOut{});
+                                                                           nullptr, nullptr, nullptr, GhostOut{});
         else
             k_mlp_bwd<NPHI, NFEAT_P, false><<<nt, kT, bwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, ybar, rhobar,
-                                                                              nullptr, nullptr, nullptr, GhostOut{});
-    } else if (bbar) {
+                                                                              nullptr, nullptr, nullptr, nullptr, GhostOut{});
+    } else if (rec) {
         if (energy)
             k_mlp_bwd<1, NFEAT, true><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar, Wt, bck,
-                                                                       bbar, gh);
+                                                                       coef, rec, gh);
         else
             k_mlp_bwd<NPHI, NFEAT, true><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar, Wt,
-                                                                          bck, bbar, gh);
+                                                                          bck, coef, rec, gh);
     } else {
         if (energy)
             k_mlp_bwd<1, NFEAT, false><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar, nullptr,
-                                                                        nullptr, nullptr, GhostOut{});
+                                                                        nullptr, nullptr, nullptr, GhostOut{});
         else
             k_mlp_bwd<NPHI, NFEAT, false><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar,
-                                                                           nullptr, nullptr, nullptr, GhostOut{});
+                                                                           nullptr, nullptr, nullptr, nullptr, GhostOut{});
     }
     return cudaGetLastError();
 }

@@ -110,7 +110,7 @@ int alloc_eval_buffers(reann_ctx* ctx, reann_nlist* nl, const std::vector<std::a
     nl->bck = nl_alloc<float>(nl, (size_t)T * n * NB);
     nl->eps = nl_alloc<float>(nl, n);
     nl->rhobar = nl_alloc<float>(nl, (size_t)n * nl->n_feat);
-    nl->bbar = nl_alloc<float>(nl, (size_t)ne * NB);
+    nl->bbar = nl_alloc<float>(nl, (size_t)ne * NREC);  // adjoint records (bbar with c)
     nl->cbar = nl_alloc<float>(nl, (size_t)n * NPHI);
     nl->grad = nl_alloc<float>(nl, (size_t)n * 3);
     nl->n_partial = (int)((n + 2047) / 2048);
@@ -140,7 +140,7 @@ int alloc_eval_buffers(reann_ctx* ctx, reann_nlist* nl, const std::vector<std::a
         REANN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->tiles, nl->tiles_h.data(), sizeof(Tile) * nl->tiles_h.size(),
                                             cudaMemcpyHostToDevice, ctx->stream));
     // unused ghost capacity keeps finite values; no live edges before the first evaluation
-    REANN_CUDA_TRY(ctx, cudaMemsetAsync(nl->bbar, 0, sizeof(float) * ne * NB, ctx->stream));
+    REANN_CUDA_TRY(ctx, cudaMemsetAsync(nl->bbar, 0, sizeof(float) * ne * NREC, ctx->stream));
     REANN_CUDA_TRY(ctx, cudaMemsetAsync(nl->live_cnt, 0, sizeof(int32_t) * n, ctx->stream));
     return REANN_OK;
 }
@@ -815,21 +815,21 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
                                                       ctx->d_flags));
             else if (!pairs)  // the FP32 backward networks also take the bbar step (fused)
                 REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, rho_t, nl->cbar, nl->rhobar,
-                                                       false, ctx->d_W + t * lw, bck_t, nl->bbar, gh));
+                                                       false, ctx->d_W + t * lw, bck_t, coef_t, nl->bbar, gh));
             else
                 REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, rho_t, nl->cbar, nl->rhobar,
                                                        true));
         }
         if (ctx->precision != REANN_MLP_FP32 || pairs) {
             ProfScope p(ctx, PR_BBAR);
-            REANN_CUDA_TRY(ctx, launch_bbar(s, nl, ctx->d_W + t * lw, bck_t, nl->rhobar, nl->bbar, pairs, gh));
+            REANN_CUDA_TRY(ctx, launch_bbar(s, nl, ctx->d_W + t * lw, bck_t, nl->rhobar, coef_t, nl->bbar, pairs, gh));
         }
         if (!gh.goff) {
             ProfScope p(ctx, PR_GATHER);  // ghost slots receive their owners' adjoints (vector-Jacobian product)
-            REANN_CUDA_TRY(ctx, launch_gather_ghost_rows(s, nl, nl->bbar, NB));
+            REANN_CUDA_TRY(ctx, launch_gather_ghost_rows(s, nl, nl->bbar, NREC));
         }
         ProfScope p(ctx, PR_DENSITY_ADJ);
-        REANN_CUDA_TRY(ctx, launch_density_adj(s, nl, ctx->radial, coef_t, nl->bbar, nl->cbar, nl->grad, t >= 1,
+        REANN_CUDA_TRY(ctx, launch_density_adj(s, nl, ctx->radial, nl->bbar, nl->cbar, nl->grad, t >= 1,
                                                ctx->d_flags, vir));
     }
     ProfScope p(ctx, PR_OUTPUT);
