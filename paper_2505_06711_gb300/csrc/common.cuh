@@ -243,6 +243,7 @@ struct reann_nlist {
     float* bck = nullptr;          // T x N x 80
     float* eps = nullptr;          // N
     float* rhobar = nullptr;       // N x 48
+    float* dsave = nullptr;        // T x N x 128 SiLU'(z1), SiLU'(z2) of the FP32 networks
     float* bbar = nullptr;         // (N + g_cap) x 96 adjoint records (bbar, c)
     float* cbar = nullptr;         // N x 8
     float* grad = nullptr;         // N x 3
@@ -370,8 +371,9 @@ cudaError_t launch_unpermute_rows(cudaStream_t s, const reann_nlist* nl, const f
                                   int width);
 
 // atomic networks, FP32 SIMT (mlp_fp32.cu)
+// dsave (N x 128, optional): the forward keeps SiLU'(z1), SiLU'(z2) of every row for the backward
 cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
-                               const float* rho, float* out, int out_stride, bool pairs = false, GhostOut gh = {});
+                               const float* rho, float* out, int out_stride, bool pairs, GhostOut gh, float* dsave);
 // atomic networks, BF16 on tcgen05 tensor cores (mlp_tc.cu)
 cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
                               bool split, const float* rho, float* out, int out_stride, int* flags, GhostOut gh = {});
@@ -379,7 +381,7 @@ cudaError_t launch_mlp_bwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTab
                               bool split, const float* rho, const float* ybar, float* rhobar, int* flags);
 
 cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
-                               const float* rho, const float* ybar, float* rhobar, bool pairs = false,
+                               const float* dsave, const float* ybar, float* rhobar, bool pairs = false,
                                const float* Wt = nullptr, const float* bck = nullptr, const float* coef = nullptr,
                                float* rec = nullptr, GhostOut gh = {});
 

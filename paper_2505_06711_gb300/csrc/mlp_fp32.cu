@@ -119,11 +119,14 @@ __device__ __forceinline__ int w3_row(int k) {
 // ----------------------------------------------------------- forward ---
 // Shared memory: weights (31 KB) and one 64 x 68 activation buffer that holds
 // the input rows, then h1; h2 stays in registers and the output layer is a
-// half-warp reduction, so four blocks fit on an SM.
+// half-warp reduction, so four blocks fit on an SM.  With dsave, the row's
+// SiLU derivatives are kept for the reverse pass: dsave[row][0..63] =
+// SiLU'(z1), dsave[row][64..127] = SiLU'(z2).
+constexpr int kSave = H1 + H2;
 template <int OUT, int FIN>
 __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __restrict__ tiles,
                                                const float* __restrict__ rho, float* __restrict__ out,
-                                               int out_stride, GhostOut gh) {
+                                               int out_stride, GhostOut gh, float* __restrict__ dsave) {
     extern __shared__ __align__(16) float sm[];
     float* sW1 = sm;                 // FIN x 64
     float* sW2 = sW1 + FIN * H1;     // 64 x 64
@@ -152,6 +155,12 @@ __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = sb1[4 * tx + j];
     mma_4x4<FIN, ldx<FIN>(), H1>(sA, sW1, ty, tx, acc);
+    if (dsave)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (4 * ty + i < tl.nrows)
+                *reinterpret_cast<float4*>(dsave + (size_t)(tl.row0 + 4 * ty + i) * kSave + 4 * tx) =
+                    make_float4(dsilu(acc[i][0]), dsilu(acc[i][1]), dsilu(acc[i][2]), dsilu(acc[i][3]));
     __syncthreads();  // every thread is done reading the input rows
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -164,6 +173,12 @@ __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = sb2[4 * tx + j];
     mma_4x4<H1, LDH, H2>(sA, sW2, ty, tx, acc);
+    if (dsave)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (4 * ty + i < tl.nrows)
+                *reinterpret_cast<float4*>(dsave + (size_t)(tl.row0 + 4 * ty + i) * kSave + H1 + 4 * tx) =
+                    make_float4(dsilu(acc[i][0]), dsilu(acc[i][1]), dsilu(acc[i][2]), dsilu(acc[i][3]));
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -205,87 +220,58 @@ __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __
 }
 
 // ---------------------------------------------------------- backward ---
-// rhobar = W1 (dsilu(z1) * (W2 (dsilu(z2) * (W3 ybar))))   per row
-// Shared memory: the forward weights, replaced by their transposes (cp.async,
-// overlapping the z2bar step) once the forward recompute is done, and two
-// 64 x 68 activation buffers (input rows -> h1 -> z2bar -> z1bar, and z1), so
-// three blocks fit on an SM.
-__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-
+// rhobar = W1 (s1 * (W2 (s2 * (W3 ybar))))   per row, with s1 = SiLU'(z1) and
+// s2 = SiLU'(z2) kept by the forward (dsave), so nothing is recomputed.
+// Shared memory: the transposed weights, ybar, one 64 x 68 buffer (z2bar, then
+// z1bar) and, with BBAR, the rhobar rows and the contraction weights.
+//
 // BBAR (Eq. 1's squares only): instead of writing rhobar, go on to the density
 // adjoint's first step for the tile's rows, bbar_{a,m} = sum_k 2 w_a g_{a,k}
 // rhobar_{l,k} W_{l,m,k} with g = b W recomputed from the b checkpoint (bck), and
 // write the rows' adjoint records, bbar with the layer's c (the separate bbar
 // kernel's work, without the rhobar round trip).
+__device__ __forceinline__ float4 ld_save(const float* dsave, const Tile& tl, int r, int col) {
+    if (r >= tl.nrows) return make_float4(0.f, 0.f, 0.f, 0.f);
+    return __ldg(reinterpret_cast<const float4*>(dsave + (size_t)(tl.row0 + r) * kSave + col));
+}
+
 template <int OUT, int FIN, bool BBAR>
 __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __restrict__ tiles,
-                                               const float* __restrict__ rho, const float* __restrict__ ybar,
+                                               const float* __restrict__ dsave, const float* __restrict__ ybar,
                                                float* __restrict__ rhobar, const float* __restrict__ Wt,
                                                const float* __restrict__ bck, const float* __restrict__ coef,
                                                float* __restrict__ rec, GhostOut gh) {
     extern __shared__ __align__(16) float sm[];
-    float* sW1 = sm;                  // FIN x 64, later W1^T 64 x FIN
-    float* sW2 = sW1 + FIN * H1;      // 64 x 64, later W2^T
-    float* sW3t = sW2 + H1 * H2;      // OUT x 64 (8 rows reserved)
-    float* sb1 = sW3t + 8 * H2;       // 64
-    float* sb2 = sb1 + H1;            // 64
-    float* sY = sb2 + H2;             // 64 x 8
-    float* sG = sY + kR * 8;          // input rows (stride FIN + 4), h1, z2bar, z1bar (stride LDH)
-    float* sZ1 = sG + abuf<FIN>();    // 64 x 68: z1, then rhobar (BBAR)
-    float* sWc = sZ1 + kR * LDH;      // (L+1) x N_phi x N_orb contraction W^t (BBAR)
+    float* sW1t = sm;                 // W1^T: 64 x FIN
+    float* sW2t = sW1t + H1 * FIN;    // W2^T: 64 x 64
+    float* sW3t = sW2t + H1 * H2;     // W3^T: OUT x 64 (8 rows reserved)
+    float* sY = sW3t + 8 * H2;        // 64 x 8
+    float* sG = sY + kR * 8;          // z2bar, then z1bar (stride LDH)
+    float* sR = sG + kR * LDH;        // rhobar rows (BBAR, stride LDH)
+    float* sWc = sR + kR * LDH;       // (L+1) x N_phi x N_orb contraction W^t (BBAR)
     const int tid = threadIdx.x;
     const Tile tl = tiles[blockIdx.x];
     if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list
+    const int ty = tid >> 4, tx = tid & 15;
+    // the thread's SiLU derivatives, in flight while the weights are staged
+    float4 s1[4], s2[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        s2[i] = ld_save(dsave, tl, 4 * ty + i, H1 + 4 * tx);
+        s1[i] = ld_save(dsave, tl, 4 * ty + i, 4 * tx);
+    }
     const NetDev& w = nets.e[tl.elem];
-    copy_f4(sW1, w.W1, FIN * H1, tid);
-    copy_f4(sW2, w.W2, H1 * H2, tid);
+    copy_f4(sW1t, w.W1t, H1 * FIN, tid);
+    copy_f4(sW2t, w.W2t, H1 * H2, tid);
     for (int i = tid; i < OUT * H2; i += kT) sW3t[i] = w.W3t[i];
-    for (int i = tid; i < H1; i += kT) sb1[i] = w.b1[i];
-    for (int i = tid; i < H2; i += kT) sb2[i] = w.b2[i];
     if (BBAR)
         for (int i = tid; i < (LMAX + 1) * NPHI * NORB; i += kT) sWc[i] = Wt[i];
     for (int i = tid; i < kR * OUT; i += kT) {
         const int r = i / OUT, o = i % OUT;
         sY[r * 8 + o] = (OUT == 1) ? 1.f : (r < tl.nrows ? ybar[(size_t)(tl.row0 + r) * OUT + o] : 0.f);
     }
-    load_rows<FIN>(sG, rho, tl.row0, tl.nrows, tid);
     __syncthreads();
-    const int ty = tid >> 4, tx = tid & 15;
-    float acc[4][4];
-    // z1, h1
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = sb1[4 * tx + j];
-    mma_4x4<FIN, ldx<FIN>(), H1>(sG, sW1, ty, tx, acc);
-    __syncthreads();  // every thread is done reading the input rows
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        *reinterpret_cast<float4*>(sZ1 + (4 * ty + i) * LDH + 4 * tx) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-        *reinterpret_cast<float4*>(sG + (4 * ty + i) * LDH + 4 * tx) =
-            make_float4(silu(acc[i][0]), silu(acc[i][1]), silu(acc[i][2]), silu(acc[i][3]));
-    }
-    __syncthreads();
-    // z2
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = sb2[4 * tx + j];
-    mma_4x4<H1, LDH, H2>(sG, sW2, ty, tx, acc);
-    float z2[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) z2[i][j] = acc[i][j];
-    __syncthreads();  // everyone is done reading h1, W1 and W2
-    // bring in the transposes while z2bar is computed
-    for (int i = tid; i < H1 * H2 / 4; i += kT) cp_async16(sW2 + 4 * i, w.W2t + 4 * i);
-    for (int i = tid; i < H1 * FIN / 4; i += kT) cp_async16(sW1 + 4 * i, w.W1t + 4 * i);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    // z2bar = (ybar W3^T) * dsilu(z2) -> sG
+    // z2bar = (ybar W3^T) * s2 -> sG
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         float v[4] = {0.f, 0.f, 0.f, 0.f};
@@ -299,23 +285,21 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
             v[3] = fmaf(y, wv.w, v[3]);
         }
         *reinterpret_cast<float4*>(sG + (4 * ty + i) * LDH + 4 * tx) =
-            make_float4(v[0] * dsilu(z2[i][0]), v[1] * dsilu(z2[i][1]), v[2] * dsilu(z2[i][2]), v[3] * dsilu(z2[i][3]));
+            make_float4(v[0] * s2[i].x, v[1] * s2[i].y, v[2] * s2[i].z, v[3] * s2[i].w);
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    // z1bar = (z2bar W2^T) * dsilu(z1)
+    // z1bar = (z2bar W2^T) * s1
+    float acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    mma_4x4<H2, LDH, H1>(sG, sW2, ty, tx, acc);
+    mma_4x4<H2, LDH, H1>(sG, sW2t, ty, tx, acc);
     __syncthreads();  // everyone is done reading z2bar
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float4 z1 = *reinterpret_cast<const float4*>(sZ1 + (4 * ty + i) * LDH + 4 * tx);
+    for (int i = 0; i < 4; ++i)
         *reinterpret_cast<float4*>(sG + (4 * ty + i) * LDH + 4 * tx) = make_float4(
-            acc[i][0] * dsilu(z1.x), acc[i][1] * dsilu(z1.y), acc[i][2] * dsilu(z1.z), acc[i][3] * dsilu(z1.w));
-    }
+            acc[i][0] * s1[i].x, acc[i][1] * s1[i].y, acc[i][2] * s1[i].z, acc[i][3] * s1[i].w);
     __syncthreads();
     // rhobar = z1bar W1^T  (64 x FIN): FIN / 4 column groups of 4 over the 16 tx
     for (int cg = tx; cg < FIN / 4; cg += 16) {
@@ -323,12 +307,12 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-        mma_4x4<H1, LDH, FIN>(sG, sW1, ty, cg, acc);
+        mma_4x4<H1, LDH, FIN>(sG, sW1t, ty, cg, acc);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int r = 4 * ty + i;
             if (BBAR) {
-                *reinterpret_cast<float4*>(sZ1 + r * LDH + 4 * cg) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+                *reinterpret_cast<float4*>(sR + r * LDH + 4 * cg) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
             } else if (r < tl.nrows) {
                 *reinterpret_cast<float4*>(rhobar + (size_t)(tl.row0 + r) * FIN + 4 * cg) =
                     make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
@@ -339,10 +323,10 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
     __syncthreads();
     // four threads per row, record values v = q, q + 4, q + 8 (angular terms, then c and 0),
     // staged in shared memory (W1^T, W2^T are no longer needed) and stored as whole lines
-    float* sRec = sW1;
+    float* sRec = sW1t;
     const int r = tid >> 2, q = tid & 3;
     const size_t row = (size_t)(tl.row0 + r);
-    const float* rb = sZ1 + r * LDH;
+    const float* rb = sR + r * LDH;
     for (int v = q; v < NREC / NPHI && r < tl.nrows; v += 4) {
         float o[NPHI];
         if (v >= NANG) {
@@ -376,12 +360,11 @@ static_assert(NFEAT * H1 + H1 * H2 >= kR * kRecLd, "record staging must fit in t
 
 template <int FIN>
 constexpr size_t fwd_smem() { return sizeof(float) * (FIN * H1 + H1 * H2 + H2 * 8 + H1 + H2 + 8 + abuf<FIN>()); }
-template <int FIN>
+template <int FIN, bool BBAR>
 constexpr size_t bwd_smem() {
-    return sizeof(float) * (FIN * H1 + H1 * H2 + 8 * H2 + H1 + H2 + kR * 8 + abuf<FIN>() + kR * LDH +
-                            (LMAX + 1) * NPHI * NORB);
+    return sizeof(float) * (H1 * FIN + H1 * H2 + 8 * H2 + kR * 8 + kR * LDH +
+                            (BBAR ? kR * LDH + (LMAX + 1) * NPHI * NORB : 0));
 }
-
 void ensure_attrs() {
     // once per device, safe under concurrent first calls
     static std::mutex mu;
@@ -390,21 +373,18 @@ void ensure_attrs() {
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(mu);
     if (dev < 64 && ((done >> dev) & 1)) return;
-    cudaFuncSetAttribute(k_mlp_fwd<1, NFEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<NFEAT>());
-    cudaFuncSetAttribute(k_mlp_fwd<NPHI, NFEAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<NFEAT>());
-    cudaFuncSetAttribute(k_mlp_bwd<1, NFEAT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<NFEAT>());
-    cudaFuncSetAttribute(k_mlp_bwd<NPHI, NFEAT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)bwd_smem<NFEAT>());
-    cudaFuncSetAttribute(k_mlp_bwd<1, NFEAT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<NFEAT>());
-    cudaFuncSetAttribute(k_mlp_bwd<NPHI, NFEAT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)bwd_smem<NFEAT>());
-    cudaFuncSetAttribute(k_mlp_fwd<1, NFEAT_P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<NFEAT_P>());
-    cudaFuncSetAttribute(k_mlp_fwd<NPHI, NFEAT_P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)fwd_smem<NFEAT_P>());
-    cudaFuncSetAttribute(k_mlp_bwd<1, NFEAT_P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)bwd_smem<NFEAT_P>());
-    cudaFuncSetAttribute(k_mlp_bwd<NPHI, NFEAT_P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)bwd_smem<NFEAT_P>());
+#define REANN_SMEM(K, BYTES) cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(BYTES))
+    REANN_SMEM((k_mlp_fwd<1, NFEAT>), fwd_smem<NFEAT>());
+    REANN_SMEM((k_mlp_fwd<NPHI, NFEAT>), fwd_smem<NFEAT>());
+    REANN_SMEM((k_mlp_fwd<1, NFEAT_P>), fwd_smem<NFEAT_P>());
+    REANN_SMEM((k_mlp_fwd<NPHI, NFEAT_P>), fwd_smem<NFEAT_P>());
+    REANN_SMEM((k_mlp_bwd<1, NFEAT, false>), (bwd_smem<NFEAT, false>()));
+    REANN_SMEM((k_mlp_bwd<NPHI, NFEAT, false>), (bwd_smem<NFEAT, false>()));
+    REANN_SMEM((k_mlp_bwd<1, NFEAT, true>), (bwd_smem<NFEAT, true>()));
+    REANN_SMEM((k_mlp_bwd<NPHI, NFEAT, true>), (bwd_smem<NFEAT, true>()));
+    REANN_SMEM((k_mlp_bwd<1, NFEAT_P, false>), (bwd_smem<NFEAT_P, false>()));
+    REANN_SMEM((k_mlp_bwd<NPHI, NFEAT_P, false>), (bwd_smem<NFEAT_P, false>()));
+#undef REANN_SMEM
     if (dev < 64) done |= (uint64_t)1 << dev;
 }
 
@@ -417,54 +397,55 @@ NetsOfLayer layer_nets(const NetTable& t, int layer) {
 }  // namespace
 
 cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
-                               const float* rho, float* out, int out_stride, bool pairs, GhostOut gh) {
+                               const float* rho, float* out, int out_stride, bool pairs, GhostOut gh, float* dsave) {
     const int nt = (int)nl->tiles_h.size();
     if (nt == 0) return cudaSuccess;
     ensure_attrs();
     const NetsOfLayer ln = layer_nets(nets, t);
+#define REANN_FWD(O, F) k_mlp_fwd<O, F><<<nt, kT, fwd_smem<F>(), s>>>(ln, nl->tiles, rho, out, out_stride, gh, dsave)
     if (pairs) {
         if (energy)
-            k_mlp_fwd<1, NFEAT_P><<<nt, kT, fwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, out, out_stride, gh);
+            REANN_FWD(1, NFEAT_P);
         else
-            k_mlp_fwd<NPHI, NFEAT_P><<<nt, kT, fwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, out, out_stride, gh);
+            REANN_FWD(NPHI, NFEAT_P);
     } else {
         if (energy)
-            k_mlp_fwd<1, NFEAT><<<nt, kT, fwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, out, out_stride, gh);
+            REANN_FWD(1, NFEAT);
         else
-            k_mlp_fwd<NPHI, NFEAT><<<nt, kT, fwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, out, out_stride, gh);
+            REANN_FWD(NPHI, NFEAT);
     }
+#undef REANN_FWD
     return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
-                               const float* rho, const float* ybar, float* rhobar, bool pairs, const float* Wt,
+                               const float* dsave, const float* ybar, float* rhobar, bool pairs, const float* Wt,
                                const float* bck, const float* coef, float* rec, GhostOut gh) {
     const int nt = (int)nl->tiles_h.size();
     if (nt == 0) return cudaSuccess;
     ensure_attrs();
     const NetsOfLayer ln = layer_nets(nets, t);
+#define REANN_BWD(O, F, B)                                                                                      \
+    k_mlp_bwd<O, F, B><<<nt, kT, bwd_smem<F, B>(), s>>>(ln, nl->tiles, dsave, ybar, rhobar, B ? Wt : nullptr, \
+                                                        B ? bck : nullptr, B ? coef : nullptr, B ? rec : nullptr, \
+                                                        B ? gh : GhostOut{})
     if (pairs) {
         if (energy)
-            k_mlp_bwd<1, NFEAT_P, false><<<nt, kT, bwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, ybar, rhobar, nullptr,
-                                                                           nullptr, nullptr, nullptr, GhostOut{});
+            REANN_BWD(1, NFEAT_P, false);
         else
-            k_mlp_bwd<NPHI, NFEAT_P, false><<<nt, kT, bwd_smem<NFEAT_P>(), s>>>(ln, nl->tiles, rho, ybar, rhobar,
-                                                                              nullptr, nullptr, nullptr, nullptr, GhostOut{});
+            REANN_BWD(NPHI, NFEAT_P, false);
     } else if (rec) {
         if (energy)
-            k_mlp_bwd<1, NFEAT, true><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar, Wt, bck,
-                                                                       coef, rec, gh);
+            REANN_BWD(1, NFEAT, true);
         else
-            k_mlp_bwd<NPHI, NFEAT, true><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar, Wt,
-                                                                          bck, coef, rec, gh);
+            REANN_BWD(NPHI, NFEAT, true);
     } else {
         if (energy)
-            k_mlp_bwd<1, NFEAT, false><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar, nullptr,
-                                                                        nullptr, nullptr, nullptr, GhostOut{});
+            REANN_BWD(1, NFEAT, false);
         else
-            k_mlp_bwd<NPHI, NFEAT, false><<<nt, kT, bwd_smem<NFEAT>(), s>>>(ln, nl->tiles, rho, ybar, rhobar,
-                                                                           nullptr, nullptr, nullptr, nullptr, GhostOut{});
+            REANN_BWD(NPHI, NFEAT, false);
     }
+#undef REANN_BWD
     return cudaGetLastError();
 }
 

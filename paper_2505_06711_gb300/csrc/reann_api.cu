@@ -110,6 +110,7 @@ int alloc_eval_buffers(reann_ctx* ctx, reann_nlist* nl, const std::vector<std::a
     nl->bck = nl_alloc<float>(nl, (size_t)T * n * NB);
     nl->eps = nl_alloc<float>(nl, n);
     nl->rhobar = nl_alloc<float>(nl, (size_t)n * nl->n_feat);
+    nl->dsave = nl_alloc<float>(nl, (size_t)T * n * (H1 + H2));
     nl->bbar = nl_alloc<float>(nl, (size_t)ne * NREC);  // adjoint records (bbar with c)
     nl->cbar = nl_alloc<float>(nl, (size_t)n * NPHI);
     nl->grad = nl_alloc<float>(nl, (size_t)n * 3);
@@ -134,7 +135,7 @@ int alloc_eval_buffers(reann_ctx* ctx, reann_nlist* nl, const std::vector<std::a
         REANN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->tiles128, nl->tiles128_h.data(), sizeof(Tile) * nl->tiles128_h.size(),
                                             cudaMemcpyHostToDevice, ctx->stream));
     if (!nl->live || !nl->live_cnt || !nl->pos_hi || !nl->pos_lo || !nl->coef || !nl->rho || !nl->bck || !nl->eps ||
-        !nl->rhobar || !nl->bbar || !nl->cbar || !nl->grad || !nl->partial || !nl->tiles)
+        !nl->rhobar || !nl->dsave || !nl->bbar || !nl->cbar || !nl->grad || !nl->partial || !nl->tiles)
         return set_error(ctx, REANN_E_NOMEM, "evaluation buffers: out of device memory");
     if (!nl->tiles_h.empty())
         REANN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->tiles, nl->tiles_h.data(), sizeof(Tile) * nl->tiles_h.size(),
@@ -791,7 +792,8 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
             REANN_CUDA_TRY(ctx, launch_mlp_fwd_tc(s, nl, ctx->tc, t, energy_net, ctx->precision == REANN_MLP_BF16X3,
                                                   rho_t, out, out_stride, ctx->d_flags, gh));
         else
-            REANN_CUDA_TRY(ctx, launch_mlp_fwd_f32(s, nl, ctx->nets, t, energy_net, rho_t, out, out_stride, pairs, gh));
+            REANN_CUDA_TRY(ctx, launch_mlp_fwd_f32(s, nl, ctx->nets, t, energy_net, rho_t, out, out_stride, pairs, gh,
+                                                  nl->dsave + (size_t)t * n * (H1 + H2)));
     }
     {
         ProfScope p(ctx, PR_ENERGY);
@@ -807,6 +809,7 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
         const float* coef_t = nl->coef + (size_t)t * ne * NPHI;
         const float* rho_t = nl->rho + (size_t)t * n * nf;
         const float* bck_t = nl->bck + (size_t)t * n * NB;
+        const float* dsave_t = nl->dsave + (size_t)t * n * (H1 + H2);
         {
             ProfScope p(ctx, PR_MLP_BWD);
             if (ctx->precision != REANN_MLP_FP32)
@@ -814,11 +817,12 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
                                                       ctx->precision == REANN_MLP_BF16X3, rho_t, nl->cbar, nl->rhobar,
                                                       ctx->d_flags));
             else if (!pairs)  // the FP32 backward networks also take the bbar step (fused)
-                REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, rho_t, nl->cbar, nl->rhobar,
-                                                       false, ctx->d_W + t * lw, bck_t, coef_t, nl->bbar, gh));
+                REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, dsave_t, nl->cbar,
+                                                       nl->rhobar, false, ctx->d_W + t * lw, bck_t, coef_t, nl->bbar,
+                                                       gh));
             else
-                REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, rho_t, nl->cbar, nl->rhobar,
-                                                       true));
+                REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, dsave_t, nl->cbar,
+                                                       nl->rhobar, true));
         }
         if (ctx->precision != REANN_MLP_FP32 || pairs) {
             ProfScope p(ctx, PR_BBAR);
