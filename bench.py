@@ -660,6 +660,7 @@ def run_ours(args):
             "value": aggregate(n_atoms, e_ms, ws),
             "unit": "atom-evals/s",
             "ms_per_step": e_ms,
+            "ms_per_step_median": statistics.median(tt) * 1e3,
             "h2d_bytes_per_step": int(h_pos.numel() * 8),
             "d2h_bytes_per_step": int(h_f.numel() * 4 + 8),
         }

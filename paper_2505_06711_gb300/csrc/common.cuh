@@ -89,6 +89,36 @@ __device__ __forceinline__ void flush_rec(const float* __restrict__ sRec, int nr
     }
 }
 
+// The bbar step of one angular term a of one atom (Eq. 1's squares):
+//   bbar_{a,m} = sum_k W_{l,m,k} gbar_{a,k},  gbar_{a,k} = 2 w_a rhobar_{l,k} sum_m' b_{a,m'} W_{l,m',k}
+// bm = b_{a,0..7}, Wl = W_{l} (N_phi x N_orb, row-major, 16 B aligned), rb = rhobar_{l,0..15}
+// (16 B aligned); blocked over 4 orbitals (W fragments are float4 loads, read again
+// for the second product rather than held in registers).
+__device__ __forceinline__ void bbar_term(const float bm[NPHI], float two_w, const float* Wl, const float* rb,
+                                          float out[NPHI]) {
+#pragma unroll
+    for (int m = 0; m < NPHI; ++m) out[m] = 0.f;
+#pragma unroll
+    for (int k4 = 0; k4 < NORB; k4 += 4) {
+        float g[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int m = 0; m < NPHI; ++m) {
+            const float4 w = *reinterpret_cast<const float4*>(Wl + m * NORB + k4);
+            g[0] = fmaf(bm[m], w.x, g[0]);
+            g[1] = fmaf(bm[m], w.y, g[1]);
+            g[2] = fmaf(bm[m], w.z, g[2]);
+            g[3] = fmaf(bm[m], w.w, g[3]);
+        }
+        const float4 r = *reinterpret_cast<const float4*>(rb + k4);
+        const float gb[4] = {two_w * g[0] * r.x, two_w * g[1] * r.y, two_w * g[2] * r.z, two_w * g[3] * r.w};
+#pragma unroll
+        for (int m = 0; m < NPHI; ++m) {
+            const float4 w = *reinterpret_cast<const float4*>(Wl + m * NORB + k4);
+            out[m] = fmaf(gb[0], w.x, fmaf(gb[1], w.y, fmaf(gb[2], w.z, fmaf(gb[3], w.w, out[m]))));
+        }
+    }
+}
+
 // Values 10 and 11 of the record: the layer's coefficients c_m of `row`, and zero.
 __device__ __forceinline__ void rec_tail(const float* __restrict__ coef, int64_t row, int v, float val[NPHI]) {
     if (v == NANG) {

@@ -307,6 +307,7 @@ __global__ void __launch_bounds__(256) k_bbar(int64_t n, const float* __restrict
     const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
     const int64_t atom = atom0 + r;
     const int nrows = n - atom0 < 64 ? (int)(n - atom0) : 64;
+#pragma unroll 1
     for (int v = q; v < NREC / NPHI && r < nrows; v += 4) {
         float out[NPHI];
         if (v >= NANG) {
@@ -345,26 +346,7 @@ __global__ void __launch_bounds__(256) k_bbar(int64_t n, const float* __restrict
 #pragma unroll
                 for (int k = 0; k < NORB_P; ++k) out[m] = fmaf(wa * gb[k], sW[(l * NPHI + m) * KO + k], out[m]);
         } else {
-            const float two_w = 2.f * ang_w(a);
-#pragma unroll
-            for (int k4 = 0; k4 < NORB; k4 += 4) {
-                float g[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                for (int m = 0; m < NPHI; ++m) {
-                    const float4 w = ld4(sW + (l * NPHI + m) * NORB + k4);
-                    g[0] = fmaf(bm[m], w.x, g[0]);
-                    g[1] = fmaf(bm[m], w.y, g[1]);
-                    g[2] = fmaf(bm[m], w.z, g[2]);
-                    g[3] = fmaf(bm[m], w.w, g[3]);
-                }
-                const float4 rb = ldg4(rhobar + (size_t)atom * NFEAT + l * NORB + k4);
-                const float gb[4] = {two_w * g[0] * rb.x, two_w * g[1] * rb.y, two_w * g[2] * rb.z, two_w * g[3] * rb.w};
-#pragma unroll
-                for (int m = 0; m < NPHI; ++m) {
-                    const float4 w = ld4(sW + (l * NPHI + m) * NORB + k4);
-                    out[m] = fmaf(gb[0], w.x, fmaf(gb[1], w.y, fmaf(gb[2], w.z, fmaf(gb[3], w.w, out[m]))));
-                }
-            }
+            bbar_term(bm, 2.f * ang_w(a), sW + l * NPHI * NORB, rhobar + (size_t)atom * NFEAT + l * NORB, out);
         }
         stage_rec(sRec, r, v, out);
     }
@@ -508,15 +490,6 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
             const float d = g1.x, fc = g1.y, dfc = g1.z;
             const float phi = gsm * fc;
             const float dphi = gsm * (dfc - two_alpha * ((d - mu_hi) - mu_lo) * fc);  // d - mu_m as a float pair
-            float A[NANG];
-            monomials(x, y, z, A);
-            // Sk = sum_a A_a bbar_k,  Sj = sum_a (-1)^l A_a bbar_j  (also cbar's edge term)
-            float Sk = bk[0], Sj = bj[0];
-#pragma unroll
-            for (int a = 1; a < NANG; ++a) {
-                Sk = fmaf(A[a], bk[a], Sk);
-                Sj = fmaf(ang_sign(a) * A[a], bj[a], Sj);
-            }
             // Gk = sum_a bbar_k grad A_a,  Gj = sum_a (-1)^l bbar_j grad A_a
             const float x2 = 2.f * x, y2 = 2.f * y, z2 = 2.f * z;
             const float gkx = fmaf(z, bk[8], fmaf(y, bk[7], fmaf(x2, bk[4], bk[1])));
@@ -525,6 +498,10 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
             const float gjx = fmaf(z, bj[8], fmaf(y, bj[7], fmaf(x2, bj[4], -bj[1])));
             const float gjy = fmaf(z, bj[9], fmaf(x, bj[7], fmaf(y2, bj[5], -bj[2])));
             const float gjz = fmaf(y, bj[9], fmaf(x, bj[8], fmaf(z2, bj[6], -bj[3])));
+            // Sk = sum_a A_a bbar_k,  Sj = sum_a (-1)^l A_a bbar_j  (also cbar's edge term): both are
+            // quadratics P(r) = p0 + l.r + r^T M r, and P = p0 + (r . (l + grad P)) / 2
+            const float Sk = fmaf(0.5f, fmaf(z, bk[3] + gkz, fmaf(y, bk[2] + gky, x * (bk[1] + gkx))), bk[0]);
+            const float Sj = fmaf(0.5f, fmaf(z, gjz - bj[3], fmaf(y, gjy - bj[2], x * (gjx - bj[1]))), bj[0]);
             // radial part (d phi / dd) A along r/d, angular part phi grad A
             const float sc = fmaf(cj * dphi, Sk, ck * dphi * Sj) * inv_d;
             const float qv = cj * phi, qt = ck * phi;

@@ -36,10 +36,12 @@ struct NetsOfLayer {
     NetDev e[MAX_ELEM];
 };
 
-__device__ __forceinline__ float silu(float z) { return z / (1.f + expf(-z)); }
-__device__ __forceinline__ float dsilu(float z) {
-    const float s = 1.f / (1.f + expf(-z));
-    return s * (1.f + z * (1.f - s));
+// SiLU(z) = z s and SiLU'(z) = s (1 + z (1 - s)) from one correctly rounded
+// reciprocal s = 1 / (1 + exp(-z)); h receives SiLU, the result is SiLU'
+__device__ __forceinline__ float silu_d(float z, float& h) {
+    const float s = __frcp_rn(1.f + expf(-z));
+    h = z * s;
+    return s * fmaf(z, 1.f - s, 1.f);
 }
 
 __device__ __forceinline__ void copy_f4(float* dst, const float* src, int count, int tid) {
@@ -155,17 +157,22 @@ __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = sb1[4 * tx + j];
     mma_4x4<FIN, ldx<FIN>(), H1>(sA, sW1, ty, tx, acc);
+    float ds[4][4];  // SiLU'(z1) (acc becomes h1)
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ds[i][j] = silu_d(acc[i][j], acc[i][j]);
     if (dsave)
 #pragma unroll
         for (int i = 0; i < 4; ++i)
             if (4 * ty + i < tl.nrows)
                 *reinterpret_cast<float4*>(dsave + (size_t)(tl.row0 + 4 * ty + i) * kSave + 4 * tx) =
-                    make_float4(dsilu(acc[i][0]), dsilu(acc[i][1]), dsilu(acc[i][2]), dsilu(acc[i][3]));
+                    make_float4(ds[i][0], ds[i][1], ds[i][2], ds[i][3]);
     __syncthreads();  // every thread is done reading the input rows
 #pragma unroll
     for (int i = 0; i < 4; ++i)
         *reinterpret_cast<float4*>(sA + (4 * ty + i) * LDH + 4 * tx) =
-            make_float4(silu(acc[i][0]), silu(acc[i][1]), silu(acc[i][2]), silu(acc[i][3]));
+            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
     __syncthreads();
     // layer 2 (h2 stays in registers)
 #pragma unroll
@@ -173,16 +180,16 @@ __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = sb2[4 * tx + j];
     mma_4x4<H1, LDH, H2>(sA, sW2, ty, tx, acc);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ds[i][j] = silu_d(acc[i][j], acc[i][j]);  // acc becomes h2
     if (dsave)
 #pragma unroll
         for (int i = 0; i < 4; ++i)
             if (4 * ty + i < tl.nrows)
                 *reinterpret_cast<float4*>(dsave + (size_t)(tl.row0 + 4 * ty + i) * kSave + H1 + 4 * tx) =
-                    make_float4(dsilu(acc[i][0]), dsilu(acc[i][1]), dsilu(acc[i][2]), dsilu(acc[i][3]));
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = silu(acc[i][j]);
+                    make_float4(ds[i][0], ds[i][1], ds[i][2], ds[i][3]);
     // layer 3: per-thread partial dot products over its 4 columns, reduced over tx
     float v[4 * OUT];
 #pragma unroll
@@ -236,7 +243,7 @@ __device__ __forceinline__ float4 ld_save(const float* dsave, const Tile& tl, in
 }
 
 template <int OUT, int FIN, bool BBAR>
-__global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __restrict__ tiles,
+__global__ void __launch_bounds__(kT, 3) k_mlp_bwd(NetsOfLayer nets, const Tile* __restrict__ tiles,
                                                const float* __restrict__ dsave, const float* __restrict__ ybar,
                                                float* __restrict__ rhobar, const float* __restrict__ Wt,
                                                const float* __restrict__ bck, const float* __restrict__ coef,
@@ -248,24 +255,24 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
     float* sY = sW3t + 8 * H2;        // 64 x 8
     float* sG = sY + kR * 8;          // z2bar, then z1bar (stride LDH)
     float* sR = sG + kR * LDH;        // rhobar rows (BBAR, stride LDH)
-    float* sWc = sR + kR * LDH;       // (L+1) x N_phi x N_orb contraction W^t (BBAR)
+    float* sWc = sR + kR * LDH;       // (L+1) x N_orb x N_phi contraction W^t, transposed per l (BBAR)
     const int tid = threadIdx.x;
     const Tile tl = tiles[blockIdx.x];
     if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list
     const int ty = tid >> 4, tx = tid & 15;
-    // the thread's SiLU derivatives, in flight while the weights are staged
-    float4 s1[4], s2[4];
+    // the thread's SiLU'(z2), in flight while the weights are staged
+    float4 s2[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        s2[i] = ld_save(dsave, tl, 4 * ty + i, H1 + 4 * tx);
-        s1[i] = ld_save(dsave, tl, 4 * ty + i, 4 * tx);
-    }
+    for (int i = 0; i < 4; ++i) s2[i] = ld_save(dsave, tl, 4 * ty + i, H1 + 4 * tx);
     const NetDev& w = nets.e[tl.elem];
     copy_f4(sW1t, w.W1t, H1 * FIN, tid);
     copy_f4(sW2t, w.W2t, H1 * H2, tid);
     for (int i = tid; i < OUT * H2; i += kT) sW3t[i] = w.W3t[i];
-    if (BBAR)
-        for (int i = tid; i < (LMAX + 1) * NPHI * NORB; i += kT) sWc[i] = Wt[i];
+    if (BBAR)  // transposed per l: sWc[(l N_orb + k) N_phi + m] = W_{l,m,k}
+        for (int i = tid; i < (LMAX + 1) * NPHI * NORB; i += kT) {
+            const int l = i / (NPHI * NORB), m = (i / NORB) % NPHI, k = i % NORB;
+            sWc[(l * NORB + k) * NPHI + m] = Wt[i];
+        }
     for (int i = tid; i < kR * OUT; i += kT) {
         const int r = i / OUT, o = i % OUT;
         sY[r * 8 + o] = (OUT == 1) ? 1.f : (r < tl.nrows ? ybar[(size_t)(tl.row0 + r) * OUT + o] : 0.f);
@@ -287,6 +294,9 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
         *reinterpret_cast<float4*>(sG + (4 * ty + i) * LDH + 4 * tx) =
             make_float4(v[0] * s2[i].x, v[1] * s2[i].y, v[2] * s2[i].z, v[3] * s2[i].w);
     }
+    float4 s1[4];  // SiLU'(z1), in flight during the z1bar product
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s1[i] = ld_save(dsave, tl, 4 * ty + i, 4 * tx);
     __syncthreads();
     // z1bar = (z2bar W2^T) * s1
     float acc[4][4];
@@ -327,6 +337,7 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
     const int r = tid >> 2, q = tid & 3;
     const size_t row = (size_t)(tl.row0 + r);
     const float* rb = sR + r * LDH;
+#pragma unroll 1
     for (int v = q; v < NREC / NPHI && r < tl.nrows; v += 4) {
         float o[NPHI];
         if (v >= NANG) {
@@ -341,14 +352,18 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(NetsOfLayer nets, const Tile* __
 #pragma unroll
         for (int m = 0; m < NPHI; ++m) o[m] = 0.f;
         const float two_w = 2.f * ang_w(a);
+        const float* wl = sWc + l * NORB * NPHI;
 #pragma unroll 4
         for (int k = 0; k < NORB; ++k) {
+            const float4 w0 = *reinterpret_cast<const float4*>(wl + k * NPHI);
+            const float4 w1 = *reinterpret_cast<const float4*>(wl + k * NPHI + 4);
+            const float wm[NPHI] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
             float g = 0.f;
 #pragma unroll
-            for (int m = 0; m < NPHI; ++m) g = fmaf(bm[m], sWc[(l * NPHI + m) * NORB + k], g);
+            for (int m = 0; m < NPHI; ++m) g = fmaf(bm[m], wm[m], g);
             const float gb = two_w * g * rb[l * NORB + k];
 #pragma unroll
-            for (int m = 0; m < NPHI; ++m) o[m] = fmaf(gb, sWc[(l * NPHI + m) * NORB + k], o[m]);
+            for (int m = 0; m < NPHI; ++m) o[m] = fmaf(gb, wm[m], o[m]);
         }
         stage_rec(sRec, r, v, o);
     }
