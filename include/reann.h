@@ -159,6 +159,10 @@ void reann_nlist_free(reann_nlist* nl);
  * motion needs more ghost slots or row entries than were sized, the affected
  * entries are dropped and reann_ctx_check() reports REANN_E_CAPACITY; build a
  * new list then.  Asynchronous.  Errors: REANN_E_ARG, REANN_E_CUDA.
+ * Repeated calls with the same arguments are replayed as one CUDA graph (the
+ * first runs directly, the second is captured) on a library-owned stream
+ * ordered after and before the context stream; with reann_ctx_profile on,
+ * every call launches its kernels directly.
  */
 int reann_nlist_rebuild(reann_ctx* ctx, reann_nlist* nl, const double* pos);
 
@@ -223,6 +227,8 @@ int reann_decomp_info(const reann_nlist* nl, int32_t* n_ranks, int64_t* local, i
  *   forces       dev, N x 3 FP32: F = -dE/dr (eV/A)
  *   atom_energy  dev, N FP32 per-atom energies eps_i, or NULL
  * Asynchronous.  Coincident atoms are reported by reann_ctx_check().
+ * Repeated calls with the same pointers, T and network precision are replayed
+ * as one CUDA graph, as for reann_nlist_rebuild.
  * Errors: REANN_E_ARG, REANN_E_MISMATCH, REANN_E_CUDA.
  */
 int reann_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy, float* forces,

@@ -235,6 +235,18 @@ struct NlistScratch {
     float4* p32s = nullptr;  // the same in bin-sorted order, slot index in .w
 };
 
+// A call replayed as a CUDA graph: the arguments it was captured with (key),
+// and whether the same call has run once uncaptured (seen) or cannot be
+// captured (nograph).
+struct GraphSlot {
+    const void* key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int ikey[4] = {0, 0, 0, 0};
+    bool seen = false, nograph = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+enum GraphSlotId { GS_REBUILD = 0, GS_EVAL, GS_HOST_REBUILD, GS_HOST_EVAL, GS_COUNT };
+
 }  // namespace reann
 
 struct reann_model {
@@ -295,6 +307,7 @@ struct reann_nlist {
     const double* md_forces_at = nullptr;  // positions the forces belong to
     cudaGraph_t md_graph = nullptr;
     cudaGraphExec_t md_exec = nullptr;
+    reann::GraphSlot graphs[reann::GS_COUNT];  // rebuild / evaluation calls replayed as graphs
     const void* md_key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     double md_dt = 0.0;
     double md_kt = 0.0, md_tau = 0.0;  // thermostat of the captured step (tau 0: NVE)
@@ -329,7 +342,7 @@ struct reann_ctx {
     int* h_flags = nullptr;        // pinned mirror
     std::string err;
     int num_sms = 0;
-    // MD: a non-blocking stream the step graph is captured on and replayed on
+    // a non-blocking stream the MD step graph and the replayed rebuild / evaluation graphs run on
     cudaStream_t md_stream = nullptr;
     cudaEvent_t md_ev[2] = {nullptr, nullptr};
     // optional per-region event profile

@@ -150,6 +150,10 @@ void free_nlist(reann_nlist* nl) {
     if (!nl) return;
     if (nl->md_exec) cudaGraphExecDestroy(nl->md_exec);
     if (nl->md_graph) cudaGraphDestroy(nl->md_graph);
+    for (GraphSlot& g : nl->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+    }
     for (void* p : nl->allocs) {
         if (nl->mem_pool)
             cudaFreeAsync(p, nl->alloc_stream);
@@ -861,18 +865,103 @@ int run_rebuild(reann_ctx* ctx, reann_nlist* nl, const double* pos) {
     return REANN_OK;
 }
 
+// Runs fn() on the context's own non-blocking stream (created on first use),
+// ordered after the work already on the caller's stream and before any work
+// the caller enqueues later; CUDA graphs are captured and replayed there.
+template <class F>
+int on_graph_stream(reann_ctx* ctx, F fn) {
+    if (!ctx->md_stream) {
+        REANN_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->md_stream, cudaStreamNonBlocking));
+        REANN_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->md_ev[0], cudaEventDisableTiming));
+        REANN_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->md_ev[1], cudaEventDisableTiming));
+    }
+    cudaStream_t user = ctx->stream;
+    REANN_CUDA_TRY(ctx, cudaEventRecord(ctx->md_ev[0], user));
+    REANN_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->md_stream, ctx->md_ev[0], 0));
+    ctx->stream = ctx->md_stream;
+    const int rc = fn();
+    ctx->stream = user;
+    REANN_CUDA_TRY(ctx, cudaEventRecord(ctx->md_ev[1], ctx->md_stream));
+    REANN_CUDA_TRY(ctx, cudaStreamWaitEvent(user, ctx->md_ev[1], 0));
+    return rc;
+}
+
+// Runs body(), which only enqueues work on ctx->stream whose launch sequence
+// is fixed by the list, the context and the key.  The first call with a key
+// runs directly (one-time set-up happens there); the second captures it into
+// a CUDA graph; later calls replay the graph.  With per-region profiling on,
+// every call runs directly.
+template <class F>
+int run_graphed(reann_ctx* ctx, reann_nlist* nl, GraphSlotId slot, const void* const key[6], const int ikey[4],
+                F body) {
+    if (ctx->prof_on) return body();
+    GraphSlot& gs = nl->graphs[slot];
+    const bool same = gs.seen && std::memcmp(gs.key, key, sizeof(gs.key)) == 0 &&
+                      std::memcmp(gs.ikey, ikey, sizeof(gs.ikey)) == 0;
+    if (!same) {
+        if (gs.exec) cudaGraphExecDestroy(gs.exec);
+        if (gs.graph) cudaGraphDestroy(gs.graph);
+        gs = GraphSlot{};
+        std::memcpy(gs.key, key, sizeof(gs.key));
+        std::memcpy(gs.ikey, ikey, sizeof(gs.ikey));
+        gs.seen = true;
+        return body();
+    }
+    if (gs.nograph) return body();
+    return on_graph_stream(ctx, [&]() -> int {
+        cudaStream_t s = ctx->stream;
+        if (!gs.exec) {
+            REANN_CUDA_TRY(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            const int rc = body();
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(s, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (ec != cudaSuccess || cudaGraphInstantiate(&gs.exec, g, 0) != cudaSuccess) {
+                // not capturable: run directly from now on
+                if (g) cudaGraphDestroy(g);
+                gs.exec = nullptr;
+                gs.nograph = true;
+                (void)cudaGetLastError();
+                return body();
+            }
+            gs.graph = g;
+        }
+        REANN_CUDA_TRY(ctx, cudaGraphLaunch(gs.exec, s));
+        return REANN_OK;
+    });
+}
+
+int graphed_rebuild(reann_ctx* ctx, reann_nlist* nl, const double* pos, GraphSlotId slot) {
+    if (nl->decomposed) return run_rebuild(ctx, nl, pos);  // refused, with its message
+    const void* key[6] = {pos, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const int ikey[4] = {0, 0, 0, 0};
+    return run_graphed(ctx, nl, slot, key, ikey, [&] { return run_rebuild(ctx, nl, pos); });
+}
+
+int graphed_eval(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy, float* forces,
+                 float* atom_energy, double* virial, float* atom_virial, GraphSlotId slot) {
+    const void* key[6] = {pos, energy, forces, atom_energy, virial, atom_virial};
+    const int ikey[4] = {T, ctx->precision, 0, 0};
+    return run_graphed(ctx, nl, slot, key, ikey, [&] {
+        return run_energy_forces(ctx, nl, pos, T, energy, forces, atom_energy, nullptr, 0, virial, atom_virial);
+    });
+}
+
 }  // namespace
 
 extern "C" int reann_nlist_rebuild(reann_ctx* ctx, reann_nlist* nl, const double* pos) {
     if (!ctx || !nl || !pos) return set_error(ctx, REANN_E_ARG, "null argument");
-    return run_rebuild(ctx, nl, pos);
+    return graphed_rebuild(ctx, nl, pos, GS_REBUILD);
 }
 
 extern "C" int reann_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy,
                                    float* forces, float* atom_energy) {
     if (!ctx || !nl || !pos || !energy || !forces) return set_error(ctx, REANN_E_ARG, "null argument");
     if (T != ctx->model.T || T != nl->T) return set_error(ctx, REANN_E_MISMATCH, "T differs from the model");
-    return run_energy_forces(ctx, nl, pos, T, energy, forces, atom_energy);
+    return graphed_eval(ctx, nl, pos, T, energy, forces, atom_energy, nullptr, nullptr, GS_EVAL);
 }
 
 extern "C" int reann_energy_forces_virial(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy,
@@ -880,7 +969,7 @@ extern "C" int reann_energy_forces_virial(reann_ctx* ctx, reann_nlist* nl, const
     if (!ctx || !nl || !pos || !energy || !forces || !virial) return set_error(ctx, REANN_E_ARG, "null argument");
     if (T != ctx->model.T || T != nl->T) return set_error(ctx, REANN_E_MISMATCH, "T differs from the model");
     if (int rc = ensure_virial(ctx, nl)) return rc;
-    return run_energy_forces(ctx, nl, pos, T, energy, forces, atom_energy, nullptr, 0, virial, atom_virial);
+    return graphed_eval(ctx, nl, pos, T, energy, forces, atom_energy, virial, atom_virial, GS_EVAL);
 }
 
 extern "C" int reann_energy_forces_host(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T, double* energy,
@@ -897,7 +986,7 @@ extern "C" int reann_energy_forces_host(reann_ctx* ctx, reann_nlist* nl, const d
     }
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(nl->h2d_pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
     if (rebuild) {
-        int rc = run_rebuild(ctx, nl, nl->h2d_pos);
+        int rc = graphed_rebuild(ctx, nl, nl->h2d_pos, GS_HOST_REBUILD);
         if (rc) return rc;
     } else {
         REANN_CUDA_TRY(ctx, launch_moved(s, nl, nl->h2d_pos, ctx->d_flags + FLAG_MOVED));
@@ -910,7 +999,7 @@ extern "C" int reann_energy_forces_host(reann_ctx* ctx, reann_nlist* nl, const d
             if (rc) return rc;
         }
     }
-    int rc = run_energy_forces(ctx, nl, nl->h2d_pos, T, nl->d_energy, nl->d_forces, nullptr);
+    int rc = graphed_eval(ctx, nl, nl->h2d_pos, T, nl->d_energy, nl->d_forces, nullptr, nullptr, nullptr, GS_HOST_EVAL);
     if (rc) return rc;
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(forces, nl->d_forces, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(energy, nl->d_energy, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1054,23 +1143,12 @@ int md_entry(reann_ctx* ctx, reann_nlist* nl, double* pos, double* vel, const do
         return set_error(ctx, REANN_E_ARG, "bad argument to reann_md_step");
     if (nl->decomposed) return set_error(ctx, REANN_E_ARG, "MD needs device rebuilds: use a single-domain list");
     if (n_steps == 0) return REANN_OK;
-    if (!ctx->md_stream) {
-        REANN_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->md_stream, cudaStreamNonBlocking));
-        REANN_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->md_ev[0], cudaEventDisableTiming));
-        REANN_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->md_ev[1], cudaEventDisableTiming));
-    }
-    // run on the MD stream, ordered after and before the caller's stream
-    cudaStream_t user = ctx->stream;
-    REANN_CUDA_TRY(ctx, cudaEventRecord(ctx->md_ev[0], user));
-    REANN_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->md_stream, ctx->md_ev[0], 0));
+    // run on the graph stream, ordered after and before the caller's stream
     const bool prof = ctx->prof_on;
-    ctx->stream = ctx->md_stream;
     ctx->prof_on = false;
-    const int rc = md_run(ctx, nl, pos, vel, mass, dt_fs, n_steps, e_pot, e_kin, th, e_bath);
-    ctx->stream = user;
+    const int rc = on_graph_stream(
+        ctx, [&] { return md_run(ctx, nl, pos, vel, mass, dt_fs, n_steps, e_pot, e_kin, th, e_bath); });
     ctx->prof_on = prof;
-    REANN_CUDA_TRY(ctx, cudaEventRecord(ctx->md_ev[1], ctx->md_stream));
-    REANN_CUDA_TRY(ctx, cudaStreamWaitEvent(user, ctx->md_ev[1], 0));
     return rc;
 }
 
