@@ -463,11 +463,13 @@ def region_flops(region: str, n_atoms: int, n_live: int, T: int, launches: int) 
 
 
 def launches_per_step(T: int) -> int:
-    """Library kernels per step (FP32 networks, single-domain list): rebuild 13
-    (wrap, 2 x 4 sort kernels, gather, scan, ghosts + extended keys, search),
-    evaluation 3 (refresh, live edges, c0) + 2T forward (density, network) + 2
-    (energy) + 2T reverse (network with bbar, density adjoint) + 1 (outputs)."""
-    return 13 + 3 + 2 * T + 2 + 2 * T + 1
+    """Library kernels per step (FP32 networks, single-domain list): rebuild 11
+    (wrap + keys + histogram, 2 x 3 sort kernels (scan, scatter, rank), gather,
+    scan, ghosts + extended keys + histogram, search), evaluation 2 (positions
+    with c0, live edges) + 2T forward (density, network; the energy network
+    also sums its tiles) + 1 (total energy) + 2T reverse (network with bbar,
+    density adjoint; the last one writes forces and atomic energies)."""
+    return 11 + 2 + 2 * T + 1 + 2 * T
 
 
 def cpu_baseline(structure, spec):

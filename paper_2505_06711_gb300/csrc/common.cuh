@@ -393,7 +393,9 @@ cudaError_t launch_ekin(cudaStream_t s, int64_t n, const double* vel, const doub
 cudaError_t launch_record(cudaStream_t s, int* counter, const double* scalars, double* epot_out, double* ekin_out,
                           double* bath_out, double gkt, double q, int n_steps, const int* gate, int* rebuilds);
 const int32_t* ghost_count_ptr(const reann_nlist* nl);
-cudaError_t launch_refresh_positions(cudaStream_t s, const reann_nlist* nl, const double* pos);
+// with c0: also the first layer's coefficients of every slot (k_init_coef's work)
+cudaError_t launch_refresh_positions(cudaStream_t s, const reann_nlist* nl, const double* pos,
+                                     const float* c0 = nullptr);
 cudaError_t launch_live_edges(cudaStream_t s, const reann_nlist* nl, float rc2, int* flags);
 int export_nlist(reann_ctx* ctx, const reann_nlist* nl, int64_t cap, int32_t* i, int32_t* j, int32_t* n, int64_t* count);
 
@@ -404,19 +406,24 @@ cudaError_t launch_density_fwd(cudaStream_t s, const reann_nlist* nl, const Radi
                                float* rho, float* bck, bool pairs = false);
 cudaError_t launch_bbar(cudaStream_t s, const reann_nlist* nl, const float* W, const float* bck, const float* rhobar,
                         const float* coef, float* rec, bool pairs = false, GhostOut gh = {});
+// forces / atom_energy (caller order): the last reverse layer writes the outputs itself
 cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* rec, float* cbar,
-                               float* grad, bool want_cbar, int* flags, float* vir = nullptr);
+                               float* grad, bool want_cbar, int* flags, float* vir = nullptr,
+                               float* forces = nullptr, float* atom_energy = nullptr);
 cudaError_t upload_pair_table();
 cudaError_t launch_virial_sum(cudaStream_t s, const reann_nlist* nl, const float* vir, double* partial, double* out);
 cudaError_t launch_energy_sum(cudaStream_t s, const reann_nlist* nl, double* energy);
-cudaError_t launch_scatter_outputs(cudaStream_t s, const reann_nlist* nl, float* forces, float* atom_energy);
 cudaError_t launch_unpermute_rows(cudaStream_t s, const reann_nlist* nl, const float* src, int src_stride, float* dst,
                                   int width);
 
 // atomic networks, FP32 SIMT (mlp_fp32.cu)
-// dsave (N x 128, optional): the forward keeps SiLU'(z1), SiLU'(z2) of every row for the backward
+// dsave (N x 128, optional): the forward keeps SiLU'(z1), SiLU'(z2) of every row for the backward;
+// epart (energy network, optional): one FP64 energy partial sum per tile (reann_nlist::tiles order)
 cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
-                               const float* rho, float* out, int out_stride, bool pairs, GhostOut gh, float* dsave);
+                               const float* rho, float* out, int out_stride, bool pairs, GhostOut gh, float* dsave,
+                               double* epart = nullptr);
+// total energy from np partial sums, in a fixed order
+cudaError_t launch_energy_final(cudaStream_t s, const double* partial, int np, double* energy);
 // atomic networks, BF16 on tcgen05 tensor cores (mlp_tc.cu)
 cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
                               bool split, const float* rho, float* out, int out_stride, int* flags, GhostOut gh = {});

@@ -374,6 +374,15 @@ constexpr int kAdjGroups = 4;  // centre atoms per warp
 constexpr int kGeoStride = 20;
 constexpr int kGroupStride = 8 * kGeoStride + 8;
 
+// With forces set (the last reverse layer), the kernel also writes F = -dE/dr
+// and the atomic energies in caller order (perm: internal -> caller index).
+struct Outputs {
+    const int32_t* perm;
+    const float* eps;
+    float* forces;
+    float* atom_energy;
+};
+
 // WANT_VIR: also W -= (dE/dr_e) r_e^T over the atom's own edges (their
 // bbar_k c_j terms: every directed edge once) into vir (N x 9, accumulated
 // over the layers like grad).
@@ -385,7 +394,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
                                                                 const float4* __restrict__ plo,
                                                                 const float* __restrict__ rec,
                                                                 float* __restrict__ cbar, float* __restrict__ grad,
-                                                                float* __restrict__ vir) {
+                                                                float* __restrict__ vir, Outputs out) {
     __shared__ __align__(16) float sGeo[kAdjWarps][kAdjGroups * kGroupStride];
     __shared__ __align__(16) float4 sPos[2][kAdjWarps * 32];  // a lane's next edge: hi, lo position of j
     __shared__ __align__(16) float4 sCen[kAdjWarps * kAdjGroups][2];  // hi, lo position of the centre atom
@@ -552,6 +561,13 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
         gr[0] += gx;
         gr[1] += gy;
         gr[2] += gz;
+        if (out.forces) {  // the last layer: F = -dE/dr and eps_i in caller order
+            const int64_t c = out.perm[atom];
+            out.forces[3 * c] = -gr[0];
+            out.forces[3 * c + 1] = -gr[1];
+            out.forces[3 * c + 2] = -gr[2];
+            if (out.atom_energy) out.atom_energy[c] = out.eps[atom];
+        }
         if (WANT_VIR) {
             float* vr = vir + (size_t)atom * 9;
 #pragma unroll
@@ -666,18 +682,6 @@ __global__ void __launch_bounds__(kSumThreads) k_virial_final(int np, const doub
     }
 }
 
-__global__ void k_scatter_outputs(int64_t n, const int32_t* __restrict__ perm, const float* __restrict__ grad,
-                                  const float* __restrict__ eps, float* __restrict__ forces,
-                                  float* __restrict__ atom_energy) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t c = perm[i];
-    forces[3 * c] = -grad[3 * i];
-    forces[3 * c + 1] = -grad[3 * i + 1];
-    forces[3 * c + 2] = -grad[3 * i + 2];
-    if (atom_energy) atom_energy[c] = eps[i];
-}
-
 __global__ void k_unpermute_rows(int64_t n, int width, const int32_t* __restrict__ perm, const float* __restrict__ src,
                                  int src_stride, float* __restrict__ dst) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -742,13 +746,14 @@ cudaError_t upload_pair_table() {
 }
 
 cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* rec, float* cbar,
-                               float* grad, bool want_cbar, int* flags, float* vir) {
+                               float* grad, bool want_cbar, int* flags, float* vir, float* forces, float* atom_energy) {
+    const Outputs out{forces ? nl->perm : nullptr, forces ? nl->eps : nullptr, forces, atom_energy};
     (void)flags;
     const int64_t per_block = kAdjWarps * kAdjGroups;
     const unsigned nb = blocks_for(nl->n, per_block);
 #define REANN_ADJ(C, V)                                                                                              \
     k_density_adj8<C, V><<<nb, kAdjWarps * 32, 0, s>>>(nl->n, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi,     \
-                                                      nl->pos_lo, rec, cbar, grad, vir)
+                                                      nl->pos_lo, rec, cbar, grad, vir, out)
     if (want_cbar && vir)
         REANN_ADJ(true, true);
     else if (want_cbar)
@@ -775,8 +780,8 @@ cudaError_t launch_energy_sum(cudaStream_t s, const reann_nlist* nl, double* ene
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_outputs(cudaStream_t s, const reann_nlist* nl, float* forces, float* atom_energy) {
-    k_scatter_outputs<<<blocks_for(nl->n, 256), 256, 0, s>>>(nl->n, nl->perm, nl->grad, nl->eps, forces, atom_energy);
+cudaError_t launch_energy_final(cudaStream_t s, const double* partial, int np, double* energy) {
+    k_energy_final<<<1, kSumThreads, 0, s>>>(np, partial, energy);
     return cudaGetLastError();
 }
 

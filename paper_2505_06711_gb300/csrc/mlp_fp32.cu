@@ -128,7 +128,8 @@ constexpr int kSave = H1 + H2;
 template <int OUT, int FIN>
 __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __restrict__ tiles,
                                                const float* __restrict__ rho, float* __restrict__ out,
-                                               int out_stride, GhostOut gh, float* __restrict__ dsave) {
+                                               int out_stride, GhostOut gh, float* __restrict__ dsave,
+                                               double* __restrict__ epart) {
     extern __shared__ __align__(16) float sm[];
     float* sW1 = sm;                 // FIN x 64
     float* sW2 = sW1 + FIN * H1;     // 64 x 64
@@ -139,7 +140,10 @@ __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __
     float* sA = sb3 + 8;             // input rows (stride FIN + 4), then h1 (stride LDH)
     const int tid = threadIdx.x;
     const Tile tl = tiles[blockIdx.x];
-    if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list
+    if (tl.nrows <= 0) {  // padding entry of a fixed-size tile list
+        if (OUT == 1 && epart && tid == 0) epart[blockIdx.x] = 0.0;
+        return;
+    }
     const NetDev& w = nets.e[tl.elem];
     copy_f4(sW1, w.W1, FIN * H1, tid);
     copy_f4(sW2, w.W2, H1 * H2, tid);
@@ -207,7 +211,20 @@ __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __
     reduce16<4 * OUT>(v, tx);
     if (OUT == 1) {
         const int r = 4 * ty + (tx >> 2);
-        if ((tx & 3) == 0 && r < tl.nrows) out[(size_t)(tl.row0 + r) * out_stride] = v[0] + sb3[0];
+        const float e = v[0] + sb3[0];
+        if ((tx & 3) == 0 && r < tl.nrows) out[(size_t)(tl.row0 + r) * out_stride] = e;
+        if (epart) {  // the tile's energy in FP64, summed in a fixed order
+            __syncthreads();  // every thread is done with the activation buffer
+            double* sE = reinterpret_cast<double*>(sA);
+            if ((tx & 3) == 0) sE[r] = r < tl.nrows ? (double)e : 0.0;
+            __syncthreads();
+            if (tid < 32) {
+                double x = sE[tid] + sE[tid + 32];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (tid == 0) epart[blockIdx.x] = x;
+            }
+        }
     } else {
         const int r = 4 * ty + (tx >> 2), o = 2 * (tx & 3);
         if (r < tl.nrows) {
@@ -412,12 +429,14 @@ NetsOfLayer layer_nets(const NetTable& t, int layer) {
 }  // namespace
 
 cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
-                               const float* rho, float* out, int out_stride, bool pairs, GhostOut gh, float* dsave) {
+                               const float* rho, float* out, int out_stride, bool pairs, GhostOut gh, float* dsave,
+                               double* epart) {
     const int nt = (int)nl->tiles_h.size();
     if (nt == 0) return cudaSuccess;
     ensure_attrs();
     const NetsOfLayer ln = layer_nets(nets, t);
-#define REANN_FWD(O, F) k_mlp_fwd<O, F><<<nt, kT, fwd_smem<F>(), s>>>(ln, nl->tiles, rho, out, out_stride, gh, dsave)
+#define REANN_FWD(O, F) \
+    k_mlp_fwd<O, F><<<nt, kT, fwd_smem<F>(), s>>>(ln, nl->tiles, rho, out, out_stride, gh, dsave, epart)
     if (pairs) {
         if (energy)
             REANN_FWD(1, NFEAT_P);

@@ -65,7 +65,8 @@ __device__ __forceinline__ int64_t ghosts_in_use(const int32_t* g_count, int64_t
 // 1. wrap + key (caller order)
 __global__ void k_wrap_key(const int* __restrict__ gate, int64_t n, const double* __restrict__ pos, const int32_t* __restrict__ species, int n_elem,
                            CellGeom g, double* __restrict__ xw, double* __restrict__ fw, int32_t* __restrict__ mw,
-                           int32_t* __restrict__ key, int* __restrict__ flags, double* __restrict__ ref) {
+                           int32_t* __restrict__ key, int32_t* __restrict__ counts, int* __restrict__ flags,
+                           double* __restrict__ ref) {
     if (gate && *gate == 0) return;  // rebuild not needed this step
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -106,81 +107,75 @@ __global__ void k_wrap_key(const int* __restrict__ gate, int64_t n, const double
         b[k] = clampi((int)floor(f * g.nb[k]), 0, g.nb[k] - 1);
     }
     int nbins = g.nb[0] * g.nb[1] * g.nb[2];
-    key[i] = sp * nbins + (b[0] * g.nb[1] + b[1]) * g.nb[2] + b[2];
+    const int k = sp * nbins + (b[0] * g.nb[1] + b[1]) * g.nb[2] + b[2];
+    key[i] = k;
+    atomicAdd(&counts[k], 1);  // the counting sort's histogram
 }
 
 // ---- deterministic counting sort ------------------------------------------
-__global__ void k_hist(const int* __restrict__ gate, int64_t n, const int32_t* __restrict__ key, int32_t* __restrict__ counts) {
-    if (gate && *gate == 0) return;  // rebuild not needed this step
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) atomicAdd(&counts[key[i]], 1);
-}
 
-// Exclusive scan of `in` (n entries) into out[0..n]; one block of kScanThreads
-// walking tiles of kScanThreads x kScanItems entries: each tile is loaded and
-// stored coalesced through shared memory (padded one word per 32 against bank
-// conflicts), each thread scans kScanItems consecutive entries, and a
-// two-level warp scan joins the threads; a running carry joins the tiles.
-constexpr int kScanItems = 8;
+// Exclusive scan of `in` (n entries) into out[0..n] by one block of
+// kScanThreads, in tiles of kScanThreads x kScanItems entries (one tile for up
+// to 24,576 entries).  Warp w takes the tile's w-th chunk of 32 x kScanItems
+// consecutive entries as kScanItems rows of 32 (coalesced loads and stores
+// straight from registers); each row is a warp scan chained to the previous
+// row's total, the warp totals are scanned by warp 0, and a running carry joins
+// the tiles.  With zero_in the entries are set to zero once read.
+constexpr int kScanItems = 24;
 
 template <typename T>
-__global__ void __launch_bounds__(kScanThreads) k_scan_single(const int* __restrict__ gate, int64_t n, const T* __restrict__ in,
-                                                                T* __restrict__ out) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_single(const int* __restrict__ gate, int64_t n,
+                                                                T* __restrict__ in, T* __restrict__ out, bool zero_in) {
     if (gate && *gate == 0) return;  // rebuild not needed this step
-    constexpr int TILE = kScanThreads * kScanItems;
-    __shared__ T buf[TILE + TILE / 32];
+    constexpr int CHUNK = 32 * kScanItems, TILE = kScanThreads * kScanItems;
     __shared__ T warp_sums[kScanThreads / 32];
+    __shared__ T tile_total;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     T carry = 0;
     for (int64_t base = 0; base < n; base += TILE) {
-#pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
-            const int x = k * kScanThreads + tid;
-            buf[x + x / 32] = (base + x < n) ? in[base + x] : (T)0;
-        }
-        __syncthreads();
+        const int64_t wb = base + (int64_t)w * CHUNK;
         T v[kScanItems];
-        T local = 0;
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
-            const int x = tid * kScanItems + k;
-            v[k] = buf[x + x / 32];
-            local += v[k];
+            const int64_t x = wb + k * 32 + lane;
+            v[k] = x < n ? in[x] : (T)0;
+            if (zero_in && x < n) in[x] = (T)0;
         }
-        T incl = local;
+        T run = 0;  // the warp's running total over its rows
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const T y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) warp_sums[w] = incl;
-        __syncthreads();
-        if (w == 0) {
-            T s = warp_sums[lane];
+        for (int k = 0; k < kScanItems; ++k) {
+            T incl = v[k];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const T y = __shfl_up_sync(0xffffffffu, s, o);
-                if (lane >= o) s += y;
+                const T y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
             }
-            warp_sums[lane] = s;  // inclusive
+            const T row_total = __shfl_sync(0xffffffffu, incl, 31);
+            v[k] = run + incl - v[k];  // exclusive within the warp's chunk
+            run += row_total;
+        }
+        if (lane == 0) warp_sums[w] = run;
+        __syncthreads();
+        if (w == 0) {
+            const T t = warp_sums[lane];
+            T incl = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const T y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            warp_sums[lane] = incl - t;  // exclusive over the warps
+            if (lane == 31) tile_total = incl;
         }
         __syncthreads();
-        T run = carry + (w > 0 ? warp_sums[w - 1] : (T)0) + incl - local;
-        const T tile_total = warp_sums[kScanThreads / 32 - 1];
+        const T off = carry + warp_sums[w];
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
-            const int x = tid * kScanItems + k;
-            buf[x + x / 32] = run;
-            run += v[k];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
-            const int x = k * kScanThreads + tid;
-            if (base + x < n) out[base + x] = buf[x + x / 32];
+            const int64_t x = wb + k * 32 + lane;
+            if (x < n) out[x] = off + v[k];
         }
         carry += tile_total;
-        __syncthreads();  // buf and warp_sums are rewritten by the next tile
+        __syncthreads();  // warp_sums and tile_total are rewritten by the next tile
     }
     if (tid == 0) out[n] = carry;
 }
@@ -201,14 +196,18 @@ __global__ void k_scatter(const int* __restrict__ gate, int64_t n, const int32_t
 // hold tens of entries); entries of buckets >= sorted_keys keep their position.
 // With `pin`, the entry's FP32 position follows it into sorted order, its index
 // carried in .w (bit pattern), so that the search reads candidates contiguously.
+// The first entry of each bucket sets the bucket's counter back to zero, so the
+// histogram of the next sort starts from zeros without a memset.
 __global__ void k_bucket_rank(const int* __restrict__ gate, int64_t n, const int32_t* __restrict__ key, const int32_t* __restrict__ start,
                               const int32_t* __restrict__ scattered, int64_t sorted_keys,
-                              int32_t* __restrict__ order, const float4* __restrict__ pin, float4* __restrict__ pout) {
+                              int32_t* __restrict__ order, const float4* __restrict__ pin, float4* __restrict__ pout,
+                              int32_t* __restrict__ counts) {
     if (gate && *gate == 0) return;  // rebuild not needed this step
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int32_t v = scattered[p];
     const int32_t b = key[v];
+    if (p == start[b]) counts[b] = 0;
     int64_t dst = p;
     if (b < sorted_keys) {
         const int lo = start[b], hi = start[b + 1];
@@ -269,12 +268,14 @@ __global__ void k_gather_internal(const int* __restrict__ gate, int64_t n, CellG
 // Extended key and FP32 position of slot (owner o, image shift (a, b, c)):
 __device__ __forceinline__ void ext_slot(const CellGeom& g, const double* __restrict__ xw, const double* __restrict__ fw,
                                          int64_t o, int a, int b, int c, int32_t* __restrict__ key,
-                                         float4* __restrict__ p32, int64_t s) {
+                                         int32_t* __restrict__ counts, float4* __restrict__ p32, int64_t s) {
     double f[3] = {fw[3 * o] + a, fw[3 * o + 1] + b, fw[3 * o + 2] + c};
     int bx[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) bx[k] = clampi((int)floor(f[k] * g.ns[k]) + g.pad[k], 0, g.nbx[k] - 1);
-    key[s] = (bx[0] * g.nbx[1] + bx[1]) * g.nbx[2] + bx[2];
+    const int k = (bx[0] * g.nbx[1] + bx[1]) * g.nbx[2] + bx[2];
+    key[s] = k;
+    atomicAdd(&counts[k], 1);  // the extended sort's histogram
     double sv[3];
     shift_vec(g, a, b, c, sv);
     p32[s] = make_float4((float)(xw[3 * o] + sv[0]), (float)(xw[3 * o + 1] + sv[1]), (float)(xw[3 * o + 2] + sv[2]), 0.f);
@@ -287,18 +288,20 @@ __device__ __forceinline__ void ext_slot(const CellGeom& g, const double* __rest
 __global__ void k_ghosts_ext(const int* __restrict__ gate, int64_t n, CellGeom g, const double* __restrict__ xw,
                              const double* __restrict__ fw, const int32_t* __restrict__ goff, int64_t g_cap,
                              int32_t* __restrict__ owner, int32_t* __restrict__ shift, int32_t* __restrict__ key,
-                             float4* __restrict__ p32, int32_t dead_key, int* __restrict__ flags) {
+                             int32_t* __restrict__ counts, float4* __restrict__ p32, int32_t dead_key,
+                             int* __restrict__ flags) {
     if (gate && *gate == 0) return;  // rebuild not needed this step
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n + g_cap) return;
     if (s >= n) {
         if (s >= n + ghosts_in_use(goff + n, g_cap)) {
             key[s] = dead_key;
+            atomicAdd(&counts[dead_key], 1);
             p32[s] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         return;  // slots in use are written by their owners
     }
-    ext_slot(g, xw, fw, s, 0, 0, 0, key, p32, s);
+    ext_slot(g, xw, fw, s, 0, 0, 0, key, counts, p32, s);
     int lo[3], hi[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) halo_interval(g, k, fw[3 * s + k], lo[k], hi[k]);
@@ -310,7 +313,7 @@ __global__ void k_ghosts_ext(const int* __restrict__ gate, int64_t n, CellGeom g
                 if (q < g_cap) {
                     owner[q] = (int32_t)s;
                     shift[q] = pack_shift(a, b, c);
-                    ext_slot(g, xw, fw, s, a, b, c, key, p32, n + q);
+                    ext_slot(g, xw, fw, s, a, b, c, key, counts, p32, n + q);
                 } else {
                     atomicOr(&flags[FLAG_GHOST_OVERFLOW], 1);
                 }
@@ -420,10 +423,13 @@ __global__ void __launch_bounds__(256) k_nbr_search(const int* __restrict__ gate
 }
 
 // per evaluation: refresh owned + ghost positions (FP64 -> hi/lo FP32 pair)
+// (with c0, also the first layer's coefficients c0[species] of every slot)
 __global__ void k_refresh(int64_t n, const int32_t* __restrict__ g_count, int64_t g_cap, CellGeom g,
                           const double* __restrict__ pos, const int32_t* __restrict__ perm,
                           const int32_t* __restrict__ wrapm, const int32_t* __restrict__ owner,
-                          const int32_t* __restrict__ shift, float4* __restrict__ hi, float4* __restrict__ lo) {
+                          const int32_t* __restrict__ shift, float4* __restrict__ hi, float4* __restrict__ lo,
+                          const int32_t* __restrict__ species, const float* __restrict__ c0,
+                          float* __restrict__ coef) {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n + ghosts_in_use(g_count, g_cap)) return;
     int64_t o = s;
@@ -447,6 +453,12 @@ __global__ void k_refresh(int64_t n, const int32_t* __restrict__ g_count, int64_
     }
     hi[s] = make_float4(h[0], h[1], h[2], 0.f);
     lo[s] = make_float4(l[0], l[1], l[2], 0.f);
+    if (c0) {
+        const float4* src = reinterpret_cast<const float4*>(c0 + species[o] * NPHI);
+        float4* dst = reinterpret_cast<float4*>(coef + (size_t)s * NPHI);
+        dst[0] = src[0];
+        dst[1] = src[1];
+    }
 }
 
 // per evaluation: live (d < r_c) entries of every row, moved to the row's front
@@ -500,19 +512,19 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 }  // namespace
 
-// Counting sort of n keys in [0, nkeys): order = indices sorted by (key, index) within the first
-// `sorted_keys` buckets (later buckets hold unused capacity whose order does not matter);
-// start = bucket offsets.
+// Counting sort of n keys in [0, nkeys) whose histogram `counts` the kernel that
+// produced the keys has filled: order = indices sorted by (key, index) within the
+// first `sorted_keys` buckets (later buckets hold unused capacity whose order does
+// not matter); start = bucket offsets.  The scan zeroes counts for the scatter's
+// cursors and the ranking zeroes them again for the next sort.
 static cudaError_t counting_sort(cudaStream_t s, const int* gate, int64_t n, int64_t nkeys, const int32_t* key,
                                  int32_t* counts, int32_t* start, int32_t* scattered, int32_t* order,
                                  int64_t sorted_keys, const float4* pin = nullptr, float4* pout = nullptr) {
-    cudaMemsetAsync(counts, 0, sizeof(int32_t) * nkeys, s);
-    if (n > 0) k_hist<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, key, counts);
-    k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(gate, nkeys, counts, start);
-    cudaMemsetAsync(counts, 0, sizeof(int32_t) * nkeys, s);
+    k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(gate, nkeys, counts, start, true);
     if (n > 0) {
         k_scatter<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, key, start, counts, scattered);
-        k_bucket_rank<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, key, start, scattered, sorted_keys, order, pin, pout);
+        k_bucket_rank<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, key, start, scattered, sorted_keys, order, pin, pout,
+                                                         counts);
     }
     return cudaGetLastError();
 }
@@ -550,11 +562,11 @@ static cudaError_t stage_sort_and_count(cudaStream_t s, reann_nlist* nl, const d
     const int64_t n = nl->n;
     NlistScratch& w = nl->w;
     k_wrap_key<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, pos, w.species_c, nl->n_elem, nl->geom, w.xw_c, w.fw_c, w.mw_c,
-                                                  w.key, flags, nl->pos_ref);
+                                                  w.key, w.counts, flags, nl->pos_ref);
     counting_sort(s, gate, n, owned_keys(nl), w.key, w.counts, w.start, w.scat, nl->perm, owned_keys(nl));
     k_gather_internal<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, nl->geom, nl->perm, w.xw_c, w.fw_c, w.mw_c, w.species_c,
                                                          w.xw, w.fw, nl->wrapm, nl->species, w.gcnt);
-    k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(gate, n, w.gcnt, w.goff);
+    k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(gate, n, w.gcnt, w.goff, false);
     return cudaGetLastError();
 }
 
@@ -564,7 +576,7 @@ static cudaError_t stage_ghosts_and_bins(cudaStream_t s, reann_nlist* nl, int* f
     NlistScratch& w = nl->w;
     const int64_t nx = ext_bins(nl);
     k_ghosts_ext<<<blocks_for(next, 256), 256, 0, s>>>(gate, n, nl->geom, w.xw, w.fw, w.goff, nl->g_cap, nl->g_owner,
-                                                       nl->g_shift, w.ekey, w.p32, (int32_t)nx, flags);
+                                                       nl->g_shift, w.ekey, w.ecounts, w.p32, (int32_t)nx, flags);
     counting_sort(s, gate, next, nx + 1, w.ekey, w.ecounts, w.estart, w.escat, w.eorder, nx, w.p32, w.p32s);
     return cudaGetLastError();
 }
@@ -602,6 +614,7 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
         !w.species_c || !w.scat || !nl->perm || !nl->species || !nl->wrapm || !nl->pos_ref)
         return set_error(ctx, REANN_E_NOMEM, "neighbour-list allocation failed");
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(w.species_c, species, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    REANN_CUDA_TRY(ctx, cudaMemsetAsync(w.counts, 0, sizeof(int32_t) * nkeys, s));  // kept zero between sorts
     REANN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * NFLAGS, s));
     REANN_CUDA_TRY(ctx, stage_sort_and_count(s, nl, pos, ctx->d_flags, nullptr));
     // sizes: element ranges of the internal order and the ghost count
@@ -634,6 +647,7 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
     w.escat = dalloc<int32_t>(nl, next);
     if (!nl->g_owner || !nl->g_shift || !w.ekey || !w.p32 || !w.p32s || !w.ecounts || !w.estart || !w.eorder || !w.escat)
         return set_error(ctx, REANN_E_NOMEM, "ghost allocation failed");
+    REANN_CUDA_TRY(ctx, cudaMemsetAsync(w.ecounts, 0, sizeof(int32_t) * (nx + 1), s));  // kept zero between sorts
     REANN_CUDA_TRY(ctx, stage_ghosts_and_bins(s, nl, ctx->d_flags, nullptr));
     // row capacity: expected neighbours from the number density, with headroom
     const CellGeom& g = nl->geom;
@@ -678,10 +692,11 @@ cudaError_t launch_moved(cudaStream_t s, const reann_nlist* nl, const double* po
 
 const int32_t* ghost_count_ptr(const reann_nlist* nl) { return nl->w.goff + nl->n; }
 
-cudaError_t launch_refresh_positions(cudaStream_t s, const reann_nlist* nl, const double* pos) {
+cudaError_t launch_refresh_positions(cudaStream_t s, const reann_nlist* nl, const double* pos, const float* c0) {
     const int64_t total = nl->n + nl->g_cap;
     k_refresh<<<blocks_for(total, 256), 256, 0, s>>>(nl->n, ghost_count_ptr(nl), nl->g_cap, nl->geom, pos, nl->perm,
-                                                     nl->wrapm, nl->g_owner, nl->g_shift, nl->pos_hi, nl->pos_lo);
+                                                     nl->wrapm, nl->g_owner, nl->g_shift, nl->pos_hi, nl->pos_lo,
+                                                     nl->species, c0, nl->coef);
     return cudaGetLastError();
 }
 

@@ -114,8 +114,6 @@ int alloc_eval_buffers(reann_ctx* ctx, reann_nlist* nl, const std::vector<std::a
     nl->bbar = nl_alloc<float>(nl, (size_t)ne * NREC);  // adjoint records (bbar with c)
     nl->cbar = nl_alloc<float>(nl, (size_t)n * NPHI);
     nl->grad = nl_alloc<float>(nl, (size_t)n * 3);
-    nl->n_partial = (int)((n + 2047) / 2048);
-    nl->partial = nl_alloc<double>(nl, nl->n_partial);
     // element tiles of the atomic networks
     std::vector<std::array<int, 3>> own;
     if (!ranges) {
@@ -129,6 +127,9 @@ int alloc_eval_buffers(reann_ctx* ctx, reann_nlist* nl, const std::vector<std::a
         for (int r = rg[1]; r < rg[2]; r += 128) nl->tiles128_h.push_back(Tile{rg[0], r, std::min(128, rg[2] - r), 0});
     }
     nl->tiles = nl_alloc<Tile>(nl, nl->tiles_h.size());
+    // energy partial sums: per 2048 atoms, or per network tile when the energy network sums them
+    nl->n_partial = (int)std::max<int64_t>((n + 2047) / 2048, (int64_t)nl->tiles_h.size());
+    nl->partial = nl_alloc<double>(nl, nl->n_partial);
     nl->tiles128 = nl_alloc<Tile>(nl, nl->tiles128_h.size());
     if (!nl->tiles128) return set_error(ctx, REANN_E_NOMEM, "evaluation buffers: out of device memory");
     if (!nl->tiles128_h.empty())
@@ -759,16 +760,15 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
     const int64_t n = nl->n, ne = nl->n + nl->g_cap;
     float* vir = virial ? nl->vir : nullptr;
     if (pos) {
-        ProfScope p(ctx, PR_REFRESH);
-        REANN_CUDA_TRY(ctx, launch_refresh_positions(s, nl, pos));
+        ProfScope p(ctx, PR_REFRESH);  // positions and the first layer's coefficients
+        REANN_CUDA_TRY(ctx, launch_refresh_positions(s, nl, pos, ctx->d_c0));
+    } else {
+        ProfScope p(ctx, PR_INIT);
+        REANN_CUDA_TRY(ctx, launch_init_coef(s, nl, ctx->d_c0));
     }
     {
         ProfScope p(ctx, PR_LIVE);
         REANN_CUDA_TRY(ctx, launch_live_edges(s, nl, ctx->radial.rc2, ctx->d_flags));
-    }
-    {
-        ProfScope p(ctx, PR_INIT);
-        REANN_CUDA_TRY(ctx, launch_init_coef(s, nl, ctx->d_c0));
     }
     const bool pairs = ctx->model.pairs;
     const size_t lw = (size_t)(LMAX + 1) * NPHI * ctx->model.n_orb();
@@ -790,6 +790,8 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
         }
         ProfScope p(ctx, PR_MLP_FWD);
         const bool energy_net = t == T - 1;
+        // the FP32 energy network also sums the tiles' energies (unless per-structure sums are wanted)
+        double* epart = energy_net && !seg ? nl->partial : nullptr;
         float* out = energy_net ? nl->eps : nl->coef + (size_t)(t + 1) * ne * NPHI;
         const int out_stride = energy_net ? 1 : NPHI;
         if (ctx->precision != REANN_MLP_FP32)
@@ -797,12 +799,14 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
                                                   rho_t, out, out_stride, ctx->d_flags, gh));
         else
             REANN_CUDA_TRY(ctx, launch_mlp_fwd_f32(s, nl, ctx->nets, t, energy_net, rho_t, out, out_stride, pairs, gh,
-                                                  nl->dsave + (size_t)t * n * (H1 + H2)));
+                                                  nl->dsave + (size_t)t * n * (H1 + H2), epart));
     }
     {
         ProfScope p(ctx, PR_ENERGY);
         if (seg)
             REANN_CUDA_TRY(ctx, launch_segment_energy(s, seg, nseg, nl->eps, energy));
+        else if (ctx->precision == REANN_MLP_FP32)
+            REANN_CUDA_TRY(ctx, launch_energy_final(s, nl->partial, (int)nl->tiles_h.size(), energy));
         else
             REANN_CUDA_TRY(ctx, launch_energy_sum(s, nl, energy));
     }
@@ -838,10 +842,10 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
         }
         ProfScope p(ctx, PR_DENSITY_ADJ);
         REANN_CUDA_TRY(ctx, launch_density_adj(s, nl, ctx->radial, nl->bbar, nl->cbar, nl->grad, t >= 1,
-                                               ctx->d_flags, vir));
+                                               ctx->d_flags, vir, t == 0 ? forces : nullptr,
+                                               t == 0 ? atom_energy : nullptr));
     }
     ProfScope p(ctx, PR_OUTPUT);
-    REANN_CUDA_TRY(ctx, launch_scatter_outputs(s, nl, forces, atom_energy));
     if (vir) {
         REANN_CUDA_TRY(ctx, launch_virial_sum(s, nl, vir, nl->vir_partial, virial));
         if (atom_virial) REANN_CUDA_TRY(ctx, launch_unpermute_rows(s, nl, vir, 9, atom_virial, 9));

@@ -51,4 +51,4 @@ def test_single_rank_identity():
 
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.aggregate(100, 2.0, 1) == pytest.approx(5e4)
-    assert bench.launches_per_step(3) == 31
+    assert bench.launches_per_step(3) == 26
