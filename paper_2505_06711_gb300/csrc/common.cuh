@@ -406,10 +406,11 @@ cudaError_t launch_density_fwd(cudaStream_t s, const reann_nlist* nl, const Radi
                                float* rho, float* bck, bool pairs = false);
 cudaError_t launch_bbar(cudaStream_t s, const reann_nlist* nl, const float* W, const float* bck, const float* rhobar,
                         const float* coef, float* rec, bool pairs = false, GhostOut gh = {});
-// forces / atom_energy (caller order): the last reverse layer writes the outputs itself
+// forces / atom_energy (caller order): the last reverse layer writes the outputs itself;
+// first: the first reverse layer writes grad (and vir) instead of accumulating
 cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* rec, float* cbar,
                                float* grad, bool want_cbar, int* flags, float* vir = nullptr,
-                               float* forces = nullptr, float* atom_energy = nullptr);
+                               float* forces = nullptr, float* atom_energy = nullptr, bool first = false);
 cudaError_t upload_pair_table();
 cudaError_t launch_virial_sum(cudaStream_t s, const reann_nlist* nl, const float* vir, double* partial, double* out);
 cudaError_t launch_energy_sum(cudaStream_t s, const reann_nlist* nl, double* energy);

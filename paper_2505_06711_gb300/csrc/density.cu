@@ -375,12 +375,15 @@ constexpr int kGeoStride = 20;
 constexpr int kGroupStride = 8 * kGeoStride + 8;
 
 // With forces set (the last reverse layer), the kernel also writes F = -dE/dr
-// and the atomic energies in caller order (perm: internal -> caller index).
+// and the atomic energies in caller order (perm: internal -> caller index);
+// with first set (the first reverse layer), grad and vir are written, not
+// accumulated.
 struct Outputs {
     const int32_t* perm;
     const float* eps;
     float* forces;
     float* atom_energy;
+    bool first;
 };
 
 // WANT_VIR: also W -= (dE/dr_e) r_e^T over the atom's own edges (their
@@ -558,9 +561,15 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
     if (!valid) return;
     if (m == 0) {
         float* gr = grad + (size_t)atom * 3;
-        gr[0] += gx;
-        gr[1] += gy;
-        gr[2] += gz;
+        if (out.first) {  // the first reverse layer starts the sums (no memset)
+            gr[0] = gx;
+            gr[1] = gy;
+            gr[2] = gz;
+        } else {
+            gr[0] += gx;
+            gr[1] += gy;
+            gr[2] += gz;
+        }
         if (out.forces) {  // the last layer: F = -dE/dr and eps_i in caller order
             const int64_t c = out.perm[atom];
             out.forces[3 * c] = -gr[0];
@@ -571,7 +580,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
         if (WANT_VIR) {
             float* vr = vir + (size_t)atom * 9;
 #pragma unroll
-            for (int q = 0; q < 9; ++q) vr[q] += w[q];
+            for (int q = 0; q < 9; ++q) vr[q] = out.first ? w[q] : vr[q] + w[q];
         }
     }
     if (WANT_CBAR) cbar[(size_t)atom * NPHI + m] = cb;
@@ -746,8 +755,9 @@ cudaError_t upload_pair_table() {
 }
 
 cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radial& r, const float* rec, float* cbar,
-                               float* grad, bool want_cbar, int* flags, float* vir, float* forces, float* atom_energy) {
-    const Outputs out{forces ? nl->perm : nullptr, forces ? nl->eps : nullptr, forces, atom_energy};
+                               float* grad, bool want_cbar, int* flags, float* vir, float* forces, float* atom_energy,
+                               bool first) {
+    const Outputs out{forces ? nl->perm : nullptr, forces ? nl->eps : nullptr, forces, atom_energy, first};
     (void)flags;
     const int64_t per_block = kAdjWarps * kAdjGroups;
     const unsigned nb = blocks_for(nl->n, per_block);

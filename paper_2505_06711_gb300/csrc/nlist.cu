@@ -114,68 +114,73 @@ __global__ void k_wrap_key(const int* __restrict__ gate, int64_t n, const double
 
 // ---- deterministic counting sort ------------------------------------------
 
-// Exclusive scan of `in` (n entries) into out[0..n] by one block of
-// kScanThreads, in tiles of kScanThreads x kScanItems entries (one tile for up
-// to 24,576 entries).  Warp w takes the tile's w-th chunk of 32 x kScanItems
-// consecutive entries as kScanItems rows of 32 (coalesced loads and stores
-// straight from registers); each row is a warp scan chained to the previous
-// row's total, the warp totals are scanned by warp 0, and a running carry joins
-// the tiles.  With zero_in the entries are set to zero once read.
-constexpr int kScanItems = 24;
+// Exclusive scan of `in` (n entries) into out[0..n]; one block of kScanThreads
+// walking tiles of kScanThreads x kScanItems entries: each tile is loaded and
+// stored coalesced through shared memory (padded one word per 32 against bank
+// conflicts), each thread scans kScanItems consecutive entries, and a
+// two-level warp scan joins the threads; a running carry joins the tiles.
+// With zero_in the entries are set to zero once read.
+constexpr int kScanItems = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(kScanThreads) k_scan_single(const int* __restrict__ gate, int64_t n,
-                                                                T* __restrict__ in, T* __restrict__ out, bool zero_in) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_single(const int* __restrict__ gate, int64_t n, T* __restrict__ in,
+                                                                T* __restrict__ out, bool zero_in) {
     if (gate && *gate == 0) return;  // rebuild not needed this step
-    constexpr int CHUNK = 32 * kScanItems, TILE = kScanThreads * kScanItems;
+    constexpr int TILE = kScanThreads * kScanItems;
+    __shared__ T buf[TILE + TILE / 32];
     __shared__ T warp_sums[kScanThreads / 32];
-    __shared__ T tile_total;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     T carry = 0;
     for (int64_t base = 0; base < n; base += TILE) {
-        const int64_t wb = base + (int64_t)w * CHUNK;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            const int x = k * kScanThreads + tid;
+            buf[x + x / 32] = (base + x < n) ? in[base + x] : (T)0;
+            if (zero_in && base + x < n) in[base + x] = (T)0;
+        }
+        __syncthreads();
         T v[kScanItems];
+        T local = 0;
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
-            const int64_t x = wb + k * 32 + lane;
-            v[k] = x < n ? in[x] : (T)0;
-            if (zero_in && x < n) in[x] = (T)0;
+            const int x = tid * kScanItems + k;
+            v[k] = buf[x + x / 32];
+            local += v[k];
         }
-        T run = 0;  // the warp's running total over its rows
+        T incl = local;
 #pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
-            T incl = v[k];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const T y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const T row_total = __shfl_sync(0xffffffffu, incl, 31);
-            v[k] = run + incl - v[k];  // exclusive within the warp's chunk
-            run += row_total;
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
         }
-        if (lane == 0) warp_sums[w] = run;
+        if (lane == 31) warp_sums[w] = incl;
         __syncthreads();
         if (w == 0) {
-            const T t = warp_sums[lane];
-            T incl = t;
+            T s = warp_sums[lane];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const T y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
+                const T y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
             }
-            warp_sums[lane] = incl - t;  // exclusive over the warps
-            if (lane == 31) tile_total = incl;
+            warp_sums[lane] = s;  // inclusive
         }
         __syncthreads();
-        const T off = carry + warp_sums[w];
+        T run = carry + (w > 0 ? warp_sums[w - 1] : (T)0) + incl - local;
+        const T tile_total = warp_sums[kScanThreads / 32 - 1];
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
-            const int64_t x = wb + k * 32 + lane;
-            if (x < n) out[x] = off + v[k];
+            const int x = tid * kScanItems + k;
+            buf[x + x / 32] = run;
+            run += v[k];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            const int x = k * kScanThreads + tid;
+            if (base + x < n) out[base + x] = buf[x + x / 32];
         }
         carry += tile_total;
-        __syncthreads();  // warp_sums and tile_total are rewritten by the next tile
+        __syncthreads();  // buf and warp_sums are rewritten by the next tile
     }
     if (tid == 0) out[n] = carry;
 }

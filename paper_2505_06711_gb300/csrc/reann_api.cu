@@ -811,8 +811,6 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
             REANN_CUDA_TRY(ctx, launch_energy_sum(s, nl, energy));
     }
     // reverse: Eqs. 3-5, one vector-Jacobian product per layer
-    REANN_CUDA_TRY(ctx, cudaMemsetAsync(nl->grad, 0, sizeof(float) * n * 3, s));
-    if (vir) REANN_CUDA_TRY(ctx, cudaMemsetAsync(vir, 0, sizeof(float) * n * 9, s));
     for (int t = T - 1; t >= 0; --t) {
         const float* coef_t = nl->coef + (size_t)t * ne * NPHI;
         const float* rho_t = nl->rho + (size_t)t * n * nf;
@@ -843,7 +841,7 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
         ProfScope p(ctx, PR_DENSITY_ADJ);
         REANN_CUDA_TRY(ctx, launch_density_adj(s, nl, ctx->radial, nl->bbar, nl->cbar, nl->grad, t >= 1,
                                                ctx->d_flags, vir, t == 0 ? forces : nullptr,
-                                               t == 0 ? atom_energy : nullptr));
+                                               t == 0 ? atom_energy : nullptr, t == T - 1));
     }
     ProfScope p(ctx, PR_OUTPUT);
     if (vir) {
