@@ -56,7 +56,7 @@ FLOP_PER_ATOM_FWD = 2880              # contraction 10x16x8 FMA + 160 squares
 FLOP_PER_LIVE_EDGE_ADJ = 640          # 80 x (2 FMA combination + 2 FMA radial/angular sums)
 FLOP_PER_LIVE_EDGE_ADJ_CBAR = 160     # 80 FMA of cbar (layers t >= 1)
 FLOP_PER_ATOM_MLP_FWD = {8: 15360, 1: 14464}
-FLOP_PER_ATOM_MLP_BWD = {8: 29696, 1: 28800}
+FLOP_PER_ATOM_MLP_BWD = {8: 15360, 1: 14464}  # the vector-Jacobian product W3, W2, W1 (no recompute)
 FLOP_PER_ATOM_BBAR = 5440             # g (1280 FMA) + gbar (160) + bbar (1280 FMA)
 
 # DRAM traffic per launch of the dominant kernel from one ncu capture of this
@@ -455,8 +455,8 @@ def region_flops(region: str, n_atoms: int, n_live: int, T: int, launches: int) 
         return T * n_live * FLOP_PER_LIVE_EDGE_ADJ + (T - 1) * n_live * FLOP_PER_LIVE_EDGE_ADJ_CBAR
     if region == "mlp_fwd":
         return n_atoms * ((T - 1) * FLOP_PER_ATOM_MLP_FWD[8] + FLOP_PER_ATOM_MLP_FWD[1])
-    if region == "mlp_bwd":
-        return n_atoms * ((T - 1) * FLOP_PER_ATOM_MLP_BWD[8] + FLOP_PER_ATOM_MLP_BWD[1])
+    if region == "mlp_bwd":  # the FP32 backward networks also take the bbar step
+        return n_atoms * ((T - 1) * FLOP_PER_ATOM_MLP_BWD[8] + FLOP_PER_ATOM_MLP_BWD[1] + T * FLOP_PER_ATOM_BBAR)
     if region == "bbar":
         return T * n_atoms * FLOP_PER_ATOM_BBAR
     return None
