@@ -28,7 +28,7 @@ namespace reann {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kWarps = 8;          // warps per block
+constexpr int kWarps = 4;          // warps per block
 constexpr int kAtomsPerWarp = 8;   // quads per warp
 constexpr int kBStride = 84;       // padded per-atom row in shared memory (16 B aligned)
 
@@ -124,7 +124,7 @@ __device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.w
 // PAIRS = true: the orbital-pair products rho_{l,(k,k')} = sum_{a in l} w_a g_{a,k} g_{a,k'},
 // k <= k' over 8 orbitals (108 features).
 template <bool PAIRS>
-__global__ void __launch_bounds__(kWarps * 32, 2) k_density_fwd(int64_t n, int stride, Radial R,
+__global__ void __launch_bounds__(kWarps * 32, 16 / kWarps) k_density_fwd(int64_t n, int stride, Radial R,
                                                             const int32_t* __restrict__ live,
                                                             const int32_t* __restrict__ live_cnt,
                                                             const float4* __restrict__ phi_hi,
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(256) k_bbar(int64_t n, const float* __restrict
 // one full 128 B line of the record), and accumulates its share of dE/dr_k;
 // cbar_{k,m} is lane m's own sum.  The force is reduced over the 8 lanes once
 // per atom.
-constexpr int kAdjWarps = 8;
+constexpr int kAdjWarps = 2;  // small blocks: the block scheduler balances the SMs at fine grain
 constexpr int kAdjGroups = 4;  // centre atoms per warp
 // Edge record in shared memory: x y z 1/d | d fc fc' - | g_0..g_7 (16 floats).
 // Strides chosen bank-conflict free: a record every 20 floats (8 lanes' float4
