@@ -175,6 +175,9 @@ struct CellGeom {
     int pad[3];      // extra search bins per side for ghosts
     int nbx[3];      // ns + 2 pad
     int sw[3];       // stencil half-width in search bins per axis
+    int ortho;       // rectangular cell with a positive diagonal: the search trims each stencil column
+    float binw[3];   // search-bin widths (A) of a rectangular cell, and their inverses
+    float binw_inv[3];
     double rcut2;    // (r_c + skin)^2
     float rcut2_f;
     float margin;    // FP32 pre-test band around rcut2 (A^2) decided in FP64

@@ -360,9 +360,31 @@ __global__ void __launch_bounds__(256) k_nbr_search(const int* __restrict__ gate
         int st = 0, len = 0;
         if (cb + lane < ncol) {
             const int col = cb + lane;
-            const int bin0 = ((x0 + col / ny) * g.nbx[1] + (y0 + col % ny)) * g.nbx[2];
-            st = bstart[bin0 + z0];
-            len = bstart[bin0 + z1 + 1] - st;
+            const int bx = x0 + col / ny, by = y0 + col % ny;
+            const int bin0 = (bx * g.nbx[1] + by) * g.nbx[2];
+            int za = z0, zb = z1;
+            if (g.ortho) {
+                // rectangular cell: bin b of axis k spans [(b - pad) w, (b - pad + 1) w) in Cartesian
+                // coordinates; keep the z-bins within sqrt(r^2 - rho^2) of the atom, rho being the
+                // atom's distance to the column.  FP32 (the FP64 units are slow) with 2e-3 A of slack,
+                // far above the rounding of coordinates and bin edges.
+                constexpr float kSlack = 2e-3f;
+                const float lx = (bx - g.pad[0]) * g.binw[0], ly = (by - g.pad[1]) * g.binw[1];
+                const float dx = fmaxf(0.f, fmaxf(lx - pi.x, pi.x - (lx + g.binw[0])) - kSlack);
+                const float dy = fmaxf(0.f, fmaxf(ly - pi.y, pi.y - (ly + g.binw[1])) - kSlack);
+                const float rho2 = dx * dx + dy * dy;
+                if (rho2 >= g.rcut2_f) {
+                    zb = za - 1;
+                } else {
+                    const float hz = sqrtf(g.rcut2_f - rho2) + kSlack;
+                    za = max(z0, (int)floorf((pi.z - hz) * g.binw_inv[2]) + g.pad[2]);
+                    zb = min(z1, (int)floorf((pi.z + hz) * g.binw_inv[2]) + g.pad[2]);
+                }
+            }
+            if (za <= zb) {
+                st = bstart[bin0 + za];
+                len = bstart[bin0 + zb + 1] - st;
+            }
         }
         int pref = len;  // inclusive scan of the run lengths
 #pragma unroll

@@ -84,6 +84,12 @@ int make_geometry(reann_ctx* ctx, const double* cell, double r_cut, CellGeom* g)
         g->nbx[k] = g->ns[k] + 2 * g->pad[k];
         maxc += std::fabs(g->h[k]) + std::fabs(g->h[3 + k]) + std::fabs(g->h[6 + k]);
     }
+    g->ortho = g->h[1] == 0.0 && g->h[2] == 0.0 && g->h[3] == 0.0 && g->h[5] == 0.0 && g->h[6] == 0.0 &&
+               g->h[7] == 0.0 && g->h[0] > 0.0 && g->h[4] > 0.0 && g->h[8] > 0.0;
+    for (int k = 0; k < 3; ++k) {
+        g->binw[k] = (float)(g->h[4 * k] / g->ns[k]);
+        g->binw_inv[k] = (float)(g->ns[k] / g->h[4 * k]);
+    }
     g->rcut2 = r_cut * r_cut;
     g->rcut2_f = (float)g->rcut2;
     // FP32 positions carry up to half an ulp of the largest coordinate each
