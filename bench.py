@@ -209,7 +209,7 @@ def run_decomp(args, steps: int = 100):
 
 
 def run_serve(args):
-    """Continuous-batching serving: Poisson arrivals of mixed water / Cu structures, T = 3, BF16 networks.
+    """Continuous-batching serving: Poisson arrivals of mixed water / Cu structures, T = 3, FP32 networks.
 
     Request mix: 50/50 water (16..2048 molecules) / fcc Cu (3..20 cells per
     side), log-uniform sizes, per-request jitter.  Baseline: the same requests
@@ -236,7 +236,7 @@ def run_serve(args):
     alone_atoms = sum(r.n_atoms for r in alone_reqs) / st["wall_s"]
     pool = {"max_atoms": 1 << 17, "max_ghosts": 1 << 18, "max_structures": 256, "stride": 160}
     server = Server(spec, pool["max_atoms"], pool["max_ghosts"], pool["max_structures"], pool["stride"],
-                    precision=binding.REANN_MLP_BF16)
+                    precision=binding.REANN_MLP_FP32)
     try:
         serve_stream(server, make_requests(templates, 64, alone_rps, seed=102))  # warm-up, graph capture
         reqs = make_requests(templates, args.serve_requests, 0.7 * alone_rps, seed=103)
@@ -254,7 +254,7 @@ def run_serve(args):
     saturated = sweep[-1]["atom_evals_per_s"]
     return {
         "workload": "Poisson arrivals; 50/50 water 16..2048 molecules / Cu fcc 3..20 cells, log-uniform sizes, "
-                    "jitter N(0, 0.02 A); T = 3; pooled launches with BF16 atomic networks",
+                    "jitter N(0, 0.02 A); T = 3; pooled launches with FP32 atomic networks",
         "pool": pool,
         "alone_fp32": {"requests": n_alone, "requests_per_s": alone_rps, "atom_evals_per_s": alone_atoms},
         "main": main,

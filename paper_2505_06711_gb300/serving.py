@@ -55,7 +55,7 @@ class Server:
     """
 
     def __init__(self, spec, max_atoms: int, max_ghosts: int, max_structures: int, stride: int = 160,
-                 precision: int = binding.REANN_MLP_BF16, skin: float = 1.0, builders: int = 4):
+                 precision: int = binding.REANN_MLP_FP32, skin: float = 1.0, builders: int = 4):
         import torch
 
         self.max_atoms, self.max_structures, self.skin = max_atoms, max_structures, skin
