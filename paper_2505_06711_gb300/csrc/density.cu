@@ -29,6 +29,7 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kWarps = 4;          // warps per block
+constexpr int kFwdStages = 2;      // forward: a lane's next kFwdStages - 1 edges are in flight (3, 4 measured slower)
 constexpr int kAtomsPerWarp = 8;   // quads per warp
 constexpr int kBStride = 84;       // padded per-atom row in shared memory (16 B aligned)
 
@@ -117,7 +118,8 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // ------------------------------------------------------------- forward ---
 // PAIRS = false: Eq. 1, rho_{l,k} = sum_{a in l} w_a g_{a,k}^2 over 16 orbitals.
@@ -134,9 +136,9 @@ __global__ void __launch_bounds__(kWarps * 32, 16 / kWarps) k_density_fwd(int64_
                                                             float* __restrict__ bck) {
     constexpr int KO = PAIRS ? NORB_P : NORB;
     __shared__ __align__(16) float sW[(LMAX + 1) * NPHI * KO];
-    // During the edge loop: two stages of a lane's next neighbours (hi, lo position
-    // and c of j), [stage][part][thread] float4; afterwards the b rows of the atoms.
-    constexpr int kStage = 2 * 4 * kWarps * 32 * 4;
+    // During the edge loop: kFwdStages stages of a lane's next neighbours (hi, lo
+    // position and c of j), [stage][part][thread] float4; afterwards the b rows.
+    constexpr int kStage = kFwdStages * 4 * kWarps * 32 * 4;
     static_assert(kStage >= kWarps * kAtomsPerWarp * kBStride, "b rows must fit in the staging area");
     __shared__ __align__(16) float sU[kStage];
     float4* stg = reinterpret_cast<float4*>(sU);
@@ -161,20 +163,25 @@ __global__ void __launch_bounds__(kWarps * 32, 16 / kWarps) k_density_fwd(int64_
             cp_async16(d + 2 * kT, coef + (size_t)j * NPHI);
             cp_async16(d + 3 * kT, coef + (size_t)j * NPHI + 4);
         };
-        // the lane's edges e = q, q + 4, ...: edge e + 4 is copied while edge e is
-        // computed, and the index of edge e + 8 is loaded
-        if (q < cnt) stage(0, row[q]);
-        cp_async_commit();
-        int j_nx = q + 4 < cnt ? row[q + 4] : 0;
-        int st = 0;
-        for (int e = q; e < cnt; e += 4) {
-            if (e + 4 < cnt) stage(st ^ 1, j_nx);
+        // the lane's edges e = q, q + 4, ...: the copies of the next kFwdStages - 1 edges
+        // are in flight while edge e is computed, and the index after them is loaded
+        constexpr int NST = kFwdStages;
+#pragma unroll
+        for (int p = 0; p < NST - 1; ++p) {
+            if (q + 4 * p < cnt) stage(p, row[q + 4 * p]);
             cp_async_commit();
-            j_nx = e + 8 < cnt ? row[e + 8] : 0;
-            cp_async_wait_prior();  // edge e's stage has landed
+        }
+        int j_nx = q + 4 * (NST - 1) < cnt ? row[q + 4 * (NST - 1)] : 0;
+        int st = 0;  // stage of edge e
+        for (int e = q; e < cnt; e += 4) {
+            const int e_st = e + 4 * (NST - 1);  // the edge copied now, into the stage edge e - 4 used
+            if (e_st < cnt) stage(st == 0 ? NST - 1 : st - 1, j_nx);
+            cp_async_commit();
+            j_nx = e_st + 4 < cnt ? row[e_st + 4] : 0;
+            cp_async_wait<NST - 1>();  // edge e's stage has landed
             const float4* src = stg + st * 4 * kT + threadIdx.x;
             const float4 hj = src[0], lj = src[kT], c0 = src[2 * kT], c1 = src[3 * kT];
-            st ^= 1;
+            st = st == NST - 1 ? 0 : st + 1;
             const float x = (hj.x - hi_i.x) + (lj.x - lo_i.x);
             const float y = (hj.y - hi_i.y) + (lj.y - lo_i.y);
             const float z = (hj.z - hi_i.z) + (lj.z - lo_i.z);
