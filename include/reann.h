@@ -61,6 +61,8 @@ extern "C" {
 #define REANN_MLP_BF16 1   /* tcgen05 tensor cores, BF16 operands, FP32 accumulation         */
 #define REANN_MLP_BF16X3 2 /* tcgen05, every operand a BF16 hi + lo pair, 3 MMAs per K step,
                               FP32 accumulation (about 16 significant bits per operand)      */
+#define REANN_MLP_FP8 3    /* tcgen05, FP8 E4M3 operands with one FP32 scale per weight
+                              matrix and per 128-row activation tile, FP32 accumulation     */
 
 typedef struct reann_model reann_model;
 typedef struct reann_ctx reann_ctx;
@@ -108,9 +110,10 @@ int reann_ctx_create(const reann_model* model, void* cuda_stream, reann_ctx** ou
 void reann_ctx_free(reann_ctx* ctx);
 
 /*
- * Precision of the atomic networks: REANN_MLP_FP32 (default), REANN_MLP_BF16
- * or REANN_MLP_BF16X3.  The density and reverse-pass edge arithmetic stays
- * FP32 and the energy sum FP64 in every mode.  Errors: REANN_E_ARG.
+ * Precision of the atomic networks: REANN_MLP_FP32 (default), REANN_MLP_BF16,
+ * REANN_MLP_BF16X3 or REANN_MLP_FP8 (the tensor-core modes for the 48-feature
+ * models only).  The density and reverse-pass edge arithmetic stays FP32 and
+ * the energy sum FP64 in every mode.  Errors: REANN_E_ARG.
  */
 int reann_ctx_set_mlp_precision(reann_ctx* ctx, int precision);
 

@@ -26,6 +26,7 @@ REANN_E_CAPACITY = -7
 REANN_MLP_FP32 = 0
 REANN_MLP_BF16 = 1
 REANN_MLP_BF16X3 = 2
+REANN_MLP_FP8 = 3
 
 _NAMES = {
     REANN_E_ARG: "REANN_E_ARG",

@@ -218,9 +218,16 @@ struct Tile {
 // K-major core-matrix layout; forward = W1^T 64x48 | W2^T 64x64 | W3^T 16x64,
 // backward = W3 64x16 | W2 64x64 | W1 48x64; lo = BF16 rounding of w - hi.
 struct TcImg {
-    const uint8_t* img;
+    const uint8_t* img;           // BF16 images (forward hi | lo | backward hi | lo)
     const float *b1, *b2, *b3;
+    const uint8_t* img8;          // FP8 E4M3 images (forward | backward), kF8Img bytes
+    const float* s8;              // their per-matrix scales s(W1), s(W2), s(W3)
 };
+// FP8 image of one (layer, element): forward W1^T 64x64 | W2^T 64x64 | W3^T 16x64,
+// backward W3 64x32 | W2 64x64 | W1 48x64 (K padded to multiples of 32)
+constexpr uint32_t kF8Fwd = 64 * 64 + 64 * 64 + 16 * 64;
+constexpr uint32_t kF8Bwd = 64 * 32 + 64 * 64 + 48 * 64;
+constexpr uint32_t kF8Img = kF8Fwd + kF8Bwd;
 struct TcTable {
     TcImg img[8][MAX_ELEM];
 };
@@ -340,6 +347,7 @@ struct reann_ctx {
     const float* d_c0 = nullptr;   // [n_elem][8]
     const float* d_W = nullptr;    // [T][3][8][16]
     void* d_bf16 = nullptr;        // BF16 weight images for the tensor-core networks
+    void* d_fp8 = nullptr;         // FP8 E4M3 weight images for the tensor-core networks
     reann::TcTable tc{};
     int* d_flags = nullptr;        // reann::NFLAGS ints
     int* h_flags = nullptr;        // pinned mirror
@@ -429,10 +437,12 @@ cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetT
 // total energy from np partial sums, in a fixed order
 cudaError_t launch_energy_final(cudaStream_t s, const double* partial, int np, double* energy);
 // atomic networks, BF16 on tcgen05 tensor cores (mlp_tc.cu)
+// precision: REANN_MLP_BF16, REANN_MLP_BF16X3 or REANN_MLP_FP8
 cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
-                              bool split, const float* rho, float* out, int out_stride, int* flags, GhostOut gh = {});
+                              int precision, const float* rho, float* out, int out_stride, int* flags,
+                              GhostOut gh = {});
 cudaError_t launch_mlp_bwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
-                              bool split, const float* rho, const float* ybar, float* rhobar, int* flags);
+                              int precision, const float* rho, const float* ybar, float* rhobar, int* flags);
 
 cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
                                const float* dsave, const float* ybar, float* rhobar, bool pairs = false,

@@ -204,6 +204,8 @@ static_assert(BwdSmem<true>::BYTES <= BwdSmem<true>::REQUEST, "backward shared m
 struct TcNet {
     const uint8_t* img;  // forward hi | forward lo | backward hi | backward lo
     const float *b1, *b2, *b3;
+    const uint8_t* img8;  // FP8: forward | backward
+    const float* s8;      // FP8: s(W1), s(W2), s(W3)
 };
 struct TcLayer {
     TcNet e[MAX_ELEM];
@@ -494,10 +496,328 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_bwd(TcLayer nets, const 
     teardown(tmem);
 }
 
+// ------------------------------------------------------------------ FP8 ---
+// E4M3 operands (tcgen05.mma kind::f8f6f4, K = 32 per instruction), FP32
+// accumulation in TMEM.  Weights are E4M3 images of W / s(W), one scale per
+// matrix (host-built); each 128-row activation tile is divided by its own
+// scale s = max |x| / 448 (a block-wide maximum) before rounding to E4M3
+// (cvt.rn.satfinite), and the accumulator is multiplied back by s(tile) s(W).
+// 8-bit core-matrix layout: 8 x 16 blocks of 128 bytes, block (r/8, k/16) at
+// (r/8 * K/16 + k/16) * 128; descriptor LBO = 128 B, SBO = 8 K bytes.
+constexpr uint32_t kF8_W1t = 0, kF8_W2t = 4096, kF8_W3t = 8192;  // forward image
+constexpr uint32_t kF8_W3 = 0, kF8_W2 = 2048, kF8_W1 = 6144;     // backward image
+
+// kind::f8f6f4 instruction descriptor: D = F32, A = B = E4M3 (format 0), both K-major
+__host__ __device__ constexpr uint32_t make_idesc_e4m3(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// D[cols] = A (K = 32 ks_count) x B^T (B: N x K), E4M3 tiles with K = KA columns
+__device__ __forceinline__ void issue8(uint32_t tmem_d, const uint8_t* A, int KA, const uint8_t* B, int N,
+                                       int ks_count) {
+    const uint32_t idesc = make_idesc_e4m3(kRows, N);
+    const uint32_t a0 = smem_addr(A), b0 = smem_addr(B);
+    for (int ks = 0; ks < ks_count; ++ks)
+        mma_e4m3(tmem_d, make_desc(a0 + ks * 256, 128, 8 * KA), make_desc(b0 + ks * 256, 128, 8 * KA), idesc,
+                 ks > 0 ? 1u : 0u);
+}
+
+// max over the CTA's 128 threads (every thread calls it)
+__device__ __forceinline__ float block_max(float m, float* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    const float r = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+    __syncthreads();  // red is reused by the next call
+    return r;
+}
+
+// the tile's scale (max |x| maps to 448, the largest finite E4M3 value)
+__device__ __forceinline__ float tile_scale(float amax) { return amax > 0.f ? amax / 448.f : 1.f; }
+
+// row r (K values, already divided by the tile's scale) -> E4M3 core-matrix tile with K columns
+template <int K>
+__device__ __forceinline__ void put_row_e4m3(uint8_t* tile, int r, const float* v) {
+#pragma unroll
+    for (int kc = 0; kc < K / 16; ++kc) {
+        uint32_t w[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            uint16_t lo, hi;  // cvt puts its first source in the upper byte
+            asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(v[16 * kc + 4 * p + 1]), "f"(v[16 * kc + 4 * p]));
+            asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;"
+                : "=h"(hi)
+                : "f"(v[16 * kc + 4 * p + 3]), "f"(v[16 * kc + 4 * p + 2]));
+            w[p] = (uint32_t)lo | ((uint32_t)hi << 16);
+        }
+        *reinterpret_cast<uint4*>(tile + ((size_t)((r >> 3) * (K / 16) + kc) * 128 + (r & 7) * 16)) =
+            make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// scale the rows of a tile by the tile's max, write them as E4M3; returns the scale
+template <int K>
+__device__ __forceinline__ float quantize_rows(uint8_t* tile, int r, float* v, float* red) {
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) m = fmaxf(m, fabsf(v[k]));
+    const float s = tile_scale(block_max(m, red)), inv = 1.f / s;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] *= inv;
+    put_row_e4m3<K>(tile, r, v);
+    return s;
+}
+
+// 64 TMEM columns [c, c + 64) of this lane, times `scale`
+__device__ __forceinline__ void tmem_row64(uint32_t tmem, int warp, int c, float scale, float* v) {
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+        tmem_ld16(lane_addr(tmem, warp, c + c0), v + c0);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[c0 + i] *= scale;
+    }
+}
+
+struct F8Fwd {  // shared memory (bytes)
+    static constexpr uint32_t W = 0, A = kF8Fwd, H = A + 128 * 64, RED = H + 128 * 64, BAR = RED + 64;
+    static constexpr int BYTES = BAR + 64;
+    static constexpr int REQUEST = 110 * 1024;  // at most 2 CTAs (2 x 256 TMEM columns) per SM
+};
+struct F8Bwd {
+    static constexpr uint32_t WF = 0, WB = kF8Fwd, A = kF8Img, H = A + 128 * 64, Y = H + 128 * 64,
+                              RED = Y + 128 * 32, BAR = RED + 64;
+    static constexpr int BYTES = BAR + 64;
+    static constexpr int REQUEST = 110 * 1024;
+};
+static_assert(F8Fwd::BYTES <= F8Fwd::REQUEST && F8Bwd::BYTES <= F8Bwd::REQUEST, "FP8 shared memory");
+static_assert(kF8Fwd % 128 == 0 && kF8Img % 128 == 0, "FP8 tiles stay 128 B aligned");
+
+// rows [row0, row0 + nrows) of a row-major FP32 [.][48] array, zero-padded to 64 columns
+__device__ __forceinline__ void load_x_row64(const float* __restrict__ x, const Tile& tl, int r, float* v) {
+#pragma unroll
+    for (int k = 0; k < 64; ++k) v[k] = 0.f;
+    if (r < tl.nrows) {
+#pragma unroll
+        for (int k = 0; k < NFEAT; k += 4) {
+            const float4 a = *reinterpret_cast<const float4*>(x + (size_t)(tl.row0 + r) * NFEAT + k);
+            v[k] = a.x, v[k + 1] = a.y, v[k + 2] = a.z, v[k + 3] = a.w;
+        }
+    }
+}
+
+// forward: TMEM columns [0,64) z1, [64,128) z2, [128,144) y
+template <int OUT>
+__global__ void __launch_bounds__(kThreads, 1) k_mlp_f8_fwd(TcLayer nets, const Tile* __restrict__ tiles,
+                                                           const float* __restrict__ rho, float* __restrict__ out,
+                                                           int out_stride, int* __restrict__ flags, GhostOut gh) {
+    using L = F8Fwd;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    float* red = reinterpret_cast<float*>(smem + L::RED);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::BAR);  // [0] weights, [1] MMA
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, r = tid;
+    const Tile tl = tiles[blockIdx.x];
+    if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list (before any TMEM allocation)
+    const TcNet& w = nets.e[tl.elem];
+    const uint32_t tmem = setup(tslot, bar);
+    if (tid == 0) {
+        mbar_expect_tx(&bar[0], kF8Fwd);
+        bulk_g2s(smem + L::W, w.img8, kF8Fwd, &bar[0]);
+    }
+    const float sw1 = w.s8[0], sw2 = w.s8[1], sw3 = w.s8[2];
+    float v[64];
+    load_x_row64(rho, tl, r, v);
+    const float sx = quantize_rows<64>(smem + L::A, r, v, red);
+    handoff();
+    bool ok = wait_all(&bar[0], 0);
+    float sh = 1.f;
+    if (!ok) {
+        fail(flags, &bar[0], 0);
+    } else {
+        if (tid == 0) {  // z1 = x W1
+            issue8(tmem, smem + L::A, 64, smem + L::W + kF8_W1t, H1, 2);
+            mma_commit(&bar[1]);
+        }
+        ok = wait_all(&bar[1], 0);
+        if (!ok) fail(flags, &bar[1], 0);
+    }
+    if (ok) {
+        tc_fence_after();
+        tmem_row64(tmem, warp, 0, sx * sw1, v);
+#pragma unroll
+        for (int i = 0; i < 64; ++i) v[i] = silu(v[i] + w.b1[i]);
+        sh = quantize_rows<64>(smem + L::H, r, v, red);
+        handoff();
+        if (tid == 0) {  // z2 = h1 W2
+            issue8(tmem + 64, smem + L::H, 64, smem + L::W + kF8_W2t, H2, 2);
+            mma_commit(&bar[1]);
+        }
+        ok = wait_all(&bar[1], 1);
+        if (!ok) fail(flags, &bar[1], 1);
+    }
+    if (ok) {
+        tc_fence_after();
+        tmem_row64(tmem, warp, 64, sh * sw2, v);
+#pragma unroll
+        for (int i = 0; i < 64; ++i) v[i] = silu(v[i] + w.b2[i]);
+        sh = quantize_rows<64>(smem + L::H, r, v, red);
+        handoff();
+        if (tid == 0) {  // y = h2 W3 (N padded to 16)
+            issue8(tmem + 128, smem + L::H, 64, smem + L::W + kF8_W3t, 16, 2);
+            mma_commit(&bar[1]);
+        }
+        ok = wait_all(&bar[1], 0);
+        if (!ok) fail(flags, &bar[1], 0);
+    }
+    if (ok) {
+        tc_fence_after();
+        float y[16];
+        tmem_ld16(lane_addr(tmem, warp, 128), y);
+        if (r < tl.nrows) {
+            const int64_t row = tl.row0 + r;
+            float* o = out + (size_t)row * out_stride;
+#pragma unroll
+            for (int i = 0; i < OUT; ++i) o[i] = y[i] * (sh * sw3) + w.b3[i];
+            if (OUT > 1 && gh.goff)  // the row's ghost images get the same coefficients
+                for (int64_t g = gh.goff[row]; g < gh.goff[row + 1] && g < gh.gcap; ++g) {
+                    float* go = out + (size_t)(gh.base + g) * out_stride;
+#pragma unroll
+                    for (int i = 0; i < OUT; ++i) go[i] = y[i] * (sh * sw3) + w.b3[i];
+                }
+        }
+    }
+    teardown(tmem);
+}
+
+// rhobar = J^T ybar, recomputing z1, z2.  TMEM columns: [0,64) z1, [64,128) z2,
+// [128,192) ybar W3^T then rhobar (48), [192,256) z2bar W2^T.
+template <int OUT>
+__global__ void __launch_bounds__(kThreads, 1) k_mlp_f8_bwd(TcLayer nets, const Tile* __restrict__ tiles,
+                                                           const float* __restrict__ rho,
+                                                           const float* __restrict__ ybar,
+                                                           float* __restrict__ rhobar, int* __restrict__ flags) {
+    using L = F8Bwd;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    float* red = reinterpret_cast<float*>(smem + L::RED);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::BAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, r = tid;
+    const Tile tl = tiles[blockIdx.x];
+    if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list (before any TMEM allocation)
+    const TcNet& w = nets.e[tl.elem];
+    const uint32_t tmem = setup(tslot, bar);
+    if (tid == 0) {
+        mbar_expect_tx(&bar[0], kF8Img);
+        bulk_g2s(smem + L::WF, w.img8, kF8Img, &bar[0]);  // forward | backward
+    }
+    const float sw1 = w.s8[0], sw2 = w.s8[1], sw3 = w.s8[2];
+    float v[64];
+    load_x_row64(rho, tl, r, v);
+    const float sx = quantize_rows<64>(smem + L::A, r, v, red);
+    float y[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) y[i] = 0.f;
+    if (r < tl.nrows) {
+        if (OUT == 1)
+            y[0] = 1.f;  // d eps_i / d eps_i
+        else
+#pragma unroll
+            for (int i = 0; i < OUT; ++i) y[i] = ybar[(size_t)(tl.row0 + r) * OUT + i];
+    }
+    const float sy = quantize_rows<32>(smem + L::Y, r, y, red);
+    handoff();
+    float sh1 = 1.f, sg = 1.f;
+    bool ok = wait_all(&bar[0], 0);
+    if (!ok) {
+        fail(flags, &bar[0], 0);
+    } else {
+        if (tid == 0) {
+            issue8(tmem, smem + L::A, 64, smem + L::WF + kF8_W1t, H1, 2);         // z1
+            issue8(tmem + 128, smem + L::Y, 32, smem + L::WB + kF8_W3, H2, 1);    // ybar W3^T
+            mma_commit(&bar[1]);
+        }
+        ok = wait_all(&bar[1], 0);
+        if (!ok) fail(flags, &bar[1], 0);
+    }
+    if (ok) {
+        tc_fence_after();
+        tmem_row64(tmem, warp, 0, sx * sw1, v);
+#pragma unroll
+        for (int i = 0; i < 64; ++i) v[i] = silu(v[i] + w.b1[i]);
+        sh1 = quantize_rows<64>(smem + L::H, r, v, red);
+        handoff();
+        if (tid == 0) {  // z2
+            issue8(tmem + 64, smem + L::H, 64, smem + L::WF + kF8_W2t, H2, 2);
+            mma_commit(&bar[1]);
+        }
+        ok = wait_all(&bar[1], 1);
+        if (!ok) fail(flags, &bar[1], 1);
+    }
+    if (ok) {
+        tc_fence_after();
+        float z[64];
+        tmem_row64(tmem, warp, 128, sy * sw3, v);  // ybar W3^T
+        tmem_row64(tmem, warp, 64, sh1 * sw2, z);  // z2 (without b2)
+#pragma unroll
+        for (int i = 0; i < 64; ++i) v[i] *= dsilu(z[i] + w.b2[i]);  // z2bar
+        sg = quantize_rows<64>(smem + L::H, r, v, red);
+        handoff();
+        if (tid == 0) {  // z2bar W2^T
+            issue8(tmem + 192, smem + L::H, 64, smem + L::WB + kF8_W2, H1, 2);
+            mma_commit(&bar[1]);
+        }
+        ok = wait_all(&bar[1], 0);
+        if (!ok) fail(flags, &bar[1], 0);
+    }
+    if (ok) {
+        tc_fence_after();
+        float z[64];
+        tmem_row64(tmem, warp, 192, sg * sw2, v);  // z2bar W2^T
+        tmem_row64(tmem, warp, 0, sx * sw1, z);    // z1 (without b1)
+#pragma unroll
+        for (int i = 0; i < 64; ++i) v[i] *= dsilu(z[i] + w.b1[i]);  // z1bar
+        sg = quantize_rows<64>(smem + L::H, r, v, red);
+        handoff();
+        if (tid == 0) {  // rhobar = z1bar W1^T
+            issue8(tmem + 128, smem + L::H, 64, smem + L::WB + kF8_W1, NFEAT, 2);
+            mma_commit(&bar[1]);
+        }
+        ok = wait_all(&bar[1], 1);
+        if (!ok) fail(flags, &bar[1], 1);
+    }
+    if (ok) {
+        tc_fence_after();
+        float g[16];
+#pragma unroll
+        for (int c0 = 0; c0 < NFEAT; c0 += 16) {
+            tmem_ld16(lane_addr(tmem, warp, 128 + c0), g);
+            if (r < tl.nrows) {
+                float4* dst = reinterpret_cast<float4*>(rhobar + (size_t)(tl.row0 + r) * NFEAT + c0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    dst[q] = make_float4(g[4 * q] * (sg * sw1), g[4 * q + 1] * (sg * sw1), g[4 * q + 2] * (sg * sw1),
+                                         g[4 * q + 3] * (sg * sw1));
+            }
+        }
+    }
+    teardown(tmem);
+}
+
 TcLayer layer_of(const TcTable& t, int layer) {
     TcLayer l;
-    for (int e = 0; e < MAX_ELEM; ++e) l.e[e] = TcNet{t.img[layer][e].img, t.img[layer][e].b1, t.img[layer][e].b2,
-                                                      t.img[layer][e].b3};
+    for (int e = 0; e < MAX_ELEM; ++e) {
+        const TcImg& i = t.img[layer][e];
+        l.e[e] = TcNet{i.img, i.b1, i.b2, i.b3, i.img8, i.s8};
+    }
     return l;
 }
 
@@ -521,6 +841,10 @@ void ensure_tc_attrs() {
     set_attrs<NPHI, false>();
     set_attrs<1, true>();
     set_attrs<NPHI, true>();
+    cudaFuncSetAttribute(k_mlp_f8_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, F8Fwd::REQUEST);
+    cudaFuncSetAttribute(k_mlp_f8_fwd<NPHI>, cudaFuncAttributeMaxDynamicSharedMemorySize, F8Fwd::REQUEST);
+    cudaFuncSetAttribute(k_mlp_f8_bwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, F8Bwd::REQUEST);
+    cudaFuncSetAttribute(k_mlp_f8_bwd<NPHI>, cudaFuncAttributeMaxDynamicSharedMemorySize, F8Bwd::REQUEST);
     if (dev < 64) done |= (uint64_t)1 << dev;
 }
 
@@ -539,11 +863,19 @@ void bwd_launch(cudaStream_t s, int nt, const TcLayer& l, const Tile* tiles, con
 }  // namespace
 
 cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
-                              bool split, const float* rho, float* out, int out_stride, int* flags, GhostOut gh) {
+                              int precision, const float* rho, float* out, int out_stride, int* flags, GhostOut gh) {
     const int nt = (int)nl->tiles128_h.size();
     if (nt == 0) return cudaSuccess;
     ensure_tc_attrs();
     const TcLayer l = layer_of(nets, t);
+    if (precision == REANN_MLP_FP8) {
+        if (energy)
+            k_mlp_f8_fwd<1><<<nt, kThreads, F8Fwd::REQUEST, s>>>(l, nl->tiles128, rho, out, out_stride, flags, gh);
+        else
+            k_mlp_f8_fwd<NPHI><<<nt, kThreads, F8Fwd::REQUEST, s>>>(l, nl->tiles128, rho, out, out_stride, flags, gh);
+        return cudaGetLastError();
+    }
+    const bool split = precision == REANN_MLP_BF16X3;
     if (energy)
         (split ? fwd_launch<1, true> : fwd_launch<1, false>)(s, nt, l, nl->tiles128, rho, out, out_stride, flags, gh);
     else
@@ -553,11 +885,19 @@ cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTab
 }
 
 cudaError_t launch_mlp_bwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
-                              bool split, const float* rho, const float* ybar, float* rhobar, int* flags) {
+                              int precision, const float* rho, const float* ybar, float* rhobar, int* flags) {
     const int nt = (int)nl->tiles128_h.size();
     if (nt == 0) return cudaSuccess;
     ensure_tc_attrs();
     const TcLayer l = layer_of(nets, t);
+    if (precision == REANN_MLP_FP8) {
+        if (energy)
+            k_mlp_f8_bwd<1><<<nt, kThreads, F8Bwd::REQUEST, s>>>(l, nl->tiles128, rho, ybar, rhobar, flags);
+        else
+            k_mlp_f8_bwd<NPHI><<<nt, kThreads, F8Bwd::REQUEST, s>>>(l, nl->tiles128, rho, ybar, rhobar, flags);
+        return cudaGetLastError();
+    }
+    const bool split = precision == REANN_MLP_BF16X3;
     if (energy)
         (split ? bwd_launch<1, true> : bwd_launch<1, false>)(s, nt, l, nl->tiles128, rho, ybar, rhobar, flags);
     else

@@ -203,6 +203,52 @@ void push_core(std::vector<uint16_t>& dst, const float* src, int ld, int rows, i
         }
 }
 
+// FP32 -> FP8 E4M3 (1 sign, 4 exponent bits with bias 7, 3 mantissa bits; no
+// infinities, largest finite 448, subnormals down to 2^-9), round to nearest
+// even, saturating at +-448.
+uint8_t to_e4m3(float x) {
+    const uint8_t sign = std::signbit(x) ? 0x80 : 0x00;
+    const double a = std::fabs((double)x);
+    if (!(a == a)) return 0x7F;
+    if (a >= 448.0) return sign | 0x7E;
+    int e = 0;
+    (void)std::frexp(a, &e);  // a = f 2^e, f in [0.5, 1): the leading bit has weight 2^(e - 1)
+    int ex = e - 1;           // unbiased exponent of a
+    if (a == 0.0 || ex < -6) {  // subnormal range: multiples of 2^-9
+        const double m = std::nearbyint(a * 512.0);  // default rounding: ties to even
+        if (m >= 8.0) return sign | 0x08;            // rounds up to the smallest normal 2^-6
+        return sign | (uint8_t)m;
+    }
+    double m = std::nearbyint((a / std::ldexp(1.0, ex) - 1.0) * 8.0);
+    if (m >= 8.0) {
+        m = 0.0;
+        ++ex;
+    }
+    if (ex > 8 || (ex == 8 && m > 6.0)) return sign | 0x7E;
+    return sign | (uint8_t)((ex + 7) << 3) | (uint8_t)m;
+}
+
+// Append an R x K FP8 E4M3 tile of src / scale (src row-major with leading
+// dimension ld, entries beyond rows x cols zero) in the K-major core-matrix
+// layout of 8-bit tcgen05.mma operands: 8 x 16 blocks of 128 bytes (8 rows of
+// 16 bytes), block (r/8, k/16) at (r/8 * K/16 + k/16) * 128.
+void push_core8(std::vector<uint8_t>& dst, const float* src, int ld, int rows, int cols, int R, int K, float scale) {
+    const size_t base = dst.size();
+    dst.resize(base + (size_t)R * K, 0);
+    for (int r = 0; r < R; ++r)
+        for (int k = 0; k < K; ++k) {
+            const float v = (r < rows && k < cols) ? src[(size_t)r * ld + k] / scale : 0.f;
+            dst[base + ((size_t)(r / 8) * (K / 16) + k / 16) * 128 + (r % 8) * 16 + (k % 16)] = to_e4m3(v);
+        }
+}
+
+// per-tensor scale of an FP8 E4M3 image: max |w| maps to 448
+float e4m3_scale(const float* w, size_t n) {
+    float m = 0.f;
+    for (size_t i = 0; i < n; ++i) m = std::max(m, std::fabs(w[i]));
+    return m > 0.f ? m / 448.f : 1.f;
+}
+
 // pad to a multiple of 4 floats so that float4 loads stay aligned
 void push_block(std::vector<float>& dst, const float* src, size_t count) {
     dst.insert(dst.end(), src, src + count);
@@ -287,10 +333,11 @@ extern "C" int reann_ctx_create(const reann_model* model, void* cuda_stream, rea
     push_block(img, p, (size_t)M.T * (LMAX + 1) * NPHI * KO);
     p += M.T * (LMAX + 1) * NPHI * KO;
     struct Off {
-        size_t W1, b1, W2, b2, W3, b3, W1t, W2t, W3t;
+        size_t W1 = 0, b1 = 0, W2 = 0, b2 = 0, W3 = 0, b3 = 0, W1t = 0, W2t = 0, W3t = 0, s8 = 0;
     };
     std::vector<Off> offs((size_t)M.T * M.n_elem);
     std::vector<uint16_t> tcimg;  // per (t, e): forward hi | forward lo | backward hi | backward lo, 16 KiB each
+    std::vector<uint8_t> f8img;   // per (t, e): forward | backward FP8 images, kF8Img bytes
     for (int t = 0; t < M.T; ++t) {
         const int outd = (t == M.T - 1) ? 1 : NPHI;
         for (int e = 0; e < M.n_elem; ++e) {
@@ -339,9 +386,25 @@ extern "C" int reann_ctx_create(const reann_model* model, void* cuda_stream, rea
                 push_core(tcimg, W2, H2, H1, H2, H1, H2, lo);        //           W2
                 push_core(tcimg, W1, H1, NFEAT, H1, NFEAT, H1, lo);  //           W1
             }
+            // FP8 E4M3 images (one scale per matrix; K a multiple of 32: 48 -> 64, 16 -> 32)
+            const float s1 = e4m3_scale(W1, (size_t)NFEAT * H1), s2 = e4m3_scale(W2, (size_t)H1 * H2),
+                        s3 = e4m3_scale(W3, (size_t)H2 * outd);
+            push_core8(f8img, w1t.data(), NFEAT, H1, NFEAT, H1, 64, s1);  // forward: W1^T (K padded to 64)
+            push_core8(f8img, w2t.data(), H1, H2, H1, H2, H1, s2);        //          W2^T
+            push_core8(f8img, tr.data(), H2, outd, H2, 16, H2, s3);       //          W3^T (rows padded to 16)
+            push_core8(f8img, W3, outd, H2, outd, H2, 32, s3);            // backward: W3 (K padded to 32)
+            push_core8(f8img, W2, H2, H1, H2, H1, H2, s2);                //           W2
+            push_core8(f8img, W1, H1, NFEAT, H1, NFEAT, H1, s1);          //           W1
+            o.s8 = img.size();
+            const float sc[4] = {s1, s2, s3, 0.f};
+            push_block(img, sc, 4);
         }
     }
     if (tcimg.empty()) tcimg.resize(1);
+    if (f8img.empty()) f8img.resize(16);
+    if (cudaMalloc(&ctx->d_fp8, f8img.size()) != cudaSuccess) return fail(REANN_E_NOMEM);
+    if (cudaMemcpy(ctx->d_fp8, f8img.data(), f8img.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(REANN_E_CUDA);
     if (cudaMalloc(&ctx->d_bf16, tcimg.size() * sizeof(uint16_t)) != cudaSuccess) return fail(REANN_E_NOMEM);
     if (cudaMemcpy(ctx->d_bf16, tcimg.data(), tcimg.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) !=
         cudaSuccess)
@@ -359,7 +422,9 @@ extern "C" int reann_ctx_create(const reann_model* model, void* cuda_stream, rea
                                          base + o.b3, base + o.W1t, base + o.W2t, base + o.W3t};
             const uint8_t* ib =
                 static_cast<const uint8_t*>(ctx->d_bf16) + (M.pairs ? 0 : ((size_t)t * M.n_elem + e) * 4 * 16384);
-            ctx->tc.img[t][e] = TcImg{ib, base + o.b1, base + o.b2, base + o.b3};
+            const uint8_t* i8 =
+                static_cast<const uint8_t*>(ctx->d_fp8) + (M.pairs ? 0 : ((size_t)t * M.n_elem + e) * kF8Img);
+            ctx->tc.img[t][e] = TcImg{ib, base + o.b1, base + o.b2, base + o.b3, i8, base + o.s8};
         }
     if (M.pairs && upload_pair_table() != cudaSuccess) return fail(REANN_E_CUDA);
     if (cudaMalloc(&ctx->d_flags, sizeof(int) * NFLAGS) != cudaSuccess) return fail(REANN_E_NOMEM);
@@ -385,6 +450,7 @@ extern "C" void reann_ctx_free(reann_ctx* ctx) {
         if (e) cudaEventDestroy(e);
     if (ctx->d_params) cudaFree(ctx->d_params);
     if (ctx->d_bf16) cudaFree(ctx->d_bf16);
+    if (ctx->d_fp8) cudaFree(ctx->d_fp8);
     if (ctx->d_flags) cudaFree(ctx->d_flags);
     if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
     delete ctx;
@@ -392,7 +458,8 @@ extern "C" void reann_ctx_free(reann_ctx* ctx) {
 
 extern "C" int reann_ctx_set_mlp_precision(reann_ctx* ctx, int precision) {
     if (!ctx) return REANN_E_ARG;
-    if (precision != REANN_MLP_FP32 && precision != REANN_MLP_BF16 && precision != REANN_MLP_BF16X3)
+    if (precision != REANN_MLP_FP32 && precision != REANN_MLP_BF16 && precision != REANN_MLP_BF16X3 &&
+        precision != REANN_MLP_FP8)
         return set_error(ctx, REANN_E_ARG, "unsupported network precision");
     if (precision != REANN_MLP_FP32 && ctx->model.pairs)
         return set_error(ctx, REANN_E_ARG, "tensor-core networks are built for the 48-feature models only");
@@ -801,7 +868,7 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
         float* out = energy_net ? nl->eps : nl->coef + (size_t)(t + 1) * ne * NPHI;
         const int out_stride = energy_net ? 1 : NPHI;
         if (ctx->precision != REANN_MLP_FP32)
-            REANN_CUDA_TRY(ctx, launch_mlp_fwd_tc(s, nl, ctx->tc, t, energy_net, ctx->precision == REANN_MLP_BF16X3,
+            REANN_CUDA_TRY(ctx, launch_mlp_fwd_tc(s, nl, ctx->tc, t, energy_net, ctx->precision,
                                                   rho_t, out, out_stride, ctx->d_flags, gh));
         else
             REANN_CUDA_TRY(ctx, launch_mlp_fwd_f32(s, nl, ctx->nets, t, energy_net, rho_t, out, out_stride, pairs, gh,
@@ -825,8 +892,8 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
         {
             ProfScope p(ctx, PR_MLP_BWD);
             if (ctx->precision != REANN_MLP_FP32)
-                REANN_CUDA_TRY(ctx, launch_mlp_bwd_tc(s, nl, ctx->tc, t, t == T - 1,
-                                                      ctx->precision == REANN_MLP_BF16X3, rho_t, nl->cbar, nl->rhobar,
+                REANN_CUDA_TRY(ctx, launch_mlp_bwd_tc(s, nl, ctx->tc, t, t == T - 1, ctx->precision, rho_t, nl->cbar,
+                                                      nl->rhobar,
                                                       ctx->d_flags));
             else if (!pairs)  // the FP32 backward networks also take the bbar step (fused)
                 REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, dsave_t, nl->cbar,
