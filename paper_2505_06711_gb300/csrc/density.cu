@@ -15,11 +15,13 @@
 // No atomics: every output row is written by the lanes of its own centre atom.
 //
 // Forward layout: a quad of 4 lanes per centre atom (8 atoms per warp).  Each
-// lane walks every 4th live neighbour, gathers the neighbour's hi/lo FP32
-// position (32 B) and coefficients (32 B) and accumulates the 80 products in
-// registers; a butterfly reduce-scatter leaves 20 of the 80 b values in each
-// lane, which then contracts its 4 orbitals from shared memory.  The adjoint
-// gathers 320 B of bbar per edge and uses 8 lanes per atom instead (below).
+// lane walks every 4th live neighbour, whose hi/lo FP32 position (32 B) and
+// coefficients (32 B) are copied into shared memory with cp.async one edge
+// ahead, and accumulates the 80 products in registers; a butterfly
+// reduce-scatter leaves 20 of the 80 b values in each lane, which then
+// contracts its 4 orbitals from shared memory.  The adjoint gathers each
+// neighbour's 384 B adjoint record (bbar and c) and uses 8 lanes per atom
+// instead (below).
 #include <cuda_runtime.h>
 
 #include "common.cuh"

@@ -10,9 +10,12 @@
 // Atoms are stored element-major, so a tile of 64 consecutive rows uses one
 // element's weights.  A block of 256 threads computes a 64x64 layer output as
 // 16x16 threads x (4 rows x 4 columns), reading float4 fragments of the
-// row-major activations and weights from shared memory.  Both kernels keep one
-// or two activation buffers only (48 KB / 68 KB of shared memory), so that
-// four / three blocks share an SM.
+// row-major activations and weights from shared memory.  The forward keeps one
+// activation buffer (48 KB of shared memory: four blocks per SM) and writes
+// SiLU'(z1), SiLU'(z2) of every row; the backward reads them instead of
+// recomputing the forward, and with the 48-feature networks also takes the
+// bbar step of Eq. 1's squares and writes the adjoint records (69 KB: three
+// blocks per SM).
 #include <cuda_runtime.h>
 
 #include <mutex>

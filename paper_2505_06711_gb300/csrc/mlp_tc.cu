@@ -1,5 +1,6 @@
 // Per-element atomic networks on the 5th-generation tensor cores (tcgen05),
-// BF16 operands, FP32 accumulation in tensor memory (TMEM).
+// BF16 (or split BF16, or FP8 E4M3: see the FP8 section below) operands, FP32
+// accumulation in tensor memory (TMEM).
 //
 // Sec. 2.1, Eq. 2: c^{t+1}_i = M^t_{Z_i}(rho^t_i), 48 -> 64 -> 64 -> 8, and the
 // energy network 48 -> 64 -> 64 -> 1, SiLU between layers; the reverse pass

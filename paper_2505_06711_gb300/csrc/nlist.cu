@@ -14,9 +14,10 @@
 //      element so neighbour gathers stay local);
 //   3. enumerate ghost images (count while gathering, scan, fill while keying);
 //   4. bin owned + ghost slots into an extended cell grid (counting sort);
-//   5. warp per owned atom: scan the stencil bins, FP32 pre-test with a
-//      margin, FP64 exact test for pairs near r_c + skin, ballot-compacted
-//      writes into a fixed-stride row.
+//   5. warp per owned atom: scan the stencil bins (in a rectangular cell each
+//      column trimmed to the sphere), FP32 pre-test with a margin, FP64 exact
+//      test for pairs near r_c + skin, ballot-compacted writes into a
+//      fixed-stride row.
 // The first build sizes the ghost and row capacities (one host round trip);
 // every later rebuild re-runs the same kernels into the resident buffers
 // without allocating or synchronising, so it can sit inside a CUDA graph.
