@@ -61,8 +61,8 @@ FLOP_PER_ATOM_BBAR = 5440             # g (1280 FMA) + gbar (160) + bbar (1280 F
 
 # DRAM traffic per launch of the dominant kernel from one ncu capture of this
 # workload (profiles/), valid only for the source it was taken on.
-TRAFFIC = {  # {(region, sha1[:12] of the kernel source): bytes per launch}
-    ("density_adj", "edd0ad31e32c"): 21838848,  # profiles/density_adj_water24576_T3.md
+TRAFFIC = {  # {(region, source_sha of the kernel source): bytes per launch}
+    ("density_adj", "9c3847b55883"): 21838848,  # profiles/density_adj_water24576_T3.md
 }
 
 
@@ -454,8 +454,14 @@ class ClockSampler:
 
 
 def source_sha(name: str) -> str:
+    """sha1[:12] of a kernel source's code: line comments and blank lines do not count."""
     path = os.path.join(ROOT, "paper_2505_06711_gb300", "csrc", name)
-    return hashlib.sha1(open(path, "rb").read()).hexdigest()[:12]
+    code = []
+    for line in open(path, encoding="utf-8").read().splitlines():
+        line = line.split("//", 1)[0].rstrip()
+        if line:
+            code.append(line)
+    return hashlib.sha1("\n".join(code).encode()).hexdigest()[:12]
 
 
 REGION_SOURCE = {
