@@ -506,6 +506,18 @@ def cpu_baseline(structure, spec):
         oracle.energy_forces(spec, structure.pos, structure.species, structure.cell, n_threads=cores)
         times.append(time.perf_counter() - t0)
     t = statistics.mean(times)
+    # the same oracle on the small boxes: all cores and one core, and its brute-force list alone
+    from synth import fcc_box, water_box
+
+    detail = {}
+    for name, sbox in (("water_192", water_box(64, seed=0)), ("cu_4000", fcc_box(10, seed=0))):
+        for label, nt in (("all_cores", cores), ("1_core", 1)):
+            t0 = time.perf_counter()
+            oracle.energy_forces(spec, sbox.pos, sbox.species, sbox.cell, n_threads=nt)
+            detail[f"{name}_{label}_atom_evals_per_s"] = sbox.n_atoms / (time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        oracle.neighbors(sbox.pos, sbox.cell, spec.r_c + SKIN, n_threads=cores)
+        detail[f"{name}_list_only_ms"] = (time.perf_counter() - t0) * 1e3
     return {
         "value": structure.n_atoms / t,
         "unit": "atom-evals/s",
@@ -513,6 +525,7 @@ def cpu_baseline(structure, spec):
         "kind": "oracle",
         "sample": f"{len(times)} full FP64 evaluations (brute-force list + forward + reverse) of the "
                   f"{structure.n_atoms}-atom water box, mean {t:.2f} s each",
+        "detail": detail,
     }
 
 
