@@ -132,12 +132,23 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_single(const int* __restr
     __shared__ T warp_sums[kScanThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     T carry = 0;
+    T nx[kScanItems];  // the next tile's entries, loaded while the current tile is scanned
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t x = k * kScanThreads + tid;
+        nx[k] = x < n ? in[x] : (T)0;
+    }
     for (int64_t base = 0; base < n; base += TILE) {
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
             const int x = k * kScanThreads + tid;
-            buf[x + x / 32] = (base + x < n) ? in[base + x] : (T)0;
+            buf[x + x / 32] = nx[k];
             if (zero_in && base + x < n) in[base + x] = (T)0;
+        }
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            const int64_t x = base + TILE + k * kScanThreads + tid;
+            nx[k] = x < n ? in[x] : (T)0;
         }
         __syncthreads();
         T v[kScanItems];
