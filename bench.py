@@ -17,7 +17,7 @@ random-weight model); the paper's datasets and trained weights are not used.
   (``reann_energy_forces_host`` with a forced rebuild): pinned host positions
   in, host forces and energy out, copies inside the timed region.
 * ``roofline``: the region with the largest device time, its algorithmic FLOPs
-  per launch (counts in the design doc) over its mean launch time, against the FP32
+  per launch (the FLOP_PER_* counts below) over its mean launch time, against the FP32
   SIMT peak of the GPU (SMs x 128 lanes x 2 FLOP x max SM clock).
 * ``cpu_baseline``: the FP64 oracle (test infrastructure) evaluating the same
   box once on the host cores, rank 0 only.
