@@ -438,11 +438,14 @@ cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetT
 cudaError_t launch_energy_final(cudaStream_t s, const double* partial, int np, double* energy);
 // atomic networks, BF16 on tcgen05 tensor cores (mlp_tc.cu)
 // precision: REANN_MLP_BF16, REANN_MLP_BF16X3 or REANN_MLP_FP8
+// BF16 / BF16x3: the forward keeps SiLU'(z1), SiLU'(z2) of every row in dsave (128
+// floats per row, the FP32 path's layout) and the backward reads them (FP8 recomputes)
 cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
                               int precision, const float* rho, float* out, int out_stride, int* flags,
-                              GhostOut gh = {});
+                              GhostOut gh, float* dsave);
 cudaError_t launch_mlp_bwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
-                              int precision, const float* rho, const float* ybar, float* rhobar, int* flags);
+                              int precision, const float* rho, const float* dsave, const float* ybar, float* rhobar,
+                              int* flags);
 
 cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
                                const float* dsave, const float* ybar, float* rhobar, bool pairs = false,

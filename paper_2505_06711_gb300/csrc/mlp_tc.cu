@@ -15,7 +15,9 @@
 // (tcgen05.ld 32x32b), applies bias and SiLU (or its derivative) in FP32,
 // rounds to BF16 and writes the next layer's A tile.  Weight images are laid
 // out once on the host in the same core-matrix layout and copied to shared
-// memory with bulk asynchronous copies (cp.async.bulk, TMA engine).
+// memory with bulk asynchronous copies (cp.async.bulk, TMA engine).  The BF16
+// forward keeps SiLU'(z1), SiLU'(z2) of every row for the backward, which then
+// needs three products and the backward weight image only.
 //
 // Two precisions share the kernels:
 //   plain BF16 (SPLIT = false): one MMA per K step, BF16 operands;
@@ -287,10 +289,12 @@ __device__ __forceinline__ void teardown(uint32_t tmem) {
     if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-// TMEM columns [c, c + 64) of this lane -> act(v + bias) -> row r of an A tile (K = 64)
+// TMEM columns [c, c + 64) of this lane -> act(v + bias) -> row r of an A tile (K = 64);
+// with dsave (the row's 64 values for this layer), SiLU'(v + bias) is kept there for the
+// reverse pass
 template <bool SPLIT>
 __device__ __forceinline__ void silu_to_tile(uint32_t tmem, int warp, int c, const float* __restrict__ bias,
-                                             uint8_t* hi, uint8_t* lo, int r) {
+                                             uint8_t* hi, uint8_t* lo, int r, float* __restrict__ dsave = nullptr) {
     float v[16], h[16];
 #pragma unroll
     for (int c0 = 0; c0 < 64; c0 += 16) {
@@ -299,6 +303,13 @@ __device__ __forceinline__ void silu_to_tile(uint32_t tmem, int warp, int c, con
         for (int i = 0; i < 16; ++i) h[i] = silu(v[i] + bias[c0 + i]);
         put8(hi, SPLIT ? lo : nullptr, 64, r, c0 / 8, h);
         put8(hi, SPLIT ? lo : nullptr, 64, r, c0 / 8 + 1, h + 8);
+        if (dsave) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) h[i] = dsilu(v[i] + bias[c0 + i]);
+            float4* d = reinterpret_cast<float4*>(dsave + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) d[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+        }
     }
 }
 
@@ -318,11 +329,35 @@ __device__ __forceinline__ void dsilu_to_tile(uint32_t tmem, int warp, int cg, i
     }
 }
 
-// forward: TMEM columns [0,64) z1, [64,128) z2, [128,144) y
+// g (TMEM columns [cg, cg + 64)) * the row's saved SiLU' values s (64 floats, or
+// zeros for rows past the tile's end) -> row r of an A tile
+template <bool SPLIT>
+__device__ __forceinline__ void scale_to_tile(uint32_t tmem, int warp, int cg, const float* __restrict__ s,
+                                              uint8_t* hi, uint8_t* lo, int r) {
+    float g[16], h[16];
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+        tmem_ld16(lane_addr(tmem, warp, cg + c0), g);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 d = s ? __ldg(reinterpret_cast<const float4*>(s + c0) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            h[4 * q] = g[4 * q] * d.x;
+            h[4 * q + 1] = g[4 * q + 1] * d.y;
+            h[4 * q + 2] = g[4 * q + 2] * d.z;
+            h[4 * q + 3] = g[4 * q + 3] * d.w;
+        }
+        put8(hi, SPLIT ? lo : nullptr, 64, r, c0 / 8, h);
+        put8(hi, SPLIT ? lo : nullptr, 64, r, c0 / 8 + 1, h + 8);
+    }
+}
+
+// forward: TMEM columns [0,64) z1, [64,128) z2, [128,144) y.  With dsave, row i's
+// SiLU'(z1), SiLU'(z2) go to dsave[i][0..63], dsave[i][64..127] for the reverse pass.
 template <int OUT, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_fwd(TcLayer nets, const Tile* __restrict__ tiles,
                                                            const float* __restrict__ rho, float* __restrict__ out,
-                                                           int out_stride, int* __restrict__ flags, GhostOut gh) {
+                                                           int out_stride, int* __restrict__ flags, GhostOut gh,
+                                                           float* __restrict__ dsave) {
     using L = FwdSmem<SPLIT>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::BAR);  // [0] weights, [1] MMA
@@ -331,6 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_fwd(TcLayer nets, const 
     const Tile tl = tiles[blockIdx.x];
     if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list (before any TMEM allocation)
     const TcNet& w = nets.e[tl.elem];
+    float* drow = dsave && r < tl.nrows ? dsave + (size_t)(tl.row0 + r) * (H1 + H2) : nullptr;
     const uint32_t tmem = setup(tslot, bar);
     if (tid == 0) {
         mbar_expect_tx(&bar[0], kImg * L::S);
@@ -352,7 +388,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_fwd(TcLayer nets, const 
     }
     if (ok) {
         tc_fence_after();
-        silu_to_tile<SPLIT>(tmem, warp, 0, w.b1, smem + L::H, smem + L::HLO, r);
+        silu_to_tile<SPLIT>(tmem, warp, 0, w.b1, smem + L::H, smem + L::HLO, r, drow);
         handoff();
         if (tid == 0) {  // z2 = h1 W2
             issue<SPLIT>(tmem + 64, smem + L::H, smem + L::HLO, H1, smem + L::W + kF_W2t, smem + L::WLO + kF_W2t, H2,
@@ -364,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_fwd(TcLayer nets, const 
     }
     if (ok) {
         tc_fence_after();
-        silu_to_tile<SPLIT>(tmem, warp, 64, w.b2, smem + L::H, smem + L::HLO, r);
+        silu_to_tile<SPLIT>(tmem, warp, 64, w.b2, smem + L::H, smem + L::HLO, r, drow ? drow + H1 : nullptr);
         handoff();
         if (tid == 0) {  // y = h2 W3 (N padded to 16)
             issue<SPLIT>(tmem + 128, smem + L::H, smem + L::HLO, H2, smem + L::W + kF_W3t, smem + L::WLO + kF_W3t, 16,
@@ -394,11 +430,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_fwd(TcLayer nets, const 
     teardown(tmem);
 }
 
-// rhobar = J^T ybar, recomputing z1, z2.  TMEM columns: [0,64) z1, [64,128) z2,
-// [128,192) ybar W3^T then rhobar (48), [192,256) z2bar W2^T.
+// rhobar = J^T ybar with SiLU'(z1), SiLU'(z2) saved by the forward (dsave, 128
+// floats per row): three products, nothing recomputed, only the backward weight
+// image staged.  TMEM columns: [128,192) ybar W3^T then rhobar (48), [192,256)
+// z2bar W2^T.
 template <int OUT, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_bwd(TcLayer nets, const Tile* __restrict__ tiles,
-                                                           const float* __restrict__ rho,
+                                                           const float* __restrict__ dsave,
                                                            const float* __restrict__ ybar,
                                                            float* __restrict__ rhobar, int* __restrict__ flags) {
     using L = BwdSmem<SPLIT>;
@@ -409,13 +447,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_bwd(TcLayer nets, const 
     const Tile tl = tiles[blockIdx.x];
     if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list (before any TMEM allocation)
     const TcNet& w = nets.e[tl.elem];
+    const float* drow = r < tl.nrows ? dsave + (size_t)(tl.row0 + r) * (H1 + H2) : nullptr;
     const uint32_t tmem = setup(tslot, bar);
     if (tid == 0) {
-        mbar_expect_tx(&bar[0], 2 * kImg * L::S);
-        bulk_g2s(smem + L::WF, w.img, kImg * L::S, &bar[0]);             // forward hi (| lo)
+        mbar_expect_tx(&bar[0], kImg * L::S);
         bulk_g2s(smem + L::WB, w.img + 2 * kImg, kImg * L::S, &bar[0]);  // backward hi (| lo)
     }
-    load_x_tile(smem + L::A, SPLIT ? smem + L::ALO : nullptr, rho, tl, r);
     {
         float y[16];
 #pragma unroll
@@ -435,11 +472,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_bwd(TcLayer nets, const 
     if (!ok) {
         fail(flags, &bar[0], 0);
     } else {
-        if (tid == 0) {
-            issue<SPLIT>(tmem, smem + L::A, smem + L::ALO, NFEAT, smem + L::WF + kF_W1t, smem + L::WFLO + kF_W1t, H1,
-                         NFEAT / 16);  // z1
+        if (tid == 0) {  // ybar W3^T
             issue<SPLIT>(tmem + 128, smem + L::Y, smem + L::YLO, 16, smem + L::WB + kB_W3p, smem + L::WBLO + kB_W3p,
-                         H2, 1);  // ybar W3^T
+                         H2, 1);
             mma_commit(&bar[1]);
         }
         ok = wait_all(&bar[1], 0);
@@ -447,39 +482,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_bwd(TcLayer nets, const 
     }
     if (ok) {
         tc_fence_after();
-        silu_to_tile<SPLIT>(tmem, warp, 0, w.b1, smem + L::H, smem + L::HLO, r);
-        handoff();
-        if (tid == 0) {  // z2
-            issue<SPLIT>(tmem + 64, smem + L::H, smem + L::HLO, H1, smem + L::WF + kF_W2t, smem + L::WFLO + kF_W2t,
-                         H2, H1 / 16);
-            mma_commit(&bar[1]);
-        }
-        ok = wait_all(&bar[1], 1);
-        if (!ok) fail(flags, &bar[1], 1);
-    }
-    if (ok) {
-        tc_fence_after();
-        dsilu_to_tile<SPLIT>(tmem, warp, 128, 64, w.b2, smem + L::H, smem + L::HLO, r);  // z2bar
+        scale_to_tile<SPLIT>(tmem, warp, 128, drow ? drow + H1 : nullptr, smem + L::H, smem + L::HLO, r);  // z2bar
         handoff();
         if (tid == 0) {  // z2bar W2^T
             issue<SPLIT>(tmem + 192, smem + L::H, smem + L::HLO, H2, smem + L::WB + kB_W2, smem + L::WBLO + kB_W2, H1,
                          H2 / 16);
             mma_commit(&bar[1]);
         }
-        ok = wait_all(&bar[1], 0);
-        if (!ok) fail(flags, &bar[1], 0);
+        ok = wait_all(&bar[1], 1);
+        if (!ok) fail(flags, &bar[1], 1);
     }
     if (ok) {
         tc_fence_after();
-        dsilu_to_tile<SPLIT>(tmem, warp, 192, 0, w.b1, smem + L::H, smem + L::HLO, r);  // z1bar
+        scale_to_tile<SPLIT>(tmem, warp, 192, drow, smem + L::H, smem + L::HLO, r);  // z1bar
         handoff();
         if (tid == 0) {  // rhobar = z1bar W1^T
             issue<SPLIT>(tmem + 128, smem + L::H, smem + L::HLO, H1, smem + L::WB + kB_W1, smem + L::WBLO + kB_W1,
                          NFEAT, H1 / 16);
             mma_commit(&bar[1]);
         }
-        ok = wait_all(&bar[1], 1);
-        if (!ok) fail(flags, &bar[1], 1);
+        ok = wait_all(&bar[1], 0);
+        if (!ok) fail(flags, &bar[1], 0);
     }
     if (ok) {
         tc_fence_after();
@@ -851,20 +874,22 @@ void ensure_tc_attrs() {
 
 template <int OUT, bool SPLIT>
 void fwd_launch(cudaStream_t s, int nt, const TcLayer& l, const Tile* tiles, const float* rho, float* out,
-                int out_stride, int* flags, GhostOut gh) {
-    k_mlp_tc_fwd<OUT, SPLIT><<<nt, kThreads, FwdSmem<SPLIT>::REQUEST, s>>>(l, tiles, rho, out, out_stride, flags, gh);
+                int out_stride, int* flags, GhostOut gh, float* dsave) {
+    k_mlp_tc_fwd<OUT, SPLIT><<<nt, kThreads, FwdSmem<SPLIT>::REQUEST, s>>>(l, tiles, rho, out, out_stride, flags, gh,
+                                                                          dsave);
 }
 
 template <int OUT, bool SPLIT>
-void bwd_launch(cudaStream_t s, int nt, const TcLayer& l, const Tile* tiles, const float* rho, const float* ybar,
+void bwd_launch(cudaStream_t s, int nt, const TcLayer& l, const Tile* tiles, const float* dsave, const float* ybar,
                 float* rhobar, int* flags) {
-    k_mlp_tc_bwd<OUT, SPLIT><<<nt, kThreads, BwdSmem<SPLIT>::REQUEST, s>>>(l, tiles, rho, ybar, rhobar, flags);
+    k_mlp_tc_bwd<OUT, SPLIT><<<nt, kThreads, BwdSmem<SPLIT>::REQUEST, s>>>(l, tiles, dsave, ybar, rhobar, flags);
 }
 
 }  // namespace
 
 cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
-                              int precision, const float* rho, float* out, int out_stride, int* flags, GhostOut gh) {
+                              int precision, const float* rho, float* out, int out_stride, int* flags, GhostOut gh,
+                              float* dsave) {
     const int nt = (int)nl->tiles128_h.size();
     if (nt == 0) return cudaSuccess;
     ensure_tc_attrs();
@@ -878,15 +903,17 @@ cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTab
     }
     const bool split = precision == REANN_MLP_BF16X3;
     if (energy)
-        (split ? fwd_launch<1, true> : fwd_launch<1, false>)(s, nt, l, nl->tiles128, rho, out, out_stride, flags, gh);
+        (split ? fwd_launch<1, true> : fwd_launch<1, false>)(s, nt, l, nl->tiles128, rho, out, out_stride, flags, gh,
+                                                             dsave);
     else
         (split ? fwd_launch<NPHI, true> : fwd_launch<NPHI, false>)(s, nt, l, nl->tiles128, rho, out, out_stride,
-                                                                    flags, gh);
+                                                                    flags, gh, dsave);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_bwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
-                              int precision, const float* rho, const float* ybar, float* rhobar, int* flags) {
+                              int precision, const float* rho, const float* dsave, const float* ybar, float* rhobar,
+                              int* flags) {
     const int nt = (int)nl->tiles128_h.size();
     if (nt == 0) return cudaSuccess;
     ensure_tc_attrs();
@@ -899,10 +926,12 @@ cudaError_t launch_mlp_bwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTab
         return cudaGetLastError();
     }
     const bool split = precision == REANN_MLP_BF16X3;
+    if (!dsave) return cudaErrorInvalidValue;  // the BF16 backward reads the forward's SiLU' values
     if (energy)
-        (split ? bwd_launch<1, true> : bwd_launch<1, false>)(s, nt, l, nl->tiles128, rho, ybar, rhobar, flags);
+        (split ? bwd_launch<1, true> : bwd_launch<1, false>)(s, nt, l, nl->tiles128, dsave, ybar, rhobar, flags);
     else
-        (split ? bwd_launch<NPHI, true> : bwd_launch<NPHI, false>)(s, nt, l, nl->tiles128, rho, ybar, rhobar, flags);
+        (split ? bwd_launch<NPHI, true> : bwd_launch<NPHI, false>)(s, nt, l, nl->tiles128, dsave, ybar, rhobar,
+                                                                    flags);
     return cudaGetLastError();
 }
 

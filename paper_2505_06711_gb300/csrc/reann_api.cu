@@ -869,7 +869,8 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
         const int out_stride = energy_net ? 1 : NPHI;
         if (ctx->precision != REANN_MLP_FP32)
             REANN_CUDA_TRY(ctx, launch_mlp_fwd_tc(s, nl, ctx->tc, t, energy_net, ctx->precision,
-                                                  rho_t, out, out_stride, ctx->d_flags, gh));
+                                                  rho_t, out, out_stride, ctx->d_flags, gh,
+                                                  nl->dsave + (size_t)t * n * (H1 + H2)));
         else
             REANN_CUDA_TRY(ctx, launch_mlp_fwd_f32(s, nl, ctx->nets, t, energy_net, rho_t, out, out_stride, pairs, gh,
                                                   nl->dsave + (size_t)t * n * (H1 + H2), epart));
@@ -892,9 +893,8 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
         {
             ProfScope p(ctx, PR_MLP_BWD);
             if (ctx->precision != REANN_MLP_FP32)
-                REANN_CUDA_TRY(ctx, launch_mlp_bwd_tc(s, nl, ctx->tc, t, t == T - 1, ctx->precision, rho_t, nl->cbar,
-                                                      nl->rhobar,
-                                                      ctx->d_flags));
+                REANN_CUDA_TRY(ctx, launch_mlp_bwd_tc(s, nl, ctx->tc, t, t == T - 1, ctx->precision, rho_t, dsave_t,
+                                                      nl->cbar, nl->rhobar, ctx->d_flags));
             else if (!pairs)  // the FP32 backward networks also take the bbar step (fused)
                 REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, dsave_t, nl->cbar,
                                                        nl->rhobar, false, ctx->d_W + t * lw, bck_t, coef_t, nl->bbar,

@@ -125,3 +125,43 @@ def test_error_paths():
     sy.evaluate()
     sy.check()
     sy.close()
+
+
+def test_empty_and_oversized_inputs_are_refused_on_the_host():
+    """N = 0 and N > 2^28 atoms: the build refuses them before any device work
+    (REANN_E_ARG) and the context stays usable; an energy sum over no atoms is 0."""
+    import ctypes
+
+    import torch
+
+    from paper_2505_06711_gb300 import binding
+
+    spec = make_model(T=3)
+    pot = potential(spec)
+    s = water_box(16, seed=0)
+    empty_pos = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    empty_sp = torch.zeros((0,), dtype=torch.int32, device="cuda")
+    _expect(binding.REANN_E_ARG,
+            lambda: binding.reann_build_nlist(pot.ctx, empty_pos, empty_sp, s.cell, spec.r_c, 1.0))
+    # a count beyond the documented limit, with valid small buffers: rejected by the host check
+    p = torch.as_tensor(s.pos, device="cuda").contiguous()
+    spc = torch.as_tensor(s.species, device="cuda").contiguous()
+    c = np.ascontiguousarray(s.cell, dtype=np.float64).reshape(9)
+    out = ctypes.c_void_p()
+    rc = binding.lib().reann_build_nlist(pot.ctx, (1 << 28) + 1, p.data_ptr(), spc.data_ptr(),
+                                         c.ctypes.data, float(spec.r_c), 1.0, ctypes.byref(out))
+    assert rc == binding.REANN_E_ARG and not out.value
+    # an energy sum over no atoms
+    e = torch.full((1,), 7.0, dtype=torch.float64, device="cuda")
+    assert binding.reann_energy_sum_noalloc(empty_pos.new_zeros((0,), dtype=torch.float32), 0, e) == binding.REANN_OK
+    torch.cuda.synchronize()
+    assert float(e.item()) == 0.0
+    # the context still evaluates a structure correctly
+    sy = pot.system(s.pos, s.species, s.cell, skin=1.0)
+    sy.evaluate()
+    sy.check()
+    torch.cuda.synchronize()
+    ref = oracle.energy_forces(spec, s.pos, s.species, s.cell)
+    assert_parity({"energy": float(sy.energy.item()), "forces": sy.forces.double().cpu().numpy()},
+                  ref, s.n_atoms)
+    sy.close()
