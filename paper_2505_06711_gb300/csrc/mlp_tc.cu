@@ -329,23 +329,26 @@ __device__ __forceinline__ void dsilu_to_tile(uint32_t tmem, int warp, int cg, i
     }
 }
 
-// g (TMEM columns [cg, cg + 64)) * the row's saved SiLU' values s (64 floats, or
-// zeros for rows past the tile's end) -> row r of an A tile
+// 64 saved SiLU' values of a row into registers (zeros for rows past the tile's
+// end); issued a stage ahead so that the loads overlap the previous product
+__device__ __forceinline__ void load64(const float* __restrict__ p, float* d) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const float4 x = p ? __ldg(reinterpret_cast<const float4*>(p) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        d[4 * q] = x.x, d[4 * q + 1] = x.y, d[4 * q + 2] = x.z, d[4 * q + 3] = x.w;
+    }
+}
+
+// g (TMEM columns [cg, cg + 64)) * the row's saved SiLU' values sd -> row r of an A tile
 template <bool SPLIT>
-__device__ __forceinline__ void scale_to_tile(uint32_t tmem, int warp, int cg, const float* __restrict__ s,
-                                              uint8_t* hi, uint8_t* lo, int r) {
+__device__ __forceinline__ void scale_to_tile(uint32_t tmem, int warp, int cg, const float* sd, uint8_t* hi,
+                                              uint8_t* lo, int r) {
     float g[16], h[16];
 #pragma unroll
     for (int c0 = 0; c0 < 64; c0 += 16) {
         tmem_ld16(lane_addr(tmem, warp, cg + c0), g);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float4 d = s ? __ldg(reinterpret_cast<const float4*>(s + c0) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-            h[4 * q] = g[4 * q] * d.x;
-            h[4 * q + 1] = g[4 * q + 1] * d.y;
-            h[4 * q + 2] = g[4 * q + 2] * d.z;
-            h[4 * q + 3] = g[4 * q + 3] * d.w;
-        }
+        for (int i = 0; i < 16; ++i) h[i] = g[i] * sd[c0 + i];
         put8(hi, SPLIT ? lo : nullptr, 64, r, c0 / 8, h);
         put8(hi, SPLIT ? lo : nullptr, 64, r, c0 / 8 + 1, h + 8);
     }
@@ -467,6 +470,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_bwd(TcLayer nets, const 
         put8(smem + L::Y, SPLIT ? smem + L::YLO : nullptr, 16, r, 0, y);
         put8(smem + L::Y, SPLIT ? smem + L::YLO : nullptr, 16, r, 1, y + 8);
     }
+    float sd[64];
+    load64(drow ? drow + H1 : nullptr, sd);  // SiLU'(z2)
     handoff();
     bool ok = wait_all(&bar[0], 0);
     if (!ok) {
@@ -482,19 +487,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_bwd(TcLayer nets, const 
     }
     if (ok) {
         tc_fence_after();
-        scale_to_tile<SPLIT>(tmem, warp, 128, drow ? drow + H1 : nullptr, smem + L::H, smem + L::HLO, r);  // z2bar
+        scale_to_tile<SPLIT>(tmem, warp, 128, sd, smem + L::H, smem + L::HLO, r);  // z2bar
         handoff();
         if (tid == 0) {  // z2bar W2^T
             issue<SPLIT>(tmem + 192, smem + L::H, smem + L::HLO, H2, smem + L::WB + kB_W2, smem + L::WBLO + kB_W2, H1,
                          H2 / 16);
             mma_commit(&bar[1]);
         }
+        load64(drow, sd);  // SiLU'(z1), while the product runs
         ok = wait_all(&bar[1], 1);
         if (!ok) fail(flags, &bar[1], 1);
     }
     if (ok) {
         tc_fence_after();
-        scale_to_tile<SPLIT>(tmem, warp, 192, drow, smem + L::H, smem + L::HLO, r);  // z1bar
+        scale_to_tile<SPLIT>(tmem, warp, 192, sd, smem + L::H, smem + L::HLO, r);  // z1bar
         handoff();
         if (tid == 0) {  // rhobar = z1bar W1^T
             issue<SPLIT>(tmem + 128, smem + L::H, smem + L::HLO, H1, smem + L::WB + kB_W1, smem + L::WBLO + kB_W1,
