@@ -469,19 +469,34 @@ extern "C" int reann_ctx_set_mlp_precision(reann_ctx* ctx, int precision) {
 
 extern "C" const char* reann_last_error(const reann_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
-extern "C" int reann_ctx_check(reann_ctx* ctx) {
-    if (!ctx) return REANN_E_ARG;
+namespace {
+
+// enqueue the read-back of the device flags and their reset on the context stream
+int enqueue_flags_readback(reann_ctx* ctx) {
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int) * NFLAGS, cudaMemcpyDeviceToHost,
                                         ctx->stream));
-    REANN_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    REANN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * NFLAGS, ctx->stream));
+    return REANN_OK;
+}
+
+// the status the flags read back by enqueue_flags_readback report (after a synchronisation)
+int flags_status(reann_ctx* ctx) {
     REANN_CUDA_TRY(ctx, cudaGetLastError());
     const int geom = ctx->h_flags[FLAG_GEOM], cap = ctx->h_flags[FLAG_NBR_OVERFLOW] | ctx->h_flags[FLAG_GHOST_OVERFLOW];
     const int timeout = ctx->h_flags[FLAG_TIMEOUT];
-    REANN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * NFLAGS, ctx->stream));
     if (geom) return set_error(ctx, REANN_E_GEOM, "coincident or non-finite atoms in an evaluation");
     if (cap) return set_error(ctx, REANN_E_CAPACITY, "neighbour or ghost capacity exceeded");
     if (timeout) return set_error(ctx, REANN_E_TIMEOUT, "a bounded device wait ran out (tensor-core network)");
     return REANN_OK;
+}
+
+}  // namespace
+
+extern "C" int reann_ctx_check(reann_ctx* ctx) {
+    if (!ctx) return REANN_E_ARG;
+    if (int rc = enqueue_flags_readback(ctx)) return rc;
+    REANN_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return flags_status(ctx);
 }
 
 namespace {
@@ -1078,8 +1093,9 @@ extern "C" int reann_energy_forces_host(reann_ctx* ctx, reann_nlist* nl, const d
     if (rc) return rc;
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(forces, nl->d_forces, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(energy, nl->d_energy, sizeof(double), cudaMemcpyDeviceToHost, s));
-    REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));
-    return reann_ctx_check(ctx);
+    if (int rc2 = enqueue_flags_readback(ctx)) return rc2;  // the flags come back with the results:
+    REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));           // one synchronisation per call
+    return flags_status(ctx);
 }
 
 namespace {
