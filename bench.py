@@ -62,7 +62,7 @@ FLOP_PER_ATOM_BBAR = 5440             # g (1280 FMA) + gbar (160) + bbar (1280 F
 # DRAM traffic per launch of the dominant kernel from one ncu capture of this
 # workload (profiles/), valid only for the source it was taken on.
 TRAFFIC = {  # {(region, source_sha of the kernel source): bytes per launch}
-    ("density_adj", "7c2b165e39e8"): 21838848,  # profiles/density_adj_water24576_T3.md
+    ("density_adj", "aaefc49e55c7"): 21837312,  # profiles/density_adj_water24576_T3.md
 }
 
 
