@@ -18,7 +18,10 @@ random-weight model); the paper's datasets and trained weights are not used.
   in, host forces and energy out, copies inside the timed region.
 * ``roofline``: the region with the largest device time, its algorithmic FLOPs
   per launch (the FLOP_PER_* counts below) over its mean launch time, against the FP32
-  SIMT peak of the GPU (SMs x 128 lanes x 2 FLOP x max SM clock).
+  SIMT peak of the GPU (SMs x 128 lanes x 2 FLOP x max SM clock); beside it the
+  same fraction with the scope table's coarser counts (``frac_alu_survey``), the
+  edge kernel's algorithmic HBM bytes over its time against the measured copy
+  bandwidth (``frac_hbm``), and ncu's L2 throughput share (``frac_l2``).
 * ``cpu_baseline``: the FP64 oracle (test infrastructure) evaluating the same
   box once on the host cores, rank 0 only.
 * ``--impl reference``: the oracle is the reference arm; each step is one full
@@ -59,10 +62,28 @@ FLOP_PER_ATOM_MLP_FWD = {8: 15360, 1: 14464}
 FLOP_PER_ATOM_MLP_BWD = {8: 15360, 1: 14464}  # the vector-Jacobian product W3, W2, W1 (no recompute)
 FLOP_PER_ATOM_BBAR = 5440             # g (1280 FMA) + gbar (160) + bbar (1280 FMA)
 
-# DRAM traffic per launch of the dominant kernel from one ncu capture of this
-# workload (profiles/), valid only for the source it was taken on.
+# The same regions counted as the hot-path scope table counts them (a coarser
+# operation count: ~130 FP32 operations per live edge forward, twice that in
+# the reverse pass), reported beside the counts above.
+FLOP_PER_LIVE_EDGE_FWD_COARSE = 130
+FLOP_PER_LIVE_EDGE_ADJ_COARSE = 260
+FLOP_PER_ATOM_CONTRACTION_COARSE = 2 * 1280
+
+# Algorithmic HBM bytes per atom and layer of the edge kernels: the neighbour
+# row (4 B per listed entry within r_c + skin), the atom's position (16 B) and
+# coefficients (32 B), the b checkpoint (320 B), and for the forward pass the
+# features rho (192 B); neighbours' positions and coefficients are re-reads
+# served by L2.
+BYTES_PER_ATOM_EDGE_FIXED = {"density_fwd": 16 + 32 + 320 + 192, "density_adj": 16 + 32 + 320}
+
+# DRAM traffic and L2 throughput (share of peak) per launch of the dominant
+# kernel, from one ncu capture of this workload; valid only for the kernel
+# source they were taken on (keyed by its hash), null otherwise.
 TRAFFIC = {  # {(region, source_sha of the kernel source): bytes per launch}
-    ("density_adj", "aaefc49e55c7"): 21837312,  # profiles/density_adj_water24576_T3.md
+    ("density_adj", "aaefc49e55c7"): 21837312,
+}
+L2_FRAC = {  # {(region, source_sha): lts__t_sectors throughput as a fraction of peak}
+    ("density_adj", "aaefc49e55c7"): 0.30,
 }
 
 
@@ -485,6 +506,32 @@ def region_flops(region: str, n_atoms: int, n_live: int, T: int, launches: int) 
     return None
 
 
+def region_flops_coarse(region: str, n_atoms: int, n_live: int, T: int) -> float | None:
+    """The same, with the scope table's coarse per-edge counts."""
+    if region == "density_fwd":
+        return T * (n_live * FLOP_PER_LIVE_EDGE_FWD_COARSE + n_atoms * FLOP_PER_ATOM_CONTRACTION_COARSE)
+    if region == "density_adj":
+        return T * n_live * FLOP_PER_LIVE_EDGE_ADJ_COARSE
+    return None
+
+
+def region_bytes(region: str, n_atoms: int, n_pairs: int, T: int) -> float | None:
+    """Algorithmic HBM bytes of all launches of an edge region in one step."""
+    fixed = BYTES_PER_ATOM_EDGE_FIXED.get(region)
+    if fixed is None:
+        return None
+    return T * (4.0 * n_pairs + n_atoms * fixed)
+
+
+def measured_peaks() -> tuple[float, str]:
+    """HBM copy bandwidth (GB/s) from the machine's measured peaks, else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
 def launches_per_step(T: int) -> int:
     """Library kernels per step (FP32 networks, single-domain list): rebuild 11
     (wrap + keys + histogram, 2 x 3 sort kernels (scan, scatter, rank), gather,
@@ -643,38 +690,10 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     ms, wall, _ = timed(False)
-    clk = clocks.stop()
     ms_prof, _, prof = timed(True)
     ms = max_over_ranks(ms, dist, "cuda")
     value = aggregate(n_atoms, ms, ws)
 
-    # roofline of the dominant region
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    region, (tot_ms, nl_launch) = dom
-    per_step_ms = tot_ms / args.steps
-    launches = nl_launch / args.steps
-    flops = region_flops(region, n_atoms, n_live, T_LAYERS, launches)
-    props = torch.cuda.get_device_properties(local)
-    max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
-    peak_tflops = props.multi_processor_count * 128 * 2 * max_mhz * 1e6 / 1e12
-    roof = None
-    if flops is not None and launches > 0:
-        achieved = flops / launches / (per_step_ms / launches * 1e-3) / 1e12
-        key = (region, source_sha(REGION_SOURCE.get(region, "density.cu")))
-        roof = {
-            "bound": "alu",
-            "kernel": region,
-            "achieved": achieved,
-            "peak": peak_tflops,
-            "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops,
-            "traffic": TRAFFIC.get(key),
-            "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 FLOP x {max_mhz:.0f} MHz",
-            "launches_per_step": launches,
-            "mean_launch_ms": per_step_ms / launches,
-            "timed_in": "second timed pass of the same steps with per-region CUDA events on the library stream",
-            "ms_per_step_with_events": ms_prof,
-        }
     breakdown = {k: round(v[0] / args.steps, 5) for k, v in prof.items() if v[1]}
 
     # end to end through the C ABI with host buffers
@@ -720,6 +739,48 @@ def run_ours(args):
             "mlp_ms_per_step": (v_prof["mlp_fwd"][0] + v_prof["mlp_bwd"][0]) / args.steps,
         }
     binding.reann_ctx_set_mlp_precision(ctx, binding.REANN_MLP_FP32)
+
+    # the sampler ran through both timed passes, the end-to-end calls and the variants
+    clk = clocks.stop()
+    # roofline of the dominant region
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    region, (tot_ms, nl_launch) = dom
+    per_step_ms = tot_ms / args.steps
+    launches = nl_launch / args.steps
+    flops = region_flops(region, n_atoms, n_live, T_LAYERS, launches)
+    props = torch.cuda.get_device_properties(local)
+    max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak_tflops = props.multi_processor_count * 128 * 2 * max_mhz * 1e6 / 1e12
+    roof = None
+    if flops is not None and launches > 0:
+        launch_s = per_step_ms / launches * 1e-3
+        achieved = flops / launches / launch_s / 1e12
+        key = (region, source_sha(REGION_SOURCE.get(region, "density.cu")))
+        hbm_gbs, hbm_src = measured_peaks()
+        coarse = region_flops_coarse(region, n_atoms, n_live, T_LAYERS)
+        nbytes = region_bytes(region, n_atoms, n_pairs, T_LAYERS)
+        roof = {
+            "bound": "alu",
+            "kernel": region,
+            "achieved": achieved,
+            "peak": peak_tflops,
+            "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops,
+            "traffic": TRAFFIC.get(key),
+            "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 FLOP x {max_mhz:.0f} MHz",
+            "flop_count": "per live edge as the kernels' formulas need them (DESIGN section 6)",
+            "frac_alu_survey": (coarse / launches / launch_s / 1e12 / peak_tflops) if coarse else None,
+            "flop_count_survey": "scope table: 130 per live edge forward + 2560 per atom contraction, 260 reverse",
+            "achieved_hbm_gbs": (nbytes / launches / launch_s / 1e9) if nbytes else None,
+            "frac_hbm": (nbytes / launches / launch_s / 1e9 / hbm_gbs) if nbytes else None,
+            "hbm_peak_gbs": hbm_gbs,
+            "hbm_peak_source": f"{hbm_src} copy bandwidth",
+            "frac_l2": L2_FRAC.get(key),
+            "launches_per_step": launches,
+            "mean_launch_ms": per_step_ms / launches,
+            "timed_in": "second timed pass of the same steps with per-region CUDA events on the library stream",
+            "ms_per_step_with_events": ms_prof,
+        }
 
     md = None if args.no_md else run_md(s, pot, args)
     t_scaling = None if args.no_t_scaling else run_t_scaling(args)

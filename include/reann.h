@@ -98,6 +98,31 @@ int reann_model_create_ex(int n_elem, int T, int n_phi, int l_max, int n_orb, in
                           double alpha, int feature_pairs, const float* params, int64_t n_params, reann_model** out);
 void reann_model_free(reann_model* model);
 
+/*
+ * Load a model from a file (host only, no CUDA call): the shape of Eqs. 1-2
+ * (n_elem, T, N_phi, L, N_orb, hidden widths, r_c, alpha, feature kind) and
+ * the flat FP32 parameter vector laid out as for reann_model_create.
+ * File layout, little-endian whatever the host:
+ *   bytes  0..7   magic "REANNMDL"          bytes  8..11  uint32 version (1)
+ *   bytes 12..43  int32 n_elem, T, n_phi, l_max, n_orb, h1, h2, feature_pairs
+ *   bytes 44..47  uint32 reserved (0)       bytes 48..55  float64 r_c
+ *   bytes 56..63  float64 alpha             bytes 64..71  int64 n_params
+ *   bytes 72..    n_params float32 parameters
+ *   path  host, NUL-terminated file name
+ *   out   receives the new model (NULL on failure); free with reann_model_free
+ * Errors: REANN_E_ARG (unreadable file, wrong magic or version, size other
+ * than 72 + 4 n_params bytes, or a shape / parameter set that
+ * reann_model_create_ex rejects), REANN_E_NOMEM.
+ */
+int reann_model_load(const char* path, reann_model** out);
+
+/*
+ * Write `model` to `path` in the layout of reann_model_load (host only; the
+ * file is replaced).  Loading it gives a model with bit-identical parameters.
+ * Errors: REANN_E_ARG (null argument, file not writable or write failed).
+ */
+int reann_model_save(const reann_model* model, const char* path);
+
 /* -------------------------------------------------------------- context --- */
 
 /*
@@ -127,6 +152,22 @@ const char* reann_last_error(const reann_ctx* ctx);
  * REANN_E_CAPACITY).  Synchronous.
  */
 int reann_ctx_check(reann_ctx* ctx);
+
+/*
+ * Failure-detection diagnostic (no counterpart in the paper).  Every
+ * mbarrier wait of the tensor-core network kernels is bounded; when one runs
+ * out, the CTA records a timeout flag, waits (bounded) until the MMAs it
+ * issued and its weight copy have completed, frees its tensor memory and
+ * returns, and reann_ctx_check() reports REANN_E_TIMEOUT.  This call enqueues
+ * on the context stream one CTA of that kind which allocates tensor memory and
+ * waits `polls` times on an mbarrier that nothing ever arrives on, so the wait
+ * runs out with no copy or MMA in flight and the same exit path runs.  The
+ * context stays usable: the next reann_ctx_check() returns REANN_E_TIMEOUT
+ * and clears the flag.  Asynchronous.
+ *   polls  1 .. 2^26 polls of the barrier before the wait gives up
+ * Errors: REANN_E_ARG, REANN_E_CUDA.
+ */
+int reann_ctx_wait_selftest(reann_ctx* ctx, int64_t polls);
 
 /* ------------------------------------------------------- neighbour list --- */
 
@@ -323,27 +364,34 @@ int reann_serve_usage(reann_serve* srv, int64_t* free_atoms, int64_t* free_ghost
 /*
  * Total energy E = sum_i eps_i in FP64 from per-atom energies the caller
  * already holds, without allocating any device memory.  The paper has no
- * counterpart; this exists for callers that cannot allocate at that moment:
- * code running while a CUDA stream is captured into a graph in the global
- * capture mode (cudaMalloc is not permitted there), and force back-ends hosted
- * by a molecular-dynamics engine whose force callback must not allocate
- * because the engine owns the device-memory budget.
+ * counterpart.  It exists for callers that must not allocate when they need
+ * the total: force back-ends hosted as plugins by a molecular-dynamics engine
+ * whose force callback may not allocate (the engine owns the device-memory
+ * budget and its pools), and latency-critical callbacks that avoid cudaMalloc
+ * because it can synchronise the device.
  *   atom_energy  dev, n_atoms FP32 (e.g. the atom_energy output of
  *                reann_energy_forces); NULL only when n_atoms == 0
  *   n_atoms      0 <= n_atoms <= reann_energy_sum_noalloc_max_atoms()
  *                (8,388,608); larger sizes return REANN_E_CAPACITY, no work
  *   energy       dev, 1 FP64, overwritten
  *   cuda_stream  cudaStream_t to enqueue on (NULL = legacy default stream)
- * The same two-level summation order as reann_energy_forces, so the result
- * equals that call's energy bit for bit on the same atom energies.
+ * The sum is FP64 throughout (blocks of 2,048 atoms, then the block sums);
+ * reann_energy_forces groups the same FP64 additions differently (per network
+ * tile, in its internal atom order), so the two totals agree to FP64 rounding,
+ * not bit for bit.
  * Scratch is a fixed 32 KiB array inside the library, held by every GPU that
  * loads it until the process exits.  The first call on each device looks up
- * that array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls share the array and it keeps the last
- * call's contents (each call writes every entry it reads): calls that overlap
- * on the GPU race and must be serialised by the caller.  Asynchronous.
+ * that array's device address (cudaGetSymbolAddress) and caches it for the
+ * life of the process; make that first call before any stream capture.  After
+ * cudaDeviceReset on a device the cached address is stale: do not call this
+ * entry point on that device again in the same process.  All calls share the
+ * array and it keeps the last call's contents (each call writes every entry it
+ * reads): calls that overlap on the GPU race and must be serialised by the
+ * caller.  Asynchronous.
  * Errors: REANN_E_ARG, REANN_E_CAPACITY, REANN_E_CUDA (returned directly; no
- * context message).
+ * context message).  REANN_E_CUDA reports an error that the CUDA runtime
+ * returned at one of this call's launches; it can also be a pending error left
+ * by earlier asynchronous work on the same device.
  */
 int reann_energy_sum_noalloc(const float* atom_energy, int64_t n_atoms, double* energy, void* cuda_stream);
 int64_t reann_energy_sum_noalloc_max_atoms(void);

@@ -52,11 +52,14 @@ _SIGS = {
     "reann_model_create": ([_int] * 7 + [_dbl, _dbl, _vp, _i64, ctypes.POINTER(_vp)], _int),
     "reann_model_create_ex": ([_int] * 7 + [_dbl, _dbl, _int, _vp, _i64, ctypes.POINTER(_vp)], _int),
     "reann_model_free": ([_vp], None),
+    "reann_model_load": ([ctypes.c_char_p, ctypes.POINTER(_vp)], _int),
+    "reann_model_save": ([_vp, ctypes.c_char_p], _int),
     "reann_ctx_create": ([_vp, _vp, ctypes.POINTER(_vp)], _int),
     "reann_ctx_free": ([_vp], None),
     "reann_ctx_set_mlp_precision": ([_vp, _int], _int),
     "reann_last_error": ([_vp], ctypes.c_char_p),
     "reann_ctx_check": ([_vp], _int),
+    "reann_ctx_wait_selftest": ([_vp, _i64], _int),
     "reann_build_nlist": ([_vp, _i64, _vp, _vp, _vp, _dbl, _dbl, ctypes.POINTER(_vp)], _int),
     "reann_nlist_free": ([_vp], None),
     "reann_nlist_info": ([_vp, _vp, _vp, _vp, _vp], _int),
@@ -166,6 +169,18 @@ def reann_model_free(model) -> None:
     lib().reann_model_free(model)
 
 
+def reann_model_load(path) -> ctypes.c_void_p:
+    """Model from a file written by reann_model_save or synth.model.write_model_file."""
+    out = _vp()
+    rc = lib().reann_model_load(os.fsencode(path), ctypes.byref(out))
+    _check(rc)
+    return out
+
+
+def reann_model_save(model, path) -> None:
+    _check(lib().reann_model_save(model, os.fsencode(path)))
+
+
 # ---------------------------------------------------------------- context --
 def reann_ctx_create(model, stream=None) -> ctypes.c_void_p:
     """``stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None (current torch stream)."""
@@ -189,6 +204,11 @@ def reann_ctx_set_mlp_precision(ctx, precision: int) -> None:
 
 def reann_last_error(ctx) -> str:
     return lib().reann_last_error(ctx).decode()
+
+
+def reann_ctx_wait_selftest(ctx, polls: int) -> None:
+    """Enqueue one bounded wait that runs out (reann_ctx_check then reports REANN_E_TIMEOUT)."""
+    _check(lib().reann_ctx_wait_selftest(ctx, int(polls)), ctx)
 
 
 def reann_ctx_check(ctx) -> None:

@@ -52,6 +52,7 @@ enum Flag {
     FLAG_SPECIES = 4,
     FLAG_MOVED = 5,
     FLAG_TIMEOUT = 6,
+    FLAG_TIMEOUT_DRAIN = 7,  // after a timeout, the CTA's own MMAs or copies did not complete either
     NFLAGS = 8
 };
 
@@ -443,6 +444,9 @@ cudaError_t launch_energy_final(cudaStream_t s, const double* partial, int np, d
 cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
                               int precision, const float* rho, float* out, int out_stride, int* flags,
                               GhostOut gh, float* dsave);
+// one CTA that waits, `polls` times, on an mbarrier nothing arrives on and then takes
+// the bounded-wait exit of the tensor-core kernels (reann_ctx_wait_selftest)
+cudaError_t launch_wait_selftest(cudaStream_t s, int* flags, long long polls);
 cudaError_t launch_mlp_bwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
                               int precision, const float* rho, const float* dsave, const float* ybar, float* rhobar,
                               int* flags);

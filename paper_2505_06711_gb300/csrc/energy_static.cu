@@ -1,14 +1,13 @@
 // reann_energy_sum_noalloc: the FP64 total-energy reduction without any
 // device allocation.
 //
-// Some callers cannot allocate device memory at the moment they need a total
-// energy: code that runs while a CUDA stream is being captured into a graph in
-// the global capture mode (cudaMalloc is not permitted there), and force
-// back-ends hosted as plugins by a molecular-dynamics engine whose force
-// callback must not allocate (the engine owns the device-memory budget and its
-// pools).  This entry point sums per-atom energies that such a caller already
-// holds, in FP64, using a fixed scratch array compiled into the library instead
-// of memory allocated per call.
+// Some callers must not allocate device memory at the moment they need a total
+// energy: force back-ends hosted as plugins by a molecular-dynamics engine
+// whose force callback may not allocate (the engine owns the device-memory
+// budget and its pools), and latency-critical callbacks that avoid cudaMalloc
+// because it can synchronise the device.  This entry point sums per-atom
+// energies that such a caller already holds, in FP64, using a fixed scratch
+// array compiled into the library instead of memory allocated per call.
 //
 // Scratch: g_energy_partials below, kMaxPartials doubles (32 KiB), one per
 // block of 2048 atoms, so at most kMaxAtoms = 8,388,608 atoms per call.  Every
@@ -16,7 +15,8 @@
 // call shares it and it keeps the last call's contents; each call writes every
 // partial it later reads, so nothing needs clearing, but two calls that overlap
 // on the GPU (different streams, or different host threads on one device) race
-// on it and must be serialised by the caller.
+// on it and must be serialised by the caller.  The array's device address is
+// looked up once per device (first call) and cached for the process lifetime.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -98,7 +98,10 @@ extern "C" int reann_energy_sum_noalloc(const float* atom_energy, int64_t n_atom
     if (rc != REANN_OK) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const int np = (int)((n_atoms + kAtomsPerBlock - 1) / kAtomsPerBlock);
-    if (np > 0) k_partial<<<np, kThreads, 0, s>>>(n_atoms, atom_energy, partials);
+    if (np > 0) {
+        k_partial<<<np, kThreads, 0, s>>>(n_atoms, atom_energy, partials);
+        if (cudaGetLastError() != cudaSuccess) return REANN_E_CUDA;
+    }
     k_final<<<1, kThreads, 0, s>>>(np, partials, energy);
     return cudaGetLastError() == cudaSuccess ? REANN_OK : REANN_E_CUDA;
 }

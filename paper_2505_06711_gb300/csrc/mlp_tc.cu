@@ -34,7 +34,8 @@
 // group).
 //
 // Every wait is bounded: after kSpinLimit polls a CTA records FLAG_TIMEOUT in
-// the context flags, frees its TMEM and returns (reann_ctx_check reports
+// the context flags, waits (bounded) until every MMA it issued and its weight
+// copy have completed, frees its TMEM and returns (reann_ctx_check reports
 // REANN_E_TIMEOUT).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -97,10 +98,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
                  : "memory");
 }
 
-// bounded wait for phase `parity`; returns false when the limit ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+// bounded wait for phase `parity`; returns false when `limit` polls ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long long limit = kSpinLimit) {
     const uint32_t a = smem_addr(mbar);
-    for (long long it = 0; it < kSpinLimit; ++it) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -219,15 +220,29 @@ __device__ __forceinline__ uint32_t lane_addr(uint32_t tmem, int warp, int col) 
 }
 
 // uniform bounded wait: every thread polls; the CTA agrees on the outcome
-__device__ __forceinline__ bool wait_all(uint64_t* bar, uint32_t parity) {
-    const bool ok = mbar_wait(bar, parity);
+__device__ __forceinline__ bool wait_all(uint64_t* bar, uint32_t parity, long long limit = kSpinLimit) {
+    const bool ok = mbar_wait(bar, parity, limit);
     return __syncthreads_and(ok);
 }
 
-__device__ __forceinline__ void fail(int* flags, uint64_t* bar, uint32_t parity) {
-    if (threadIdx.x == 0) atomicOr(&flags[FLAG_TIMEOUT], 1);
-    mbar_wait(bar, parity);  // give work in flight one more bounded chance to land
-    __syncthreads();
+// After a wait ran out (bar[0]: the weight copy, bar[1]: MMA completion, bar[2]:
+// spare): record FLAG_TIMEOUT, then make sure nothing this CTA started is still in
+// flight before the caller releases its TMEM and shared memory.  Thread 0 commits
+// every tcgen05 operation it issued to the spare barrier (it arrives once all of
+// them completed, at once when there were none); when the weight copy was not seen
+// to land, its barrier is waited for again.  Both waits are bounded; if either runs
+// out as well, FLAG_TIMEOUT_DRAIN is recorded too (the CTA still frees its TMEM and
+// returns, and the host reports that the device state is suspect).
+__device__ __forceinline__ void fail(int* flags, uint64_t* bar, bool weights_landed) {
+    if (threadIdx.x == 0) {
+        atomicOr(&flags[FLAG_TIMEOUT], 1);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_addr(&bar[2]))
+                     : "memory");
+    }
+    bool drained = mbar_wait(&bar[2], 0);
+    if (!weights_landed) drained = mbar_wait(&bar[0], 0) && drained;
+    if (!__syncthreads_and(drained) && threadIdx.x == 0) atomicOr(&flags[FLAG_TIMEOUT_DRAIN], 1);
 }
 
 // rows [row0, row0 + nrows) of a row-major FP32 [.][48] array -> BF16 core-matrix tile(s) (K = 48)
@@ -275,6 +290,7 @@ __device__ __forceinline__ uint32_t setup(uint32_t* tslot, uint64_t* bar) {
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
+        mbar_init(&bar[2], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
@@ -364,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_fwd(TcLayer nets, const 
     using L = FwdSmem<SPLIT>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::BAR);  // [0] weights, [1] MMA
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 3);
     const int tid = threadIdx.x, warp = tid >> 5, r = tid;
     const Tile tl = tiles[blockIdx.x];
     if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list (before any TMEM allocation)
@@ -379,7 +395,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_fwd(TcLayer nets, const 
     handoff();
     bool ok = wait_all(&bar[0], 0);
     if (!ok) {
-        fail(flags, &bar[0], 0);
+        fail(flags, bar, false);
     } else {
         if (tid == 0) {  // z1 = x W1
             issue<SPLIT>(tmem, smem + L::A, smem + L::ALO, NFEAT, smem + L::W + kF_W1t, smem + L::WLO + kF_W1t, H1,
@@ -387,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_fwd(TcLayer nets, const 
             mma_commit(&bar[1]);
         }
         ok = wait_all(&bar[1], 0);
-        if (!ok) fail(flags, &bar[1], 0);
+        if (!ok) fail(flags, bar, true);
     }
     if (ok) {
         tc_fence_after();
@@ -399,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_fwd(TcLayer nets, const 
             mma_commit(&bar[1]);
         }
         ok = wait_all(&bar[1], 1);
-        if (!ok) fail(flags, &bar[1], 1);
+        if (!ok) fail(flags, bar, true);
     }
     if (ok) {
         tc_fence_after();
@@ -411,7 +427,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_fwd(TcLayer nets, const 
             mma_commit(&bar[1]);
         }
         ok = wait_all(&bar[1], 0);
-        if (!ok) fail(flags, &bar[1], 0);
+        if (!ok) fail(flags, bar, true);
     }
     if (ok) {
         tc_fence_after();
@@ -445,7 +461,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_bwd(TcLayer nets, const 
     using L = BwdSmem<SPLIT>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::BAR);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 3);
     const int tid = threadIdx.x, warp = tid >> 5, r = tid;
     const Tile tl = tiles[blockIdx.x];
     if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list (before any TMEM allocation)
@@ -475,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_bwd(TcLayer nets, const 
     handoff();
     bool ok = wait_all(&bar[0], 0);
     if (!ok) {
-        fail(flags, &bar[0], 0);
+        fail(flags, bar, false);
     } else {
         if (tid == 0) {  // ybar W3^T
             issue<SPLIT>(tmem + 128, smem + L::Y, smem + L::YLO, 16, smem + L::WB + kB_W3p, smem + L::WBLO + kB_W3p,
@@ -483,7 +499,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_bwd(TcLayer nets, const 
             mma_commit(&bar[1]);
         }
         ok = wait_all(&bar[1], 0);
-        if (!ok) fail(flags, &bar[1], 0);
+        if (!ok) fail(flags, bar, true);
     }
     if (ok) {
         tc_fence_after();
@@ -496,7 +512,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_bwd(TcLayer nets, const 
         }
         load64(drow, sd);  // SiLU'(z1), while the product runs
         ok = wait_all(&bar[1], 1);
-        if (!ok) fail(flags, &bar[1], 1);
+        if (!ok) fail(flags, bar, true);
     }
     if (ok) {
         tc_fence_after();
@@ -508,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc_bwd(TcLayer nets, const 
             mma_commit(&bar[1]);
         }
         ok = wait_all(&bar[1], 0);
-        if (!ok) fail(flags, &bar[1], 0);
+        if (!ok) fail(flags, bar, true);
     }
     if (ok) {
         tc_fence_after();
@@ -653,7 +669,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_f8_fwd(TcLayer nets, const 
     extern __shared__ __align__(1024) uint8_t smem[];
     float* red = reinterpret_cast<float*>(smem + L::RED);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::BAR);  // [0] weights, [1] MMA
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 3);
     const int tid = threadIdx.x, warp = tid >> 5, r = tid;
     const Tile tl = tiles[blockIdx.x];
     if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list (before any TMEM allocation)
@@ -671,14 +687,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_f8_fwd(TcLayer nets, const 
     bool ok = wait_all(&bar[0], 0);
     float sh = 1.f;
     if (!ok) {
-        fail(flags, &bar[0], 0);
+        fail(flags, bar, false);
     } else {
         if (tid == 0) {  // z1 = x W1
             issue8(tmem, smem + L::A, 64, smem + L::W + kF8_W1t, H1, 2);
             mma_commit(&bar[1]);
         }
         ok = wait_all(&bar[1], 0);
-        if (!ok) fail(flags, &bar[1], 0);
+        if (!ok) fail(flags, bar, true);
     }
     if (ok) {
         tc_fence_after();
@@ -692,7 +708,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_f8_fwd(TcLayer nets, const 
             mma_commit(&bar[1]);
         }
         ok = wait_all(&bar[1], 1);
-        if (!ok) fail(flags, &bar[1], 1);
+        if (!ok) fail(flags, bar, true);
     }
     if (ok) {
         tc_fence_after();
@@ -706,7 +722,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_f8_fwd(TcLayer nets, const 
             mma_commit(&bar[1]);
         }
         ok = wait_all(&bar[1], 0);
-        if (!ok) fail(flags, &bar[1], 0);
+        if (!ok) fail(flags, bar, true);
     }
     if (ok) {
         tc_fence_after();
@@ -739,7 +755,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_f8_bwd(TcLayer nets, const 
     extern __shared__ __align__(1024) uint8_t smem[];
     float* red = reinterpret_cast<float*>(smem + L::RED);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::BAR);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 3);
     const int tid = threadIdx.x, warp = tid >> 5, r = tid;
     const Tile tl = tiles[blockIdx.x];
     if (tl.nrows <= 0) return;  // padding entry of a fixed-size tile list (before any TMEM allocation)
@@ -768,7 +784,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_f8_bwd(TcLayer nets, const 
     float sh1 = 1.f, sg = 1.f;
     bool ok = wait_all(&bar[0], 0);
     if (!ok) {
-        fail(flags, &bar[0], 0);
+        fail(flags, bar, false);
     } else {
         if (tid == 0) {
             issue8(tmem, smem + L::A, 64, smem + L::WF + kF8_W1t, H1, 2);         // z1
@@ -776,7 +792,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_f8_bwd(TcLayer nets, const 
             mma_commit(&bar[1]);
         }
         ok = wait_all(&bar[1], 0);
-        if (!ok) fail(flags, &bar[1], 0);
+        if (!ok) fail(flags, bar, true);
     }
     if (ok) {
         tc_fence_after();
@@ -790,7 +806,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_f8_bwd(TcLayer nets, const 
             mma_commit(&bar[1]);
         }
         ok = wait_all(&bar[1], 1);
-        if (!ok) fail(flags, &bar[1], 1);
+        if (!ok) fail(flags, bar, true);
     }
     if (ok) {
         tc_fence_after();
@@ -806,7 +822,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_f8_bwd(TcLayer nets, const 
             mma_commit(&bar[1]);
         }
         ok = wait_all(&bar[1], 0);
-        if (!ok) fail(flags, &bar[1], 0);
+        if (!ok) fail(flags, bar, true);
     }
     if (ok) {
         tc_fence_after();
@@ -822,7 +838,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_f8_bwd(TcLayer nets, const 
             mma_commit(&bar[1]);
         }
         ok = wait_all(&bar[1], 1);
-        if (!ok) fail(flags, &bar[1], 1);
+        if (!ok) fail(flags, bar, true);
     }
     if (ok) {
         tc_fence_after();
@@ -839,6 +855,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_f8_bwd(TcLayer nets, const 
             }
         }
     }
+    teardown(tmem);
+}
+
+// The bounded-wait exit with nothing in flight: allocate TMEM, wait `polls` times on
+// an mbarrier that nothing arrives on, then fail() (flag, drain, release) as the
+// network kernels do when a wait runs out.
+__global__ void __launch_bounds__(kThreads, 1) k_wait_selftest(int* __restrict__ flags, long long polls) {
+    __shared__ __align__(8) uint64_t bar[4];
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 3);
+    const uint32_t tmem = setup(tslot, bar);
+    if (!wait_all(&bar[1], 0, polls)) fail(flags, bar, true);
     teardown(tmem);
 }
 
@@ -914,6 +941,11 @@ cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTab
     else
         (split ? fwd_launch<NPHI, true> : fwd_launch<NPHI, false>)(s, nt, l, nl->tiles128, rho, out, out_stride,
                                                                     flags, gh, dsave);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(cudaStream_t s, int* flags, long long polls) {
+    k_wait_selftest<<<1, kThreads, 0, s>>>(flags, polls);
     return cudaGetLastError();
 }
 

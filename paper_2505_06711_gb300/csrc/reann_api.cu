@@ -483,14 +483,26 @@ int enqueue_flags_readback(reann_ctx* ctx) {
 int flags_status(reann_ctx* ctx) {
     REANN_CUDA_TRY(ctx, cudaGetLastError());
     const int geom = ctx->h_flags[FLAG_GEOM], cap = ctx->h_flags[FLAG_NBR_OVERFLOW] | ctx->h_flags[FLAG_GHOST_OVERFLOW];
-    const int timeout = ctx->h_flags[FLAG_TIMEOUT];
+    const int timeout = ctx->h_flags[FLAG_TIMEOUT], drain = ctx->h_flags[FLAG_TIMEOUT_DRAIN];
     if (geom) return set_error(ctx, REANN_E_GEOM, "coincident or non-finite atoms in an evaluation");
     if (cap) return set_error(ctx, REANN_E_CAPACITY, "neighbour or ghost capacity exceeded");
+    if (drain)
+        return set_error(ctx, REANN_E_TIMEOUT,
+                         "a bounded device wait ran out and the kernel's own tensor-core work or copy did not "
+                         "complete either: results are invalid and the device state is suspect");
     if (timeout) return set_error(ctx, REANN_E_TIMEOUT, "a bounded device wait ran out (tensor-core network)");
     return REANN_OK;
 }
 
 }  // namespace
+
+extern "C" int reann_ctx_wait_selftest(reann_ctx* ctx, int64_t polls) {
+    if (!ctx) return REANN_E_ARG;
+    if (polls < 1 || polls > (int64_t(1) << 26))
+        return set_error(ctx, REANN_E_ARG, "polls must be in [1, 2^26]");
+    REANN_CUDA_TRY(ctx, launch_wait_selftest(ctx->stream, ctx->d_flags, (long long)polls));
+    return REANN_OK;
+}
 
 extern "C" int reann_ctx_check(reann_ctx* ctx) {
     if (!ctx) return REANN_E_ARG;

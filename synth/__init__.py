@@ -26,4 +26,4 @@ from .structures import (  # noqa: F401
     SPECIES_HEA,
     MASS_AMU,
 )
-from .model import ModelSpec, make_model, param_layout  # noqa: F401
+from .model import ModelSpec, make_model, param_layout, write_model_file  # noqa: F401

@@ -203,3 +203,29 @@ def make_model(
             put((t, e, "W3"), w3)
             put((t, e, "b3"), np.zeros(out))
     return ModelSpec(n_elem, T, n_phi, l_max, n_orb, h1, h2, float(r_c), float(alpha), p.astype(np.float32), pairs)
+
+
+MODEL_FILE_MAGIC = b"REANNMDL"
+MODEL_FILE_VERSION = 1
+
+
+def write_model_file(spec: ModelSpec, path) -> None:
+    """Write ``spec`` in the model-file layout that ``reann_model_load`` reads.
+
+    Little-endian: the 8-byte magic, uint32 version, int32 n_elem, T, n_phi,
+    l_max, n_orb, h1, h2, feature_pairs, uint32 0, float64 r_c, alpha, int64
+    n_params, then the float32 parameters.  Layout only: no REANN arithmetic.
+    """
+    params = np.ascontiguousarray(spec.params, dtype="<f4")
+    head = np.array(
+        [spec.n_elem, spec.T, spec.n_phi, spec.l_max, spec.n_orb, spec.h1, spec.h2, int(bool(spec.pairs))],
+        dtype="<i4",
+    )
+    with open(path, "wb") as f:
+        f.write(MODEL_FILE_MAGIC)
+        f.write(np.array([MODEL_FILE_VERSION], dtype="<u4").tobytes())
+        f.write(head.tobytes())
+        f.write(np.array([0], dtype="<u4").tobytes())
+        f.write(np.array([spec.r_c, spec.alpha], dtype="<f8").tobytes())
+        f.write(np.array([params.size], dtype="<i8").tobytes())
+        f.write(params.tobytes())

@@ -165,3 +165,73 @@ def test_empty_and_oversized_inputs_are_refused_on_the_host():
     assert_parity({"energy": float(sy.energy.item()), "forces": sy.forces.double().cpu().numpy()},
                   ref, s.n_atoms)
     sy.close()
+
+
+def test_model_file_evaluates_like_created_model(tmp_path):
+    """A model written to a file and loaded with reann_model_load evaluates bit for bit
+    like the same parameters given to reann_model_create."""
+    import torch
+
+    from paper_2505_06711_gb300 import binding
+    from synth import write_model_file
+
+    spec = make_model(T=3)
+    s = water_box(64, seed=11)
+    path = tmp_path / "water.reann"
+    write_model_file(spec, path)
+    model = binding.reann_model_load(path)
+    ctx = binding.reann_ctx_create(model)
+    binding.reann_model_free(model)
+    pos = torch.as_tensor(s.pos, device="cuda").contiguous()
+    species = torch.as_tensor(s.species, dtype=torch.int32, device="cuda").contiguous()
+    nl = binding.reann_build_nlist(ctx, pos, species, s.cell, spec.r_c, 1.0)
+    energy = torch.zeros(1, dtype=torch.float64, device="cuda")
+    forces = torch.zeros((s.n_atoms, 3), dtype=torch.float32, device="cuda")
+    binding.reann_energy_forces(ctx, nl, pos, spec.T, energy, forces, None)
+    binding.reann_ctx_check(ctx)
+    torch.cuda.synchronize()
+    e_file, f_file = float(energy.item()), forces.cpu().numpy().copy()
+    binding.reann_nlist_free(nl)
+    binding.reann_ctx_free(ctx)
+    sy = potential(spec).system(s.pos, s.species, s.cell, skin=1.0)
+    sy.evaluate()
+    sy.check()
+    torch.cuda.synchronize()
+    assert e_file == float(sy.energy.item())
+    assert np.array_equal(f_file, sy.forces.cpu().numpy())
+    sy.close()
+
+
+def test_bounded_wait_runs_out_and_context_recovers():
+    """Failure detection without a fault: a tensor-core CTA waits on an mbarrier that
+    nothing arrives on (no copy or MMA in flight), gives up after a few thousand polls,
+    drains and frees its tensor memory; reann_ctx_check reports REANN_E_TIMEOUT once,
+    and the same context then evaluates exactly as before."""
+    import torch
+
+    from paper_2505_06711_gb300 import Potential, ReannError, binding
+
+    spec = make_model(T=3)
+    s = water_box(64, seed=5)
+    pot = Potential(spec, precision=binding.REANN_MLP_BF16)
+    sy = pot.system(s.pos, s.species, s.cell, skin=1.0)
+    sy.evaluate()
+    sy.check()
+    torch.cuda.synchronize()
+    e0, f0 = float(sy.energy.item()), sy.forces.cpu().numpy().copy()
+    binding.reann_ctx_wait_selftest(pot.ctx, 4096)
+    with pytest.raises(ReannError) as err:
+        sy.check()
+    assert err.value.code == binding.REANN_E_TIMEOUT
+    assert "suspect" not in str(err.value)  # the drain after the timeout completed
+    sy.check()  # the flag was cleared by the previous check
+    with pytest.raises(ReannError):
+        binding.reann_ctx_wait_selftest(pot.ctx, 0)
+    sy.forces.zero_()
+    sy.evaluate()
+    sy.check()
+    torch.cuda.synchronize()
+    assert float(sy.energy.item()) == e0
+    assert np.array_equal(sy.forces.cpu().numpy(), f0)
+    sy.close()
+    pot.close()

@@ -1,18 +1,22 @@
 """The energy sum that allocates nothing (reann_energy_sum_noalloc).
 
-Callers that cannot allocate device memory when they need a total energy
-(code running under CUDA graph capture in the global mode, where cudaMalloc is
-not allowed, or a force back-end inside an MD engine that owns the memory
-budget) sum per-atom energies they already hold with this entry point, which
-uses a fixed scratch array compiled into the library.  These tests call it
-through the C ABI and compare it with the energy reann_energy_forces returns
-for the same atom energies, twice in a row with different sizes (the scratch
-is shared between calls), and check that oversized inputs are refused.
+Callers that must not allocate device memory when they need a total energy (a
+force back-end inside an MD engine that owns the memory budget, or a
+latency-critical callback that avoids cudaMalloc because it can synchronise
+the device) sum per-atom energies they already hold with this entry point,
+which uses a fixed scratch array compiled into the library.  These tests call
+it through the C ABI and compare it with the energy reann_energy_forces returns
+for the same atom energies (the same FP64 sum grouped differently, so within
+the FP32 path's energy tolerance) and with an exact FP64 sum on the host,
+twice in a row with different sizes (the scratch is shared between calls), and
+check that oversized inputs are refused.
 
 The file name makes pytest collect it last.
 """
 
 from __future__ import annotations
+
+import math
 
 import pytest
 
@@ -51,6 +55,10 @@ def test_noalloc_sum_matches_energy_forces_twice():
     got = out.cpu().tolist()
     assert abs(got[0] - e_big) <= E_TOL_PER_ATOM * big.n
     assert abs(got[1] - e_small) <= E_TOL_PER_ATOM * small.n
+    # both are FP64 sums of the same FP32 values: only the grouping differs
+    for sy, g in ((big, got[0]), (small, got[1])):
+        host = math.fsum(sy.atom_energy.double().cpu().tolist())
+        assert abs(g - host) <= 1e-12 * max(1.0, abs(host)) * sy.n ** 0.5
     big.close()
     small.close()
 
