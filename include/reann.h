@@ -57,12 +57,17 @@ extern "C" {
 #define REANN_E_TIMEOUT (-6)  /* a bounded device wait ran out                */
 #define REANN_E_CAPACITY (-7) /* a neighbour/ghost capacity was exceeded (rebuild) */
 
+/* Network precisions.  The tensor-core modes round, in every 128-atom tile of
+ * one element, only the deviations of a product's inputs from the tile's
+ * column means; the means' products, the output layer (64 -> 8 or 1) and the
+ * first reverse product are FP32, so the low precision never shifts every
+ * atom alike.  All modes accumulate in FP32.                                    */
 #define REANN_MLP_FP32 0   /* atomic networks in FP32 SIMT arithmetic                        */
-#define REANN_MLP_BF16 1   /* tcgen05 tensor cores, BF16 operands, FP32 accumulation         */
-#define REANN_MLP_BF16X3 2 /* tcgen05, every operand a BF16 hi + lo pair, 3 MMAs per K step,
-                              FP32 accumulation (about 16 significant bits per operand)      */
-#define REANN_MLP_FP8 3    /* tcgen05, FP8 E4M3 operands with one FP32 scale per weight
-                              matrix and per 128-row activation tile, FP32 accumulation     */
+#define REANN_MLP_BF16 1   /* tcgen05 tensor cores, BF16 operands                           */
+#define REANN_MLP_BF16X3 2 /* tcgen05, every operand a BF16 hi + lo pair, 3 MMAs per K step
+                              (about 16 significant bits per operand)                       */
+#define REANN_MLP_FP8 3    /* tcgen05, FP8 E4M3 operands; activation rows scaled by powers
+                              of two, weights per output unit by max |w| / 448              */
 
 typedef struct reann_model reann_model;
 typedef struct reann_ctx reann_ctx;
@@ -138,7 +143,11 @@ void reann_ctx_free(reann_ctx* ctx);
  * Precision of the atomic networks: REANN_MLP_FP32 (default), REANN_MLP_BF16,
  * REANN_MLP_BF16X3 or REANN_MLP_FP8 (the tensor-core modes for the 48-feature
  * models only).  The density and reverse-pass edge arithmetic stays FP32 and
- * the energy sum FP64 in every mode.  Errors: REANN_E_ARG.
+ * the energy sum FP64 in every mode.  The tensor-core modes round deviations
+ * from per-tile means, so their results depend (at rounding level) on which
+ * atoms share a 128-atom tile: a structure evaluated alone or in a serving
+ * pool gives the same bits, a decomposed list (other tiles) does not.
+ * Errors: REANN_E_ARG.
  */
 int reann_ctx_set_mlp_precision(reann_ctx* ctx, int precision);
 

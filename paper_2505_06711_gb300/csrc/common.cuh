@@ -214,21 +214,27 @@ struct Tile {
     int elem, row0, nrows, pad;
 };
 
-// BF16 weight images of one (layer, element) network for the tensor-core path,
-// 64 KiB: forward hi | forward lo | backward hi | backward lo, each 16 KiB in the
-// K-major core-matrix layout; forward = W1^T 64x48 | W2^T 64x64 | W3^T 16x64,
-// backward = W3 64x16 | W2 64x64 | W1 48x64; lo = BF16 rounding of w - hi.
+// Weights of one (layer, element) network for the tensor-core path.  B
+// operands (N rows of K, K-major core-matrix layout, see mlp_tc.cu):
+//   BF16  forward  W1^T (64 x 48) | W2^T (64 x 64)   14336 B, hi then lo (BF16
+//         backward W2   (64 x 64) | W1   (48 x 64)   rounding of w - hi) each
+//   FP8   forward  W1^T (64 x 64, K padded) | W2^T (64 x 64)     8192 B
+//         backward W2   (64 x 64)           | W1   (48 x 64)     7168 B
+// with every B row divided by its own scale max |w| / 448 (s8).  The FP32
+// copies serve the anchors and the FP32 output layer.
 struct TcImg {
-    const uint8_t* img;           // BF16 images (forward hi | lo | backward hi | lo)
-    const float *b1, *b2, *b3;
-    const uint8_t* img8;          // FP8 E4M3 images (forward | backward), kF8Img bytes
-    const float* s8;              // their per-matrix scales s(W1), s(W2), s(W3)
+    const uint8_t* wf;   // BF16 forward images (hi | lo)
+    const uint8_t* wb;   // BF16 backward images (hi | lo)
+    const uint8_t* wf8;  // FP8 forward image
+    const uint8_t* wb8;  // FP8 backward image
+    const float *W1, *W2, *W3, *W1t, *W2t, *b1, *b2, *b3;
+    const float* s8;     // FP8 B-row scales: forward W1^T (64), W2^T (64), backward W2 (64), W1 (48)
 };
-// FP8 image of one (layer, element): forward W1^T 64x64 | W2^T 64x64 | W3^T 16x64,
-// backward W3 64x32 | W2 64x64 | W1 48x64 (K padded to multiples of 32)
-constexpr uint32_t kF8Fwd = 64 * 64 + 64 * 64 + 16 * 64;
-constexpr uint32_t kF8Bwd = 64 * 32 + 64 * 64 + 48 * 64;
+constexpr uint32_t kBfImg = 14336;
+constexpr uint32_t kF8Fwd = 8192;
+constexpr uint32_t kF8Bwd = 7168;
 constexpr uint32_t kF8Img = kF8Fwd + kF8Bwd;
+constexpr int kF8Scales = 64 + 64 + 64 + 48;
 struct TcTable {
     TcImg img[8][MAX_ELEM];
 };
@@ -437,19 +443,20 @@ cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetT
                                double* epart = nullptr);
 // total energy from np partial sums, in a fixed order
 cudaError_t launch_energy_final(cudaStream_t s, const double* partial, int np, double* energy);
-// atomic networks, BF16 on tcgen05 tensor cores (mlp_tc.cu)
-// precision: REANN_MLP_BF16, REANN_MLP_BF16X3 or REANN_MLP_FP8
-// BF16 / BF16x3: the forward keeps SiLU'(z1), SiLU'(z2) of every row in dsave (128
-// floats per row, the FP32 path's layout) and the backward reads them (FP8 recomputes)
+// atomic networks on tcgen05 tensor cores (mlp_tc.cu), precision REANN_MLP_BF16,
+// REANN_MLP_BF16X3 or REANN_MLP_FP8.  The forward keeps SiLU'(z1), SiLU'(z2) of every
+// row in dsave (128 floats per row) and, for the energy network, writes one FP64
+// energy partial per 128-row tile to epart (nullable); the backward reads dsave, takes
+// the bbar step and writes the adjoint records (rec, ghost images through gh).
 cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
                               int precision, const float* rho, float* out, int out_stride, int* flags,
-                              GhostOut gh, float* dsave);
+                              GhostOut gh, float* dsave, double* epart);
+cudaError_t launch_mlp_bwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
+                              int precision, const float* dsave, const float* ybar, const float* Wc, const float* bck,
+                              const float* coef, float* rec, GhostOut gh, int* flags);
 // one CTA that waits, `polls` times, on an mbarrier nothing arrives on and then takes
 // the bounded-wait exit of the tensor-core kernels (reann_ctx_wait_selftest)
 cudaError_t launch_wait_selftest(cudaStream_t s, int* flags, long long polls);
-cudaError_t launch_mlp_bwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
-                              int precision, const float* rho, const float* dsave, const float* ybar, float* rhobar,
-                              int* flags);
 
 cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
                                const float* dsave, const float* ybar, float* rhobar, bool pairs = false,

@@ -4,8 +4,12 @@ The paper's scheme exchanges the ghost atoms' coefficients before every
 message-passing layer (and their gradients in the reverse pass), so a
 subdomain needs a halo of r_c (+ skin) whatever T is, and the result equals
 the undivided model's.  Here the rows keep the single-domain entry order and
-ghost slots hold exact copies, so forces must agree bit for bit and energies
-to the order of the FP64 sum.
+ghost slots hold exact copies, so with FP32 networks forces must agree bit for
+bit and energies to the order of the FP64 sum.  The tensor-core networks round
+each 128-row tile's deviations from its own column mean, and a rank-major
+layout groups the atoms into other tiles, so there the two lists agree within
+the precision's own bar (BF16: the mixed-precision bound; BF16X3: the FP32
+bar).
 """
 
 from __future__ import annotations
@@ -64,9 +68,16 @@ def test_decomposed_equals_single_domain(name, ranks, T, precision):
           f"ghosts={infok['ghosts'].tolist()} remote={infok['remote'].tolist()} dE={ek - e1:.3e}")
     assert len(infok["local"]) == k and int(infok["local"].sum()) == s.n_atoms
     assert (infok["remote"] > 0).all()  # every rank receives ghosts from another rank
-    assert np.array_equal(fk, f1), f"max|dF| = {np.abs(fk - f1).max():.3e}"
-    assert np.array_equal(ak, a1)
-    assert abs(ek - e1) <= 1e-12 * abs(e1)
+    if precision == 0:
+        assert np.array_equal(fk, f1), f"max|dF| = {np.abs(fk - f1).max():.3e}"
+        assert np.array_equal(ak, a1)
+        assert abs(ek - e1) <= 1e-12 * abs(e1)
+    elif precision == 1:  # BF16: within the mixed-precision bound of each other
+        assert abs(ek - e1) / s.n_atoms <= 1e-3
+        assert float(np.sqrt(np.mean((fk - f1) ** 2))) <= 20e-3
+    else:  # BF16X3: within the FP32 bar of each other
+        assert abs(ek - e1) / s.n_atoms <= 1e-6
+        assert float(np.abs(fk - f1).max()) <= 1e-4
 
 
 def test_halo_does_not_grow_with_T():

@@ -1,13 +1,13 @@
 """FP8 E4M3 atomic networks on tcgen05 (REANN_MLP_FP8) against the FP64 oracle.
 
-Every network GEMM (forward and the vector-Jacobian product) runs with E4M3
-operands and FP32 accumulation: weights scaled per matrix, activations per
-128-row tile, each by max |x| / 448.  E4M3 keeps 3 mantissa bits, so one
-rounding is off by up to 2^-4 relative; the bars below allow the resulting
-few-percent network error (the edge arithmetic and the energy sum stay FP32 /
-FP64).  The FP8 results must also be deterministic and land within the same
-bars at any tile position (single structure vs a serving pool is covered for
-the other precisions).
+Every network product but the output layer runs with E4M3 operands and FP32
+accumulation on anchored activations: each 128-row tile subtracts its column
+mean before rounding and adds the mean's product back in FP32 (an exact
+identity), activations are scaled per row and weights per output unit, each by
+max |.| / 448 (rounded up to a power of two for the activations).  The bar is the mixed-precision
+bound of the workload configuration: energy within 1 meV/atom and forces
+within 20 meV/A RMS of the oracle on every structure, crystals included.  The
+kernel arithmetic itself is pinned by the emulation test below.
 """
 
 from __future__ import annotations
@@ -16,20 +16,12 @@ import numpy as np
 import pytest
 
 import oracle
-from synth import fcc_box, make_model, water_box
+from synth import fcc_box, hea_box, make_model, water_box
 
 pytestmark = pytest.mark.gpu
 
-# FP8 bars (eV/atom, eV/A RMS and max).  E4M3 rounds each operand by up to
-# 2^-4 relative (BF16: 2^-9), so the FP8 network errors are about 32 x the
-# BF16 ones (< 1 meV/atom): measured 2 meV/atom and 12 meV/A RMS on water,
-# 11-26 meV/atom and 0.12-0.20 eV/A RMS on the Cu crystal, where every atom
-# feeds the networks nearly the same inputs and the roundings do not average
-# out.  The bars are twice the measured errors; the kernel arithmetic itself
-# is pinned by the emulation test below.
-E_TOL = 5e-2
-F_RMS_TOL = 0.4
-F_MAX_TOL = 2.0
+E_TOL = 1e-3  # eV/atom
+F_RMS_TOL = 20e-3  # eV/A
 
 
 def _eval(spec, s, precision):
@@ -51,32 +43,33 @@ def _eval(spec, s, precision):
 
 
 @pytest.mark.parametrize(
-    "name,make,T",
+    "name,make,T,n_elem",
     [
-        ("water192", lambda: water_box(64, seed=0), 3),
-        ("cu4000", lambda: fcc_box(10, seed=0), 3),
-        ("cu4000", lambda: fcc_box(10, seed=0), 5),
+        ("water192", lambda: water_box(64, seed=0), 3, 3),
+        ("water24576", lambda: water_box(8192, seed=0), 3, 3),
+        ("cu4000", lambda: fcc_box(10, seed=0), 3, 3),
+        ("cu4000", lambda: fcc_box(10, seed=0), 5, 3),
+        ("hea4000", lambda: hea_box(10, seed=0), 3, 8),
     ],
 )
-def test_fp8_networks_against_oracle(name, make, T):
+def test_fp8_networks_against_oracle(name, make, T, n_elem):
     from paper_2505_06711_gb300 import binding
 
-    spec = make_model(T=T)
+    spec = make_model(T=T, n_elem=n_elem)
     s = make()
     ref = oracle.energy_forces(spec, s.pos, s.species, s.cell)
     e8, f8 = _eval(spec, s, binding.REANN_MLP_FP8)
     e32, f32 = _eval(spec, s, binding.REANN_MLP_FP32)
     n = s.n_atoms
     de8 = abs(e8 - ref["energy"]) / n
-    df8 = f8 - ref["forces"]
-    rms8, max8 = float(np.sqrt(np.mean(df8 ** 2))), float(np.abs(df8).max())
+    rms8 = float(np.sqrt(np.mean((f8 - ref["forces"]) ** 2)))
     de32 = abs(e32 - ref["energy"]) / n
     rms32 = float(np.sqrt(np.mean((f32 - ref["forces"]) ** 2)))
-    print(f"[fp8] {name} T={T} |dE|/N={de8:.3e} F rms={rms8:.3e} max={max8:.3e}  "
+    print(f"[fp8] {name} T={T} |dE|/N={de8:.3e} F rms={rms8:.3e}  "
           f"(fp32: |dE|/N={de32:.3e} F rms={rms32:.3e}; |F| rms={np.sqrt(np.mean(ref['forces'] ** 2)):.3e})")
     assert np.isfinite(e8) and np.isfinite(f8).all()
-    assert de8 <= E_TOL and rms8 <= F_RMS_TOL and max8 <= F_MAX_TOL
-    assert de8 > de32  # the FP8 path really ran (it cannot match FP32)
+    assert de8 <= E_TOL and rms8 <= F_RMS_TOL
+    assert rms8 > rms32  # the FP8 path really ran (it cannot match FP32)
 
 
 def test_fp8_deterministic_and_momentum_free():
@@ -101,9 +94,11 @@ def e4m3(x):
     return np.sign(x) * np.minimum(np.round(a / q) * q, 448.0)
 
 
-def _scale(a):
-    m = np.float32(np.abs(a).max())
-    return np.float32(m / np.float32(448.0)) if m > 0 else np.float32(1.0)
+def _pow2_scale(amax):
+    """2^e with amax / 2^e in [224, 448) (1 for zero), per entry, as the kernel and the host pick them."""
+    amax = np.asarray(amax, np.float32)
+    _, e = np.frexp((amax * np.float32(1.0 / 448.0)).astype(np.float32))
+    return np.where(amax > 0, np.ldexp(np.float32(1.0), e), np.float32(1.0)).astype(np.float32)
 
 
 def _silu(z):
@@ -114,11 +109,14 @@ def _silu(z):
 def test_fp8_first_network_matches_emulation():
     """The first coefficient network in FP8 against numpy doing the same roundings.
 
-    In the 192-atom water box each element's rows form a single 128-row tile, so
-    every activation scale is the element's max |x| / 448; the weights use one
-    scale per matrix.  The kernel accumulates in FP32 (the emulation in FP64),
-    which can flip a rounding decision only where an operand sits on an E4M3
-    rounding boundary: nearly every output agrees to FP32 precision."""
+    In the 192-atom water box each element's rows form a single 128-row tile:
+    the anchor is the element's column mean, the deviations of each row are
+    divided by the row's power-of-two scale and rounded to E4M3, the weights by
+    max |w| / 448 per output unit, and the anchors' products and the output
+    layer are FP32.  The kernel accumulates in FP32 (the emulation in
+    FP64) and sums the means in another order, which can flip a rounding
+    decision only where an operand sits on an E4M3 rounding boundary: nearly
+    every output agrees to FP32 precision."""
     import torch
 
     from paper_2505_06711_gb300 import Potential, binding
@@ -147,21 +145,25 @@ def test_fp8_first_network_matches_emulation():
         pot.close()
     species = np.asarray(s.species)
     worst = []
+
+    def product(x, w):
+        """(x - mean) rounded per row, w rounded per output column, the mean's product in FP32."""
+        xb = x.mean(axis=0, dtype=np.float64).astype(np.float32)
+        d = (x - xb).astype(np.float32)
+        sr = _pow2_scale(np.abs(d).max(axis=1))
+        sc = (np.abs(w).max(axis=0).astype(np.float32) / np.float32(448.0)).astype(np.float32)
+        qd = e4m3(d / sr[:, None])
+        qw = e4m3(w / sc[None, :])
+        return ((qd @ qw) * sr[:, None] * sc[None, :]).astype(np.float32) + (xb.astype(np.float64) @ w).astype(np.float32)
+
     for e in np.unique(species):
         rows = species == e
         assert rows.sum() <= 128  # one tile per element
         W1, b1, W2, b2, W3, b3 = (blk(0, e, k) for k in ("W1", "b1", "W2", "b2", "W3", "b3"))
-        s1, s2, s3 = _scale(W1), _scale(W2), _scale(W3)
-        q1, q2, q3 = (e4m3((w / sc).astype(np.float32)) for w, sc in ((W1, s1), (W2, s2), (W3, s3)))
         x = rho0[rows].astype(np.float32)
-        sx = _scale(x)
-        z1 = (e4m3(x * (np.float32(1.0) / sx)) @ q1).astype(np.float32) * np.float32(sx * s1) + b1
-        h1 = _silu(z1)
-        sh1 = _scale(h1)
-        z2 = (e4m3(h1 * (np.float32(1.0) / sh1)) @ q2).astype(np.float32) * np.float32(sh1 * s2) + b2
-        h2 = _silu(z2)
-        sh2 = _scale(h2)
-        y = (e4m3(h2 * (np.float32(1.0) / sh2)) @ q3).astype(np.float32) * np.float32(sh2 * s3) + b3
+        h1 = _silu(product(x, W1) + b1)
+        h2 = _silu(product(h1, W2) + b2)
+        y = (h2.astype(np.float64) @ W3 + b3).astype(np.float32)
         rel = np.abs(c1[rows] - y) / (np.abs(y).max() + 1e-30)
         worst.append(rel)
         print(f"[fp8 emulation] element {e}: rows {rows.sum()}, median {np.median(rel):.2e}, "
