@@ -137,3 +137,40 @@ def test_config1_water_24576_full_parity():
     ref = oracle.energy_forces(spec, s.pos, s.species, s.cell)
     de, df = assert_parity(g, ref, s.n_atoms)
     g["system"].close()
+
+
+def _keys(i, j, sh, n):
+    """(i, j, image shift) triples as sorted int64 keys (shifts within +-8)."""
+    assert np.abs(sh).max() <= 8
+    k = (i.astype(np.int64) * n + j.astype(np.int64)) * 17
+    k = ((k + sh[:, 0] + 8) * 17 + sh[:, 1] + 8) * 17 + sh[:, 2] + 8
+    return np.sort(k)
+
+
+@pytest.mark.parametrize("name", ["water24576", "cu4000"])
+def test_neighbor_sets_bit_exact_full_size(name):
+    """The r_c + skin list at the bench's size (24,576-atom water box) and on the
+    4,000-atom Cu crystal equals the oracle's brute-force list as a set, including
+    the r_c .. r_c + skin shell that the FP32 pre-test with its margin decides;
+    then again after a device rebuild at displaced positions."""
+    import torch
+
+    s = water_box(8192, seed=0) if name == "water24576" else fcc_box(10, seed=0)
+    spec = make_model(T=3)
+    pot = potential(spec)
+    sy = pot.system(s.pos, s.species, s.cell, skin=1.0)
+    for step in range(2):
+        pos = s.pos if step == 0 else s.pos + np.random.default_rng(5).normal(0, 0.2, s.pos.shape)
+        if step == 1:
+            p = torch.as_tensor(pos, device="cuda").contiguous()
+            sy.rebuild(p)
+            sy.check()
+        gi, gj, gs = sy.neighbors()
+        oi, oj, osh = oracle.neighbors(pos, s.cell, spec.r_c + 1.0)
+        d_skin = np.linalg.norm(pos[oj] + osh @ s.cell - pos[oi], axis=1)
+        n_shell = int((d_skin >= spec.r_c).sum())
+        print(f"[nbr] {name} step {step}: {len(oi)} entries, {n_shell} in the r_c .. r_c + skin shell")
+        assert n_shell > 0
+        assert len(gi) == len(oi)
+        assert np.array_equal(_keys(gi, gj, gs, s.n_atoms), _keys(oi, oj, osh, s.n_atoms))
+    sy.close()
