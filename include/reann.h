@@ -340,9 +340,16 @@ int reann_energy_forces_host(reann_ctx* ctx, reann_nlist* nl, const double* pos,
  *                       rows [offset, offset + n) of each launched slot in its
  *                       caller order, the last row is scratch).  `slots`
  *                       (host, max_structures, nullable) and *count receive the
- *                       launched slots.  The sequence is captured as a CUDA
- *                       graph on the first launch (per precision and output
- *                       pointers) and replayed afterwards.  Asynchronous: the
+ *                       launched slots.  The launch covers only the pool's
+ *                       rows and ghost slots below the launched structures'
+ *                       highest ones, rounded up to a size class (the pool's
+ *                       capacity divided by 1, 2, 4, ... 128, at least 2,048
+ *                       rows), so its cost follows the work, not the pool's
+ *                       size.  Every class is captured as a CUDA graph on the
+ *                       first launch (per precision and output pointers; that
+ *                       launch itself runs directly) and replayed afterwards;
+ *                       submissions take the lowest free ranges, which keeps
+ *                       the classes small.  Asynchronous: the
  *                       context stream waits for it.  A slot is evaluated
  *                       once; later launches leave its energy entry and force
  *                       rows untouched until it is released.

@@ -272,6 +272,12 @@ struct reann_model {
 
 struct reann_nlist {
     int64_t n = 0, g = 0, g_cap = 0;  // atoms, ghosts, ghost capacity
+    // Bounds of the work an evaluation launches for (a serving pool sets them per launch
+    // to the rows and ghost slots in use, rounded up to a size class; -1: all): owned rows
+    // [0, n_rows), ghost slots [n, n + g_rows), network tiles [0, tiles_active) and
+    // [0, tiles128_active) of the tile lists.
+    int64_t n_rows = -1, g_rows = -1;
+    int64_t tiles_active = -1, tiles128_active = -1;
     int stride = 0;                   // neighbour row capacity
     int max_count = 0;                // longest row found by the first build
     int n_elem = 0, T = 0;
@@ -372,6 +378,16 @@ struct reann_ctx {
 };
 
 namespace reann {
+
+// the launch bounds of an evaluation of nl (see reann_nlist::n_rows)
+inline int64_t rows_of(const reann_nlist* nl) { return nl->n_rows >= 0 ? nl->n_rows : nl->n; }
+inline int64_t ghost_rows_of(const reann_nlist* nl) { return nl->g_rows >= 0 ? nl->g_rows : nl->g_cap; }
+inline int64_t tiles_of(const reann_nlist* nl) {
+    return nl->tiles_active >= 0 ? nl->tiles_active : (int64_t)nl->tiles_h.size();
+}
+inline int64_t tiles128_of(const reann_nlist* nl) {
+    return nl->tiles128_active >= 0 ? nl->tiles128_active : (int64_t)nl->tiles128_h.size();
+}
 
 int set_error(reann_ctx* ctx, int code, const std::string& msg);
 

@@ -604,12 +604,20 @@ __device__ __forceinline__ int64_t ghosts_in_use(const int32_t* g_count, int64_t
     return g < g_cap ? g : g_cap;
 }
 
-__global__ void k_init_coef(int64_t n, const int32_t* __restrict__ g_count, int64_t g_cap,
-                            const int32_t* __restrict__ species, const int32_t* __restrict__ owner,
+// first-layer coefficients c0 of owned rows [0, n_rows) and ghost slots n + [0, g_rows)
+__global__ void k_init_coef(int64_t n, int64_t n_rows, int64_t g_rows, const int32_t* __restrict__ g_count,
+                            int64_t g_cap, const int32_t* __restrict__ species, const int32_t* __restrict__ owner,
                             const float* __restrict__ c0, float* __restrict__ coef) {
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n + ghosts_in_use(g_count, g_cap)) return;
-    const int64_t o = s < n ? s : owner[s - n];
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t s, o;
+    if (t < n_rows) {
+        s = o = t;
+    } else {
+        const int64_t gi = t - n_rows;
+        if (gi >= g_rows || gi >= ghosts_in_use(g_count, g_cap)) return;
+        s = n + gi;
+        o = owner[gi];
+    }
     const int e = species[o];
     const float4* src = reinterpret_cast<const float4*>(c0 + e * NPHI);
     float4* dst = reinterpret_cast<float4*>(coef + (size_t)s * NPHI);
@@ -717,17 +725,18 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 }  // namespace
 
 cudaError_t launch_init_coef(cudaStream_t s, const reann_nlist* nl, const float* c0) {
-    const int64_t total = nl->n + nl->g_cap;
-    k_init_coef<<<blocks_for(total, 256), 256, 0, s>>>(nl->n, ghost_count_ptr(nl), nl->g_cap, nl->species, nl->g_owner,
-                                                       c0, nl->coef);
+    const int64_t nr = rows_of(nl), gr = ghost_rows_of(nl);
+    if (nr + gr == 0) return cudaSuccess;
+    k_init_coef<<<blocks_for(nr + gr, 256), 256, 0, s>>>(nl->n, nr, gr, ghost_count_ptr(nl), nl->g_cap, nl->species,
+                                                         nl->g_owner, c0, nl->coef);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather_ghost_rows(cudaStream_t s, const reann_nlist* nl, float* base, int width) {
-    if (nl->g_cap == 0) return cudaSuccess;
+    const int64_t gr = ghost_rows_of(nl);
+    if (gr == 0) return cudaSuccess;
     const int w4 = width / 4;
-    k_gather_rows<<<blocks_for(nl->g_cap * w4, 256), 256, 0, s>>>(nl->n, ghost_count_ptr(nl), nl->g_cap, w4,
-                                                                  nl->g_owner, base);
+    k_gather_rows<<<blocks_for(gr * w4, 256), 256, 0, s>>>(nl->n, ghost_count_ptr(nl), gr, w4, nl->g_owner, base);
     return cudaGetLastError();
 }
 
@@ -762,22 +771,26 @@ cudaError_t launch_density_fwd(cudaStream_t s, const reann_nlist* nl, const Radi
                                float* rho, float* bck, bool pairs) {
     ensure_edge_attrs();
     const int64_t per_block = kWarps * kAtomsPerWarp;
-    const unsigned nb = blocks_for(nl->n, per_block);
+    const int64_t nr = rows_of(nl);
+    if (nr == 0) return cudaSuccess;
+    const unsigned nb = blocks_for(nr, per_block);
     if (pairs)
-        k_density_fwd<true><<<nb, kWarps * 32, 0, s>>>(nl->n, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi,
+        k_density_fwd<true><<<nb, kWarps * 32, 0, s>>>(nr, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi,
                                                        nl->pos_lo, coef, W, rho, bck);
     else
-        k_density_fwd<false><<<nb, kWarps * 32, 0, s>>>(nl->n, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi,
+        k_density_fwd<false><<<nb, kWarps * 32, 0, s>>>(nr, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi,
                                                         nl->pos_lo, coef, W, rho, bck);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bbar(cudaStream_t s, const reann_nlist* nl, const float* W, const float* bck, const float* rhobar,
                         const float* coef, float* rec, bool pairs, GhostOut gh) {
+    const int64_t nr = rows_of(nl);
+    if (nr == 0) return cudaSuccess;
     if (pairs)
-        k_bbar<true><<<blocks_for(nl->n, kBbarAtoms), 4 * kBbarAtoms, 0, s>>>(nl->n, W, bck, rhobar, coef, rec, gh);
+        k_bbar<true><<<blocks_for(nr, kBbarAtoms), 4 * kBbarAtoms, 0, s>>>(nr, W, bck, rhobar, coef, rec, gh);
     else
-        k_bbar<false><<<blocks_for(nl->n, kBbarAtoms), 4 * kBbarAtoms, 0, s>>>(nl->n, W, bck, rhobar, coef, rec, gh);
+        k_bbar<false><<<blocks_for(nr, kBbarAtoms), 4 * kBbarAtoms, 0, s>>>(nr, W, bck, rhobar, coef, rec, gh);
     return cudaGetLastError();
 }
 
@@ -801,9 +814,11 @@ cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radi
     (void)flags;
     ensure_edge_attrs();
     const int64_t per_block = kAdjWarps * kAdjGroups;
-    const unsigned nb = blocks_for(nl->n, per_block);
+    const int64_t nr = rows_of(nl);
+    if (nr == 0) return cudaSuccess;
+    const unsigned nb = blocks_for(nr, per_block);
 #define REANN_ADJ(C, V)                                                                                              \
-    k_density_adj8<C, V><<<nb, kAdjWarps * 32, 0, s>>>(nl->n, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi,     \
+    k_density_adj8<C, V><<<nb, kAdjWarps * 32, 0, s>>>(nr, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi,        \
                                                       nl->pos_lo, rec, cbar, grad, vir, out)
     if (want_cbar && vir)
         REANN_ADJ(true, true);

@@ -434,7 +434,7 @@ NetsOfLayer layer_nets(const NetTable& t, int layer) {
 cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
                                const float* rho, float* out, int out_stride, bool pairs, GhostOut gh, float* dsave,
                                double* epart) {
-    const int nt = (int)nl->tiles_h.size();
+    const int nt = (int)tiles_of(nl);
     if (nt == 0) return cudaSuccess;
     ensure_attrs();
     const NetsOfLayer ln = layer_nets(nets, t);
@@ -458,7 +458,7 @@ cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetT
 cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
                                const float* dsave, const float* ybar, float* rhobar, bool pairs, const float* Wt,
                                const float* bck, const float* coef, float* rec, GhostOut gh) {
-    const int nt = (int)nl->tiles_h.size();
+    const int nt = (int)tiles_of(nl);
     if (nt == 0) return cudaSuccess;
     ensure_attrs();
     const NetsOfLayer ln = layer_nets(nets, t);

@@ -933,7 +933,7 @@ void bwd_launch(cudaStream_t s, int nt, const TcLayer& l, const Tile* tiles, con
 cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
                               int precision, const float* rho, float* out, int out_stride, int* flags, GhostOut gh,
                               float* dsave, double* epart) {
-    const int nt = (int)nl->tiles128_h.size();
+    const int nt = (int)tiles128_of(nl);
     if (nt == 0) return cudaSuccess;
     if (!dsave) return cudaErrorInvalidValue;
     ensure_tc_attrs();
@@ -950,7 +950,7 @@ cudaError_t launch_mlp_fwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTab
 cudaError_t launch_mlp_bwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTable& nets, int t, bool energy,
                               int precision, const float* dsave, const float* ybar, const float* Wc, const float* bck,
                               const float* coef, float* rec, GhostOut gh, int* flags) {
-    const int nt = (int)nl->tiles128_h.size();
+    const int nt = (int)tiles128_of(nl);
     if (nt == 0) return cudaSuccess;
     if (!dsave) return cudaErrorInvalidValue;  // the backward reads the forward's SiLU' values
     ensure_tc_attrs();

@@ -740,8 +740,10 @@ cudaError_t launch_refresh_positions(cudaStream_t s, const reann_nlist* nl, cons
 }
 
 cudaError_t launch_live_edges(cudaStream_t s, const reann_nlist* nl, float rc2, int* flags) {
-    k_live<<<blocks_for(nl->n * 32, 256), 256, 0, s>>>(nl->n, nl->stride, rc2, nl->nbr, nl->nbr_cnt, nl->pos_hi,
-                                                       nl->pos_lo, nl->live, nl->live_cnt, flags);
+    const int64_t nr = rows_of(nl);
+    if (nr == 0) return cudaSuccess;
+    k_live<<<blocks_for(nr * 32, 256), 256, 0, s>>>(nr, nl->stride, rc2, nl->nbr, nl->nbr_cnt, nl->pos_hi, nl->pos_lo,
+                                                    nl->live, nl->live_cnt, flags);
     return cudaGetLastError();
 }
 

@@ -920,8 +920,8 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
             REANN_CUDA_TRY(ctx, launch_segment_energy(s, seg, nseg, nl->eps, energy));
         else  // the energy network summed its tiles (64-row FP32 tiles or 128-row tensor-core tiles)
             REANN_CUDA_TRY(ctx, launch_energy_final(s, nl->partial,
-                                                    (int)(ctx->precision == REANN_MLP_FP32 ? nl->tiles_h.size()
-                                                                                           : nl->tiles128_h.size()),
+                                                    (int)(ctx->precision == REANN_MLP_FP32 ? tiles_of(nl)
+                                                                                           : tiles128_of(nl)),
                                                     energy));
     }
     // reverse: Eqs. 3-5, one vector-Jacobian product per layer
@@ -1382,8 +1382,11 @@ struct reann_serve {
     cudaMemPool_t build_pool = nullptr;  // stream-ordered blocks of the per-submission lists
     cudaEvent_t staged = nullptr, done = nullptr, user_ready = nullptr;
     std::vector<std::pair<reann_nlist*, cudaEvent_t>> deferred;  // built lists freed once their pack has run
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    // one captured pass per size class k: owned rows [0, n >> k), ghost slots [0, g_cap >> k)
+    static constexpr int kClasses = 8;
+    static constexpr int64_t kMinRows = 2048;
+    cudaGraph_t graph[kClasses] = {};
+    cudaGraphExec_t exec[kClasses] = {};
     int graph_precision = -1;
     const void* graph_out[2] = {nullptr, nullptr};
 };
@@ -1421,8 +1424,10 @@ extern "C" void reann_serve_free(reann_serve* srv) {
     serve_reap(srv, true);
     if (srv->stream) cudaStreamSynchronize(srv->stream);
     if (srv->build_pool) cudaMemPoolDestroy(srv->build_pool);
-    if (srv->exec) cudaGraphExecDestroy(srv->exec);
-    if (srv->graph) cudaGraphDestroy(srv->graph);
+    for (int k = 0; k < reann_serve::kClasses; ++k) {
+        if (srv->exec[k]) cudaGraphExecDestroy(srv->exec[k]);
+        if (srv->graph[k]) cudaGraphDestroy(srv->graph[k]);
+    }
     free_nlist(srv->pool);
     if (srv->d_seg) cudaFree(srv->d_seg);
     if (srv->h_seg) cudaFreeHost(srv->h_seg);
@@ -1590,9 +1595,12 @@ extern "C" int reann_serve_launch(reann_serve* srv, double* energies, float* for
     REANN_CUDA_TRY(ctx, cudaEventSynchronize(srv->staged));
     size_t n64 = 0, n128 = 0;
     int nseg = 0;
+    int64_t hi = 0, ghi = 0;  // owned rows and ghost slots the launched structures occupy
     for (int k = 0; k < srv->max_slots; ++k) {
         ServeSlot& sl = srv->slots[k];
         if (!sl.used || !sl.pending) continue;
+        hi = std::max<int64_t>(hi, sl.ob + sl.n);
+        ghi = std::max<int64_t>(ghi, sl.gb + sl.g);
         for (const Tile& t : sl.t64) srv->h_t64[n64++] = t;
         for (const Tile& t : sl.t128) srv->h_t128[n128++] = t;
         srv->h_seg[nseg] = make_int4((int)sl.ob, (int)sl.n, k, 0);
@@ -1614,38 +1622,65 @@ extern "C" int reann_serve_launch(reann_serve* srv, double* energies, float* for
                                         cudaMemcpyHostToDevice, s));
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(srv->d_seg, srv->h_seg, sizeof(int4) * srv->max_slots, cudaMemcpyHostToDevice, s));
     REANN_CUDA_TRY(ctx, cudaEventRecord(srv->staged, s));
-    // one evaluation of the whole pool, captured once per (precision, outputs) and replayed
+    // One evaluation of the pool, sized to the work: size class k covers owned rows
+    // [0, n >> k) and ghost slots [0, g_cap >> k), the smallest class holding every
+    // launched structure (free and retired rows inside it have no neighbours).  Each
+    // class is captured once per (precision, outputs) and replayed.
+    int cls = 0, ncls = 1;
+    while (ncls < reann_serve::kClasses && (p->n >> ncls) >= reann_serve::kMinRows) ++ncls;
+    while (cls + 1 < ncls && (p->n >> (cls + 1)) >= hi && (p->g_cap >> (cls + 1)) >= ghi) ++cls;
+    const auto set_class = [&](int k) {
+        const int64_t rows = p->n >> k;
+        p->n_rows = rows;
+        p->g_rows = p->g_cap >> k;
+        // tiles of the launched structures: at most rows / tile + one partial tile per element and structure
+        const int64_t ms = std::min<int64_t>(srv->max_slots, rows) * p->n_elem + 1;
+        p->tiles_active = std::min<int64_t>((int64_t)p->tiles_h.size(), rows / MLP_TILE + ms);
+        p->tiles128_active = std::min<int64_t>((int64_t)p->tiles128_h.size(), rows / 128 + ms);
+    };
+    set_class(cls);
     cudaStream_t user = ctx->stream;
     const bool prof = ctx->prof_on;
     ctx->stream = s;
     ctx->prof_on = false;
     int rc = REANN_OK;
-    const bool same = srv->exec && srv->graph_precision == ctx->precision && srv->graph_out[0] == energies &&
-                      srv->graph_out[1] == forces;
-    if (!same) {
-        if (srv->exec) cudaGraphExecDestroy(srv->exec);
-        if (srv->graph) cudaGraphDestroy(srv->graph);
-        srv->exec = nullptr;
-        srv->graph = nullptr;
-        // one plain run first (sets kernel attributes outside capture), then capture the same sequence
+    if (srv->graph_precision != ctx->precision || srv->graph_out[0] != energies || srv->graph_out[1] != forces) {
+        for (int k = 0; k < reann_serve::kClasses; ++k) {  // another key: every class is captured again
+            if (srv->exec[k]) cudaGraphExecDestroy(srv->exec[k]);
+            if (srv->graph[k]) cudaGraphDestroy(srv->graph[k]);
+            srv->exec[k] = nullptr;
+            srv->graph[k] = nullptr;
+        }
+        srv->graph_precision = ctx->precision;
+        srv->graph_out[0] = energies;
+        srv->graph_out[1] = forces;
+    }
+    if (!srv->exec[cls]) {
+        // this launch runs directly (which also sets kernel attributes outside capture);
+        // then every size class is captured, so that no later launch pays for a capture
         rc = pool_pass(ctx, srv, energies, forces);
-        if (!rc && cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        for (int k = 0; k < ncls && !rc; ++k) {
+            if (srv->exec[k]) continue;
+            set_class(k);
+            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                rc = set_error(ctx, REANN_E_CUDA, "serving graph capture failed");
+                break;
+            }
             rc = pool_pass(ctx, srv, energies, forces);
             cudaGraph_t g = nullptr;
             const cudaError_t ec = cudaStreamEndCapture(s, &g);
-            if (!rc && ec == cudaSuccess && cudaGraphInstantiate(&srv->exec, g, 0) == cudaSuccess) {
-                srv->graph = g;
-                srv->graph_precision = ctx->precision;
-                srv->graph_out[0] = energies;
-                srv->graph_out[1] = forces;
+            if (!rc && ec == cudaSuccess && cudaGraphInstantiate(&srv->exec[k], g, 0) == cudaSuccess) {
+                srv->graph[k] = g;
             } else {
                 if (g) cudaGraphDestroy(g);
+                srv->exec[k] = nullptr;
                 if (!rc) rc = set_error(ctx, REANN_E_CUDA, "serving graph capture failed");
             }
         }
-    } else if (cudaGraphLaunch(srv->exec, s) != cudaSuccess) {
+    } else if (cudaGraphLaunch(srv->exec[cls], s) != cudaSuccess) {
         rc = set_error(ctx, REANN_E_CUDA, "serving graph launch failed");
     }
+    p->n_rows = p->g_rows = p->tiles_active = p->tiles128_active = -1;
     ctx->stream = user;
     ctx->prof_on = prof;
     REANN_CUDA_TRY(ctx, cudaEventRecord(srv->done, s));

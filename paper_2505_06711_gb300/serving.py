@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import gc
 import math
 import threading
 import time
@@ -157,6 +158,10 @@ def serve_stream(server: Server, requests: list[Request]):
                 cv.notify_all()
 
     threads = [threading.Thread(target=builder, args=(b,), daemon=True) for b in range(len(server.builds))]
+    # the cyclic garbage collector stays off while requests are in flight (a full pass over
+    # the stream's result arrays stalls every thread for tens of milliseconds)
+    gc_was_enabled = gc.isenabled()
+    gc.disable()
     for t in threads:
         t.start()
     in_flight = None  # (slots, event, {slot: request index})
@@ -219,6 +224,8 @@ def serve_stream(server: Server, requests: list[Request]):
             cv.notify_all()
         for t in threads:
             t.join()
+        if gc_was_enabled:
+            gc.enable()
     wall = time.perf_counter() - t0
     atoms = sum(r.n_atoms for r in requests)
     return results, {"wall_s": wall, "launches": launches, "mean_batch": float(np.mean(batch)) if batch else 0.0,
