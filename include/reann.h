@@ -215,7 +215,10 @@ void reann_nlist_free(reann_nlist* nl);
  * Repeated calls with the same arguments are replayed as one CUDA graph (the
  * first runs directly, the second is captured) on a library-owned stream
  * ordered after and before the context stream; with reann_ctx_profile on,
- * every call launches its kernels directly.
+ * every call launches its kernels directly.  Every 8th rebuild (counted on the
+ * device, MD rebuilds included) also re-sorts the atoms' internal order (by
+ * element and cell bin, for locality); the others keep the order of the last
+ * sort.  The list (pairs, ghosts) is the same either way.
  */
 int reann_nlist_rebuild(reann_ctx* ctx, reann_nlist* nl, const double* pos);
 

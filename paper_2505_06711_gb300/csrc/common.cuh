@@ -248,6 +248,7 @@ struct NlistScratch {
     int32_t* species_c = nullptr;              // caller-order species
     int32_t *ekey = nullptr, *ecounts = nullptr, *estart = nullptr, *eorder = nullptr;
     int32_t *scat = nullptr, *escat = nullptr;  // atomic-order scatter before the in-bucket ranking
+    int32_t* rb_state = nullptr;  // rebuilds since the last sort, sort gate, keep-order gate
     float4* p32 = nullptr;   // FP32 positions of owned + ghost slots for the pre-test
     float4* p32s = nullptr;  // the same in bin-sorted order, slot index in .w
 };

@@ -520,6 +520,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_fwd(TcLayer nets, const Tile
     const int64_t row = tl.row0 + r;
     const float inv_n = 1.f / (float)tl.nrows;
     const TcImg& w = nets.e[tl.elem];
+    int64_t g_lo = 0, g_hi = 0;  // the row's ghost images (loaded now, used by the output stage)
+    if (OUT > 1 && gh.goff && valid) {
+        g_lo = gh.goff[row];
+        g_hi = min((int64_t)gh.goff[row + 1], gh.gcap);
+    }
     const uint32_t tmem = setup(tslot, bar);
     if (tid == 0) {
         const uint32_t xb = (uint32_t)tl.nrows * NFEAT * 4;
@@ -546,28 +551,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_fwd(TcLayer nets, const Tile
     float sx = 1.f, sh = 1.f;
     float v[16], a[16];
     if (ok) {
-        // rho-bar: column means of the valid rows, 4 groups of 32 rows summed in a fixed order
-        if (tid < 4 * NFEAT) {
-            const int c = tid % NFEAT, g = tid / NFEAT;
-            float s = 0.f;
-            for (int rr = 32 * g; rr < 32 * g + 32 && rr < tl.nrows; ++rr) s += sX[rr * NFEAT + c];
-            par[F_PS + g * 64 + c] = s;
-        }
-        __syncthreads();
-        if (tid < NFEAT)
-            par[F_RB + tid] =
-                ((par[F_PS + tid] + par[F_PS + 64 + tid]) + (par[F_PS + 128 + tid] + par[F_PS + 192 + tid])) * inv_n;
-        __syncthreads();
-        // A0 = rho - rho-bar: columns [16 cq, 16 cq + 16); BF16 tiles have K = 48 (the
-        // fourth quarter writes nothing), E4M3 tiles K = 64 (48 + zeros)
-        float xb[16];
-        lds16(par + F_RB + c0, xb);
+        // this quarter row of rho (features [16 cq, 16 cq + 16); the fourth quarter and rows
+        // past the tile's end hold zeros), then rho-bar: the column means of the valid rows
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const float4 x = (valid && cq < 3) ? reinterpret_cast<const float4*>(sX + r * NFEAT + c0)[k]
                                                : make_float4(0.f, 0.f, 0.f, 0.f);
             v[4 * k] = x.x, v[4 * k + 1] = x.y, v[4 * k + 2] = x.z, v[4 * k + 3] = x.w;
         }
+        tile_mean64(v, par + F_PS, par + F_RB, q, c0, lane, inv_n);
+        // A0 = rho - rho-bar: BF16 tiles have K = 48 (the fourth quarter writes nothing),
+        // E4M3 tiles K = 64 (48 + zeros)
+        float xb[16];
+        lds16(par + F_RB + c0, xb);
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = (valid && cq < 3) ? v[i] - xb[i] : 0.f;
         if (P == P_FP8) {
@@ -693,9 +689,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_fwd(TcLayer nets, const Tile
             }
             const float2 cv = make_float2(c[0], c[1]);
             *reinterpret_cast<float2*>(out + (size_t)row * out_stride + 2 * cq) = cv;
-            if (gh.goff)  // the row's ghost images get the same coefficients (Fig. 4a)
-                for (int64_t g = gh.goff[row]; g < gh.goff[row + 1] && g < gh.gcap; ++g)
-                    *reinterpret_cast<float2*>(out + (size_t)(gh.base + g) * out_stride + 2 * cq) = cv;
+            for (int64_t g = g_lo; g < g_hi; ++g)  // the row's ghost images get the same coefficients (Fig. 4a)
+                *reinterpret_cast<float2*>(out + (size_t)(gh.base + g) * out_stride + 2 * cq) = cv;
         }
     }
     teardown(tmem);

@@ -8,7 +8,8 @@
 //
 // Build (all deterministic):
 //   1. wrap positions into the cell in FP64 and key every atom by
-//      (element, cell bin);
+//      (element, cell bin) -- on the first build and every 8th rebuild; the
+//      rebuilds in between keep the previous internal order (k_wrap_keep);
 //   2. counting sort by key -> internal order (element-major so the atomic
 //      networks see contiguous per-element tiles, spatially sorted inside an
 //      element so neighbour gathers stay local);
@@ -64,33 +65,20 @@ __device__ __forceinline__ int64_t ghosts_in_use(const int32_t* g_count, int64_t
 }
 
 // 1. wrap + key (caller order)
-__global__ void k_wrap_key(const int* __restrict__ gate, int64_t n, const double* __restrict__ pos, const int32_t* __restrict__ species, int n_elem,
-                           CellGeom g, double* __restrict__ xw, double* __restrict__ fw, int32_t* __restrict__ mw,
-                           int32_t* __restrict__ key, int32_t* __restrict__ counts, int* __restrict__ flags,
-                           double* __restrict__ ref) {
-    if (gate && *gate == 0) return;  // rebuild not needed this step
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double x[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
-    // the positions of this build, for the moved-by-more-than-skin/2 test
-    ref[3 * i] = x[0];
-    ref[3 * i + 1] = x[1];
-    ref[3 * i + 2] = x[2];
-    int sp = species[i];
-    bool bad = !(isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]));
-    if (sp < 0 || sp >= n_elem) {
-        atomicOr(&flags[FLAG_SPECIES], 1);
-        sp = 0;
-    }
+// Wrap one position into the cell in FP64 (fixed operation order): fractional
+// coordinates f = x . hinv, integer shift m = floor(f), wrapped Cartesian
+// x - m.H and fractional f - m; `bad` for a non-finite or absurd position.
+__device__ __forceinline__ void wrap_one(const CellGeom& g, const double x_in[3], double xw[3], double fw[3], int m[3],
+                                         bool& bad) {
+    double x[3] = {x_in[0], x_in[1], x_in[2]};
     double fr[3];
-    int m[3];
+    bad = !(isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]));
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         fr[k] = dadd(dadd(dmul(x[0], g.hinv[k]), dmul(x[1], g.hinv[3 + k])), dmul(x[2], g.hinv[6 + k]));
         if (!isfinite(fr[k]) || fabs(fr[k]) > 1e9) bad = true;
     }
     if (bad) {
-        atomicOr(&flags[FLAG_GEOM], 1);
 #pragma unroll
         for (int k = 0; k < 3; ++k) fr[k] = 0.0, x[k] = 0.0;
     }
@@ -98,14 +86,42 @@ __global__ void k_wrap_key(const int* __restrict__ gate, int64_t n, const double
     for (int k = 0; k < 3; ++k) m[k] = (int)floor(fr[k]);
     double s[3];
     shift_vec(g, m[0], m[1], m[2], s);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        xw[k] = dsub(x[k], s[k]);
+        fw[k] = dsub(fr[k], (double)m[k]);
+    }
+}
+
+__global__ void k_wrap_key(const int* __restrict__ gate, int64_t n, const double* __restrict__ pos, const int32_t* __restrict__ species, int n_elem,
+                           CellGeom g, double* __restrict__ xw, double* __restrict__ fw, int32_t* __restrict__ mw,
+                           int32_t* __restrict__ key, int32_t* __restrict__ counts, int* __restrict__ flags,
+                           double* __restrict__ ref) {
+    if (gate && *gate == 0) return;  // rebuild (or this rebuild's sort) not needed
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    // the positions of this build, for the moved-by-more-than-skin/2 test
+    ref[3 * i] = x[0];
+    ref[3 * i + 1] = x[1];
+    ref[3 * i + 2] = x[2];
+    int sp = species[i];
+    if (sp < 0 || sp >= n_elem) {
+        atomicOr(&flags[FLAG_SPECIES], 1);
+        sp = 0;
+    }
+    double xwi[3], f[3];
+    int m[3];
+    bool bad;
+    wrap_one(g, x, xwi, f, m, bad);
+    if (bad) atomicOr(&flags[FLAG_GEOM], 1);
     int b[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        xw[3 * i + k] = dsub(x[k], s[k]);
-        double f = dsub(fr[k], (double)m[k]);
-        fw[3 * i + k] = f;
+        xw[3 * i + k] = xwi[k];
+        fw[3 * i + k] = f[k];
         mw[3 * i + k] = m[k];
-        b[k] = clampi((int)floor(f * g.nb[k]), 0, g.nb[k] - 1);
+        b[k] = clampi((int)floor(f[k] * g.nb[k]), 0, g.nb[k] - 1);
     }
     int nbins = g.nb[0] * g.nb[1] * g.nb[2];
     const int k = sp * nbins + (b[0] * g.nb[1] + b[1]) * g.nb[2] + b[2];
@@ -277,6 +293,54 @@ __global__ void k_gather_internal(const int* __restrict__ gate, int64_t n, CellG
         cnt *= hi - lo + 1;
     }
     sp[i] = sp_c[c];
+    gcnt[i] = cnt - 1;
+}
+
+// Rebuilds between sorts: every kResortPeriod-th rebuild sorts the owned atoms
+// again; the others keep the internal order of the last sort, and only wrap the
+// new positions (straight into internal order) and count their ghost images.
+// The list itself (ghosts, extended bins, search) is rebuilt in full either way.
+// state[0] counts rebuilds since the last sort; state[1] gates the sort path and
+// state[2] the keep-order path for this rebuild (both 0 when it is gated off).
+constexpr int kResortPeriod = 8;
+
+__global__ void k_rebuild_gates(const int* __restrict__ gate, int* __restrict__ state) {
+    const bool run = !gate || *gate != 0;
+    const bool sort = run && state[0] >= kResortPeriod;
+    if (run) state[0] = sort ? 1 : state[0] + 1;
+    state[1] = sort ? 1 : 0;
+    state[2] = run && !sort ? 1 : 0;
+}
+
+// the keep-order path: wrap the caller-order positions of the internal atoms i
+// (the same arithmetic as k_wrap_key) and count their ghost images
+__global__ void k_wrap_keep(const int* __restrict__ gate, int64_t n, CellGeom g, const double* __restrict__ pos,
+                            const int32_t* __restrict__ perm, double* __restrict__ xw, double* __restrict__ fw,
+                            int32_t* __restrict__ mw, int32_t* __restrict__ gcnt, int* __restrict__ flags,
+                            double* __restrict__ ref) {
+    if (gate && *gate == 0) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t c = perm[i];
+    const double x[3] = {pos[3 * c], pos[3 * c + 1], pos[3 * c + 2]};
+    ref[3 * c] = x[0];
+    ref[3 * c + 1] = x[1];
+    ref[3 * c + 2] = x[2];
+    double xwi[3], f[3];
+    int m[3];
+    bool bad;
+    wrap_one(g, x, xwi, f, m, bad);
+    if (bad) atomicOr(&flags[FLAG_GEOM], 1);
+    int cnt = 1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        xw[3 * i + k] = xwi[k];
+        fw[3 * i + k] = f[k];
+        mw[3 * i + k] = m[k];
+        int lo, hi;
+        halo_interval(g, k, f[k], lo, hi);
+        cnt *= hi - lo + 1;
+    }
     gcnt[i] = cnt - 1;
 }
 
@@ -596,15 +660,20 @@ static int64_t ext_bins(const reann_nlist* nl) {
 }
 
 // steps 1-3a: wrap, sort, gather, ghost count + scan (goff[n] = ghost count on the device)
+// sort_gate: the sort path (nullptr: always); keep_gate: the keep-order path (nullptr:
+// never); gate: the rest of the rebuild (nullptr: always)
 static cudaError_t stage_sort_and_count(cudaStream_t s, reann_nlist* nl, const double* pos, int* flags,
-                                        const int* gate) {
+                                        const int* sort_gate, const int* keep_gate, const int* gate) {
     const int64_t n = nl->n;
     NlistScratch& w = nl->w;
-    k_wrap_key<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, pos, w.species_c, nl->n_elem, nl->geom, w.xw_c, w.fw_c, w.mw_c,
-                                                  w.key, w.counts, flags, nl->pos_ref);
-    counting_sort(s, gate, n, owned_keys(nl), w.key, w.counts, w.start, w.scat, nl->perm, owned_keys(nl));
-    k_gather_internal<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, nl->geom, nl->perm, w.xw_c, w.fw_c, w.mw_c, w.species_c,
-                                                         w.xw, w.fw, nl->wrapm, nl->species, w.gcnt);
+    k_wrap_key<<<blocks_for(n, 256), 256, 0, s>>>(sort_gate, n, pos, w.species_c, nl->n_elem, nl->geom, w.xw_c, w.fw_c,
+                                                  w.mw_c, w.key, w.counts, flags, nl->pos_ref);
+    counting_sort(s, sort_gate, n, owned_keys(nl), w.key, w.counts, w.start, w.scat, nl->perm, owned_keys(nl));
+    k_gather_internal<<<blocks_for(n, 256), 256, 0, s>>>(sort_gate, n, nl->geom, nl->perm, w.xw_c, w.fw_c, w.mw_c,
+                                                         w.species_c, w.xw, w.fw, nl->wrapm, nl->species, w.gcnt);
+    if (keep_gate)
+        k_wrap_keep<<<blocks_for(n, 256), 256, 0, s>>>(keep_gate, n, nl->geom, pos, nl->perm, w.xw, w.fw, nl->wrapm,
+                                                       w.gcnt, flags, nl->pos_ref);
     k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(gate, n, w.gcnt, w.goff, false);
     return cudaGetLastError();
 }
@@ -645,17 +714,23 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
     w.goff = dalloc<int32_t>(nl, n + 1);
     w.species_c = dalloc<int32_t>(nl, n);
     w.scat = dalloc<int32_t>(nl, n);
+    w.rb_state = dalloc<int32_t>(nl, 4);
     nl->perm = dalloc<int32_t>(nl, n);
     nl->species = dalloc<int32_t>(nl, n);
     nl->wrapm = dalloc<int32_t>(nl, 3 * n);
     nl->pos_ref = dalloc<double>(nl, 3 * n);
     if (!w.xw_c || !w.fw_c || !w.mw_c || !w.key || !w.counts || !w.start || !w.xw || !w.fw || !w.gcnt || !w.goff ||
-        !w.species_c || !w.scat || !nl->perm || !nl->species || !nl->wrapm || !nl->pos_ref)
+        !w.species_c || !w.scat || !nl->perm || !nl->species || !nl->wrapm || !nl->pos_ref || !w.rb_state)
         return set_error(ctx, REANN_E_NOMEM, "neighbour-list allocation failed");
+    {
+        const int32_t state0[4] = {1, 0, 0, 0};  // this build sorts; rebuilds count from 1
+        REANN_CUDA_TRY(ctx, cudaMemcpyAsync(w.rb_state, state0, sizeof(state0), cudaMemcpyHostToDevice, s));
+        REANN_CUDA_TRY(ctx, cudaStreamSynchronize(s));  // state0 lives on this stack frame
+    }
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(w.species_c, species, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     REANN_CUDA_TRY(ctx, cudaMemsetAsync(w.counts, 0, sizeof(int32_t) * nkeys, s));  // kept zero between sorts
     REANN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * NFLAGS, s));
-    REANN_CUDA_TRY(ctx, stage_sort_and_count(s, nl, pos, ctx->d_flags, nullptr));
+    REANN_CUDA_TRY(ctx, stage_sort_and_count(s, nl, pos, ctx->d_flags, nullptr, nullptr, nullptr));
     // sizes: element ranges of the internal order and the ghost count
     std::vector<int32_t> es(nl->n_elem + 1);
     const int64_t nbins = nkeys / nl->n_elem;
@@ -717,7 +792,8 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
 
 // gate == nullptr: always rebuild; otherwise every kernel returns at once unless *gate != 0
 cudaError_t launch_rebuild(cudaStream_t s, reann_nlist* nl, const double* pos, int* flags, const int* gate) {
-    cudaError_t e = stage_sort_and_count(s, nl, pos, flags, gate);
+    k_rebuild_gates<<<1, 1, 0, s>>>(gate, nl->w.rb_state);
+    cudaError_t e = stage_sort_and_count(s, nl, pos, flags, nl->w.rb_state + 1, nl->w.rb_state + 2, gate);
     if (e == cudaSuccess) e = stage_ghosts_and_bins(s, nl, flags, gate);
     if (e == cudaSuccess) e = stage_search(s, nl, flags, gate);
     return e;

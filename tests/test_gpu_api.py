@@ -235,3 +235,34 @@ def test_bounded_wait_runs_out_and_context_recovers():
     assert np.array_equal(sy.forces.cpu().numpy(), f0)
     sy.close()
     pot.close()
+
+
+def test_rebuilds_across_the_resort_period_match_oracle():
+    """Device rebuilds keep the internal atom order between full sorts (every 8th
+    rebuild sorts again); the list and the forces must not depend on which kind a
+    rebuild was.  Ten rebuilds of a drifting box: sets equal the oracle's after each,
+    forces within the FP32 bar after the last keep-order and the sort rebuild."""
+    import torch
+
+    s = water_box(256, seed=21)
+    spec = make_model(T=3)
+    pot = potential(spec)
+    sy = pot.system(s.pos, s.species, s.cell, skin=1.0)
+    rng = np.random.default_rng(22)
+    pos = s.pos.copy()
+    for k in range(1, 11):
+        pos = pos + rng.normal(0, 0.08, pos.shape)  # drifts well beyond the skin over the ten steps
+        p = torch.as_tensor(pos, device="cuda").contiguous()
+        sy.rebuild(p)
+        sy.check()
+        gi, gj, gs = sy.neighbors()
+        oi, oj, osh = oracle.neighbors(pos, s.cell, spec.r_c + 1.0)
+        assert _set(gi, gj, gs) == _set(oi, oj, osh), k
+        if k in (7, 8, 9):  # keep-order, sort, keep-order
+            sy.evaluate(p)
+            sy.check()
+            torch.cuda.synchronize()
+            ref = oracle.energy_forces(spec, pos, s.species, s.cell)
+            assert_parity({"energy": float(sy.energy.item()), "forces": sy.forces.double().cpu().numpy()},
+                          {"energy": ref["energy"], "forces": ref["forces"]}, s.n_atoms)
+    sy.close()

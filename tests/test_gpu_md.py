@@ -56,8 +56,11 @@ def test_one_step_is_velocity_verlet():
 def test_nve_conserves_energy_across_device_rebuilds():
     import torch
 
+    # dt 0.25 fs: the random model heats this box and drives molecules into close
+    # contacts, where the Verlet error of a single trajectory (~dt^2) dominates the
+    # drift statistic at 0.5 fs; rebuild errors would show as jumps at any dt
     s, spec, pot, sy, vel, mass = _setup(512, 2)
-    n_steps, dt = 2000, 0.5
+    n_steps, dt = 2000, 0.25
     e_pot, e_kin = sy.md(vel, mass, dt, n_steps)
     sy.check()
     torch.cuda.synchronize()
@@ -66,11 +69,16 @@ def test_nve_conserves_energy_across_device_rebuilds():
     assert rebuilds >= 1  # atoms moved beyond skin/2: the list was rebuilt on the device
     etot = ((e_pot + e_kin) / s.n_atoms).cpu().numpy()
     t_ps = np.arange(1, n_steps + 1) * dt * 1e-3
-    slope = np.polyfit(t_ps, etot, 1)[0]  # eV/atom/ps
+    slope, icpt = np.polyfit(t_ps, etot, 1)  # eV/atom/ps
+    fluct = float((etot - (slope * t_ps + icpt)).std())  # about the linear drift
     print(f"[md] rebuilds={rebuilds} drift={slope * 1e3:.4f} meV/atom/ps "
-          f"fluct={etot.std() * 1e3:.4f} meV/atom ekin/N={e_kin[-1].item() / s.n_atoms:.4f}")
+          f"fluct={fluct * 1e3:.4f} meV/atom max step {np.abs(np.diff(etot)).max() * 1e3:.4f} meV/atom "
+          f"ekin/N={e_kin[-1].item() / s.n_atoms:.4f}")
     assert abs(slope) < 1e-3  # |drift| < 1 meV/atom/ps
-    assert etot.std() < 2e-4
+    assert fluct < 2e-4
+    # no jump where the list was rebuilt: the largest step-to-step change of E_tot is
+    # of the size of the ordinary Verlet fluctuation
+    assert np.abs(np.diff(etot)).max() < 2e-4
     # the trajectory's last state agrees with a fresh build at the final positions
     ref = oracle.energy_forces(spec, sy.pos.cpu().numpy(), s.species, s.cell)
     assert abs(e_pot[-1].item() - ref["energy"]) / s.n_atoms < 1e-6
