@@ -533,13 +533,15 @@ def measured_peaks() -> tuple[float, str]:
 
 
 def launches_per_step(T: int) -> int:
-    """Library kernels per step (FP32 networks, single-domain list): rebuild 11
-    (wrap + keys + histogram, 2 x 3 sort kernels (scan, scatter, rank), gather,
-    scan, ghosts + extended keys + histogram, search), evaluation 2 (positions
-    with c0, live edges) + 2T forward (density, network; the energy network
-    also sums its tiles) + 1 (total energy) + 2T reverse (network with bbar,
-    density adjoint; the last one writes forces and atomic energies)."""
-    return 11 + 2 + 2 * T + 1 + 2 * T
+    """Library kernel launches per step (single-domain list, any network precision):
+    rebuild 13 (sort-or-keep gate; wrap + keys + histogram, 3 sort kernels (scan,
+    scatter, rank) and the gather, which return at once on rebuilds that keep the
+    atom order; the keep-order wrap; ghost-count scan; ghosts + extended keys +
+    histogram, 3 sort kernels, search), evaluation 2 (positions with c0, live
+    edges) + 2T forward (density, network; the energy network also sums its
+    tiles) + 1 (total energy) + 2T reverse (network with bbar, density adjoint;
+    the last one writes forces and atomic energies)."""
+    return 13 + 2 + 2 * T + 1 + 2 * T
 
 
 def cpu_baseline(structure, spec):
