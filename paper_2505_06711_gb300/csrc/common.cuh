@@ -457,7 +457,7 @@ cudaError_t launch_unpermute_rows(cudaStream_t s, const reann_nlist* nl, const f
 // epart (energy network, optional): one FP64 energy partial sum per tile (reann_nlist::tiles order)
 cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
                                const float* rho, float* out, int out_stride, bool pairs, GhostOut gh, float* dsave,
-                               double* epart = nullptr);
+                               double* epart, int* flags);
 // total energy from np partial sums, in a fixed order
 cudaError_t launch_energy_final(cudaStream_t s, const double* partial, int np, double* energy);
 // atomic networks on tcgen05 tensor cores (mlp_tc.cu), precision REANN_MLP_BF16,
@@ -476,7 +476,7 @@ cudaError_t launch_mlp_bwd_tc(cudaStream_t s, const reann_nlist* nl, const TcTab
 cudaError_t launch_wait_selftest(cudaStream_t s, int* flags, long long polls);
 
 cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
-                               const float* dsave, const float* ybar, float* rhobar, bool pairs = false,
+                               const float* dsave, const float* ybar, float* rhobar, int* flags, bool pairs = false,
                                const float* Wt = nullptr, const float* bck = nullptr, const float* coef = nullptr,
                                float* rec = nullptr, GhostOut gh = {});
 

@@ -20,6 +20,7 @@
 
 #include <mutex>
 
+#include "bulk.cuh"
 #include "common.cuh"
 
 namespace reann {
@@ -28,10 +29,10 @@ namespace {
 constexpr int kT = 256;       // threads per block
 constexpr int kR = MLP_TILE;  // 64 rows per tile
 constexpr int LDH = H1 + 4;     // 68
-// input rows of FIN features are held with stride FIN + 4 (52 or 112) in the
-// buffer that later holds h1 (stride LDH)
+// input rows of FIN features are held with stride FIN (one bulk copy of the
+// tile's contiguous rows) in the buffer that later holds h1 (stride LDH)
 template <int FIN>
-__host__ __device__ constexpr int ldx() { return FIN + 4; }
+__host__ __device__ constexpr int ldx() { return FIN; }
 template <int FIN>
 __host__ __device__ constexpr int abuf() { return kR * (ldx<FIN>() > LDH ? ldx<FIN>() : LDH); }
 
@@ -45,6 +46,20 @@ __device__ __forceinline__ float silu_d(float z, float& h) {
     const float s = __frcp_rn(1.f + expf(-z));
     h = z * s;
     return s * fmaf(z, 1.f - s, 1.f);
+}
+
+// Wait (bounded) for the tile's bulk copies on `bar`; all threads agree.  Thread 0
+// initialised `bar` and issued the copies before it reaches the first barrier
+// here, so no thread polls the mbarrier before its initialisation.  When the
+// wait runs out: record FLAG_TIMEOUT, wait once more for the copies in flight
+// (FLAG_TIMEOUT_DRAIN if they still have not landed) and return false.
+__device__ __forceinline__ bool staged(uint64_t* bar, int* flags) {
+    __syncthreads();
+    if (__syncthreads_and(bulk::mbar_wait(bar, 0))) return true;
+    if (threadIdx.x == 0) atomicOr(&flags[FLAG_TIMEOUT], 1);
+    const bool drained = __syncthreads_and(bulk::mbar_wait(bar, 0));
+    if (!drained && threadIdx.x == 0) atomicOr(&flags[FLAG_TIMEOUT_DRAIN], 1);
+    return false;
 }
 
 __device__ __forceinline__ void copy_f4(float* dst, const float* src, int count, int tid) {
@@ -132,7 +147,8 @@ template <int OUT, int FIN>
 __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __restrict__ tiles,
                                                const float* __restrict__ rho, float* __restrict__ out,
                                                int out_stride, GhostOut gh, float* __restrict__ dsave,
-                                               double* __restrict__ epart) {
+                                               double* __restrict__ epart, int* __restrict__ flags) {
+    __shared__ __align__(8) uint64_t bar;
     extern __shared__ __align__(16) float sm[];
     float* sW1 = sm;                 // FIN x 64
     float* sW2 = sW1 + FIN * H1;     // 64 x 64
@@ -148,14 +164,21 @@ __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __
         return;
     }
     const NetDev& w = nets.e[tl.elem];
-    copy_f4(sW1, w.W1, FIN * H1, tid);
-    copy_f4(sW2, w.W2, H1 * H2, tid);
+    if (tid == 0) {  // W1, W2 and the tile's input rows by bulk copies (TMA engine)
+        bulk::mbar_init(&bar, 1);
+        bulk::mbar_init_fence();
+        const uint32_t xb = (uint32_t)tl.nrows * FIN * 4;
+        bulk::mbar_expect_tx(&bar, (FIN * H1 + H1 * H2) * 4 + xb);
+        bulk::bulk_g2s(sW1, w.W1, FIN * H1 * 4, &bar);
+        bulk::bulk_g2s(sW2, w.W2, H1 * H2 * 4, &bar);
+        bulk::bulk_g2s(sA, rho + (size_t)tl.row0 * FIN, xb, &bar);
+    }
     for (int i = tid; i < H2 * OUT; i += kT) sW3[w3_row<OUT>(i / OUT) * OUT + i % OUT] = w.W3[i];
     for (int i = tid; i < H1; i += kT) sb1[i] = w.b1[i];
     for (int i = tid; i < H2; i += kT) sb2[i] = w.b2[i];
     if (tid < OUT) sb3[tid] = w.b3[tid];
-    load_rows<FIN>(sA, rho, tl.row0, tl.nrows, tid);
-    __syncthreads();
+    for (int i = tl.nrows * FIN + tid; i < kR * FIN; i += kT) sA[i] = 0.f;  // rows past the tile's end
+    if (!staged(&bar, flags)) return;
     const int ty = tid >> 4, tx = tid & 15;
     float acc[4][4];
     // layer 1
@@ -267,7 +290,8 @@ __global__ void __launch_bounds__(kT, 3) k_mlp_bwd(NetsOfLayer nets, const Tile*
                                                const float* __restrict__ dsave, const float* __restrict__ ybar,
                                                float* __restrict__ rhobar, const float* __restrict__ Wt,
                                                const float* __restrict__ bck, const float* __restrict__ coef,
-                                               float* __restrict__ rec, GhostOut gh) {
+                                               float* __restrict__ rec, GhostOut gh, int* __restrict__ flags) {
+    __shared__ __align__(8) uint64_t bar;
     extern __shared__ __align__(16) float sm[];
     float* sW1t = sm;                 // W1^T: 64 x FIN
     float* sW2t = sW1t + H1 * FIN;    // W2^T: 64 x 64
@@ -285,9 +309,14 @@ __global__ void __launch_bounds__(kT, 3) k_mlp_bwd(NetsOfLayer nets, const Tile*
 #pragma unroll
     for (int i = 0; i < 4; ++i) s2[i] = ld_save(dsave, tl, 4 * ty + i, H1 + 4 * tx);
     const NetDev& w = nets.e[tl.elem];
-    copy_f4(sW1t, w.W1t, H1 * FIN, tid);
-    copy_f4(sW2t, w.W2t, H1 * H2, tid);
-    for (int i = tid; i < OUT * H2; i += kT) sW3t[i] = w.W3t[i];
+    if (tid == 0) {  // W1^T, W2^T, W3^T by bulk copies (TMA engine)
+        bulk::mbar_init(&bar, 1);
+        bulk::mbar_init_fence();
+        bulk::mbar_expect_tx(&bar, (H1 * FIN + H1 * H2 + OUT * H2) * 4);
+        bulk::bulk_g2s(sW1t, w.W1t, H1 * FIN * 4, &bar);
+        bulk::bulk_g2s(sW2t, w.W2t, H1 * H2 * 4, &bar);
+        bulk::bulk_g2s(sW3t, w.W3t, OUT * H2 * 4, &bar);
+    }
     if (BBAR)  // transposed per l: sWc[(l N_orb + k) N_phi + m] = W_{l,m,k}
         for (int i = tid; i < (LMAX + 1) * NPHI * NORB; i += kT) {
             const int l = i / (NPHI * NORB), m = (i / NORB) % NPHI, k = i % NORB;
@@ -297,7 +326,7 @@ __global__ void __launch_bounds__(kT, 3) k_mlp_bwd(NetsOfLayer nets, const Tile*
         const int r = i / OUT, o = i % OUT;
         sY[r * 8 + o] = (OUT == 1) ? 1.f : (r < tl.nrows ? ybar[(size_t)(tl.row0 + r) * OUT + o] : 0.f);
     }
-    __syncthreads();
+    if (!staged(&bar, flags)) return;
     // z2bar = (ybar W3^T) * s2 -> sG
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -433,13 +462,13 @@ NetsOfLayer layer_nets(const NetTable& t, int layer) {
 
 cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
                                const float* rho, float* out, int out_stride, bool pairs, GhostOut gh, float* dsave,
-                               double* epart) {
+                               double* epart, int* flags) {
     const int nt = (int)tiles_of(nl);
     if (nt == 0) return cudaSuccess;
     ensure_attrs();
     const NetsOfLayer ln = layer_nets(nets, t);
 #define REANN_FWD(O, F) \
-    k_mlp_fwd<O, F><<<nt, kT, fwd_smem<F>(), s>>>(ln, nl->tiles, rho, out, out_stride, gh, dsave, epart)
+    k_mlp_fwd<O, F><<<nt, kT, fwd_smem<F>(), s>>>(ln, nl->tiles, rho, out, out_stride, gh, dsave, epart, flags)
     if (pairs) {
         if (energy)
             REANN_FWD(1, NFEAT_P);
@@ -456,8 +485,8 @@ cudaError_t launch_mlp_fwd_f32(cudaStream_t s, const reann_nlist* nl, const NetT
 }
 
 cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetTable& nets, int t, bool energy,
-                               const float* dsave, const float* ybar, float* rhobar, bool pairs, const float* Wt,
-                               const float* bck, const float* coef, float* rec, GhostOut gh) {
+                               const float* dsave, const float* ybar, float* rhobar, int* flags, bool pairs,
+                               const float* Wt, const float* bck, const float* coef, float* rec, GhostOut gh) {
     const int nt = (int)tiles_of(nl);
     if (nt == 0) return cudaSuccess;
     ensure_attrs();
@@ -465,7 +494,7 @@ cudaError_t launch_mlp_bwd_f32(cudaStream_t s, const reann_nlist* nl, const NetT
 #define REANN_BWD(O, F, B)                                                                                      \
     k_mlp_bwd<O, F, B><<<nt, kT, bwd_smem<F, B>(), s>>>(ln, nl->tiles, dsave, ybar, rhobar, B ? Wt : nullptr, \
                                                         B ? bck : nullptr, B ? coef : nullptr, B ? rec : nullptr, \
-                                                        B ? gh : GhostOut{})
+                                                        B ? gh : GhostOut{}, flags)
     if (pairs) {
         if (energy)
             REANN_BWD(1, NFEAT_P, false);

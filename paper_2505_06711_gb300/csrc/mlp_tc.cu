@@ -58,6 +58,7 @@
 
 #include <mutex>
 
+#include "bulk.cuh"
 #include "common.cuh"
 
 namespace reann {
@@ -66,7 +67,7 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kRows = 128;
 constexpr uint32_t kTmemCols = 128;
-constexpr long long kSpinLimit = 1ll << 26;
+constexpr long long kSpinLimit = bulk::kSpinLimit;
 
 enum Prec { P_BF16 = 0, P_SPLIT = 1, P_FP8 = 2 };
 
@@ -76,9 +77,12 @@ struct TcLayer {
 };
 
 // ------------------------------------------------------------- PTX glue ---
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
+using bulk::bulk_g2s;
+using bulk::fence_async_smem;
+using bulk::mbar_expect_tx;
+using bulk::mbar_init;
+using bulk::mbar_wait;
+using bulk::smem_addr;
 
 // K-major, no swizzle, sm_100-family descriptor (version field = 1 at bit 46)
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -125,41 +129,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
-                 : "memory");
-}
-
-// bounded wait for phase `parity`; returns false when `limit` polls ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long long limit = kSpinLimit) {
-    const uint32_t a = smem_addr(mbar);
-    for (long long it = 0; it < limit; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.b32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-// global -> shared bulk copy (TMA engine), completion counted on the mbarrier
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(mbar))
-        : "memory");
-}
-
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 

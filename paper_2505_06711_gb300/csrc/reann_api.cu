@@ -912,7 +912,7 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
                                                   nl->dsave + (size_t)t * n * (H1 + H2), epart));
         else
             REANN_CUDA_TRY(ctx, launch_mlp_fwd_f32(s, nl, ctx->nets, t, energy_net, rho_t, out, out_stride, pairs, gh,
-                                                  nl->dsave + (size_t)t * n * (H1 + H2), epart));
+                                                  nl->dsave + (size_t)t * n * (H1 + H2), epart, ctx->d_flags));
     }
     {
         ProfScope p(ctx, PR_ENERGY);
@@ -938,11 +938,11 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
                                                       ctx->d_flags));
             else if (!pairs)  // the FP32 backward networks also take the bbar step (fused)
                 REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, dsave_t, nl->cbar,
-                                                       nl->rhobar, false, ctx->d_W + t * lw, bck_t, coef_t, nl->bbar,
-                                                       gh));
+                                                       nl->rhobar, ctx->d_flags, false, ctx->d_W + t * lw, bck_t,
+                                                       coef_t, nl->bbar, gh));
             else
                 REANN_CUDA_TRY(ctx, launch_mlp_bwd_f32(s, nl, ctx->nets, t, t == T - 1, dsave_t, nl->cbar,
-                                                       nl->rhobar, true));
+                                                       nl->rhobar, ctx->d_flags, true));
         }
         if (pairs) {
             ProfScope p(ctx, PR_BBAR);
