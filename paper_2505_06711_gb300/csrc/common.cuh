@@ -41,6 +41,19 @@ constexpr int MLP_TILE = 64;  // rows per FP32 network tile
 __device__ __forceinline__ int ang_l(int a) { return a == 0 ? 0 : (a < 4 ? 1 : 2); }
 __device__ __forceinline__ float ang_w(int a) { return a >= 7 ? 2.f : 1.f; }
 __device__ __forceinline__ float ang_sign(int a) { return (a >= 1 && a <= 3) ? -1.f : 1.f; }
+
+// Programmatic dependent launch.  A kernel started by launch_pdl() may become
+// resident while the previous kernel on its stream is still draining; before
+// it reads or writes global memory that an earlier kernel of the stream reads
+// or writes, and on every path before it exits, it runs pdl_enter():
+// griddepcontrol.wait returns once every prerequisite grid has completed and
+// its writes are visible (so completion stays transitive along the stream),
+// and launch_dependents then lets the next kernel be scheduled early.  Without
+// a programmatic prerequisite both instructions return at once.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 #endif
 
 // Device-side error flags (ctx->d_flags)
@@ -391,6 +404,28 @@ inline int64_t tiles128_of(const reann_nlist* nl) {
 }
 
 int set_error(reann_ctx* ctx, int code, const std::string& msg);
+
+// Launches k with the programmatic-stream-serialization attribute; every
+// kernel of the library calls pdl_enter() first.  In a captured graph the
+// attribute becomes a programmatic edge.  The network kernels are launched
+// without it: their grids are one wave of tiles, and blocks that become
+// resident while the previous kernel drains pile up on the SMs that freed
+// first (measured: FP32 step 0.489 -> 0.502 ms with them, 0.489 -> 0.487 ms
+// for the edge and rebuild kernels alone).
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<P>(args)...);
+}
 
 #define REANN_CUDA_TRY(ctx, expr)                                                                   \
     do {                                                                                            \

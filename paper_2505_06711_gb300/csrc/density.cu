@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(kWarps * 32, 16 / kWarps) k_density_fwd(int64_
                                                             const float* __restrict__ coef,
                                                             const float* __restrict__ Wt, float* __restrict__ rho,
                                                             float* __restrict__ bck) {
+    pdl_enter();
     constexpr int KO = PAIRS ? NORB_P : NORB;
     __shared__ __align__(16) float sW[(LMAX + 1) * NPHI * KO];
     // During the edge loop: kFwdStages stages of a lane's next neighbours (hi, lo
@@ -310,6 +311,7 @@ template <bool PAIRS>
 __global__ void __launch_bounds__(4 * kBbarAtoms) k_bbar(int64_t n, const float* __restrict__ Wt, const float* __restrict__ bck,
                                               const float* __restrict__ rhobar, const float* __restrict__ coef,
                                               float* __restrict__ rec, GhostOut gh) {
+    pdl_enter();
     constexpr int KO = PAIRS ? NORB_P : NORB;
     __shared__ __align__(16) float sW[(LMAX + 1) * NPHI * KO];
     __shared__ __align__(16) float sRec[kBbarAtoms * kRecLd];
@@ -410,6 +412,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
                                                                 const float* __restrict__ rec,
                                                                 float* __restrict__ cbar, float* __restrict__ grad,
                                                                 float* __restrict__ vir, Outputs out) {
+    pdl_enter();
     __shared__ __align__(16) float sGeo[kAdjWarps][kAdjGroups * kGroupStride];
     __shared__ __align__(16) float4 sPos[2][kAdjWarps * 32];  // a lane's next edge: hi, lo position of j
     __shared__ __align__(16) float4 sCen[kAdjWarps * kAdjGroups][2];  // hi, lo position of the centre atom
@@ -608,6 +611,7 @@ __device__ __forceinline__ int64_t ghosts_in_use(const int32_t* g_count, int64_t
 __global__ void k_init_coef(int64_t n, int64_t n_rows, int64_t g_rows, const int32_t* __restrict__ g_count,
                             int64_t g_cap, const int32_t* __restrict__ species, const int32_t* __restrict__ owner,
                             const float* __restrict__ c0, float* __restrict__ coef) {
+    pdl_enter();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t s, o;
     if (t < n_rows) {
@@ -628,6 +632,7 @@ __global__ void k_init_coef(int64_t n, int64_t n_rows, int64_t g_rows, const int
 // ghost rows <- owner rows (the per-layer ghost refresh of Fig. 4a), width in floats, multiple of 4
 __global__ void k_gather_rows(int64_t n, const int32_t* __restrict__ g_count, int64_t g_cap, int w4,
                               const int32_t* __restrict__ owner, float* __restrict__ base) {
+    pdl_enter();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ghosts_in_use(g_count, g_cap) * w4) return;
     const int64_t gi = t / w4;
@@ -640,6 +645,7 @@ constexpr int kSumThreads = 256, kSumPer = 8;
 
 __global__ void __launch_bounds__(kSumThreads) k_energy_partial(int64_t n, const float* __restrict__ eps,
                                                                double* __restrict__ partial) {
+    pdl_enter();
     __shared__ double sm[kSumThreads];
     const int64_t base = (int64_t)blockIdx.x * kSumThreads * kSumPer;
     double s = 0.0;
@@ -659,6 +665,7 @@ __global__ void __launch_bounds__(kSumThreads) k_energy_partial(int64_t n, const
 
 __global__ void __launch_bounds__(kSumThreads) k_energy_final(int np, const double* __restrict__ partial,
                                                              double* __restrict__ energy) {
+    pdl_enter();
     __shared__ double sm[kSumThreads];
     double s = 0.0;
     for (int i = threadIdx.x; i < np; i += kSumThreads) s += partial[i];
@@ -674,6 +681,7 @@ __global__ void __launch_bounds__(kSumThreads) k_energy_final(int np, const doub
 // FP64 sum of the per-atom virials (N x 9): partial sums per 2048 atoms, then one block
 __global__ void __launch_bounds__(kSumThreads) k_virial_partial(int64_t n, const float* __restrict__ vir,
                                                                double* __restrict__ partial) {
+    pdl_enter();
     __shared__ double sm[kSumThreads];
     const int64_t base = (int64_t)blockIdx.x * kSumThreads * kSumPer;
     for (int c = 0; c < 9; ++c) {
@@ -696,6 +704,7 @@ __global__ void __launch_bounds__(kSumThreads) k_virial_partial(int64_t n, const
 
 __global__ void __launch_bounds__(kSumThreads) k_virial_final(int np, const double* __restrict__ partial,
                                                              double* __restrict__ out) {
+    pdl_enter();
     __shared__ double sm[kSumThreads];
     for (int c = 0; c < 9; ++c) {
         double s = 0.0;
@@ -713,6 +722,7 @@ __global__ void __launch_bounds__(kSumThreads) k_virial_final(int np, const doub
 
 __global__ void k_unpermute_rows(int64_t n, int width, const int32_t* __restrict__ perm, const float* __restrict__ src,
                                  int src_stride, float* __restrict__ dst) {
+    pdl_enter();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n * width) return;
     const int64_t i = t / width;
@@ -727,8 +737,8 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 cudaError_t launch_init_coef(cudaStream_t s, const reann_nlist* nl, const float* c0) {
     const int64_t nr = rows_of(nl), gr = ghost_rows_of(nl);
     if (nr + gr == 0) return cudaSuccess;
-    k_init_coef<<<blocks_for(nr + gr, 256), 256, 0, s>>>(nl->n, nr, gr, ghost_count_ptr(nl), nl->g_cap, nl->species,
-                                                         nl->g_owner, c0, nl->coef);
+    launch_pdl(k_init_coef, blocks_for(nr + gr, 256), 256, 0, s, nl->n, nr, gr, ghost_count_ptr(nl), nl->g_cap,
+               nl->species, nl->g_owner, c0, nl->coef);
     return cudaGetLastError();
 }
 
@@ -736,7 +746,8 @@ cudaError_t launch_gather_ghost_rows(cudaStream_t s, const reann_nlist* nl, floa
     const int64_t gr = ghost_rows_of(nl);
     if (gr == 0) return cudaSuccess;
     const int w4 = width / 4;
-    k_gather_rows<<<blocks_for(gr * w4, 256), 256, 0, s>>>(nl->n, ghost_count_ptr(nl), gr, w4, nl->g_owner, base);
+    launch_pdl(k_gather_rows, blocks_for(gr * w4, 256), 256, 0, s, nl->n, ghost_count_ptr(nl), gr, w4, nl->g_owner,
+               base);
     return cudaGetLastError();
 }
 
@@ -775,11 +786,11 @@ cudaError_t launch_density_fwd(cudaStream_t s, const reann_nlist* nl, const Radi
     if (nr == 0) return cudaSuccess;
     const unsigned nb = blocks_for(nr, per_block);
     if (pairs)
-        k_density_fwd<true><<<nb, kWarps * 32, 0, s>>>(nr, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi,
-                                                       nl->pos_lo, coef, W, rho, bck);
+        launch_pdl(k_density_fwd<true>, nb, kWarps * 32, 0, s, nr, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi,
+                   nl->pos_lo, coef, W, rho, bck);
     else
-        k_density_fwd<false><<<nb, kWarps * 32, 0, s>>>(nr, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi,
-                                                        nl->pos_lo, coef, W, rho, bck);
+        launch_pdl(k_density_fwd<false>, nb, kWarps * 32, 0, s, nr, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi,
+                   nl->pos_lo, coef, W, rho, bck);
     return cudaGetLastError();
 }
 
@@ -788,9 +799,9 @@ cudaError_t launch_bbar(cudaStream_t s, const reann_nlist* nl, const float* W, c
     const int64_t nr = rows_of(nl);
     if (nr == 0) return cudaSuccess;
     if (pairs)
-        k_bbar<true><<<blocks_for(nr, kBbarAtoms), 4 * kBbarAtoms, 0, s>>>(nr, W, bck, rhobar, coef, rec, gh);
+        launch_pdl(k_bbar<true>, blocks_for(nr, kBbarAtoms), 4 * kBbarAtoms, 0, s, nr, W, bck, rhobar, coef, rec, gh);
     else
-        k_bbar<false><<<blocks_for(nr, kBbarAtoms), 4 * kBbarAtoms, 0, s>>>(nr, W, bck, rhobar, coef, rec, gh);
+        launch_pdl(k_bbar<false>, blocks_for(nr, kBbarAtoms), 4 * kBbarAtoms, 0, s, nr, W, bck, rhobar, coef, rec, gh);
     return cudaGetLastError();
 }
 
@@ -818,8 +829,8 @@ cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radi
     if (nr == 0) return cudaSuccess;
     const unsigned nb = blocks_for(nr, per_block);
 #define REANN_ADJ(C, V)                                                                                              \
-    k_density_adj8<C, V><<<nb, kAdjWarps * 32, 0, s>>>(nr, nl->stride, r, nl->live, nl->live_cnt, nl->pos_hi,        \
-                                                      nl->pos_lo, rec, cbar, grad, vir, out)
+    launch_pdl(k_density_adj8<C, V>, nb, kAdjWarps * 32, 0, s, nr, nl->stride, r, nl->live, nl->live_cnt,       \
+               nl->pos_hi, nl->pos_lo, rec, cbar, grad, vir, out)
     if (want_cbar && vir)
         REANN_ADJ(true, true);
     else if (want_cbar)
@@ -834,26 +845,27 @@ cudaError_t launch_density_adj(cudaStream_t s, const reann_nlist* nl, const Radi
 
 cudaError_t launch_virial_sum(cudaStream_t s, const reann_nlist* nl, const float* vir, double* partial, double* out) {
     const int np = (int)blocks_for(nl->n, kSumThreads * kSumPer);
-    k_virial_partial<<<np, kSumThreads, 0, s>>>(nl->n, vir, partial);
-    k_virial_final<<<1, kSumThreads, 0, s>>>(np, partial, out);
+    launch_pdl(k_virial_partial, np, kSumThreads, 0, s, nl->n, vir, partial);
+    launch_pdl(k_virial_final, 1, kSumThreads, 0, s, np, partial, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_energy_sum(cudaStream_t s, const reann_nlist* nl, double* energy) {
     const int np = (int)blocks_for(nl->n, kSumThreads * kSumPer);
-    k_energy_partial<<<np, kSumThreads, 0, s>>>(nl->n, nl->eps, nl->partial);
-    k_energy_final<<<1, kSumThreads, 0, s>>>(np, nl->partial, energy);
+    launch_pdl(k_energy_partial, np, kSumThreads, 0, s, nl->n, nl->eps, nl->partial);
+    launch_pdl(k_energy_final, 1, kSumThreads, 0, s, np, nl->partial, energy);
     return cudaGetLastError();
 }
 
 cudaError_t launch_energy_final(cudaStream_t s, const double* partial, int np, double* energy) {
-    k_energy_final<<<1, kSumThreads, 0, s>>>(np, partial, energy);
+    launch_pdl(k_energy_final, 1, kSumThreads, 0, s, np, partial, energy);
     return cudaGetLastError();
 }
 
 cudaError_t launch_unpermute_rows(cudaStream_t s, const reann_nlist* nl, const float* src, int src_stride, float* dst,
                                   int width) {
-    k_unpermute_rows<<<blocks_for(nl->n * width, 256), 256, 0, s>>>(nl->n, width, nl->perm, src, src_stride, dst);
+    launch_pdl(k_unpermute_rows, blocks_for(nl->n * width, 256), 256, 0, s, nl->n, width, nl->perm, src, src_stride,
+               dst);
     return cudaGetLastError();
 }
 

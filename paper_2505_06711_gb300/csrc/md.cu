@@ -26,6 +26,7 @@ constexpr int kThreads = 256, kPer = 8;
 // v = s v + (dt/2) F/m, s read from the device (1 without a thermostat)
 __global__ void k_kick(int64_t n, double* __restrict__ vel, const float* __restrict__ forces,
                        const double* __restrict__ mass, double half_dt, const double* __restrict__ scale) {
+    pdl_enter();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * n) return;
     const double v = scale ? vel[t] * *scale : vel[t];
@@ -33,12 +34,14 @@ __global__ void k_kick(int64_t n, double* __restrict__ vel, const float* __restr
 }
 
 __global__ void k_scale(int64_t n, double* __restrict__ vel, const double* __restrict__ scale) {
+    pdl_enter();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < 3 * n) vel[t] *= *scale;
 }
 
 // thermostat half step on the device scalars: sc[1] K, sc[2] xi, sc[3] eta, sc[4] s
 __global__ void k_nh_half(double* __restrict__ sc, double dt, double gkt, double q) {
+    pdl_enter();
     double K = sc[1], xi = sc[2], eta = sc[3];
     xi += 0.25 * dt * (2.0 * K - gkt) / q;
     eta += 0.5 * dt * xi;
@@ -52,6 +55,7 @@ __global__ void k_nh_half(double* __restrict__ sc, double dt, double gkt, double
 }
 
 __global__ void k_drift(int64_t n, double* __restrict__ pos, const double* __restrict__ vel, double dt) {
+    pdl_enter();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < 3 * n) pos[t] += dt * vel[t];
 }
@@ -60,6 +64,7 @@ __global__ void k_drift(int64_t n, double* __restrict__ pos, const double* __res
 __global__ void __launch_bounds__(kThreads) k_ekin_partial(int64_t n, const double* __restrict__ vel,
                                                            const double* __restrict__ mass,
                                                            double* __restrict__ partial) {
+    pdl_enter();
     __shared__ double sm[kThreads];
     const int64_t base = (int64_t)blockIdx.x * kThreads * kPer;
     double s = 0.0;
@@ -82,6 +87,7 @@ __global__ void __launch_bounds__(kThreads) k_ekin_partial(int64_t n, const doub
 
 __global__ void __launch_bounds__(kThreads) k_ekin_final(int np, const double* __restrict__ partial,
                                                          double* __restrict__ out) {
+    pdl_enter();
     __shared__ double sm[kThreads];
     double s = 0.0;
     for (int i = threadIdx.x; i < np; i += kThreads) s += partial[i];
@@ -99,6 +105,7 @@ __global__ void __launch_bounds__(kThreads) k_ekin_final(int np, const double* _
 __global__ void k_record(int* __restrict__ counter, const double* __restrict__ sc, double* __restrict__ epot_out,
                          double* __restrict__ ekin_out, double* __restrict__ bath_out, double gkt, double q,
                          int n_steps, const int* __restrict__ gate, int* __restrict__ rebuilds) {
+    pdl_enter();
     const int k = *counter;
     if (k < n_steps) {
         if (epot_out) epot_out[k] = sc[0];
@@ -115,36 +122,36 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 
 cudaError_t launch_kick(cudaStream_t s, int64_t n, double* vel, const float* forces, const double* mass,
                         double half_dt, const double* scale) {
-    k_kick<<<blocks_for(3 * n, 256), 256, 0, s>>>(n, vel, forces, mass, half_dt, scale);
+    launch_pdl(k_kick, blocks_for(3 * n, 256), 256, 0, s, n, vel, forces, mass, half_dt, scale);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scale(cudaStream_t s, int64_t n, double* vel, const double* scale) {
-    k_scale<<<blocks_for(3 * n, 256), 256, 0, s>>>(n, vel, scale);
+    launch_pdl(k_scale, blocks_for(3 * n, 256), 256, 0, s, n, vel, scale);
     return cudaGetLastError();
 }
 
 cudaError_t launch_nh_half(cudaStream_t s, double* scalars, double dt, double gkt, double q) {
-    k_nh_half<<<1, 1, 0, s>>>(scalars, dt, gkt, q);
+    launch_pdl(k_nh_half, 1, 1, 0, s, scalars, dt, gkt, q);
     return cudaGetLastError();
 }
 
 cudaError_t launch_drift(cudaStream_t s, int64_t n, double* pos, const double* vel, double dt) {
-    k_drift<<<blocks_for(3 * n, 256), 256, 0, s>>>(n, pos, vel, dt);
+    launch_pdl(k_drift, blocks_for(3 * n, 256), 256, 0, s, n, pos, vel, dt);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ekin(cudaStream_t s, int64_t n, const double* vel, const double* mass, double* partial,
                         double* out) {
     const int np = (int)blocks_for(n, kThreads * kPer);
-    k_ekin_partial<<<np, kThreads, 0, s>>>(n, vel, mass, partial);
-    k_ekin_final<<<1, kThreads, 0, s>>>(np, partial, out);
+    launch_pdl(k_ekin_partial, np, kThreads, 0, s, n, vel, mass, partial);
+    launch_pdl(k_ekin_final, 1, kThreads, 0, s, np, partial, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_record(cudaStream_t s, int* counter, const double* scalars, double* epot_out, double* ekin_out,
                           double* bath_out, double gkt, double q, int n_steps, const int* gate, int* rebuilds) {
-    k_record<<<1, 1, 0, s>>>(counter, scalars, epot_out, ekin_out, bath_out, gkt, q, n_steps, gate, rebuilds);
+    launch_pdl(k_record, 1, 1, 0, s, counter, scalars, epot_out, ekin_out, bath_out, gkt, q, n_steps, gate, rebuilds);
     return cudaGetLastError();
 }
 

@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(kT) k_mlp_fwd(NetsOfLayer nets, const Tile* __
                                                const float* __restrict__ rho, float* __restrict__ out,
                                                int out_stride, GhostOut gh, float* __restrict__ dsave,
                                                double* __restrict__ epart, int* __restrict__ flags) {
+    pdl_enter();
     __shared__ __align__(8) uint64_t bar;
     extern __shared__ __align__(16) float sm[];
     float* sW1 = sm;                 // FIN x 64
@@ -291,6 +292,7 @@ __global__ void __launch_bounds__(kT, 3) k_mlp_bwd(NetsOfLayer nets, const Tile*
                                                float* __restrict__ rhobar, const float* __restrict__ Wt,
                                                const float* __restrict__ bck, const float* __restrict__ coef,
                                                float* __restrict__ rec, GhostOut gh, int* __restrict__ flags) {
+    pdl_enter();
     __shared__ __align__(8) uint64_t bar;
     extern __shared__ __align__(16) float sm[];
     float* sW1t = sm;                 // W1^T: 64 x FIN

@@ -468,6 +468,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_fwd(TcLayer nets, const Tile
                                                        const float* __restrict__ rho, float* __restrict__ out,
                                                        int out_stride, int* __restrict__ flags, GhostOut gh,
                                                        float* __restrict__ dsave, double* __restrict__ epart) {
+    pdl_enter();
     using L = FwdL<P>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::BAR);
@@ -676,6 +677,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_bwd(TcLayer nets, const Tile
                                                        const float* __restrict__ Wc, const float* __restrict__ bck,
                                                        const float* __restrict__ coef, float* __restrict__ rec,
                                                        GhostOut gh, int* __restrict__ flags) {
+    pdl_enter();
     using L = BwdL<P>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::BAR);
@@ -840,6 +842,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tc_bwd(TcLayer nets, const Tile
 // an mbarrier that nothing arrives on, then fail() (flag, drain, release) as the
 // network kernels do when a wait runs out.
 __global__ void __launch_bounds__(kThreads, 1) k_wait_selftest(int* __restrict__ flags, long long polls) {
+    pdl_enter();
     __shared__ __align__(8) uint64_t bar[4];
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 3);
     const uint32_t tmem = setup(tslot, bar);

@@ -97,6 +97,7 @@ __global__ void k_wrap_key(const int* __restrict__ gate, int64_t n, const double
                            CellGeom g, double* __restrict__ xw, double* __restrict__ fw, int32_t* __restrict__ mw,
                            int32_t* __restrict__ key, int32_t* __restrict__ counts, int* __restrict__ flags,
                            double* __restrict__ ref) {
+    pdl_enter();
     if (gate && *gate == 0) return;  // rebuild (or this rebuild's sort) not needed
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -142,6 +143,7 @@ constexpr int kScanItems = 8;
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_single(const int* __restrict__ gate, int64_t n, T* __restrict__ in,
                                                                 T* __restrict__ out, bool zero_in) {
+    pdl_enter();
     if (gate && *gate == 0) return;  // rebuild not needed this step
     constexpr int TILE = kScanThreads * kScanItems;
     __shared__ T buf[TILE + TILE / 32];
@@ -215,6 +217,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_single(const int* __restr
 
 __global__ void k_scatter(const int* __restrict__ gate, int64_t n, const int32_t* __restrict__ key, const int32_t* __restrict__ start,
                           int32_t* __restrict__ cursor, int32_t* __restrict__ order) {
+    pdl_enter();
     if (gate && *gate == 0) return;  // rebuild not needed this step
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -235,6 +238,7 @@ __global__ void k_bucket_rank(const int* __restrict__ gate, int64_t n, const int
                               const int32_t* __restrict__ scattered, int64_t sorted_keys,
                               int32_t* __restrict__ order, const float4* __restrict__ pin, float4* __restrict__ pout,
                               int32_t* __restrict__ counts) {
+    pdl_enter();
     if (gate && *gate == 0) return;  // rebuild not needed this step
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -277,6 +281,7 @@ __global__ void k_gather_internal(const int* __restrict__ gate, int64_t n, CellG
                                   const int32_t* __restrict__ mw_c, const int32_t* __restrict__ sp_c,
                                   double* __restrict__ xw, double* __restrict__ fw, int32_t* __restrict__ mw,
                                   int32_t* __restrict__ sp, int32_t* __restrict__ gcnt) {
+    pdl_enter();
     if (gate && *gate == 0) return;  // rebuild not needed this step
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -305,6 +310,7 @@ __global__ void k_gather_internal(const int* __restrict__ gate, int64_t n, CellG
 constexpr int kResortPeriod = 8;
 
 __global__ void k_rebuild_gates(const int* __restrict__ gate, int* __restrict__ state) {
+    pdl_enter();
     const bool run = !gate || *gate != 0;
     const bool sort = run && state[0] >= kResortPeriod;
     if (run) state[0] = sort ? 1 : state[0] + 1;
@@ -318,6 +324,7 @@ __global__ void k_wrap_keep(const int* __restrict__ gate, int64_t n, CellGeom g,
                             const int32_t* __restrict__ perm, double* __restrict__ xw, double* __restrict__ fw,
                             int32_t* __restrict__ mw, int32_t* __restrict__ gcnt, int* __restrict__ flags,
                             double* __restrict__ ref) {
+    pdl_enter();
     if (gate && *gate == 0) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -371,6 +378,7 @@ __global__ void k_ghosts_ext(const int* __restrict__ gate, int64_t n, CellGeom g
                              int32_t* __restrict__ owner, int32_t* __restrict__ shift, int32_t* __restrict__ key,
                              int32_t* __restrict__ counts, float4* __restrict__ p32, int32_t dead_key,
                              int* __restrict__ flags) {
+    pdl_enter();
     if (gate && *gate == 0) return;  // rebuild not needed this step
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n + g_cap) return;
@@ -415,6 +423,7 @@ __global__ void __launch_bounds__(256) k_nbr_search(const int* __restrict__ gate
                                                    const float4* __restrict__ p32s, const int32_t* __restrict__ bstart,
                                                    int stride, int32_t* __restrict__ nbr, int32_t* __restrict__ cnt_out,
                                                    int* __restrict__ flags) {
+    pdl_enter();
     if (gate && *gate == 0) return;  // rebuild not needed this step
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -533,6 +542,7 @@ __global__ void k_refresh(int64_t n, const int32_t* __restrict__ g_count, int64_
                           const int32_t* __restrict__ shift, float4* __restrict__ hi, float4* __restrict__ lo,
                           const int32_t* __restrict__ species, const float* __restrict__ c0,
                           float* __restrict__ coef) {
+    pdl_enter();
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n + ghosts_in_use(g_count, g_cap)) return;
     int64_t o = s;
@@ -569,6 +579,7 @@ __global__ void __launch_bounds__(256) k_live(int64_t n, int stride, float rc2, 
                                              const int32_t* __restrict__ cnt, const float4* __restrict__ hi,
                                              const float4* __restrict__ lo, int32_t* __restrict__ live,
                                              int32_t* __restrict__ live_cnt, int* __restrict__ flags) {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
@@ -604,6 +615,7 @@ __global__ void __launch_bounds__(256) k_live(int64_t n, int stride, float rc2, 
 // largest displacement since the build: flag when any atom moved more than half the skin
 __global__ void k_moved(int64_t n, const double* __restrict__ pos, const double* __restrict__ ref, double thr2,
                         int* __restrict__ moved) {
+    pdl_enter();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double dx = pos[3 * i] - ref[3 * i], dy = pos[3 * i + 1] - ref[3 * i + 1], dz = pos[3 * i + 2] - ref[3 * i + 2];
@@ -623,11 +635,11 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 static cudaError_t counting_sort(cudaStream_t s, const int* gate, int64_t n, int64_t nkeys, const int32_t* key,
                                  int32_t* counts, int32_t* start, int32_t* scattered, int32_t* order,
                                  int64_t sorted_keys, const float4* pin = nullptr, float4* pout = nullptr) {
-    k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(gate, nkeys, counts, start, true);
+    launch_pdl(k_scan_single<int32_t>, 1, kScanThreads, 0, s, gate, nkeys, counts, start, true);
     if (n > 0) {
-        k_scatter<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, key, start, counts, scattered);
-        k_bucket_rank<<<blocks_for(n, 256), 256, 0, s>>>(gate, n, key, start, scattered, sorted_keys, order, pin, pout,
-                                                         counts);
+        launch_pdl(k_scatter, blocks_for(n, 256), 256, 0, s, gate, n, key, start, counts, scattered);
+        launch_pdl(k_bucket_rank, blocks_for(n, 256), 256, 0, s, gate, n, key, start, scattered, sorted_keys, order,
+                   pin, pout, counts);
     }
     return cudaGetLastError();
 }
@@ -666,15 +678,15 @@ static cudaError_t stage_sort_and_count(cudaStream_t s, reann_nlist* nl, const d
                                         const int* sort_gate, const int* keep_gate, const int* gate) {
     const int64_t n = nl->n;
     NlistScratch& w = nl->w;
-    k_wrap_key<<<blocks_for(n, 256), 256, 0, s>>>(sort_gate, n, pos, w.species_c, nl->n_elem, nl->geom, w.xw_c, w.fw_c,
-                                                  w.mw_c, w.key, w.counts, flags, nl->pos_ref);
+    launch_pdl(k_wrap_key, blocks_for(n, 256), 256, 0, s, sort_gate, n, pos, w.species_c, nl->n_elem, nl->geom,
+               w.xw_c, w.fw_c, w.mw_c, w.key, w.counts, flags, nl->pos_ref);
     counting_sort(s, sort_gate, n, owned_keys(nl), w.key, w.counts, w.start, w.scat, nl->perm, owned_keys(nl));
-    k_gather_internal<<<blocks_for(n, 256), 256, 0, s>>>(sort_gate, n, nl->geom, nl->perm, w.xw_c, w.fw_c, w.mw_c,
-                                                         w.species_c, w.xw, w.fw, nl->wrapm, nl->species, w.gcnt);
+    launch_pdl(k_gather_internal, blocks_for(n, 256), 256, 0, s, sort_gate, n, nl->geom, nl->perm, w.xw_c, w.fw_c,
+               w.mw_c, w.species_c, w.xw, w.fw, nl->wrapm, nl->species, w.gcnt);
     if (keep_gate)
-        k_wrap_keep<<<blocks_for(n, 256), 256, 0, s>>>(keep_gate, n, nl->geom, pos, nl->perm, w.xw, w.fw, nl->wrapm,
-                                                       w.gcnt, flags, nl->pos_ref);
-    k_scan_single<int32_t><<<1, kScanThreads, 0, s>>>(gate, n, w.gcnt, w.goff, false);
+        launch_pdl(k_wrap_keep, blocks_for(n, 256), 256, 0, s, keep_gate, n, nl->geom, pos, nl->perm, w.xw, w.fw,
+                   nl->wrapm, w.gcnt, flags, nl->pos_ref);
+    launch_pdl(k_scan_single<int32_t>, 1, kScanThreads, 0, s, gate, n, w.gcnt, w.goff, false);
     return cudaGetLastError();
 }
 
@@ -683,8 +695,8 @@ static cudaError_t stage_ghosts_and_bins(cudaStream_t s, reann_nlist* nl, int* f
     const int64_t n = nl->n, next = n + nl->g_cap;
     NlistScratch& w = nl->w;
     const int64_t nx = ext_bins(nl);
-    k_ghosts_ext<<<blocks_for(next, 256), 256, 0, s>>>(gate, n, nl->geom, w.xw, w.fw, w.goff, nl->g_cap, nl->g_owner,
-                                                       nl->g_shift, w.ekey, w.ecounts, w.p32, (int32_t)nx, flags);
+    launch_pdl(k_ghosts_ext, blocks_for(next, 256), 256, 0, s, gate, n, nl->geom, w.xw, w.fw, w.goff, nl->g_cap,
+               nl->g_owner, nl->g_shift, w.ekey, w.ecounts, w.p32, (int32_t)nx, flags);
     counting_sort(s, gate, next, nx + 1, w.ekey, w.ecounts, w.estart, w.escat, w.eorder, nx, w.p32, w.p32s);
     return cudaGetLastError();
 }
@@ -692,8 +704,8 @@ static cudaError_t stage_ghosts_and_bins(cudaStream_t s, reann_nlist* nl, int* f
 static cudaError_t stage_search(cudaStream_t s, reann_nlist* nl, int* flags, const int* gate) {
     const int64_t n = nl->n;
     NlistScratch& w = nl->w;
-    k_nbr_search<<<blocks_for(n * 32, 256), 256, 0, s>>>(gate, n, nl->geom, w.xw, w.fw, nl->g_owner, nl->g_shift, w.p32,
-                                                         w.p32s, w.estart, nl->stride, nl->nbr, nl->nbr_cnt, flags);
+    launch_pdl(k_nbr_search, blocks_for(n * 32, 256), 256, 0, s, gate, n, nl->geom, w.xw, w.fw, nl->g_owner,
+               nl->g_shift, w.p32, w.p32s, w.estart, nl->stride, nl->nbr, nl->nbr_cnt, flags);
     return cudaGetLastError();
 }
 
@@ -792,7 +804,7 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
 
 // gate == nullptr: always rebuild; otherwise every kernel returns at once unless *gate != 0
 cudaError_t launch_rebuild(cudaStream_t s, reann_nlist* nl, const double* pos, int* flags, const int* gate) {
-    k_rebuild_gates<<<1, 1, 0, s>>>(gate, nl->w.rb_state);
+    launch_pdl(k_rebuild_gates, 1, 1, 0, s, gate, nl->w.rb_state);
     cudaError_t e = stage_sort_and_count(s, nl, pos, flags, nl->w.rb_state + 1, nl->w.rb_state + 2, gate);
     if (e == cudaSuccess) e = stage_ghosts_and_bins(s, nl, flags, gate);
     if (e == cudaSuccess) e = stage_search(s, nl, flags, gate);
@@ -801,7 +813,7 @@ cudaError_t launch_rebuild(cudaStream_t s, reann_nlist* nl, const double* pos, i
 
 cudaError_t launch_moved(cudaStream_t s, const reann_nlist* nl, const double* pos, int* moved) {
     const double half = 0.5 * nl->skin;
-    k_moved<<<blocks_for(nl->n, 256), 256, 0, s>>>(nl->n, pos, nl->pos_ref, half * half, moved);
+    launch_pdl(k_moved, blocks_for(nl->n, 256), 256, 0, s, nl->n, pos, nl->pos_ref, half * half, moved);
     return cudaGetLastError();
 }
 
@@ -809,17 +821,16 @@ const int32_t* ghost_count_ptr(const reann_nlist* nl) { return nl->w.goff + nl->
 
 cudaError_t launch_refresh_positions(cudaStream_t s, const reann_nlist* nl, const double* pos, const float* c0) {
     const int64_t total = nl->n + nl->g_cap;
-    k_refresh<<<blocks_for(total, 256), 256, 0, s>>>(nl->n, ghost_count_ptr(nl), nl->g_cap, nl->geom, pos, nl->perm,
-                                                     nl->wrapm, nl->g_owner, nl->g_shift, nl->pos_hi, nl->pos_lo,
-                                                     nl->species, c0, nl->coef);
+    launch_pdl(k_refresh, blocks_for(total, 256), 256, 0, s, nl->n, ghost_count_ptr(nl), nl->g_cap, nl->geom, pos,
+               nl->perm, nl->wrapm, nl->g_owner, nl->g_shift, nl->pos_hi, nl->pos_lo, nl->species, c0, nl->coef);
     return cudaGetLastError();
 }
 
 cudaError_t launch_live_edges(cudaStream_t s, const reann_nlist* nl, float rc2, int* flags) {
     const int64_t nr = rows_of(nl);
     if (nr == 0) return cudaSuccess;
-    k_live<<<blocks_for(nr * 32, 256), 256, 0, s>>>(nr, nl->stride, rc2, nl->nbr, nl->nbr_cnt, nl->pos_hi, nl->pos_lo,
-                                                    nl->live, nl->live_cnt, flags);
+    launch_pdl(k_live, blocks_for(nr * 32, 256), 256, 0, s, nr, nl->stride, rc2, nl->nbr, nl->nbr_cnt, nl->pos_hi,
+               nl->pos_lo, nl->live, nl->live_cnt, flags);
     return cudaGetLastError();
 }
 

@@ -58,6 +58,7 @@ struct PackDst {
 
 // owned atoms: rows (remapped), species, destination, positions
 __global__ void k_pack_owned(PackSrc s, PackDst d) {
+    pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n) return;
     const int c = s.cnt[i];
@@ -80,6 +81,7 @@ __global__ void k_pack_owned(PackSrc s, PackDst d) {
 
 // ghost slots: owner (pool index) and image position
 __global__ void k_pack_ghosts(PackSrc s, PackDst d) {
+    pdl_enter();
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= s.g) return;
     const int64_t o = s.owner[q];
@@ -97,6 +99,7 @@ __global__ void k_pack_ghosts(PackSrc s, PackDst d) {
 
 // a released owned range: no neighbours, outputs to the sink row
 __global__ void k_release(int64_t ob, int64_t n, int32_t sink, int32_t* __restrict__ cnt, int32_t* __restrict__ perm) {
+    pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     cnt[ob + i] = 0;
@@ -107,6 +110,7 @@ __global__ void k_release(int64_t ob, int64_t n, int32_t sink, int32_t* __restri
 // sink so that later pool launches leave their result rows untouched
 __global__ void k_retire(const int4* __restrict__ seg, int32_t sink, int32_t* __restrict__ cnt,
                          int32_t* __restrict__ perm) {
+    pdl_enter();
     const int4 sg = seg[blockIdx.x];
     for (int i = threadIdx.x; i < sg.y; i += blockDim.x) {
         cnt[sg.x + i] = 0;
@@ -117,6 +121,7 @@ __global__ void k_retire(const int4* __restrict__ seg, int32_t sink, int32_t* __
 // per-structure FP64 energy: one block per segment, fixed summation order
 __global__ void __launch_bounds__(256) k_segment_energy(const int4* __restrict__ seg, const float* __restrict__ eps,
                                                         double* __restrict__ energies) {
+    pdl_enter();
     __shared__ double sm[256];
     const int4 sg = seg[blockIdx.x];  // x = owned base, y = atoms, z = output index
     double s = 0.0;
@@ -140,23 +145,23 @@ cudaError_t launch_pack(cudaStream_t s, const reann_nlist* src, const double* ca
               src->perm,    src->wrapm, src->g_owner, src->g_shift, caller_pos,   src->geom};
     PackDst b{pool->n, ob, gb, pool->stride, pool->nbr, pool->nbr_cnt, pool->species, pool->perm, pool->g_owner,
               pool->pos_hi, pool->pos_lo};
-    k_pack_owned<<<blocks_for(src->n, 128), 128, 0, s>>>(a, b);
-    if (src->g > 0) k_pack_ghosts<<<blocks_for(src->g, 256), 256, 0, s>>>(a, b);
+    launch_pdl(k_pack_owned, blocks_for(src->n, 128), 128, 0, s, a, b);
+    if (src->g > 0) launch_pdl(k_pack_ghosts, blocks_for(src->g, 256), 256, 0, s, a, b);
     return cudaGetLastError();
 }
 
 cudaError_t launch_release(cudaStream_t s, reann_nlist* pool, int64_t ob, int64_t n) {
-    if (n > 0) k_release<<<blocks_for(n, 256), 256, 0, s>>>(ob, n, (int32_t)pool->n, pool->nbr_cnt, pool->perm);
+    if (n > 0) launch_pdl(k_release, blocks_for(n, 256), 256, 0, s, ob, n, (int32_t)pool->n, pool->nbr_cnt, pool->perm);
     return cudaGetLastError();
 }
 
 cudaError_t launch_retire(cudaStream_t s, const int4* seg, int nseg, reann_nlist* pool) {
-    if (nseg > 0) k_retire<<<nseg, 256, 0, s>>>(seg, (int32_t)pool->n, pool->nbr_cnt, pool->perm);
+    if (nseg > 0) launch_pdl(k_retire, nseg, 256, 0, s, seg, (int32_t)pool->n, pool->nbr_cnt, pool->perm);
     return cudaGetLastError();
 }
 
 cudaError_t launch_segment_energy(cudaStream_t s, const int4* seg, int nseg, const float* eps, double* energies) {
-    if (nseg > 0) k_segment_energy<<<nseg, 256, 0, s>>>(seg, eps, energies);
+    if (nseg > 0) launch_pdl(k_segment_energy, nseg, 256, 0, s, seg, eps, energies);
     return cudaGetLastError();
 }
 

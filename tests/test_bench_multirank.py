@@ -51,4 +51,5 @@ def test_single_rank_identity():
 
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.aggregate(100, 2.0, 1) == pytest.approx(5e4)
-    assert bench.launches_per_step(3) == 26
+    # 13 rebuild + 15 evaluation kernels, as an ncu launch list of one T = 3 step counts them
+    assert bench.launches_per_step(3) == 28
