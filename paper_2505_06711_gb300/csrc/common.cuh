@@ -258,9 +258,11 @@ struct NlistScratch {
     double *xw_c = nullptr, *fw_c = nullptr, *xw = nullptr, *fw = nullptr;  // wrapped Cartesian / fractional
     int32_t *mw_c = nullptr, *key = nullptr, *counts = nullptr, *start = nullptr;
     int32_t *gcnt = nullptr, *goff = nullptr;  // ghosts per atom and offsets; goff[n] = ghost count
+    int32_t* halo = nullptr;                    // per atom and axis: the image interval (pack_halo)
     int32_t* species_c = nullptr;              // caller-order species
     int32_t *ekey = nullptr, *ecounts = nullptr, *estart = nullptr, *eorder = nullptr;
     int32_t *scat = nullptr, *escat = nullptr;  // atomic-order scatter before the in-bucket ranking
+    int32_t *tsum = nullptr, *etsum = nullptr;  // look-back status words of the scans (owned / extended)
     int32_t* rb_state = nullptr;  // rebuilds since the last sort, sort gate, keep-order gate
     float4* p32 = nullptr;   // FP32 positions of owned + ghost slots for the pre-test
     float4* p32s = nullptr;  // the same in bin-sorted order, slot index in .w

@@ -37,13 +37,33 @@
 namespace reann {
 namespace {
 
-constexpr int kScanThreads = 1024;
+constexpr int kScanThreads = 256;
+// Per-slot kernels whose time goes to FP64 arithmetic (wrapping, image shifts, halo tests) run
+// in 64-thread blocks: 24,576 atoms then spread over all SMs' FP64 units (256-thread blocks
+// left a third of the SMs without work)
+constexpr int kFp64Threads = 64;
 
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
 
+// n h rounded as the FP64 product, without the FP64 multiply for the image shifts -1, 0, 1
+// (0 h is a zero with the sign of h): GB300's FP64 pipe is narrow, and the rebuild's
+// per-slot kernels are bound by it
+__device__ __forceinline__ double smul(int n, double h) {
+    if (n == 0) return copysign(0.0, h);
+    if (n == 1) return h;
+    if (n == -1) return -h;
+    return dmul((double)n, h);
+}
+
 __device__ __forceinline__ void shift_vec(const CellGeom& g, int n0, int n1, int n2, double s[3]) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) s[d] = dadd(dadd(smul(n0, g.h[d]), smul(n1, g.h[3 + d])), smul(n2, g.h[6 + d]));
+}
+// the same vector with plain FP64 products (bitwise equal): for the neighbour search's
+// boundary test, where the lanes of a warp hold different shifts and branches diverge
+__device__ __forceinline__ void shift_vec_mul(const CellGeom& g, int n0, int n1, int n2, double s[3]) {
 #pragma unroll
     for (int d = 0; d < 3; ++d)
         s[d] = dadd(dadd(dmul((double)n0, g.h[d]), dmul((double)n1, g.h[3 + d])), dmul((double)n2, g.h[6 + d]));
@@ -132,97 +152,151 @@ __global__ void k_wrap_key(const int* __restrict__ gate, int64_t n, const double
 
 // ---- deterministic counting sort ------------------------------------------
 
-// Exclusive scan of `in` (n entries) into out[0..n]; one block of kScanThreads
-// walking tiles of kScanThreads x kScanItems entries: each tile is loaded and
-// stored coalesced through shared memory (padded one word per 32 against bank
-// conflicts), each thread scans kScanItems consecutive entries, and a
-// two-level warp scan joins the threads; a running carry joins the tiles.
-// With zero_in the entries are set to zero once read.
-constexpr int kScanItems = 8;
+// Exclusive scan of `in` (n entries, int32) into out[0..n], one launch over
+// tiles of kScanTile entries, one block per tile, joined by decoupled look-back
+// (D. Merrill and M. Garland, Single-pass Parallel Prefix Scan with Decoupled
+// Look-back, NVIDIA technical report NVR-2016-002): a block takes its tile
+// number from a ticket counter (so every lower tile's block has started),
+// publishes its tile's sum, walks back over the published words of the tiles
+// before it (one warp, 32 words per read) until one carries an inclusive
+// prefix, and publishes its own inclusive prefix.  A tile is loaded and stored
+// coalesced through shared memory (padded one word per 32 against bank
+// conflicts), each thread scans kScanPer consecutive entries, and a two-level
+// warp scan joins the threads.
+// The status words (scan_tiles(n) + 2: one per tile, the ticket, the count of
+// finished blocks) start at zero; the last block to finish sets them back to
+// zero.  A wait on a lower tile is bounded (kScanSpin polls, seconds): when it
+// runs out the block sets FLAG_TIMEOUT and goes on with a wrong carry.
+constexpr int kScanPer = 8;
+constexpr int kScanTile = kScanThreads * kScanPer;
+constexpr int32_t kScanAgg = 1 << 30, kScanIncl = (int32_t)0x80000000u, kScanVal = (1 << 30) - 1;
+constexpr long long kScanSpin = 1ll << 22;
 
-template <typename T>
-__global__ void __launch_bounds__(kScanThreads) k_scan_single(const int* __restrict__ gate, int64_t n, T* __restrict__ in,
-                                                                T* __restrict__ out, bool zero_in) {
+__global__ void __launch_bounds__(kScanThreads) k_scan(const int* __restrict__ gate, int64_t n,
+                                                       const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                                                       int32_t* __restrict__ status, int* __restrict__ flags) {
     pdl_enter();
     if (gate && *gate == 0) return;  // rebuild not needed this step
-    constexpr int TILE = kScanThreads * kScanItems;
-    __shared__ T buf[TILE + TILE / 32];
-    __shared__ T warp_sums[kScanThreads / 32];
+    __shared__ int32_t buf[kScanTile + kScanTile / 32];
+    __shared__ int32_t warp_sums[kScanThreads / 32];
+    __shared__ int32_t s_tile, s_carry;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    T carry = 0;
-    T nx[kScanItems];  // the next tile's entries, loaded while the current tile is scanned
+    const int nb = (int)gridDim.x;
+    if (tid == 0) s_tile = atomicAdd(&status[nb], 1);
+    __syncthreads();
+    const int tile = s_tile;
+    const int64_t base = (int64_t)tile * kScanTile;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const int64_t x = k * kScanThreads + tid;
-        nx[k] = x < n ? in[x] : (T)0;
+    for (int k = 0; k < kScanPer; ++k) {
+        const int x = k * kScanThreads + tid;
+        buf[x + x / 32] = base + x < n ? in[base + x] : 0;
     }
-    for (int64_t base = 0; base < n; base += TILE) {
+    __syncthreads();
+    int32_t v[kScanPer];
+    int32_t local = 0;
 #pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
-            const int x = k * kScanThreads + tid;
-            buf[x + x / 32] = nx[k];
-            if (zero_in && base + x < n) in[base + x] = (T)0;
-        }
+    for (int k = 0; k < kScanPer; ++k) {
+        const int x = tid * kScanPer + k;
+        v[k] = buf[x + x / 32];
+        local += v[k];
+    }
+    int32_t incl = local;
 #pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
-            const int64_t x = base + TILE + k * kScanThreads + tid;
-            nx[k] = x < n ? in[x] : (T)0;
-        }
-        __syncthreads();
-        T v[kScanItems];
-        T local = 0;
-#pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
-            const int x = tid * kScanItems + k;
-            v[k] = buf[x + x / 32];
-            local += v[k];
-        }
-        T incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sums[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int32_t t = lane < kScanThreads / 32 ? warp_sums[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const T y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
+            const int32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
         }
-        if (lane == 31) warp_sums[w] = incl;
-        __syncthreads();
-        if (w == 0) {
-            T s = warp_sums[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const T y = __shfl_up_sync(0xffffffffu, s, o);
-                if (lane >= o) s += y;
-            }
-            warp_sums[lane] = s;  // inclusive
-        }
-        __syncthreads();
-        T run = carry + (w > 0 ? warp_sums[w - 1] : (T)0) + incl - local;
-        const T tile_total = warp_sums[kScanThreads / 32 - 1];
-#pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
-            const int x = tid * kScanItems + k;
-            buf[x + x / 32] = run;
-            run += v[k];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
-            const int x = k * kScanThreads + tid;
-            if (base + x < n) out[base + x] = buf[x + x / 32];
-        }
-        carry += tile_total;
-        __syncthreads();  // buf and warp_sums are rewritten by the next tile
+        if (lane < kScanThreads / 32) warp_sums[lane] = t;  // inclusive
     }
-    if (tid == 0) out[n] = carry;
+    __syncthreads();
+    const int32_t total = warp_sums[kScanThreads / 32 - 1];
+    if (w == 0) {  // look-back by one warp: lane l reads the word of tile top - l
+        int32_t carry = 0;
+        if (tile == 0) {
+            if (lane == 0) atomicExch(&status[0], kScanIncl | total);
+        } else {
+            if (lane == 0) atomicExch(&status[tile], kScanAgg | total);
+            bool late = false;
+            for (int top = tile - 1; top >= 0; top -= 32) {
+                const int q = top - lane;
+                int32_t word = kScanIncl;  // below tile 0: an inclusive zero
+                if (q >= 0) {
+                    long long spins = 0;
+                    do {
+                        word = *reinterpret_cast<volatile int32_t*>(status + q);
+                    } while (word == 0 && ++spins <= kScanSpin);
+                    if (word == 0) {
+                        late = true;
+                        word = kScanIncl;
+                    }
+                }
+                // the nearest tile with an inclusive prefix ends the walk
+                const unsigned inc = __ballot_sync(0xffffffffu, (word & kScanIncl) != 0);
+                const int stop = inc ? __ffs(inc) - 1 : 31;
+                int32_t val = lane <= stop ? (word & kScanVal) : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+                carry += val;
+                if (inc) break;
+            }
+            if (__any_sync(0xffffffffu, late) && lane == 0) atomicOr(&flags[FLAG_TIMEOUT], 1);
+            if (lane == 0) atomicExch(&status[tile], kScanIncl | (carry + total));
+        }
+        if (lane == 0) s_carry = carry;
+    }
+    __syncthreads();
+    int32_t run = s_carry + (w > 0 ? warp_sums[w - 1] : 0) + incl - local;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        const int x = tid * kScanPer + k;
+        buf[x + x / 32] = run;
+        run += v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        const int x = k * kScanThreads + tid;
+        if (base + x < n) out[base + x] = buf[x + x / 32];
+    }
+    if (tid == 0) {
+        if (tile == nb - 1) out[n] = s_carry + total;
+        __threadfence();
+        if (atomicAdd(&status[nb + 1], 1) == nb - 1) {  // every block is past its look-back
+            for (int q = 0; q < nb + 2; ++q) status[q] = 0;
+        }
+    }
 }
 
-__global__ void k_scatter(const int* __restrict__ gate, int64_t n, const int32_t* __restrict__ key, const int32_t* __restrict__ start,
-                          int32_t* __restrict__ cursor, int32_t* __restrict__ order) {
+inline int64_t scan_tiles(int64_t n) { return n > 0 ? (n + kScanTile - 1) / kScanTile : 1; }
+inline int64_t scan_status_words(int64_t n) { return scan_tiles(n) + 2; }
+
+// out[0..n] = exclusive scan of in[0..n), out[n] the total; status: scan_status_words(n)
+// zeroed words
+static void scan_exclusive(cudaStream_t s, const int* gate, int64_t n, const int32_t* in, int32_t* out,
+                           int32_t* status, int* flags) {
+    launch_pdl(k_scan, (unsigned)scan_tiles(n), kScanThreads, 0, s, gate, n, in, out, status, flags);
+}
+
+__global__ void k_scatter(const int* __restrict__ gate, int64_t n, const int32_t* __restrict__ key,
+                          const int32_t* __restrict__ start, int32_t* __restrict__ counts,
+                          int32_t* __restrict__ order) {
     pdl_enter();
     if (gate && *gate == 0) return;  // rebuild not needed this step
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int k = key[i];
-    int p = start[k] + atomicAdd(&cursor[k], 1);
+    // counting the histogram back down: the bucket's entries take its slots from the top,
+    // and the counts end at zero, ready for the next sort's histogram
+    int p = start[k] + atomicSub(&counts[k], 1) - 1;
     order[p] = (int32_t)i;
 }
 
@@ -232,19 +306,16 @@ __global__ void k_scatter(const int* __restrict__ gate, int64_t n, const int32_t
 // hold tens of entries); entries of buckets >= sorted_keys keep their position.
 // With `pin`, the entry's FP32 position follows it into sorted order, its index
 // carried in .w (bit pattern), so that the search reads candidates contiguously.
-// The first entry of each bucket sets the bucket's counter back to zero, so the
-// histogram of the next sort starts from zeros without a memset.
-__global__ void k_bucket_rank(const int* __restrict__ gate, int64_t n, const int32_t* __restrict__ key, const int32_t* __restrict__ start,
-                              const int32_t* __restrict__ scattered, int64_t sorted_keys,
-                              int32_t* __restrict__ order, const float4* __restrict__ pin, float4* __restrict__ pout,
-                              int32_t* __restrict__ counts) {
+__global__ void k_bucket_rank(const int* __restrict__ gate, int64_t n, const int32_t* __restrict__ key,
+                              const int32_t* __restrict__ start, const int32_t* __restrict__ scattered,
+                              int64_t sorted_keys, int32_t* __restrict__ order, const float4* __restrict__ pin,
+                              float4* __restrict__ pout) {
     pdl_enter();
     if (gate && *gate == 0) return;  // rebuild not needed this step
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int32_t v = scattered[p];
     const int32_t b = key[v];
-    if (p == start[b]) counts[b] = 0;
     int64_t dst = p;
     if (b < sorted_keys) {
         const int lo = start[b], hi = start[b + 1];
@@ -257,6 +328,13 @@ __global__ void k_bucket_rank(const int* __restrict__ gate, int64_t n, const int
         const float4 x = pin[v];
         pout[dst] = make_float4(x.x, x.y, x.z, __int_as_float(v));
     }
+}
+
+// an axis's image interval [lo, hi] in one word (|lo|, |hi| < 128)
+__device__ __forceinline__ int32_t pack_halo(int lo, int hi) { return (lo + 128) | ((hi + 128) << 8); }
+__device__ __forceinline__ void unpack_halo(int32_t p, int& lo, int& hi) {
+    lo = (p & 255) - 128;
+    hi = ((p >> 8) & 255) - 128;
 }
 
 // admissible image shifts of one axis: those keeping f + a within (-reach, 1 + reach),
@@ -280,7 +358,7 @@ __global__ void k_gather_internal(const int* __restrict__ gate, int64_t n, CellG
                                   const double* __restrict__ xw_c, const double* __restrict__ fw_c,
                                   const int32_t* __restrict__ mw_c, const int32_t* __restrict__ sp_c,
                                   double* __restrict__ xw, double* __restrict__ fw, int32_t* __restrict__ mw,
-                                  int32_t* __restrict__ sp, int32_t* __restrict__ gcnt) {
+                                  int32_t* __restrict__ sp, int32_t* __restrict__ gcnt, int32_t* __restrict__ halo) {
     pdl_enter();
     if (gate && *gate == 0) return;  // rebuild not needed this step
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -295,6 +373,7 @@ __global__ void k_gather_internal(const int* __restrict__ gate, int64_t n, CellG
         mw[3 * i + k] = mw_c[3 * (int64_t)c + k];
         int lo, hi;
         halo_interval(g, k, f, lo, hi);
+        halo[3 * i + k] = pack_halo(lo, hi);
         cnt *= hi - lo + 1;
     }
     sp[i] = sp_c[c];
@@ -322,8 +401,8 @@ __global__ void k_rebuild_gates(const int* __restrict__ gate, int* __restrict__ 
 // (the same arithmetic as k_wrap_key) and count their ghost images
 __global__ void k_wrap_keep(const int* __restrict__ gate, int64_t n, CellGeom g, const double* __restrict__ pos,
                             const int32_t* __restrict__ perm, double* __restrict__ xw, double* __restrict__ fw,
-                            int32_t* __restrict__ mw, int32_t* __restrict__ gcnt, int* __restrict__ flags,
-                            double* __restrict__ ref) {
+                            int32_t* __restrict__ mw, int32_t* __restrict__ gcnt, int32_t* __restrict__ halo,
+                            int* __restrict__ flags, double* __restrict__ ref) {
     pdl_enter();
     if (gate && *gate == 0) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -346,6 +425,7 @@ __global__ void k_wrap_keep(const int* __restrict__ gate, int64_t n, CellGeom g,
         mw[3 * i + k] = m[k];
         int lo, hi;
         halo_interval(g, k, f[k], lo, hi);
+        halo[3 * i + k] = pack_halo(lo, hi);
         cnt *= hi - lo + 1;
     }
     gcnt[i] = cnt - 1;
@@ -369,6 +449,20 @@ __device__ __forceinline__ void ext_slot(const CellGeom& g, const double* __rest
     p32[s] = make_float4((float)(xw[3 * o] + sv[0]), (float)(xw[3 * o + 1] + sv[1]), (float)(xw[3 * o + 2] + sv[2]), 0.f);
 }
 
+// ext_slot for the atom itself (shift 0): f + 0 and x + 0 without the FP64 adds (they
+// differ at most in the sign of a zero, which no bin or distance sees)
+__device__ __forceinline__ void ext_slot_self(const CellGeom& g, const double* __restrict__ xw,
+                                              const double* __restrict__ fw, int64_t o, int32_t* __restrict__ key,
+                                              int32_t* __restrict__ counts, float4* __restrict__ p32) {
+    int bx[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) bx[k] = clampi((int)floor(fw[3 * o + k] * g.ns[k]) + g.pad[k], 0, g.nbx[k] - 1);
+    const int k = (bx[0] * g.nbx[1] + bx[1]) * g.nbx[2] + bx[2];
+    key[o] = k;
+    atomicAdd(&counts[k], 1);
+    p32[o] = make_float4((float)xw[3 * o], (float)xw[3 * o + 1], (float)xw[3 * o + 2], 0.f);
+}
+
 // 3-4. ghost images and the extended binning, one thread per slot of [0, n + g_cap):
 // owned slot i keys itself and fills its images' slots [goff[i], goff[i+1])
 // (owner, shift, key, FP32 position) in the order a, b, c of the per-axis
@@ -377,7 +471,7 @@ __global__ void k_ghosts_ext(const int* __restrict__ gate, int64_t n, CellGeom g
                              const double* __restrict__ fw, const int32_t* __restrict__ goff, int64_t g_cap,
                              int32_t* __restrict__ owner, int32_t* __restrict__ shift, int32_t* __restrict__ key,
                              int32_t* __restrict__ counts, float4* __restrict__ p32, int32_t dead_key,
-                             int* __restrict__ flags) {
+                             const int32_t* __restrict__ halo, int* __restrict__ flags) {
     pdl_enter();
     if (gate && *gate == 0) return;  // rebuild not needed this step
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -390,10 +484,10 @@ __global__ void k_ghosts_ext(const int* __restrict__ gate, int64_t n, CellGeom g
         }
         return;  // slots in use are written by their owners
     }
-    ext_slot(g, xw, fw, s, 0, 0, 0, key, counts, p32, s);
-    int lo[3], hi[3];
+    ext_slot_self(g, xw, fw, s, key, counts, p32);
+    int lo[3], hi[3];  // the intervals the wrap computed
 #pragma unroll
-    for (int k = 0; k < 3; ++k) halo_interval(g, k, fw[3 * s + k], lo[k], hi[k]);
+    for (int k = 0; k < 3; ++k) unpack_halo(halo[3 * s + k], lo[k], hi[k]);
     int64_t q = goff[s];
     for (int a = lo[0]; a <= hi[0]; ++a)
         for (int b = lo[1]; b <= hi[1]; ++b)
@@ -509,7 +603,7 @@ __global__ void __launch_bounds__(256) k_nbr_search(const int* __restrict__ gate
                             unpack_shift(shift[j - n], a0, a1, a2);
                         }
                         double sv[3];
-                        shift_vec(g, a0, a1, a2, sv);
+                        shift_vec_mul(g, a0, a1, a2, sv);
                         double rr[3];
 #pragma unroll
                         for (int k = 0; k < 3; ++k) rr[k] = dadd(dsub(xw[3 * o + k], xi[k]), sv[k]);
@@ -588,26 +682,38 @@ __global__ void __launch_bounds__(256) k_live(int64_t n, int stride, float rc2, 
     const int32_t* row = nbr + (size_t)i * stride;
     int32_t* out = live + (size_t)i * stride;
     int count = 0;
-    for (int base = 0; base < c; base += 32) {
-        const int e = base + lane;
-        bool keep = false;
-        int j = 0;
-        if (e < c) {
-            j = row[e];
-            const float4 hj = hi[j], lj = lo[j];
-            const float x = (hj.x - hi_i.x) + (lj.x - lo_i.x);
-            const float y = (hj.y - hi_i.y) + (lj.y - lo_i.y);
-            const float z = (hj.z - hi_i.z) + (lj.z - lo_i.z);
-            const float d2 = x * x + y * y + z * z;
-            keep = d2 < rc2;
-            if (!(d2 > 1e-16f)) {
-                keep = false;
-                atomicOr(&flags[FLAG_GEOM], 4);
+    // 128 neighbours per round, 4 per lane: every index and position load of the round is
+    // issued before the first distance test (the gathers' latency overlaps)
+    constexpr int U = 4;
+    for (int base = 0; base < c; base += 32 * U) {
+        int j[U];
+        float4 hj[U], lj[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) j[u] = base + 32 * u + lane < c ? row[base + 32 * u + lane] : -1;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (j[u] >= 0) {
+                hj[u] = hi[j[u]];
+                lj[u] = lo[j[u]];
             }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            bool keep = false;
+            if (j[u] >= 0) {
+                const float x = (hj[u].x - hi_i.x) + (lj[u].x - lo_i.x);
+                const float y = (hj[u].y - hi_i.y) + (lj[u].y - lo_i.y);
+                const float z = (hj[u].z - hi_i.z) + (lj[u].z - lo_i.z);
+                const float d2 = x * x + y * y + z * z;
+                keep = d2 < rc2;
+                if (!(d2 > 1e-16f)) {
+                    keep = false;
+                    atomicOr(&flags[FLAG_GEOM], 4);
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (keep) out[count + __popc(m & ((1u << lane) - 1u))] = j[u];
+            count += __popc(m);
         }
-        const unsigned m = __ballot_sync(0xffffffffu, keep);
-        if (keep) out[count + __popc(m & ((1u << lane) - 1u))] = j;
-        count += __popc(m);
     }
     if (lane == 0) live_cnt[i] = count;
 }
@@ -630,16 +736,17 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 // Counting sort of n keys in [0, nkeys) whose histogram `counts` the kernel that
 // produced the keys has filled: order = indices sorted by (key, index) within the
 // first `sorted_keys` buckets (later buckets hold unused capacity whose order does
-// not matter); start = bucket offsets.  The scan zeroes counts for the scatter's
-// cursors and the ranking zeroes them again for the next sort.
+// not matter); start = bucket offsets.  The scatter counts the histogram back down
+// to zero for the next sort.
 static cudaError_t counting_sort(cudaStream_t s, const int* gate, int64_t n, int64_t nkeys, const int32_t* key,
                                  int32_t* counts, int32_t* start, int32_t* scattered, int32_t* order,
-                                 int64_t sorted_keys, const float4* pin = nullptr, float4* pout = nullptr) {
-    launch_pdl(k_scan_single<int32_t>, 1, kScanThreads, 0, s, gate, nkeys, counts, start, true);
+                                 int64_t sorted_keys, int32_t* tsum, int* flags, const float4* pin = nullptr,
+                                 float4* pout = nullptr) {
+    scan_exclusive(s, gate, nkeys, counts, start, tsum, flags);
     if (n > 0) {
         launch_pdl(k_scatter, blocks_for(n, 256), 256, 0, s, gate, n, key, start, counts, scattered);
         launch_pdl(k_bucket_rank, blocks_for(n, 256), 256, 0, s, gate, n, key, start, scattered, sorted_keys, order,
-                   pin, pout, counts);
+                   pin, pout);
     }
     return cudaGetLastError();
 }
@@ -678,15 +785,16 @@ static cudaError_t stage_sort_and_count(cudaStream_t s, reann_nlist* nl, const d
                                         const int* sort_gate, const int* keep_gate, const int* gate) {
     const int64_t n = nl->n;
     NlistScratch& w = nl->w;
-    launch_pdl(k_wrap_key, blocks_for(n, 256), 256, 0, s, sort_gate, n, pos, w.species_c, nl->n_elem, nl->geom,
-               w.xw_c, w.fw_c, w.mw_c, w.key, w.counts, flags, nl->pos_ref);
-    counting_sort(s, sort_gate, n, owned_keys(nl), w.key, w.counts, w.start, w.scat, nl->perm, owned_keys(nl));
-    launch_pdl(k_gather_internal, blocks_for(n, 256), 256, 0, s, sort_gate, n, nl->geom, nl->perm, w.xw_c, w.fw_c,
-               w.mw_c, w.species_c, w.xw, w.fw, nl->wrapm, nl->species, w.gcnt);
+    launch_pdl(k_wrap_key, blocks_for(n, kFp64Threads), kFp64Threads, 0, s, sort_gate, n, pos, w.species_c,
+               nl->n_elem, nl->geom, w.xw_c, w.fw_c, w.mw_c, w.key, w.counts, flags, nl->pos_ref);
+    counting_sort(s, sort_gate, n, owned_keys(nl), w.key, w.counts, w.start, w.scat, nl->perm, owned_keys(nl),
+                  w.tsum, flags);
+    launch_pdl(k_gather_internal, blocks_for(n, kFp64Threads), kFp64Threads, 0, s, sort_gate, n, nl->geom, nl->perm,
+               w.xw_c, w.fw_c, w.mw_c, w.species_c, w.xw, w.fw, nl->wrapm, nl->species, w.gcnt, w.halo);
     if (keep_gate)
-        launch_pdl(k_wrap_keep, blocks_for(n, 256), 256, 0, s, keep_gate, n, nl->geom, pos, nl->perm, w.xw, w.fw,
-                   nl->wrapm, w.gcnt, flags, nl->pos_ref);
-    launch_pdl(k_scan_single<int32_t>, 1, kScanThreads, 0, s, gate, n, w.gcnt, w.goff, false);
+        launch_pdl(k_wrap_keep, blocks_for(n, kFp64Threads), kFp64Threads, 0, s, keep_gate, n, nl->geom, pos,
+                   nl->perm, w.xw, w.fw, nl->wrapm, w.gcnt, w.halo, flags, nl->pos_ref);
+    scan_exclusive(s, gate, n, w.gcnt, w.goff, w.tsum, flags);
     return cudaGetLastError();
 }
 
@@ -695,9 +803,10 @@ static cudaError_t stage_ghosts_and_bins(cudaStream_t s, reann_nlist* nl, int* f
     const int64_t n = nl->n, next = n + nl->g_cap;
     NlistScratch& w = nl->w;
     const int64_t nx = ext_bins(nl);
-    launch_pdl(k_ghosts_ext, blocks_for(next, 256), 256, 0, s, gate, n, nl->geom, w.xw, w.fw, w.goff, nl->g_cap,
-               nl->g_owner, nl->g_shift, w.ekey, w.ecounts, w.p32, (int32_t)nx, flags);
-    counting_sort(s, gate, next, nx + 1, w.ekey, w.ecounts, w.estart, w.escat, w.eorder, nx, w.p32, w.p32s);
+    launch_pdl(k_ghosts_ext, blocks_for(next, kFp64Threads), kFp64Threads, 0, s, gate, n, nl->geom, w.xw, w.fw,
+               w.goff, nl->g_cap, nl->g_owner, nl->g_shift, w.ekey, w.ecounts, w.p32, (int32_t)nx, w.halo, flags);
+    counting_sort(s, gate, next, nx + 1, w.ekey, w.ecounts, w.estart, w.escat, w.eorder, nx, w.etsum, flags,
+                  w.p32, w.p32s);
     return cudaGetLastError();
 }
 
@@ -714,6 +823,8 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
     const int64_t n = nl->n;
     NlistScratch& w = nl->w;
     const int64_t nkeys = owned_keys(nl);
+    if (n >= (int64_t(1) << 28))  // the scans' status words carry sums below 2^30 (atoms + ghost capacity)
+        return set_error(ctx, REANN_E_ARG, "more than 2^28 atoms in one list");
     w.xw_c = dalloc<double>(nl, 3 * n);
     w.fw_c = dalloc<double>(nl, 3 * n);
     w.mw_c = dalloc<int32_t>(nl, 3 * n);
@@ -723,16 +834,20 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
     w.xw = dalloc<double>(nl, 3 * n);
     w.fw = dalloc<double>(nl, 3 * n);
     w.gcnt = dalloc<int32_t>(nl, n);
+    w.halo = dalloc<int32_t>(nl, 3 * n);
     w.goff = dalloc<int32_t>(nl, n + 1);
     w.species_c = dalloc<int32_t>(nl, n);
     w.scat = dalloc<int32_t>(nl, n);
     w.rb_state = dalloc<int32_t>(nl, 4);
+    w.tsum = dalloc<int32_t>(nl, std::max(scan_status_words(nkeys), scan_status_words(n)));
     nl->perm = dalloc<int32_t>(nl, n);
     nl->species = dalloc<int32_t>(nl, n);
     nl->wrapm = dalloc<int32_t>(nl, 3 * n);
     nl->pos_ref = dalloc<double>(nl, 3 * n);
     if (!w.xw_c || !w.fw_c || !w.mw_c || !w.key || !w.counts || !w.start || !w.xw || !w.fw || !w.gcnt || !w.goff ||
-        !w.species_c || !w.scat || !nl->perm || !nl->species || !nl->wrapm || !nl->pos_ref || !w.rb_state)
+        !w.halo ||
+        !w.species_c || !w.scat || !nl->perm || !nl->species || !nl->wrapm || !nl->pos_ref || !w.rb_state ||
+        !w.tsum)
         return set_error(ctx, REANN_E_NOMEM, "neighbour-list allocation failed");
     {
         const int32_t state0[4] = {1, 0, 0, 0};  // this build sorts; rebuilds count from 1
@@ -741,6 +856,8 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
     }
     REANN_CUDA_TRY(ctx, cudaMemcpyAsync(w.species_c, species, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     REANN_CUDA_TRY(ctx, cudaMemsetAsync(w.counts, 0, sizeof(int32_t) * nkeys, s));  // kept zero between sorts
+    REANN_CUDA_TRY(ctx, cudaMemsetAsync(w.tsum, 0,
+                                        sizeof(int32_t) * std::max(scan_status_words(nkeys), scan_status_words(n)), s));
     REANN_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * NFLAGS, s));
     REANN_CUDA_TRY(ctx, stage_sort_and_count(s, nl, pos, ctx->d_flags, nullptr, nullptr, nullptr));
     // sizes: element ranges of the internal order and the ghost count
@@ -771,9 +888,12 @@ int build_nlist_device(reann_ctx* ctx, reann_nlist* nl, const double* pos, const
     w.estart = dalloc<int32_t>(nl, nx + 2);
     w.eorder = dalloc<int32_t>(nl, next);
     w.escat = dalloc<int32_t>(nl, next);
-    if (!nl->g_owner || !nl->g_shift || !w.ekey || !w.p32 || !w.p32s || !w.ecounts || !w.estart || !w.eorder || !w.escat)
+    w.etsum = dalloc<int32_t>(nl, scan_status_words(nx + 1));
+    if (!nl->g_owner || !nl->g_shift || !w.ekey || !w.p32 || !w.p32s || !w.ecounts || !w.estart || !w.eorder ||
+        !w.escat || !w.etsum)
         return set_error(ctx, REANN_E_NOMEM, "ghost allocation failed");
     REANN_CUDA_TRY(ctx, cudaMemsetAsync(w.ecounts, 0, sizeof(int32_t) * (nx + 1), s));  // kept zero between sorts
+    REANN_CUDA_TRY(ctx, cudaMemsetAsync(w.etsum, 0, sizeof(int32_t) * scan_status_words(nx + 1), s));
     REANN_CUDA_TRY(ctx, stage_ghosts_and_bins(s, nl, ctx->d_flags, nullptr));
     // row capacity: expected neighbours from the number density, with headroom
     const CellGeom& g = nl->geom;
@@ -813,7 +933,8 @@ cudaError_t launch_rebuild(cudaStream_t s, reann_nlist* nl, const double* pos, i
 
 cudaError_t launch_moved(cudaStream_t s, const reann_nlist* nl, const double* pos, int* moved) {
     const double half = 0.5 * nl->skin;
-    launch_pdl(k_moved, blocks_for(nl->n, 256), 256, 0, s, nl->n, pos, nl->pos_ref, half * half, moved);
+    launch_pdl(k_moved, blocks_for(nl->n, kFp64Threads), kFp64Threads, 0, s, nl->n, pos, nl->pos_ref, half * half,
+               moved);
     return cudaGetLastError();
 }
 
@@ -821,8 +942,9 @@ const int32_t* ghost_count_ptr(const reann_nlist* nl) { return nl->w.goff + nl->
 
 cudaError_t launch_refresh_positions(cudaStream_t s, const reann_nlist* nl, const double* pos, const float* c0) {
     const int64_t total = nl->n + nl->g_cap;
-    launch_pdl(k_refresh, blocks_for(total, 256), 256, 0, s, nl->n, ghost_count_ptr(nl), nl->g_cap, nl->geom, pos,
-               nl->perm, nl->wrapm, nl->g_owner, nl->g_shift, nl->pos_hi, nl->pos_lo, nl->species, c0, nl->coef);
+    launch_pdl(k_refresh, blocks_for(total, kFp64Threads), kFp64Threads, 0, s, nl->n, ghost_count_ptr(nl), nl->g_cap,
+               nl->geom, pos, nl->perm, nl->wrapm, nl->g_owner, nl->g_shift, nl->pos_hi, nl->pos_lo, nl->species, c0,
+               nl->coef);
     return cudaGetLastError();
 }
 
