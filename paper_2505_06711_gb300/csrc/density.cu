@@ -378,7 +378,10 @@ __global__ void __launch_bounds__(4 * kBbarAtoms) k_bbar(int64_t n, const float*
 // from j's adjoint record (3 float4 loads per lane; per load the 8 lanes read
 // one full 128 B line of the record), and accumulates its share of dE/dr_k;
 // cbar_{k,m} is lane m's own sum.  The force is reduced over the 8 lanes once
-// per atom.
+// per atom.  Each record is gathered just before its edge is computed: without
+// records held in registers ahead of use the kernel fits 64 registers and 32
+// warps per SM (prefetching one edge ahead took 80 registers and 24 warps, and
+// was 3 % slower).
 constexpr int kAdjWarps = 2;  // small blocks: the block scheduler balances the SMs at fine grain
 constexpr int kAdjGroups = 4;  // centre atoms per warp
 // Edge record in shared memory: x y z 1/d | d fc fc' - | g_0..g_7 (16 floats).
@@ -455,9 +458,8 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
 #pragma unroll
     for (int q = 0; q < 9; ++q) w[q] = 0.f;
     // Pipeline across batches of 8 edges: while batch b is computed, the
-    // positions of batch b + 1 are copied into shared memory (cp.async), the
-    // indices of batch b + 2 are loaded, and the record of batch b + 1's first
-    // edge is gathered during b's last edge.
+    // positions of batch b + 1 are copied into shared memory (cp.async) and the
+    // indices of batch b + 2 are loaded.
     int j_cur = 0;
     if (m < cnt) {
         j_cur = row[m];
@@ -466,13 +468,6 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
     }
     cp_async_commit();
     int j_nx = 8 + m < cnt ? row[8 + m] : 0;
-    float bjA[12], bjB[12];
-#pragma unroll
-    for (int a = 0; a < 12; ++a) bjA[a] = bjB[a] = 0.f;
-    {
-        const int js = __shfl_sync(FULL, j_cur, lane & ~7);
-        if (cnt > 0) load_rec(js, bjA);
-    }
     for (int e0 = 0; e0 < cmax; e0 += 8) {
         const int ns = cnt - e0;
         // geometry of edge e0 + m, one edge per lane, from the staged positions
@@ -499,10 +494,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
             cp_async16(my_lo, plo + j_nx);
         }
         cp_async_commit();
-        const int j_first_nx = __shfl_sync(FULL, j_nx, lane & ~7);
         const int j_nx2 = 16 + m < ns ? row[e0 + 16 + m] : 0;
-        // software pipeline over the batch: the gathers of edge s + 1 (register set
-        // B, or A) are in flight while edge s (set A, or B) is computed
         auto gather = [&](int s, float* bj) {
             if (s < ns) load_rec(__float_as_int(geo[s * kGeoStride + 7]), bj);
         };
@@ -548,14 +540,10 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_density_adj8(int64_t n, int 
             }
         };
 #pragma unroll
-        for (int s = 0; s < 8; s += 2) {
-            gather(s + 1, bjB);
-            edge(s, bjA);
-            if (s + 2 < 8)
-                gather(s + 2, bjA);
-            else if (8 < ns)
-                load_rec(j_first_nx, bjA);  // the next batch's first edge
-            edge(s + 1, bjB);
+        for (int s = 0; s < 8; ++s) {
+            float bj[12];
+            gather(s, bj);
+            edge(s, bj);
         }
         __syncwarp();
         j_cur = j_nx;
@@ -754,7 +742,8 @@ cudaError_t launch_gather_ghost_rows(cudaStream_t s, const reann_nlist* nl, floa
 // Preferred shared-memory carveout (percent of the 228 KB maximum) of the edge
 // kernels; the rest of the 256 KB per SM serves as L1 for the neighbour
 // gathers.  40 % (a 100 KB configuration) holds four forward blocks and 50 %
-// (132 KB) twelve adjoint blocks, their occupancy limits by registers; on the
+// (132 KB) sixteen adjoint blocks, their occupancy limits by registers (60 % and
+// 80 % were 1 % and 4 % slower for the adjoint); on the
 // 24,576-atom water box this is 2 % faster for the forward than the driver's
 // choice, and a 0 % hint (fewer resident blocks) 1.5-6 x slower.
 constexpr int kFwdCarveout = 40;
