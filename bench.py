@@ -80,10 +80,10 @@ BYTES_PER_ATOM_EDGE_FIXED = {"density_fwd": 16 + 32 + 320 + 192, "density_adj": 
 # kernel, from one ncu capture of this workload; valid only for the kernel
 # source they were taken on (keyed by its hash), null otherwise.
 TRAFFIC = {  # {(region, source_sha of the kernel source): bytes per launch}
-    ("density_adj", "aaefc49e55c7"): 21837312,
+    ("density_adj", "3dae6077f620"): 22066603,  # mean of the three launches of one step
 }
 L2_FRAC = {  # {(region, source_sha): lts__t_sectors throughput as a fraction of peak}
-    ("density_adj", "aaefc49e55c7"): 0.30,
+    ("density_adj", "3dae6077f620"): 0.319,
 }
 
 

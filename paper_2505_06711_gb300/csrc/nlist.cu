@@ -682,38 +682,26 @@ __global__ void __launch_bounds__(256) k_live(int64_t n, int stride, float rc2, 
     const int32_t* row = nbr + (size_t)i * stride;
     int32_t* out = live + (size_t)i * stride;
     int count = 0;
-    // 128 neighbours per round, 4 per lane: every index and position load of the round is
-    // issued before the first distance test (the gathers' latency overlaps)
-    constexpr int U = 4;
-    for (int base = 0; base < c; base += 32 * U) {
-        int j[U];
-        float4 hj[U], lj[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) j[u] = base + 32 * u + lane < c ? row[base + 32 * u + lane] : -1;
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (j[u] >= 0) {
-                hj[u] = hi[j[u]];
-                lj[u] = lo[j[u]];
+    for (int base = 0; base < c; base += 32) {
+        const int e = base + lane;
+        bool keep = false;
+        int j = 0;
+        if (e < c) {
+            j = row[e];
+            const float4 hj = hi[j], lj = lo[j];
+            const float x = (hj.x - hi_i.x) + (lj.x - lo_i.x);
+            const float y = (hj.y - hi_i.y) + (lj.y - lo_i.y);
+            const float z = (hj.z - hi_i.z) + (lj.z - lo_i.z);
+            const float d2 = x * x + y * y + z * z;
+            keep = d2 < rc2;
+            if (!(d2 > 1e-16f)) {
+                keep = false;
+                atomicOr(&flags[FLAG_GEOM], 4);
             }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            bool keep = false;
-            if (j[u] >= 0) {
-                const float x = (hj[u].x - hi_i.x) + (lj[u].x - lo_i.x);
-                const float y = (hj[u].y - hi_i.y) + (lj[u].y - lo_i.y);
-                const float z = (hj[u].z - hi_i.z) + (lj[u].z - lo_i.z);
-                const float d2 = x * x + y * y + z * z;
-                keep = d2 < rc2;
-                if (!(d2 > 1e-16f)) {
-                    keep = false;
-                    atomicOr(&flags[FLAG_GEOM], 4);
-                }
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, keep);
-            if (keep) out[count + __popc(m & ((1u << lane) - 1u))] = j[u];
-            count += __popc(m);
         }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) out[count + __popc(m & ((1u << lane) - 1u))] = j;
+        count += __popc(m);
     }
     if (lane == 0) live_cnt[i] = count;
 }
