@@ -515,6 +515,7 @@ __global__ void __launch_bounds__(256) k_nbr_search(const int* __restrict__ gate
                                                    const double* __restrict__ fw, const int32_t* __restrict__ owner,
                                                    const int32_t* __restrict__ shift, const float4* __restrict__ p32,
                                                    const float4* __restrict__ p32s, const int32_t* __restrict__ bstart,
+                                                   const int32_t* __restrict__ ekey,
                                                    int stride, int32_t* __restrict__ nbr, int32_t* __restrict__ cnt_out,
                                                    int* __restrict__ flags) {
     pdl_enter();
@@ -525,9 +526,15 @@ __global__ void __launch_bounds__(256) k_nbr_search(const int* __restrict__ gate
     if (i >= n) return;
     const float4 pi = p32[i];
     const double xi[3] = {xw[3 * i], xw[3 * i + 1], xw[3 * i + 2]};
+    // the atom's own bin, as the extended keying computed it (its FP64 floor, evaluated by
+    // every lane here, kept a third of GB300's narrow FP64 pipe busy)
     int b[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) b[k] = clampi((int)floor(fw[3 * i + k] * g.ns[k]) + g.pad[k], 0, g.nbx[k] - 1);
+    {
+        const int key = ekey[i];
+        b[2] = key % g.nbx[2];
+        b[1] = (key / g.nbx[2]) % g.nbx[1];
+        b[0] = key / (g.nbx[2] * g.nbx[1]);
+    }
     const int x0 = max(0, b[0] - g.sw[0]), x1 = min(g.nbx[0] - 1, b[0] + g.sw[0]);
     const int y0 = max(0, b[1] - g.sw[1]), y1 = min(g.nbx[1] - 1, b[1] + g.sw[1]);
     const int z0 = max(0, b[2] - g.sw[2]), z1 = min(g.nbx[2] - 1, b[2] + g.sw[2]);
@@ -802,7 +809,7 @@ static cudaError_t stage_search(cudaStream_t s, reann_nlist* nl, int* flags, con
     const int64_t n = nl->n;
     NlistScratch& w = nl->w;
     launch_pdl(k_nbr_search, blocks_for(n * 32, 256), 256, 0, s, gate, n, nl->geom, w.xw, w.fw, nl->g_owner,
-               nl->g_shift, w.p32, w.p32s, w.estart, nl->stride, nl->nbr, nl->nbr_cnt, flags);
+               nl->g_shift, w.p32, w.p32s, w.estart, w.ekey, nl->stride, nl->nbr, nl->nbr_cnt, flags);
     return cudaGetLastError();
 }
 
