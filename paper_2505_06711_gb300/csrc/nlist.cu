@@ -511,8 +511,8 @@ __global__ void k_ghosts_ext(const int* __restrict__ gate, int64_t n, CellGeom g
 // time (a binary search over the scanned lengths maps a candidate to its
 // column), reading the sorted FP32 positions with their slot index in .w.
 // Candidates come in the same order as a bin-by-bin walk (x, then y, then z).
-__global__ void __launch_bounds__(256) k_nbr_search(const int* __restrict__ gate, int64_t n, CellGeom g, const double* __restrict__ xw,
-                                                   const double* __restrict__ fw, const int32_t* __restrict__ owner,
+__global__ void __launch_bounds__(256) k_nbr_search(const int* __restrict__ gate, int64_t n, CellGeom g,
+                                                   const double* __restrict__ xw, const int32_t* __restrict__ owner,
                                                    const int32_t* __restrict__ shift, const float4* __restrict__ p32,
                                                    const float4* __restrict__ p32s, const int32_t* __restrict__ bstart,
                                                    const int32_t* __restrict__ ekey,
@@ -808,7 +808,7 @@ static cudaError_t stage_ghosts_and_bins(cudaStream_t s, reann_nlist* nl, int* f
 static cudaError_t stage_search(cudaStream_t s, reann_nlist* nl, int* flags, const int* gate) {
     const int64_t n = nl->n;
     NlistScratch& w = nl->w;
-    launch_pdl(k_nbr_search, blocks_for(n * 32, 256), 256, 0, s, gate, n, nl->geom, w.xw, w.fw, nl->g_owner,
+    launch_pdl(k_nbr_search, blocks_for(n * 32, 256), 256, 0, s, gate, n, nl->geom, w.xw, nl->g_owner,
                nl->g_shift, w.p32, w.p32s, w.estart, w.ekey, nl->stride, nl->nbr, nl->nbr_cnt, flags);
     return cudaGetLastError();
 }

@@ -927,7 +927,6 @@ int run_energy_forces(reann_ctx* ctx, reann_nlist* nl, const double* pos, int T,
     // reverse: Eqs. 3-5, one vector-Jacobian product per layer
     for (int t = T - 1; t >= 0; --t) {
         const float* coef_t = nl->coef + (size_t)t * ne * NPHI;
-        const float* rho_t = nl->rho + (size_t)t * n * nf;
         const float* bck_t = nl->bck + (size_t)t * n * NB;
         const float* dsave_t = nl->dsave + (size_t)t * n * (H1 + H2);
         {
