@@ -676,7 +676,8 @@ __global__ void k_refresh(int64_t n, const int32_t* __restrict__ g_count, int64_
 }
 
 // per evaluation: live (d < r_c) entries of every row, moved to the row's front
-__global__ void __launch_bounds__(256) k_live(int64_t n, int stride, float rc2, const int32_t* __restrict__ nbr,
+__global__ void __launch_bounds__(256) k_live(int64_t n, int stride, float rc2, float band,
+                                             const int32_t* __restrict__ nbr,
                                              const int32_t* __restrict__ cnt, const float4* __restrict__ hi,
                                              const float4* __restrict__ lo, int32_t* __restrict__ live,
                                              int32_t* __restrict__ live_cnt, int* __restrict__ flags) {
@@ -695,15 +696,26 @@ __global__ void __launch_bounds__(256) k_live(int64_t n, int stride, float rc2, 
         int j = 0;
         if (e < c) {
             j = row[e];
-            const float4 hj = hi[j], lj = lo[j];
-            const float x = (hj.x - hi_i.x) + (lj.x - lo_i.x);
-            const float y = (hj.y - hi_i.y) + (lj.y - lo_i.y);
-            const float z = (hj.z - hi_i.z) + (lj.z - lo_i.z);
-            const float d2 = x * x + y * y + z * z;
-            keep = d2 < rc2;
-            if (!(d2 > 1e-16f)) {
+            // the high parts decide unless d^2 is within `band` of rc2 (or tiny): then the hi + lo
+            // difference decides, as it always did, so the decision is the same with half the loads
+            const float4 hj = hi[j];
+            const float xh = hj.x - hi_i.x, yh = hj.y - hi_i.y, zh = hj.z - hi_i.z;
+            const float d2h = xh * xh + yh * yh + zh * zh;
+            if (d2h < rc2 - band && d2h > 0.01f) {
+                keep = true;
+            } else if (d2h > rc2 + band) {
                 keep = false;
-                atomicOr(&flags[FLAG_GEOM], 4);
+            } else {
+                const float4 lj = lo[j];
+                const float x = (hj.x - hi_i.x) + (lj.x - lo_i.x);
+                const float y = (hj.y - hi_i.y) + (lj.y - lo_i.y);
+                const float z = (hj.z - hi_i.z) + (lj.z - lo_i.z);
+                const float d2 = x * x + y * y + z * z;
+                keep = d2 < rc2;
+                if (!(d2 > 1e-16f)) {
+                    keep = false;
+                    atomicOr(&flags[FLAG_GEOM], 4);
+                }
             }
         }
         const unsigned m = __ballot_sync(0xffffffffu, keep);
@@ -946,8 +958,11 @@ cudaError_t launch_refresh_positions(cudaStream_t s, const reann_nlist* nl, cons
 cudaError_t launch_live_edges(cudaStream_t s, const reann_nlist* nl, float rc2, int* flags) {
     const int64_t nr = rows_of(nl);
     if (nr == 0) return cudaSuccess;
-    launch_pdl(k_live, blocks_for(nr * 32, 256), 256, 0, s, nr, nl->stride, rc2, nl->nbr, nl->nbr_cnt, nl->pos_hi,
-               nl->pos_lo, nl->live, nl->live_cnt, flags);
+    // the band bounds the low parts' share of d^2 with room to spare: the search's FP32 margin
+    // (16 r_cut ulp(largest coordinate) + 1e-4 A^2) plus 0.05 A^2
+    const float band = nl->geom.margin + 0.05f;
+    launch_pdl(k_live, blocks_for(nr * 32, 256), 256, 0, s, nr, nl->stride, rc2, band, nl->nbr, nl->nbr_cnt,
+               nl->pos_hi, nl->pos_lo, nl->live, nl->live_cnt, flags);
     return cudaGetLastError();
 }
 
